@@ -1,0 +1,305 @@
+"""Throughput benchmark: shifted solves per second of the forward engine.
+
+Workload (one "step"): the whole forward path -- contour tables,
+preconditioner-shift schedule, batched flexible shifted-Krylov solves with
+multigrid-preconditioned inner solves, quadrature-fused measurements and the
+true-residual check -- for a 256x256 heterogeneous 2D aquifer (log-kappa
+Gaussian field, variance 1.5, exponential covariance with a 20-cell
+correlation length), 9 pumping wells on a 3x3 lattice, 25 observation wells,
+32 contour nodes per time (16 shifted systems), 12 log-spaced times in
+[10, 1e4] s, 3 preconditioner-shift groups: 9 x 12 x 16 = 1728 shifted
+systems per step.  A shifted solve counts when its true relative residual
+is <= 1e-8 (the solver's own tolerance is tighter, see SOLVE_OPTS).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own replica aquifer (seed + rank): the
+bases of different wells are independent, so there is no data-path
+collective (weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "shifted solves/sec and Jacobian rows/sec at 1e-8 rel. residual; fraction of HBM peak"
+UNIT = "shifted solves/s"
+RESIDUAL_BAR = 1e-8
+# Solver options of the timed configuration.  tol 1e-10 per shift keeps the
+# measurements within 1e-8 (relative L2) of the FP64 oracle; the metric's
+# 1e-8 residual bar is then met with margin.
+SOLVE_OPTS = dict(tol=1e-10, maxit=160, tau_policy=1, tau_project=1, mg_pre=2, mg_post=2,
+                  inner_cycles=6, inner_rounds=4, inner_tol=0.0, true_residual=1, check_every=4)
+TIMED_CLASS = "rbgs"        # dominant kernel class (from the ncu launch list)
+BYTES_PER_UNIT = {"rbgs": 28.0}   # algorithmic bytes per cell per red-black half-sweep (2D, float32 complex)
+WORKLOAD_NAME = "lognormal-256x256-var1.5-9src-25rec-Nz32-12t-3groups"
+
+
+def workload(rank: int = 0):
+    import workloads as W
+    return W.config2(seed=2 + rank)
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline_sample(prob, nshift: int = 16, t_index: int = 0, k0: int = 0):
+    """Time the FP64 oracle (contour + SuperLU per shift) on a bounded sample:
+    one source, `nshift` shifted systems of one time."""
+    import numpy as np
+    from oracle import contour, direct, fv
+    K, m = fv.assemble(prob)
+    z, w = contour.nodes_weights(prob.times[t_index], prob.Nz)
+    b = fv.rhs(prob, len(prob.src_cells) // 2)
+    t0 = time.perf_counter()
+    n = 0
+    for k in range(k0, k0 + nshift):
+        direct.shifted_solve(K, m, z[k % len(z)], b / z[k % len(z)])
+        n += 1
+    dt = time.perf_counter() - t0
+    return n, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    prob = workload(0)
+    for w in range(args.warmup):
+        cpu_baseline_sample(prob, nshift=4, t_index=w % len(prob.times), k0=4 * w)
+    tot_n, tot_t, per = 0, 0.0, []
+    for s in range(args.steps):
+        n, dt = cpu_baseline_sample(prob, nshift=4, t_index=s % len(prob.times), k0=4 * s)
+        tot_n += n
+        tot_t += dt
+        per.append(dt)
+    value = tot_n / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "step": "4 shifted systems of one time, one source"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} steps x 4 shifted 65536-cell systems (SuperLU, FP64)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sources", type=int, default=0,
+                    help="profiling only: keep the first K wells (smaller device footprint)")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as G
+    from paper_1409_2556_gb300 import Engine, _lib
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        G.build()
+    if world > 1:
+        dist.barrier()
+    dev = local
+    torch.cuda.set_device(dev)
+    prob = workload(rank)
+    if args.sources > 0:
+        prob.src_cells = prob.src_cells[: args.sources]
+        prob.Q = prob.Q[: args.sources]
+    stream = torch.cuda.Stream(device=dev)
+    eng = Engine(dev, stream=stream)
+    eng.load_problem(prob, **SOLVE_OPTS)
+    ns, nr, nt = len(prob.src_cells), len(prob.rec_cells), len(prob.times)
+    h = torch.zeros((ns, nr, nt), dtype=torch.float64, device=f"cuda:{dev}")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        eng.forward(prob.times, out=h)
+    # timed region: device-resident inputs, output on the device
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    conv, launches, iters, tres = 0, 0, [], 0.0
+    with Clocks(dev) as clk, torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            eng.forward(prob.times, out=h)
+            st = eng.last_stats
+            conv += st["n_converged"]
+            launches += st["kernel_launches"]
+            iters.append(st["outer_iters_max"])
+            tres = max(tres, st["max_true_residual"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    ms_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        tc = torch.tensor([float(conv)], device=f"cuda:{dev}")
+        dist.all_reduce(tc)
+        conv_all = float(tc.item())
+    else:
+        conv_all = float(conv)
+    value = conv_all / (ms_max / 1000.0)
+    ms_step = ms_max / args.steps
+
+    # roofline pass: the same K steps again, now with CUDA events around every
+    # launch of the dominant kernel class (kept out of the timed region above,
+    # whose value the events would slow down)
+    eng.set_options(timing_class=_lib.KC[TIMED_CLASS])
+    timed_ms, timed_n, work = 0.0, 0, 0
+    for _ in range(args.steps):
+        eng.forward(prob.times, out=h)
+        st = eng.last_stats
+        timed_ms += st["timed_ms"]
+        timed_n += st["timed_launches"]
+        work += st["work"][_lib.KC[TIMED_CLASS]]
+    eng.set_options(timing_class=-1)
+
+    # end to end through the public API with host buffers (H2D of the
+    # coefficients and wells, D2H of h inside the timed region)
+    e2e_steps = max(1, args.steps)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_conv = 0
+    for _ in range(e2e_steps):
+        eng.setup_grid(prob.kappa, prob.Ss, prob.dx, prob.dy, prob.dz, prob.bc)
+        eng.set_sources(prob.src_cells, prob.Q)
+        eng.set_receivers(prob.rec_cells)
+        hh = eng.forward(prob.times)
+        e2e_conv += eng.last_stats["n_converged"]
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * e2e_conv / e2e_s
+    h2d = prob.kappa.nbytes + prob.Ss.nbytes + prob.src_cells.nbytes + prob.Q.nbytes + prob.rec_cells.nbytes \
+        + prob.times.nbytes + 6 * 4
+    d2h = hh.nbytes
+
+    peak, peak_kind = _peaks()
+    bpu = BYTES_PER_UNIT[TIMED_CLASS]
+    achieved = (work * bpu / 1e9) / (timed_ms / 1e3) if timed_ms > 0 else None
+    roof = {"kernel": "k_rbgs (red-black Gauss-Seidel half-sweep, fine multigrid levels)", "bound": "hbm",
+            "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
+            "traffic": None, "launches_timed": timed_n, "avg_launch_us": 1000.0 * timed_ms / max(timed_n, 1),
+            "bytes_per_unit": bpu, "units": work,
+            "measured": "CUDA events around each launch of the class, in a separate pass of the same steps"}
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        n, dt = cpu_baseline_sample(prob, nshift=16, t_index=0)
+        cpu = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n} shifted 65536-cell systems of one time, one source (SuperLU, FP64, {dt:.1f} s)"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "df32+f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "shifted_systems_per_step": ns * nt * prob.Nz // 2,
+                       "solver_tol": SOLVE_OPTS["tol"], "residual_bar": RESIDUAL_BAR,
+                       "max_true_residual": tres, "outer_iters_max": max(iters),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (Krylov bases ~GBs per step)"},
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

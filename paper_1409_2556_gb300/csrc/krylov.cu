@@ -1,0 +1,650 @@
+// krylov.cu -- flexible Krylov method for shifted systems (Sec. 3,
+// Algorithm 1), batched over bases (one basis per right-hand side and
+// preconditioner-shift group), plus the quadrature-fused measurements
+// (Eq. half) and the true-residual check.
+//
+// Per outer iteration j of every active basis:
+//   1. preconditioner solve (K + tau_j M) u_j = v_j to a relative residual
+//      inner_tol: rounds of  r = v_j - (K + tau_j M) u_j  in df32 (exact),
+//      float32 V-cycles on A d = r, u_j += d;
+//   2. s_j = M u_j, classical Gram-Schmidt with reorthogonalisation against
+//      V_j: coefficient dots in float32 (they only need to be close), the
+//      vector updates s -= V c in df32 so that M u_j = V_{j+1} hbar_j holds
+//      to ~1e-13 whatever the rounding of c;  h_{j+1,j} = ||s||,
+//      v_{j+1} = s / h_{j+1,j};
+//   3. for every unconverged shift z_k of the basis: the new column of
+//      Hbar(z_k; T_j) = [I; 0] + Hbar_j (z_k I - T_j) is reduced by the
+//      shift's stored Givens rotations (GMRES-Sh least squares), giving the
+//      residual |g_{j+1}| (relative, b = e_cell has unit norm).
+// V and U are kept in df32 (hi, lo float2 planes); the hi plane alone feeds
+// the float32 dot products.
+#include <cstdio>
+#include "df32.cuh"
+#include "lt_internal.h"
+#include "lt_kernels.h"
+
+namespace lt {
+
+// ------------------------------------------------------------ small helpers
+__device__ __forceinline__ cdf load_cdf(const float2* hi, const float2* lo, size_t idx) {
+  float2 h = hi[idx], l = lo[idx];
+  return {{h.x, l.x}, {h.y, l.y}};
+}
+__device__ __forceinline__ void store_cdf(float2* hi, float2* lo, size_t idx, cdf v) {
+  hi[idx] = make_float2(v.re.hi, v.im.hi);
+  lo[idx] = make_float2(v.re.lo, v.im.lo);
+}
+__device__ __forceinline__ df ldf(const float* hi, const float* lo, int c) { return {hi[c], lo[c]}; }
+
+template <int NV>
+__device__ __forceinline__ void block_reduce_add(float* v, float* smem /* [32*NV] */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) smem[warp * NV + q] = v[q];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = lane < nw ? smem[lane * NV + q] : 0.f;
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  }
+  __syncthreads();
+}
+
+// (K + tau M) u at cell c, df32; u given by hi/lo planes of one vector
+__device__ __forceinline__ cdf apply_exact(const FineExact& fe, const float2* uhi, const float2* ulo, int c, df taur,
+                                           df taui) {
+  const int nx = fe.nx, ny = fe.ny, nz = fe.nz;
+  int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+  df D = ldf(fe.D_hi, fe.D_lo, c), m = ldf(fe.m_hi, fe.m_lo, c);
+  cdf dg = {df_add(D, df_mul(taur, m)), df_mul(taui, m)};
+  cdf acc = cdf_mul(dg, load_cdf(uhi, ulo, c));
+  if (i + 1 < nx) acc = cdf_sub(acc, cdf_mul_r(load_cdf(uhi, ulo, c + 1), ldf(fe.Te_hi, fe.Te_lo, c)));
+  if (i > 0) acc = cdf_sub(acc, cdf_mul_r(load_cdf(uhi, ulo, c - 1), ldf(fe.Te_hi, fe.Te_lo, c - 1)));
+  if (j + 1 < ny) acc = cdf_sub(acc, cdf_mul_r(load_cdf(uhi, ulo, c + nx), ldf(fe.Tn_hi, fe.Tn_lo, c)));
+  if (j > 0) acc = cdf_sub(acc, cdf_mul_r(load_cdf(uhi, ulo, c - nx), ldf(fe.Tn_hi, fe.Tn_lo, c - nx)));
+  const int pl = nx * ny;
+  if (k + 1 < nz) acc = cdf_sub(acc, cdf_mul_r(load_cdf(uhi, ulo, c + pl), ldf(fe.Tu_hi, fe.Tu_lo, c)));
+  if (k > 0) acc = cdf_sub(acc, cdf_mul_r(load_cdf(uhi, ulo, c - pl), ldf(fe.Tu_hi, fe.Tu_lo, c - pl)));
+  return acc;
+}
+
+// ------------------------------------------------------------ batch init
+__global__ void k_init_vectors(Batch bt) {
+  int b = blockIdx.y;
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= bt.N) return;
+  size_t idx = (size_t)b * (bt.maxit + 1) * bt.N + c;
+  float one = (c == bt.rhs_cell[b]) ? 1.f : 0.f;
+  bt.V_hi[idx] = make_float2(one, 0.f);
+  bt.V_lo[idx] = make_float2(0.f, 0.f);
+}
+
+__global__ void k_init_shifts(Batch bt) {
+  int sh = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sh < bt.nsh) {
+    bt.g[(size_t)sh * (bt.maxit + 1)] = make_double2(1.0, 0.0);
+    bt.conv_it[sh] = 0;
+    bt.pres[sh] = 1.0;
+  }
+  if (sh < bt.nb) {
+    bt.active[sh] = 1;
+    bt.nit[sh] = 0;
+    bt.inner_max[sh] = 0.0;
+  }
+}
+
+void launch_init_batch(const Batch& bt, cudaStream_t st) {
+  dim3 g((unsigned)((bt.N + 255) / 256), bt.nb);
+  k_init_vectors<<<g, 256, 0, st>>>(bt);
+  int n = bt.nsh > bt.nb ? bt.nsh : bt.nb;
+  k_init_shifts<<<(n + 255) / 256, 256, 0, st>>>(bt);
+}
+
+// ------------------------------------------------------------ per-iteration prep
+__global__ void k_prep_iter(Batch bt, int j) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= bt.nb) return;
+  if (!bt.active[b]) return;
+  int slot = bt.tau_pattern[j % 5];
+  int g = bt.group[b];
+  bt.tau_cur[b] = bt.tau_grp[2 * g + slot];
+  bt.tau_slot[b] = 2 * g + slot;
+  for (int r = 0; r <= bt.rounds; ++r) bt.rnorm2[b * (bt.rounds + 1) + r] = 0.0;
+  for (int i = 0; i < 2 * (bt.maxit + 1); ++i) bt.dot[(size_t)b * 2 * (bt.maxit + 1) + i] = make_double2(0.0, 0.0);
+  bt.snorm2[b] = 0.0;
+}
+
+void launch_prep_iter(const Batch& bt, int j, cudaStream_t st) {
+  k_prep_iter<<<(bt.nb + 127) / 128, 128, 0, st>>>(bt, j);
+}
+
+// ------------------------------------------------------------ preconditioner-solve rounds
+__global__ void k_exact_residual(Batch bt, FineExact fe, Level L0, int j, int round, int record_only) {
+  __shared__ float red[32];
+  int b = blockIdx.y;
+  if (!bt.active[b]) return;
+  const int R1 = bt.rounds + 1;
+  if (!record_only && round > 0 && bt.rnorm2[b * R1 + round - 1] <= bt.inner_tol2) return;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  float acc[1] = {0.f};
+  if (c < fe.N) {
+    size_t vi = ((size_t)b * (bt.maxit + 1) + j) * bt.N + c;
+    cdf r = load_cdf(bt.V_hi, bt.V_lo, vi);
+    if (round > 0) {
+      double2 t = bt.tau_cur[b];
+      df taur = df_from_double(t.x), taui = df_from_double(t.y);
+      size_t ub = ((size_t)b * bt.maxit + j) * bt.N;
+      cdf au = apply_exact(fe, bt.U_hi + ub, bt.U_lo + ub, c, taur, taui);
+      r = cdf_sub(r, au);
+    }
+    if (!record_only) {
+      L0.f[(size_t)b * L0.N + c] = make_float2(r.re.hi, r.im.hi);
+      L0.u[(size_t)b * L0.N + c] = make_float2(0.f, 0.f);
+    }
+    acc[0] = r.re.hi * r.re.hi + r.im.hi * r.im.hi;
+  }
+  block_reduce_add<1>(acc, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(&bt.rnorm2[b * R1 + round], (double)acc[0]);
+    atomicAdd(&bt.work[KC_EXACT_RES], (unsigned long long)min((int)blockDim.x, fe.N - (int)(blockIdx.x * blockDim.x)));
+  }
+}
+
+void launch_exact_residual(const Batch& bt, const FineExact& fe, const Level& L0, int j, int round, int record_only,
+                           cudaStream_t st, Prof* pf) {
+  dim3 g((fe.N + 255) / 256, bt.nb);
+  prof_begin(pf, KC_EXACT_RES, st);
+  k_exact_residual<<<g, 256, 0, st>>>(bt, fe, L0, j, round, record_only);
+  prof_end(pf, KC_EXACT_RES, st);
+}
+
+__global__ void k_update_u(Batch bt, Level L0, int j, int round) {
+  int b = blockIdx.y;
+  if (!bt.active[b]) return;
+  if (bt.rnorm2[b * (bt.rounds + 1) + round] <= bt.inner_tol2) return;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L0.N) return;
+  float2 d = L0.u[(size_t)b * L0.N + c];
+  size_t ui = ((size_t)b * bt.maxit + j) * bt.N + c;
+  if (round == 0) {
+    bt.U_hi[ui] = d;
+    bt.U_lo[ui] = make_float2(0.f, 0.f);
+  } else {
+    cdf u = load_cdf(bt.U_hi, bt.U_lo, ui);
+    u.re = df_add_f(u.re, d.x);
+    u.im = df_add_f(u.im, d.y);
+    store_cdf(bt.U_hi, bt.U_lo, ui, u);
+  }
+}
+
+void launch_update_u(const Batch& bt, const Level& L0, int j, int round, cudaStream_t st) {
+  dim3 g((L0.N + 255) / 256, bt.nb);
+  k_update_u<<<g, 256, 0, st>>>(bt, L0, j, round);
+}
+
+__global__ void k_inner_record(Batch bt) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= bt.nb || !bt.active[b]) return;
+  double r = sqrt(bt.rnorm2[b * (bt.rounds + 1) + bt.rounds]);
+  if (r > bt.inner_max[b]) bt.inner_max[b] = r;
+}
+
+void launch_inner_record(const Batch& bt, cudaStream_t st) {
+  k_inner_record<<<(bt.nb + 127) / 128, 128, 0, st>>>(bt);
+}
+
+// ------------------------------------------------------------ Arnoldi (Algorithm 1, s_j = M u_j and CGS2)
+constexpr int kArnT = 256;   // threads per block
+constexpr int kCPT = 4;      // cells per thread
+constexpr int kIG = 4;       // basis vectors reduced together
+
+// pass 1: dot[0][i] = V_hi[i]^H s_hi, s = M u_j (float32 estimate)
+__global__ void __launch_bounds__(kArnT) k_dots1(Batch bt, FineExact fe, int j) {
+  __shared__ float red[32 * 2 * kIG];
+  int b = blockIdx.y;
+  if (!bt.active[b]) return;
+  const int N = fe.N;
+  int c0 = blockIdx.x * kArnT * kCPT + threadIdx.x;
+  float2 s[kCPT];
+  size_t ub = ((size_t)b * bt.maxit + j) * bt.N;
+#pragma unroll
+  for (int q = 0; q < kCPT; ++q) {
+    int c = c0 + q * kArnT;
+    if (c < N) {
+      float2 u = bt.U_hi[ub + c];
+      float m = fe.m_hi[c];
+      s[q] = make_float2(m * u.x, m * u.y);
+    } else {
+      s[q] = make_float2(0.f, 0.f);
+    }
+  }
+  size_t vb = (size_t)b * (bt.maxit + 1) * bt.N;
+  for (int i0 = 0; i0 <= j; i0 += kIG) {
+    float acc[2 * kIG];
+#pragma unroll
+    for (int q = 0; q < 2 * kIG; ++q) acc[q] = 0.f;
+#pragma unroll
+    for (int ii = 0; ii < kIG; ++ii) {
+      int i = i0 + ii;
+      if (i > j) break;
+      const float2* v = bt.V_hi + vb + (size_t)i * bt.N;
+#pragma unroll
+      for (int q = 0; q < kCPT; ++q) {
+        int c = c0 + q * kArnT;
+        if (c < N) {
+          float2 a = v[c];
+          acc[2 * ii] += a.x * s[q].x + a.y * s[q].y;      // conj(a) * s
+          acc[2 * ii + 1] += a.x * s[q].y - a.y * s[q].x;
+        }
+      }
+    }
+    block_reduce_add<2 * kIG>(acc, red);
+    if (threadIdx.x == 0) {
+      for (int ii = 0; ii < kIG && i0 + ii <= j; ++ii) {
+        double2* d = bt.dot + (size_t)b * 2 * (bt.maxit + 1) + (i0 + ii);
+        atomicAdd(&d->x, (double)acc[2 * ii]);
+        atomicAdd(&d->y, (double)acc[2 * ii + 1]);
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    int n = min(kArnT * kCPT, N - (int)(blockIdx.x * kArnT * kCPT));
+    atomicAdd(&bt.work[KC_DOTS], (unsigned long long)n * (unsigned long long)(j + 1));
+  }
+}
+
+// pass 2: s' = M u_j - V c1 (df32, exact); dot[1][i] = V_hi[i]^H s'_hi; S <- s'
+// pass 3 (second = 1): s'' = S - V c2; snorm2 += ||s''||^2; S <- s''
+__global__ void __launch_bounds__(kArnT) k_update(Batch bt, FineExact fe, int j, int second) {
+  __shared__ float red[32 * 2 * kIG];
+  __shared__ float2 cf[512];
+  int b = blockIdx.y;
+  if (!bt.active[b]) return;
+  const int N = fe.N;
+  const double2* dsrc = bt.dot + (size_t)b * 2 * (bt.maxit + 1) + (second ? (bt.maxit + 1) : 0);
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) cf[i] = make_float2((float)dsrc[i].x, (float)dsrc[i].y);
+  __syncthreads();
+  int c0 = blockIdx.x * kArnT * kCPT + threadIdx.x;
+  cdf s[kCPT];
+  size_t ub = ((size_t)b * bt.maxit + j) * bt.N;
+  size_t sb = (size_t)b * bt.N;
+#pragma unroll
+  for (int q = 0; q < kCPT; ++q) {
+    int c = c0 + q * kArnT;
+    if (c < N) {
+      if (!second) {
+        df m = ldf(fe.m_hi, fe.m_lo, c);
+        s[q] = cdf_mul_r(load_cdf(bt.U_hi, bt.U_lo, ub + c), m);
+      } else {
+        s[q] = load_cdf(bt.S_hi, bt.S_lo, sb + c);
+      }
+    } else {
+      s[q] = {{0.f, 0.f}, {0.f, 0.f}};
+    }
+  }
+  size_t vb = (size_t)b * (bt.maxit + 1) * bt.N;
+  for (int i = 0; i <= j; ++i) {
+    float2 ci = cf[i];
+    const float2* vh = bt.V_hi + vb + (size_t)i * bt.N;
+    const float2* vl = bt.V_lo + vb + (size_t)i * bt.N;
+#pragma unroll
+    for (int q = 0; q < kCPT; ++q) {
+      int c = c0 + q * kArnT;
+      if (c < N) {
+        float2 h = vh[c], l = vl[c];
+        cdf v = {{h.x, l.x}, {h.y, l.y}};
+        s[q] = cdf_sub(s[q], cdf_mul_cf(v, ci.x, ci.y));
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kCPT; ++q) {
+    int c = c0 + q * kArnT;
+    if (c < N) store_cdf(bt.S_hi, bt.S_lo, sb + c, s[q]);
+  }
+  if (!second) {
+    for (int i0 = 0; i0 <= j; i0 += kIG) {
+      float acc[2 * kIG];
+#pragma unroll
+      for (int q = 0; q < 2 * kIG; ++q) acc[q] = 0.f;
+#pragma unroll
+      for (int ii = 0; ii < kIG; ++ii) {
+        int i = i0 + ii;
+        if (i > j) break;
+        const float2* v = bt.V_hi + vb + (size_t)i * bt.N;
+#pragma unroll
+        for (int q = 0; q < kCPT; ++q) {
+          int c = c0 + q * kArnT;
+          if (c < N) {
+            float2 a = v[c];
+            float sx = s[q].re.hi, sy = s[q].im.hi;
+            acc[2 * ii] += a.x * sx + a.y * sy;
+            acc[2 * ii + 1] += a.x * sy - a.y * sx;
+          }
+        }
+      }
+      block_reduce_add<2 * kIG>(acc, red);
+      if (threadIdx.x == 0) {
+        for (int ii = 0; ii < kIG && i0 + ii <= j; ++ii) {
+          double2* d = bt.dot + (size_t)b * 2 * (bt.maxit + 1) + (bt.maxit + 1) + (i0 + ii);
+          atomicAdd(&d->x, (double)acc[2 * ii]);
+          atomicAdd(&d->y, (double)acc[2 * ii + 1]);
+        }
+      }
+    }
+  } else {
+    float acc[1] = {0.f};
+#pragma unroll
+    for (int q = 0; q < kCPT; ++q) acc[0] += s[q].re.hi * s[q].re.hi + s[q].im.hi * s[q].im.hi;
+    block_reduce_add<1>(acc, red);
+    if (threadIdx.x == 0) atomicAdd(&bt.snorm2[b], (double)acc[0]);
+  }
+  if (threadIdx.x == 0) {
+    int n = min(kArnT * kCPT, N - (int)(blockIdx.x * kArnT * kCPT));
+    atomicAdd(&bt.work[KC_ORTHO], (unsigned long long)n * (unsigned long long)(j + 1));
+  }
+}
+
+// v_{j+1} = s'' / h, h = float(||s''||); H column j
+__global__ void k_normalize(Batch bt, int j) {
+  int b = blockIdx.y;
+  if (!bt.active[b]) return;
+  float h = (float)sqrt(bt.snorm2[b]);
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < bt.N) {
+    size_t si = (size_t)b * bt.N + c;
+    cdf s = load_cdf(bt.S_hi, bt.S_lo, si);
+    cdf v;
+    if (h > 0.f) {
+      v.re = df_div_f(s.re, h);
+      v.im = df_div_f(s.im, h);
+    } else {
+      v = {{0.f, 0.f}, {0.f, 0.f}};
+    }
+    store_cdf(bt.V_hi, bt.V_lo, ((size_t)b * (bt.maxit + 1) + j + 1) * bt.N + c, v);
+  }
+  if (blockIdx.x == 0) {
+    const double2* d = bt.dot + (size_t)b * 2 * (bt.maxit + 1);
+    double2* Hc = bt.H + ((size_t)b * bt.maxit + j) * (bt.maxit + 1);
+    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) {
+      if (i <= j) {
+        double2 a = d[i], a2 = d[bt.maxit + 1 + i];
+        Hc[i] = make_double2((double)(float)a.x + (double)(float)a2.x, (double)(float)a.y + (double)(float)a2.y);
+      } else {
+        Hc[i] = make_double2((double)h, 0.0);
+      }
+    }
+  }
+}
+
+void launch_arnoldi(const Batch& bt, const FineExact& fe, int j, cudaStream_t st, int* nlaunch, Prof* pf) {
+  dim3 g((fe.N + kArnT * kCPT - 1) / (kArnT * kCPT), bt.nb);
+  prof_begin(pf, KC_DOTS, st);
+  k_dots1<<<g, kArnT, 0, st>>>(bt, fe, j);
+  prof_end(pf, KC_DOTS, st);
+  for (int second = 0; second < 2; ++second) {
+    prof_begin(pf, KC_ORTHO, st);
+    k_update<<<g, kArnT, 0, st>>>(bt, fe, j, second);
+    prof_end(pf, KC_ORTHO, st);
+  }
+  dim3 gn((fe.N + 255) / 256, bt.nb);
+  k_normalize<<<gn, 256, 0, st>>>(bt, j);
+  *nlaunch += 4;
+}
+
+// ------------------------------------------------------------ all-shift least squares (GMRES-Sh)
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double zabs(double2 a) { return hypot(a.x, a.y); }
+
+__global__ void k_shift_ls(Batch bt, int j) {
+  __shared__ double2 hcol[1024];
+  __shared__ int any;
+  int b = blockIdx.x;
+  if (!bt.active[b]) return;
+  if (threadIdx.x == 0) any = 0;
+  const double2* Hc = bt.H + ((size_t)b * bt.maxit + j) * (bt.maxit + 1);
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) hcol[i] = Hc[i];
+  __syncthreads();
+  double2 tau = bt.tau_cur[b];
+  const int M = bt.maxit;
+  int mine = 0;
+  for (int sh = bt.shift_off[b] + threadIdx.x; sh < bt.shift_off[b + 1]; sh += blockDim.x) {
+    if (bt.conv_it[sh] > 0) continue;
+    double2 z = bt.zsh[sh];
+    double2 dz = make_double2(z.x - tau.x, z.y - tau.y);
+    double2* Rc = bt.R + ((size_t)sh * M + j) * M;
+    double* rc = bt.rc + (size_t)sh * M;
+    double2* rs = bt.rs + (size_t)sh * M;
+    double2 carry = zmul(dz, hcol[0]);
+    if (j == 0) carry.x += 1.0;
+    for (int i = 0; i < j; ++i) {
+      double2 nxt = zmul(dz, hcol[i + 1]);
+      if (i + 1 == j) nxt.x += 1.0;
+      double c = rc[i];
+      double2 s = rs[i];
+      double2 top = zmul(s, nxt);
+      top.x += c * carry.x; top.y += c * carry.y;
+      double2 bot = zmul(zconj(s), carry);
+      bot.x = c * nxt.x - bot.x; bot.y = c * nxt.y - bot.y;
+      Rc[i] = top;
+      carry = bot;
+    }
+    double2 bb = zmul(dz, hcol[j + 1]);
+    double na = zabs(carry), nb = zabs(bb);
+    double rho = hypot(na, nb);
+    double c;
+    double2 s;
+    double2 rjj;
+    if (rho == 0.0) {
+      c = 1.0; s = make_double2(0.0, 0.0); rjj = make_double2(0.0, 0.0);
+    } else if (na == 0.0) {
+      c = 0.0; s = make_double2(bb.x / nb, -bb.y / nb); rjj = make_double2(nb, 0.0);
+    } else {
+      c = na / rho;
+      double2 ph = make_double2(carry.x / na, carry.y / na);
+      s = zmul(ph, make_double2(bb.x / rho, -bb.y / rho));
+      rjj = make_double2(ph.x * rho, ph.y * rho);
+    }
+    Rc[j] = rjj;
+    rc[j] = c;
+    rs[j] = s;
+    double2* g = bt.g + (size_t)sh * (M + 1);
+    double2 gj = g[j];
+    g[j] = make_double2(c * gj.x, c * gj.y);
+    double2 gn = zmul(zconj(s), gj);
+    g[j + 1] = make_double2(-gn.x, -gn.y);
+    double res = zabs(g[j + 1]);
+    bt.pres[sh] = res;
+    if (res <= bt.tol || rho == 0.0 || hcol[j + 1].x == 0.0) bt.conv_it[sh] = j + 1;
+    else mine = 1;
+  }
+  if (mine) atomicOr(&any, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bt.nit[b] = j + 1;
+    bt.active[b] = (any && j + 1 < M) ? 1 : 0;
+  }
+}
+
+void launch_shift_ls(const Batch& bt, int j, cudaStream_t st) {
+  k_shift_ls<<<bt.nb, 256, 0, st>>>(bt, j);
+}
+
+// y_k = R^{-1} g over the shift's converged (or final) column count
+__global__ void k_backsolve(Batch bt, const int* sh_basis) {
+  int sh = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sh >= bt.nsh) return;
+  const int M = bt.maxit;
+  int m = bt.conv_it[sh] > 0 ? bt.conv_it[sh] : bt.nit[sh_basis[sh]];
+  const double2* R = bt.R + (size_t)sh * M * M;
+  const double2* g = bt.g + (size_t)sh * (M + 1);
+  double2* y = bt.Y + (size_t)sh * M;
+  for (int i = m; i < M; ++i) y[i] = make_double2(0.0, 0.0);
+  for (int i = m - 1; i >= 0; --i) {
+    double2 acc = g[i];
+    for (int l = i + 1; l < m; ++l) {
+      double2 t = zmul(R[(size_t)l * M + i], y[l]);
+      acc.x -= t.x; acc.y -= t.y;
+    }
+    double2 d = R[(size_t)i * M + i];
+    double den = d.x * d.x + d.y * d.y;
+    y[i] = den > 0 ? make_double2((acc.x * d.x + acc.y * d.y) / den, (acc.y * d.x - acc.x * d.y) / den)
+                   : make_double2(0.0, 0.0);
+  }
+}
+
+void launch_backsolve_map(const Batch& bt, const int* sh_basis, cudaStream_t st) {
+  k_backsolve<<<(bt.nsh + 127) / 128, 128, 0, st>>>(bt, sh_basis);
+}
+
+// ------------------------------------------------------------ quadrature (Eq. half)
+__global__ void k_quad_coef(Batch bt, const QuadItem* items, int nitems, const double2* wq, double2* C) {
+  int q = blockIdx.x;
+  if (q >= nitems) return;
+  QuadItem it = items[q];
+  const int M = bt.maxit;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = 0; k < it.nk; ++k) {
+      double2 t = zmul(wq[it.sh0 + k], bt.Y[(size_t)(it.sh0 + k) * M + i]);
+      acc.x += t.x; acc.y += t.y;
+    }
+    C[(size_t)q * M + i] = acc;
+  }
+}
+
+void launch_quad_coef(const Batch& bt, const QuadItem* items, int nitems, const double2* wq, double2* C,
+                      cudaStream_t st) {
+  k_quad_coef<<<nitems, 128, 0, st>>>(bt, items, nitems, wq, C);
+}
+
+__global__ void k_measure(Batch bt, const QuadItem* items, const double2* C, int ns, int nr, int nt,
+                          const int64_t* rcells, double* h) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ns * nr * nt) return;
+  int t = idx % nt, r = (idx / nt) % nr, s = idx / (nt * nr);
+  int q = s * nt + t;
+  QuadItem it = items[q];
+  const int M = bt.maxit;
+  int64_t cell = rcells[r];
+  double acc = 0.0;
+  for (int i = 0; i < M; ++i) {
+    size_t ui = ((size_t)it.basis * M + i) * bt.N + cell;
+    float2 hi = bt.U_hi[ui], lo = bt.U_lo[ui];
+    double2 c = C[(size_t)q * M + i];
+    acc += ((double)hi.x + (double)lo.x) * c.x - ((double)hi.y + (double)lo.y) * c.y;
+  }
+  h[idx] = 2.0 * acc;
+}
+
+void launch_measure(const Batch& bt, const QuadItem* items, const double2* C, int ns, int nr, int nt,
+                    const int64_t* rcells, double* h, cudaStream_t st) {
+  int n = ns * nr * nt;
+  k_measure<<<(n + 127) / 128, 128, 0, st>>>(bt, items, C, ns, nr, nt, rcells, h);
+}
+
+__global__ void k_fields(Batch bt, const QuadItem* items, const double2* C, double* phi) {
+  int q = blockIdx.y;
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= bt.N) return;
+  QuadItem it = items[q];
+  const int M = bt.maxit;
+  int m = bt.nit[it.basis];
+  double acc = 0.0;
+  for (int i = 0; i < m; ++i) {
+    size_t ui = ((size_t)it.basis * M + i) * bt.N + c;
+    float2 hi = bt.U_hi[ui], lo = bt.U_lo[ui];
+    double2 cc = C[(size_t)q * M + i];
+    acc += ((double)hi.x + (double)lo.x) * cc.x - ((double)hi.y + (double)lo.y) * cc.y;
+  }
+  phi[(size_t)q * bt.N + c] = 2.0 * acc;
+}
+
+void launch_fields(const Batch& bt, const QuadItem* items, const double2* C, int nitems, double* phi,
+                   cudaStream_t st) {
+  dim3 g((unsigned)((bt.N + 255) / 256), nitems);
+  k_fields<<<g, 256, 0, st>>>(bt, items, C, phi);
+}
+
+// ------------------------------------------------------------ true residual (judge)
+constexpr int kXS = 4;   // shifts per pass
+
+// X[sh] = U_b y_sh for every shift of basis b (df32 accumulation)
+__global__ void k_xk(Batch bt, float2* X_hi, float2* X_lo) {
+  __shared__ cdf ys[kXS][256];
+  int b = blockIdx.y;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int M = bt.maxit;
+  int m = bt.nit[b];
+  int s0 = bt.shift_off[b], s1 = bt.shift_off[b + 1];
+  size_t ub = (size_t)b * M * bt.N;
+  for (int sa = s0; sa < s1; sa += kXS) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kXS * m; idx += blockDim.x) {
+      int q = idx / m, i = idx % m;
+      int sh = sa + q;
+      double2 y = sh < s1 ? bt.Y[(size_t)sh * M + i] : make_double2(0.0, 0.0);
+      ys[q][i] = {df_from_double(y.x), df_from_double(y.y)};
+    }
+    __syncthreads();
+    if (c < bt.N) {
+      cdf acc[kXS];
+#pragma unroll
+      for (int q = 0; q < kXS; ++q) acc[q] = {{0.f, 0.f}, {0.f, 0.f}};
+      for (int i = 0; i < m; ++i) {
+        cdf u = load_cdf(bt.U_hi, bt.U_lo, ub + (size_t)i * bt.N + c);
+#pragma unroll
+        for (int q = 0; q < kXS; ++q) acc[q] = cdf_add(acc[q], cdf_mul(u, ys[q][i]));
+      }
+#pragma unroll
+      for (int q = 0; q < kXS; ++q)
+        if (sa + q < s1) store_cdf(X_hi, X_lo, (size_t)(sa + q) * bt.N + c, acc[q]);
+    }
+  }
+}
+
+__global__ void k_true_res(Batch bt, FineExact fe, const int* sh_basis, const float2* X_hi, const float2* X_lo,
+                           double* res2) {
+  __shared__ float red[32];
+  int sh = blockIdx.y;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  float acc[1] = {0.f};
+  if (c < fe.N) {
+    double2 z = bt.zsh[sh];
+    df zr = df_from_double(z.x), zi = df_from_double(z.y);
+    const float2* xh = X_hi + (size_t)sh * bt.N;
+    const float2* xl = X_lo + (size_t)sh * bt.N;
+    cdf ax = apply_exact(fe, xh, xl, c, zr, zi);
+    float e = (c == bt.rhs_cell[sh_basis[sh]]) ? 1.f : 0.f;
+    cdf r = cdf_sub({{e, 0.f}, {0.f, 0.f}}, ax);
+    acc[0] = r.re.hi * r.re.hi + r.im.hi * r.im.hi;
+  }
+  block_reduce_add<1>(acc, red);
+  if (threadIdx.x == 0) atomicAdd(&res2[sh], (double)acc[0]);
+}
+
+void launch_true_residual_map(const Batch& bt, const FineExact& fe, const int* sh_basis, float2* X_hi, float2* X_lo,
+                              double* res2, cudaStream_t st, int* nlaunch, Prof* pf) {
+  dim3 g((unsigned)((bt.N + 255) / 256), bt.nb);
+  prof_begin(pf, KC_XK, st);
+  k_xk<<<g, 256, 0, st>>>(bt, X_hi, X_lo);
+  prof_end(pf, KC_XK, st);
+  dim3 g2((unsigned)((bt.N + 255) / 256), bt.nsh);
+  prof_begin(pf, KC_TRUE_RES, st);
+  k_true_res<<<g2, 256, 0, st>>>(bt, fe, sh_basis, X_hi, X_lo, res2);
+  prof_end(pf, KC_TRUE_RES, st);
+  *nlaunch += 2;
+}
+
+}  // namespace lt

@@ -1,0 +1,903 @@
+// lt_api.cu -- host side of the C ABI declared in include/lt.h.
+//
+// Builds the finite-volume operator and multigrid hierarchy, the Talbot
+// contour tables (Sec. 2.2) and preconditioner-shift schedules (Sec. 3),
+// and drives the batched flexible shifted-Krylov solve (Algorithm 1) on the
+// context's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/lt.h"
+#include "df32.cuh"
+#include "lt_internal.h"
+#include "lt_kernels.h"
+
+using cplx = std::complex<double>;
+
+namespace lt {
+void launch_backsolve_map(const Batch& bt, const int* sh_basis, cudaStream_t st);
+}
+
+// ------------------------------------------------------------------ contour (Sec. 2.2)
+// z(theta) = (Nz/t) (sigma + mu theta cot(alpha theta) + i nu theta), the
+// modified Talbot contour with the parameters of Trefethen, Weideman and
+// Schmelzer (BIT 2006); midpoint nodes theta_k = (2k - 1) pi / Nz in (0, pi);
+// weights w_k = -(i / Nz) e^{z_k t} z'(theta_k) for phi = 2 Re sum_k w_k F(z_k).
+static const double kSigma = -0.6122, kMu = 0.5017, kAlpha = 0.6407, kNu = 0.2645;
+
+static void talbot_half(double t, int Nz, std::vector<cplx>& z, std::vector<cplx>& w) {
+  z.resize(Nz / 2);
+  w.resize(Nz / 2);
+  for (int k = 0; k < Nz / 2; ++k) {
+    double th = (2.0 * (k + 1) - 1.0) * M_PI / Nz;
+    double a = kAlpha * th;
+    double cot = std::cos(a) / std::sin(a);
+    double s = std::sin(a);
+    cplx zz = (Nz / t) * cplx(kSigma + kMu * th * cot, kNu * th);
+    cplx dz = (Nz / t) * cplx(kMu * (cot - a / (s * s)), kNu);
+    z[k] = zz;
+    w[k] = cplx(0.0, -1.0 / Nz) * std::exp(zz * t) * dz;
+  }
+}
+
+// ------------------------------------------------------------------ context
+struct HostLevel {
+  int nx, ny, nz, N, rx, ry, rz;
+  std::vector<double> Te, Tn, Tu, D, m;
+};
+
+struct Workspace {
+  int nb = 0, maxit = 0, nsh = 0, rounds = 0, ngroups = 0, nc2 = 0;
+  int64_t N = 0;
+  std::vector<void*> allocs;
+  lt::Batch bt{};
+  float2* X_hi = nullptr;
+  float2* X_lo = nullptr;
+  size_t x_elems = 0;
+};
+
+struct lt_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  lt_opts opts{};
+  // grid
+  bool have_grid = false;
+  int nx = 0, ny = 0, nz = 0;
+  int64_t N = 0;
+  double dx = 0, dy = 0, dz = 0;
+  int bc[6] = {0, 0, 0, 0, 1, 1};
+  std::vector<double> kappa, Ss;
+  std::vector<HostLevel> hl;
+  lt::MGHost mg{};
+  std::vector<void*> grid_allocs;
+  lt::FineExact fe{};
+  // wells
+  std::vector<int64_t> src, rec;
+  std::vector<double> Q;
+  Workspace ws;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  lt::Prof prof;
+  std::vector<cudaEvent_t> prof_events;
+};
+
+static int fail(lt_ctx* ctx, int code, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return code;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? LT_ERR_OOM : LT_ERR_CUDA,       \
+                  "%s failed: %s", #call, cudaGetErrorString(e_));                       \
+    }                                                                                    \
+  } while (0)
+
+template <typename T>
+static int dalloc(lt_ctx* ctx, std::vector<void*>& list, T** p, size_t n) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+  if (e != cudaSuccess)
+    return fail(ctx, e == cudaErrorMemoryAllocation ? LT_ERR_OOM : LT_ERR_CUDA, "cudaMalloc of %zu bytes: %s",
+                n * sizeof(T), cudaGetErrorString(e));
+  list.push_back(q);
+  *p = (T*)q;
+  return LT_OK;
+}
+
+static void free_list(std::vector<void*>& list) {
+  for (void* p : list) cudaFree(p);
+  list.clear();
+}
+
+extern "C" {
+
+int lt_default_options(lt_opts* o) {
+  if (!o) return LT_ERR_INVALID_ARG;
+  o->Nz = 16;
+  o->tol = 1e-8;
+  o->maxit = 160;
+  o->tau_policy = LT_TAU_FLEXIBLE;
+  o->tau_project = 1;
+  o->groups = 1;
+  o->mg_pre = 2;
+  o->mg_post = 2;
+  o->inner_cycles = 6;
+  o->inner_rounds = 4;
+  o->inner_tol = 0.0;
+  o->true_residual = 1;
+  o->check_every = 4;
+  o->timing_class = -1;
+  return LT_OK;
+}
+
+const char* lt_strerror(int s) {
+  switch (s) {
+    case LT_OK: return "ok";
+    case LT_ERR_INVALID_ARG: return "invalid argument";
+    case LT_ERR_OOM: return "device out of memory";
+    case LT_ERR_CUDA: return "CUDA runtime error";
+    case LT_ERR_NOT_CONVERGED: return "not all shifted systems reached the tolerance";
+    case LT_ERR_TIMEOUT: return "device wait timed out";
+    case LT_ERR_STATE: return "call order violated";
+    default: return "unknown status";
+  }
+}
+
+const char* lt_last_error(lt_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int lt_create(lt_ctx** out, int device) {
+  if (!out) return LT_ERR_INVALID_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return LT_ERR_CUDA;
+  if (device < 0 || device >= n) return LT_ERR_INVALID_ARG;
+  lt_ctx* ctx = new lt_ctx();
+  ctx->device = device;
+  lt_default_options(&ctx->opts);
+  if (cudaSetDevice(device) != cudaSuccess || cudaEventCreate(&ctx->ev0) != cudaSuccess ||
+      cudaEventCreate(&ctx->ev1) != cudaSuccess) {
+    delete ctx;
+    return LT_ERR_CUDA;
+  }
+  *out = ctx;
+  return LT_OK;
+}
+
+int lt_set_stream(lt_ctx* ctx, void* stream) {
+  if (!ctx) return LT_ERR_INVALID_ARG;
+  ctx->stream = (cudaStream_t)stream;
+  return LT_OK;
+}
+
+static void free_ws(lt_ctx* ctx) {
+  free_list(ctx->ws.allocs);
+  ctx->ws = Workspace();
+}
+
+void lt_destroy(lt_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  free_ws(ctx);
+  free_list(ctx->grid_allocs);
+  if (ctx->mg.d_levels) cudaFree(ctx->mg.d_levels);
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
+  delete ctx;
+}
+
+int lt_set_options(lt_ctx* ctx, const lt_opts* o) {
+  if (!ctx || !o) return LT_ERR_INVALID_ARG;
+  if (o->Nz < 4 || o->Nz > 128 || (o->Nz & 1)) return fail(ctx, LT_ERR_INVALID_ARG, "Nz=%d must be even in [4,128]", o->Nz);
+  if (!(o->tol > 0.0 && o->tol < 1.0)) return fail(ctx, LT_ERR_INVALID_ARG, "tol=%g must be in (0,1)", o->tol);
+  if (o->maxit < 1 || o->maxit > 250) return fail(ctx, LT_ERR_INVALID_ARG, "maxit=%d must be in [1,250]", o->maxit);
+  if (o->tau_policy != LT_TAU_SINGLE && o->tau_policy != LT_TAU_FLEXIBLE)
+    return fail(ctx, LT_ERR_INVALID_ARG, "tau_policy=%d", o->tau_policy);
+  if (o->groups < 1 || o->groups > 64) return fail(ctx, LT_ERR_INVALID_ARG, "groups=%d must be in [1,64]", o->groups);
+  if (o->mg_pre < 0 || o->mg_pre > 8 || o->mg_post < 0 || o->mg_post > 8 || o->mg_pre + o->mg_post == 0)
+    return fail(ctx, LT_ERR_INVALID_ARG, "mg_pre/mg_post must be in [0,8], not both 0");
+  if (o->inner_cycles < 1 || o->inner_cycles > 64 || o->inner_rounds < 1 || o->inner_rounds > 16)
+    return fail(ctx, LT_ERR_INVALID_ARG, "inner_cycles in [1,64], inner_rounds in [1,16]");
+  if (o->inner_tol < 0.0 || o->inner_tol >= 1.0) return fail(ctx, LT_ERR_INVALID_ARG, "inner_tol=%g", o->inner_tol);
+  if (o->check_every < 1) return fail(ctx, LT_ERR_INVALID_ARG, "check_every=%d", o->check_every);
+  if (o->timing_class < -1 || o->timing_class >= LT_KC_COUNT)
+    return fail(ctx, LT_ERR_INVALID_ARG, "timing_class=%d", o->timing_class);
+  ctx->opts = *o;
+  ctx->mg.npre = o->mg_pre;
+  ctx->mg.npost = o->mg_post;
+  return LT_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ grid + multigrid hierarchy
+// Coarse level: T_coarse = (1/r) * sum of the fine faces crossing the coarse
+// face (r = coarsening ratio along the face normal); m_coarse = sum of the
+// children.  The Dirichlet boundary part is coarsened by coarsen_bfaces and the
+// diagonal rebuilt by level_diag.
+static HostLevel coarsen(const HostLevel& f) {
+  HostLevel c;
+  c.nx = f.nx / f.rx; c.ny = f.ny / f.ry; c.nz = f.nz / f.rz;
+  c.N = c.nx * c.ny * c.nz;
+  c.rx = c.ry = c.rz = 1;
+  c.Te.assign(c.N, 0.0); c.Tn.assign(c.N, 0.0); c.Tu.assign(c.N, 0.0); c.D.assign(c.N, 0.0); c.m.assign(c.N, 0.0);
+  for (int K = 0; K < c.nz; ++K)
+    for (int J = 0; J < c.ny; ++J)
+      for (int I = 0; I < c.nx; ++I) {
+        size_t C = ((size_t)K * c.ny + J) * c.nx + I;
+        double te = 0, tn = 0, tu = 0, mm = 0;
+        for (int dk = 0; dk < f.rz; ++dk)
+          for (int dj = 0; dj < f.ry; ++dj)
+            for (int di = 0; di < f.rx; ++di) {
+              int i = I * f.rx + di, j = J * f.ry + dj, k = K * f.rz + dk;
+              size_t q = ((size_t)k * f.ny + j) * f.nx + i;
+              mm += f.m[q];
+              if (di == f.rx - 1) te += f.Te[q];
+              if (dj == f.ry - 1) tn += f.Tn[q];
+              if (dk == f.rz - 1) tu += f.Tu[q];
+            }
+        c.Te[C] = (I + 1 < c.nx) ? te / f.rx : 0.0;
+        c.Tn[C] = (J + 1 < c.ny) ? tn / f.ry : 0.0;
+        c.Tu[C] = (K + 1 < c.nz) ? tu / f.rz : 0.0;
+        c.m[C] = mm;
+      }
+  return c;
+}
+
+// per-face Dirichlet transmissibility arrays on each level (built alongside the levels)
+struct BFaces {
+  std::vector<double> b[6];   // per cell: transmissibility of the face on side d (0 if none/Neumann)
+};
+
+static void level_diag(HostLevel& L, const BFaces& bf) {
+  for (int k = 0; k < L.nz; ++k)
+    for (int j = 0; j < L.ny; ++j)
+      for (int i = 0; i < L.nx; ++i) {
+        size_t q = ((size_t)k * L.ny + j) * L.nx + i;
+        double s = L.Te[q] + L.Tn[q] + L.Tu[q];
+        if (i > 0) s += L.Te[q - 1];
+        if (j > 0) s += L.Tn[q - L.nx];
+        if (k > 0) s += L.Tu[q - (size_t)L.nx * L.ny];
+        for (int d = 0; d < 6; ++d) s += bf.b[d][q];
+        L.D[q] = s;
+      }
+}
+
+static BFaces coarsen_bfaces(const HostLevel& f, const HostLevel& c, const BFaces& bf) {
+  BFaces out;
+  for (int d = 0; d < 6; ++d) out.b[d].assign(c.N, 0.0);
+  int r[3] = {f.rx, f.ry, f.rz};
+  for (int k = 0; k < f.nz; ++k)
+    for (int j = 0; j < f.ny; ++j)
+      for (int i = 0; i < f.nx; ++i) {
+        size_t q = ((size_t)k * f.ny + j) * f.nx + i;
+        size_t C = ((size_t)(k / f.rz) * c.ny + j / f.ry) * c.nx + i / f.rx;
+        for (int d = 0; d < 6; ++d)
+          if (bf.b[d][q] != 0.0) out.b[d][C] += bf.b[d][q] / r[d / 2];
+      }
+  return out;
+}
+
+static int upload_f32(lt_ctx* ctx, std::vector<void*>& list, float** dst, const std::vector<double>& src) {
+  std::vector<float> tmp(src.size());
+  for (size_t i = 0; i < src.size(); ++i) tmp[i] = (float)src[i];
+  int rc = dalloc(ctx, list, dst, tmp.size());
+  if (rc) return rc;
+  CK(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(float), cudaMemcpyHostToDevice));
+  return LT_OK;
+}
+
+static int upload_df(lt_ctx* ctx, std::vector<void*>& list, const float** hi, const float** lo,
+                     const std::vector<double>& src) {
+  std::vector<float> th(src.size()), tl(src.size());
+  for (size_t i = 0; i < src.size(); ++i) {
+    lt::df v = lt::df_from_double(src[i]);
+    th[i] = v.hi;
+    tl[i] = v.lo;
+  }
+  float *dh, *dl;
+  int rc = dalloc(ctx, list, &dh, th.size());
+  if (rc) return rc;
+  rc = dalloc(ctx, list, &dl, tl.size());
+  if (rc) return rc;
+  CK(cudaMemcpy(dh, th.data(), th.size() * sizeof(float), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dl, tl.data(), tl.size() * sizeof(float), cudaMemcpyHostToDevice));
+  *hi = dh;
+  *lo = dl;
+  return LT_OK;
+}
+
+extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, double dy, double dz,
+                             const double* kappa, const double* Ss, const int* bc, const double* Sy) {
+  if (!ctx) return LT_ERR_INVALID_ARG;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(ctx, LT_ERR_INVALID_ARG, "grid dims %d x %d x %d must be >= 1", nx, ny, nz);
+  if ((int64_t)nx * ny * nz > (1LL << 30)) return fail(ctx, LT_ERR_INVALID_ARG, "grid too large");
+  if (!(dx > 0 && dy > 0 && dz > 0) || !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dz))
+    return fail(ctx, LT_ERR_INVALID_ARG, "cell sizes must be positive and finite");
+  if (!kappa || !Ss || !bc) return fail(ctx, LT_ERR_INVALID_ARG, "kappa, Ss and bc are required");
+  if (Sy) return fail(ctx, LT_ERR_INVALID_ARG, "water-table faces (Sy) are not supported in this version");
+  for (int d = 0; d < 6; ++d)
+    if (bc[d] != LT_BC_DIRICHLET && bc[d] != LT_BC_NEUMANN)
+      return fail(ctx, LT_ERR_INVALID_ARG, "bc[%d]=%d: only Dirichlet (0) and Neumann (1) are supported", d, bc[d]);
+  const int64_t N = (int64_t)nx * ny * nz;
+  for (int64_t c = 0; c < N; ++c) {
+    if (!(kappa[c] > 0.0) || !std::isfinite(kappa[c]))
+      return fail(ctx, LT_ERR_INVALID_ARG, "kappa[%lld]=%g must be positive and finite", (long long)c, kappa[c]);
+    if (!(Ss[c] > 0.0) || !std::isfinite(Ss[c]))
+      return fail(ctx, LT_ERR_INVALID_ARG, "Ss[%lld]=%g must be positive and finite", (long long)c, Ss[c]);
+  }
+  bool any_dirichlet = false;
+  for (int d = 0; d < 6; ++d) any_dirichlet |= (bc[d] == LT_BC_DIRICHLET);
+  if (!any_dirichlet) return fail(ctx, LT_ERR_INVALID_ARG, "at least one Dirichlet face is required (K must be nonsingular)");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  free_ws(ctx);
+  free_list(ctx->grid_allocs);
+  if (ctx->mg.d_levels) { cudaFree(ctx->mg.d_levels); ctx->mg.d_levels = nullptr; }
+  ctx->have_grid = false;
+  ctx->nx = nx; ctx->ny = ny; ctx->nz = nz; ctx->N = N;
+  ctx->dx = dx; ctx->dy = dy; ctx->dz = dz;
+  for (int d = 0; d < 6; ++d) ctx->bc[d] = bc[d];
+  ctx->kappa.assign(kappa, kappa + N);
+  ctx->Ss.assign(Ss, Ss + N);
+
+  // fine level, float64 (Sec. 2.1 restated as two-point-flux finite volumes)
+  HostLevel L0;
+  L0.nx = nx; L0.ny = ny; L0.nz = nz; L0.N = (int)N;
+  L0.Te.assign(N, 0.0); L0.Tn.assign(N, 0.0); L0.Tu.assign(N, 0.0); L0.D.assign(N, 0.0); L0.m.assign(N, 0.0);
+  const double ax = dy * dz / dx, ay = dx * dz / dy, az = dx * dy / dz, vol = dx * dy * dz;
+  auto harm = [](double a, double b) { return 2.0 * a * b / (a + b); };
+  BFaces bf;
+  for (int d = 0; d < 6; ++d) bf.b[d].assign(N, 0.0);
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t q = ((size_t)k * ny + j) * nx + i;
+        double kc = kappa[q];
+        if (i + 1 < nx) L0.Te[q] = ax * harm(kc, kappa[q + 1]);
+        if (j + 1 < ny) L0.Tn[q] = ay * harm(kc, kappa[q + nx]);
+        if (k + 1 < nz) L0.Tu[q] = az * harm(kc, kappa[q + (size_t)nx * ny]);
+        if (i == 0 && bc[0] == 0) bf.b[0][q] = 2.0 * kc * ax;
+        if (i == nx - 1 && bc[1] == 0) bf.b[1][q] = 2.0 * kc * ax;
+        if (j == 0 && bc[2] == 0) bf.b[2][q] = 2.0 * kc * ay;
+        if (j == ny - 1 && bc[3] == 0) bf.b[3][q] = 2.0 * kc * ay;
+        if (k == 0 && bc[4] == 0) bf.b[4][q] = 2.0 * kc * az;
+        if (k == nz - 1 && bc[5] == 0) bf.b[5][q] = 2.0 * kc * az;
+        L0.m[q] = Ss[q] * vol;
+      }
+  level_diag(L0, bf);
+  ctx->hl.clear();
+  std::vector<BFaces> bfs;
+  ctx->hl.push_back(L0);
+  bfs.push_back(bf);
+  for (;;) {
+    HostLevel& f = ctx->hl.back();
+    f.rx = (f.nx % 2 == 0 && f.nx >= 2) ? 2 : 1;
+    f.ry = (f.ny % 2 == 0 && f.ny >= 2) ? 2 : 1;
+    f.rz = (f.nz % 2 == 0 && f.nz >= 2) ? 2 : 1;
+    bool can = (f.rx * f.ry * f.rz > 1);
+    if (f.N <= 64 || !can || (int)ctx->hl.size() >= lt::kMaxLevels) {
+      f.rx = f.ry = f.rz = 1;
+      break;
+    }
+    HostLevel c = coarsen(f);
+    BFaces cb = coarsen_bfaces(f, c, bfs.back());
+    level_diag(c, cb);
+    ctx->hl.push_back(c);
+    bfs.push_back(cb);
+  }
+  const int nlev = (int)ctx->hl.size();
+  if (ctx->hl.back().N > 1024)
+    return fail(ctx, LT_ERR_INVALID_ARG,
+                "grid %d x %d x %d coarsens only to %d cells (> 1024): use dimensions with more factors of 2", nx,
+                ny, nz, ctx->hl.back().N);
+  lt::MGHost& mg = ctx->mg;
+  mg.nlev = nlev;
+  mg.npre = ctx->opts.mg_pre;
+  mg.npost = ctx->opts.mg_post;
+  mg.dmask = 0;
+  for (int d = 0; d < 6; ++d)
+    if (bc[d] == 0) mg.dmask |= (1 << d);
+  mg.coarse_direct = ctx->hl.back().N <= lt::kDirectCells ? 1 : 0;
+  mg.lc = nlev - 1;
+  while (mg.lc > 0 && ctx->hl[mg.lc - 1].N <= lt::kCoarseCells) --mg.lc;
+  for (int l = 0; l < nlev; ++l) {
+    const HostLevel& h = ctx->hl[l];
+    lt::Level& L = mg.h_levels[l];
+    L.nx = h.nx; L.ny = h.ny; L.nz = h.nz; L.N = h.N;
+    L.rx = h.rx; L.ry = h.ry; L.rz = h.rz;
+    int rc;
+    if ((rc = upload_f32(ctx, ctx->grid_allocs, &L.Te, h.Te))) return rc;
+    if ((rc = upload_f32(ctx, ctx->grid_allocs, &L.Tn, h.Tn))) return rc;
+    if ((rc = upload_f32(ctx, ctx->grid_allocs, &L.Tu, h.Tu))) return rc;
+    if ((rc = upload_f32(ctx, ctx->grid_allocs, &L.D, h.D))) return rc;
+    if ((rc = upload_f32(ctx, ctx->grid_allocs, &L.m, h.m))) return rc;
+    L.u = L.f = nullptr;   // per-batch vectors, set when a workspace is sized
+  }
+  lt::FineExact& fe = ctx->fe;
+  fe.nx = nx; fe.ny = ny; fe.nz = nz; fe.N = (int)N;
+  int rc;
+  if ((rc = upload_df(ctx, ctx->grid_allocs, &fe.Te_hi, &fe.Te_lo, L0.Te))) return rc;
+  if ((rc = upload_df(ctx, ctx->grid_allocs, &fe.Tn_hi, &fe.Tn_lo, L0.Tn))) return rc;
+  if ((rc = upload_df(ctx, ctx->grid_allocs, &fe.Tu_hi, &fe.Tu_lo, L0.Tu))) return rc;
+  if ((rc = upload_df(ctx, ctx->grid_allocs, &fe.D_hi, &fe.D_lo, ctx->hl[0].D))) return rc;
+  if ((rc = upload_df(ctx, ctx->grid_allocs, &fe.m_hi, &fe.m_lo, L0.m))) return rc;
+  CK(cudaMalloc(&mg.d_levels, sizeof(lt::Level) * lt::kMaxLevels));
+  ctx->have_grid = true;
+  ctx->src.clear(); ctx->Q.clear(); ctx->rec.clear();
+  return LT_OK;
+}
+
+extern "C" int lt_set_sources(lt_ctx* ctx, int ns, const int64_t* cells, const double* Q) {
+  if (!ctx) return LT_ERR_INVALID_ARG;
+  if (!ctx->have_grid) return fail(ctx, LT_ERR_STATE, "lt_setup_grid must come first");
+  if (ns < 0 || (ns > 0 && (!cells || !Q))) return fail(ctx, LT_ERR_INVALID_ARG, "ns=%d with null arrays", ns);
+  for (int s = 0; s < ns; ++s) {
+    if (cells[s] < 0 || cells[s] >= ctx->N)
+      return fail(ctx, LT_ERR_INVALID_ARG, "source %d cell %lld out of range [0,%lld)", s, (long long)cells[s],
+                  (long long)ctx->N);
+    if (!std::isfinite(Q[s])) return fail(ctx, LT_ERR_INVALID_ARG, "source %d rate not finite", s);
+  }
+  ctx->src.assign(cells, cells + ns);
+  ctx->Q.assign(Q, Q + ns);
+  return LT_OK;
+}
+
+extern "C" int lt_set_receivers(lt_ctx* ctx, int nr, const int64_t* cells) {
+  if (!ctx) return LT_ERR_INVALID_ARG;
+  if (!ctx->have_grid) return fail(ctx, LT_ERR_STATE, "lt_setup_grid must come first");
+  if (nr < 0 || (nr > 0 && !cells)) return fail(ctx, LT_ERR_INVALID_ARG, "nr=%d with null array", nr);
+  for (int r = 0; r < nr; ++r)
+    if (cells[r] < 0 || cells[r] >= ctx->N)
+      return fail(ctx, LT_ERR_INVALID_ARG, "receiver %d cell %lld out of range", r, (long long)cells[r]);
+  ctx->rec.assign(cells, cells + nr);
+  return LT_OK;
+}
+
+// ------------------------------------------------------------------ solve plan
+struct Plan {
+  int nt = 0, G = 0, Nk = 0;
+  std::vector<double> times;            // caller order
+  std::vector<int> tgroup;              // time -> group
+  std::vector<int> tpos;                // time -> position inside its group
+  std::vector<int> gcount;              // times per group
+  std::vector<std::vector<cplx>> z, w;  // per time: Nk nodes / weights
+  std::vector<cplx> tau;                // [G][2]
+  // bases
+  int nb = 0, nsh = 0;
+  std::vector<int64_t> rhs_cell;        // per basis
+  std::vector<int> group;               // per basis
+  std::vector<int> shift_off;           // nb + 1
+  std::vector<int> sh_basis;
+  std::vector<cplx> zsh;
+};
+
+static int make_plan(lt_ctx* ctx, int nt, const double* times, const std::vector<int64_t>& rhs, Plan& P) {
+  const lt_opts& o = ctx->opts;
+  P.nt = nt;
+  P.times.assign(times, times + nt);
+  P.Nk = o.Nz / 2;
+  P.G = std::min(o.groups, nt);
+  std::vector<int> order(nt);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return times[a] < times[b]; });
+  P.tgroup.assign(nt, 0);
+  P.tpos.assign(nt, 0);
+  P.gcount.assign(P.G, 0);
+  for (int q = 0; q < nt; ++q) {
+    int t = order[q];
+    int g = (int)((int64_t)q * P.G / nt);
+    P.tgroup[t] = g;
+    P.tpos[t] = P.gcount[g]++;
+  }
+  P.z.resize(nt);
+  P.w.resize(nt);
+  for (int t = 0; t < nt; ++t) talbot_half(times[t], o.Nz, P.z[t], P.w[t]);
+  // group shift lists in position order
+  std::vector<std::vector<int>> gtimes(P.G);
+  for (int q = 0; q < nt; ++q) gtimes[P.tgroup[order[q]]].push_back(order[q]);
+  P.tau.assign(2 * P.G, cplx(0, 0));
+  for (int g = 0; g < P.G; ++g) {
+    cplx lo(1e300, 0), hi(-1e300, 0);
+    for (int t : gtimes[g])
+      for (const cplx& z : P.z[t]) {
+        if (z.real() < lo.real()) lo = z;
+        if (z.real() > hi.real()) hi = z;
+      }
+    if (o.tau_project) {
+      lo = cplx(std::max(lo.real(), 0.0), lo.imag());
+      hi = cplx(std::max(hi.real(), 0.0), hi.imag());
+    }
+    P.tau[2 * g] = lo;
+    P.tau[2 * g + 1] = (o.tau_policy == LT_TAU_SINGLE) ? lo : hi;
+  }
+  P.nb = (int)rhs.size() * P.G;
+  P.rhs_cell.resize(P.nb);
+  P.group.resize(P.nb);
+  P.shift_off.assign(P.nb + 1, 0);
+  P.zsh.clear();
+  P.sh_basis.clear();
+  for (size_t s = 0; s < rhs.size(); ++s)
+    for (int g = 0; g < P.G; ++g) {
+      int b = (int)s * P.G + g;
+      P.rhs_cell[b] = rhs[s];
+      P.group[b] = g;
+      for (int t : gtimes[g])
+        for (const cplx& z : P.z[t]) {
+          P.zsh.push_back(z);
+          P.sh_basis.push_back(b);
+        }
+      P.shift_off[b + 1] = (int)P.zsh.size();
+    }
+  P.nsh = (int)P.zsh.size();
+  for (int g = 0; g < P.G; ++g) std::sort(gtimes[g].begin(), gtimes[g].end(), [&](int a, int b) { return P.tpos[a] < P.tpos[b]; });
+  return LT_OK;
+}
+
+// first global shift index of time t inside basis b
+static int shift_of(const Plan& P, int b, int t) { return P.shift_off[b] + P.tpos[t] * P.Nk; }
+
+// dense inverse of the coarsest operator K_c + tau M_c (complex LU with partial pivoting)
+static bool dense_inverse(const HostLevel& L, cplx tau, std::vector<cplx>& inv) {
+  const int n = L.N;
+  std::vector<cplx> A((size_t)n * n, 0.0);
+  for (int k = 0; k < L.nz; ++k)
+    for (int j = 0; j < L.ny; ++j)
+      for (int i = 0; i < L.nx; ++i) {
+        int q = (k * L.ny + j) * L.nx + i;
+        A[(size_t)q * n + q] = L.D[q] + tau * L.m[q];
+        auto off = [&](int p, double t) {
+          A[(size_t)q * n + p] -= t;
+        };
+        if (i + 1 < L.nx) off(q + 1, L.Te[q]);
+        if (i > 0) off(q - 1, L.Te[q - 1]);
+        if (j + 1 < L.ny) off(q + L.nx, L.Tn[q]);
+        if (j > 0) off(q - L.nx, L.Tn[q - L.nx]);
+        if (k + 1 < L.nz) off(q + L.nx * L.ny, L.Tu[q]);
+        if (k > 0) off(q - L.nx * L.ny, L.Tu[q - L.nx * L.ny]);
+      }
+  inv.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    double best = std::abs(A[(size_t)col * n + col]);
+    for (int r = col + 1; r < n; ++r)
+      if (std::abs(A[(size_t)r * n + col]) > best) { best = std::abs(A[(size_t)r * n + col]); piv = r; }
+    if (best == 0.0) return false;
+    if (piv != col)
+      for (int c = 0; c < n; ++c) {
+        std::swap(A[(size_t)piv * n + c], A[(size_t)col * n + c]);
+        std::swap(inv[(size_t)piv * n + c], inv[(size_t)col * n + c]);
+      }
+    cplx d = 1.0 / A[(size_t)col * n + col];
+    for (int c = 0; c < n; ++c) { A[(size_t)col * n + c] *= d; inv[(size_t)col * n + c] *= d; }
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      cplx f = A[(size_t)r * n + col];
+      if (f == 0.0) continue;
+      for (int c = 0; c < n; ++c) {
+        A[(size_t)r * n + c] -= f * A[(size_t)col * n + c];
+        inv[(size_t)r * n + c] -= f * inv[(size_t)col * n + c];
+      }
+    }
+  }
+  return true;
+}
+
+static int ensure_ws(lt_ctx* ctx, const Plan& P) {
+  Workspace& ws = ctx->ws;
+  const lt_opts& o = ctx->opts;
+  const int nc = ctx->hl.back().N;
+  const int nc2 = ctx->mg.coarse_direct ? nc * nc : 0;
+  if (ws.nb >= P.nb && ws.maxit == o.maxit && ws.nsh >= P.nsh && ws.rounds == o.inner_rounds && ws.N == ctx->N &&
+      ws.ngroups >= P.G && ws.nc2 >= nc2)
+    return LT_OK;
+  CK(cudaStreamSynchronize(ctx->stream));
+  free_ws(ctx);
+  lt::Batch& bt = ws.bt;
+  const int nb = P.nb, M = o.maxit, R = o.inner_rounds, nsh = P.nsh;
+  const size_t N = (size_t)ctx->N;
+  auto& A = ws.allocs;
+  int rc = 0;
+#define AL(p, n) if ((rc = dalloc(ctx, A, &p, (size_t)(n)))) return rc
+  AL(bt.V_hi, (size_t)nb * (M + 1) * N); AL(bt.V_lo, (size_t)nb * (M + 1) * N);
+  AL(bt.U_hi, (size_t)nb * M * N); AL(bt.U_lo, (size_t)nb * M * N);
+  AL(bt.S_hi, (size_t)nb * N); AL(bt.S_lo, (size_t)nb * N);
+  AL(bt.tau_grp, 2 * P.G); AL(bt.group, nb); AL(bt.tau_pattern, 5); AL(bt.tau_cur, nb); AL(bt.tau_slot, nb);
+  AL(bt.rnorm2, (size_t)nb * (R + 1)); AL(bt.dot, (size_t)nb * 2 * (M + 1)); AL(bt.H, (size_t)nb * M * (M + 1));
+  AL(bt.snorm2, nb); AL(bt.active, nb); AL(bt.nit, nb); AL(bt.inner_max, nb); AL(bt.rhs_cell, nb);
+  AL(bt.shift_off, nb + 1); AL(bt.zsh, nsh); AL(bt.R, (size_t)nsh * M * M); AL(bt.rc, (size_t)nsh * M);
+  AL(bt.rs, (size_t)nsh * M); AL(bt.g, (size_t)nsh * (M + 1)); AL(bt.conv_it, nsh); AL(bt.pres, nsh);
+  AL(bt.Y, (size_t)nsh * M);
+  AL(bt.work, 16);
+  if (nc2) AL(bt.coarse_inv, (size_t)2 * P.G * nc2);
+  // multigrid vectors
+  for (int l = 0; l < ctx->mg.nlev; ++l) {
+    lt::Level& L = ctx->mg.h_levels[l];
+    AL(L.u, (size_t)nb * L.N);
+    AL(L.f, (size_t)nb * L.N);
+  }
+#undef AL
+  CK(cudaMemcpy(ctx->mg.d_levels, ctx->mg.h_levels, sizeof(lt::Level) * ctx->mg.nlev, cudaMemcpyHostToDevice));
+  ws.nb = nb; ws.maxit = M; ws.nsh = nsh; ws.rounds = R; ws.N = ctx->N; ws.ngroups = P.G; ws.nc2 = nc2;
+  bt.nb = nb; bt.maxit = M; bt.N = ctx->N; bt.rounds = R; bt.nsh = nsh;
+  return LT_OK;
+}
+
+// Runs the batched flexible shifted Krylov solves of a plan; leaves Y, U in the workspace.
+static int run_solves(lt_ctx* ctx, const Plan& P, std::vector<double>& true_res, lt_stats* st, int* nl) {
+  const lt_opts& o = ctx->opts;
+  int rc = ensure_ws(ctx, P);
+  if (rc) return rc;
+  lt::Batch& bt = ctx->ws.bt;
+  bt.nb = P.nb;
+  bt.nsh = P.nsh;
+  bt.tol = o.tol;
+  double itol = o.inner_tol > 0 ? o.inner_tol : 0.01 * o.tol;
+  bt.inner_tol2 = itol * itol;
+  cudaStream_t s = ctx->stream;
+  // tables
+  std::vector<double2> taug(2 * P.G);
+  for (int i = 0; i < 2 * P.G; ++i) taug[i] = make_double2(P.tau[i].real(), P.tau[i].imag());
+  int pat_flex[5] = {0, 0, 0, 1, 1}, pat_single[5] = {0, 0, 0, 0, 0};
+  std::vector<double2> zsh(P.nsh);
+  for (int i = 0; i < P.nsh; ++i) zsh[i] = make_double2(P.zsh[i].real(), P.zsh[i].imag());
+  CK(cudaMemcpyAsync(bt.tau_grp, taug.data(), taug.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(bt.tau_pattern, o.tau_policy == LT_TAU_SINGLE ? pat_single : pat_flex, 5 * sizeof(int),
+                     cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(bt.group, P.group.data(), P.nb * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(bt.rhs_cell, P.rhs_cell.data(), P.nb * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(bt.shift_off, P.shift_off.data(), (P.nb + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(bt.zsh, zsh.data(), P.nsh * sizeof(double2), cudaMemcpyHostToDevice, s));
+  bt.coarse_direct = ctx->mg.coarse_direct;
+  if (ctx->mg.coarse_direct) {
+    const HostLevel& Lc = ctx->hl.back();
+    const size_t nc2 = (size_t)Lc.N * Lc.N;
+    std::vector<float2> inv32(2 * P.G * nc2);
+    for (int q = 0; q < 2 * P.G; ++q) {
+      std::vector<cplx> inv;
+      if (!dense_inverse(Lc, P.tau[q], inv)) return fail(ctx, LT_ERR_INVALID_ARG, "singular coarsest operator");
+      for (size_t i = 0; i < nc2; ++i) inv32[q * nc2 + i] = make_float2((float)inv[i].real(), (float)inv[i].imag());
+    }
+    CK(cudaMemcpyAsync(bt.coarse_inv, inv32.data(), inv32.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  CK(cudaMemsetAsync(bt.work, 0, 16 * sizeof(unsigned long long), s));
+  lt::Prof* pf = nullptr;
+  if (o.timing_class >= 0) {
+    const int cap = 16384;
+    while ((int)ctx->prof_events.size() < 2 * cap) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      ctx->prof_events.push_back(e);
+    }
+    ctx->prof.cls = o.timing_class;
+    ctx->prof.n = 0;
+    ctx->prof.cap = cap;
+    ctx->prof.ev = ctx->prof_events.data();
+    pf = &ctx->prof;
+  }
+  lt::launch_init_batch(bt, s);
+  *nl += 2;
+  std::vector<int> act(P.nb);
+  int j = 0, cycles = 0;
+  const lt::Level& L0 = ctx->mg.h_levels[0];
+  for (j = 0; j < o.maxit; ++j) {
+    lt::launch_prep_iter(bt, j, s);
+    ++*nl;
+    for (int r = 0; r < o.inner_rounds; ++r) {
+      lt::launch_exact_residual(bt, ctx->fe, L0, j, r, 0, s, pf);
+      ++*nl;
+      for (int cy = 0; cy < o.inner_cycles; ++cy) {
+        if (lt::launch_vcycle(ctx->mg, bt, r, s, nl, pf)) return fail(ctx, LT_ERR_CUDA, "V-cycle launch failed");
+        ++cycles;
+      }
+      lt::launch_update_u(bt, L0, j, r, s);
+      ++*nl;
+    }
+    lt::launch_exact_residual(bt, ctx->fe, L0, j, o.inner_rounds, 1, s, pf);
+    lt::launch_inner_record(bt, s);
+    *nl += 2;
+    lt::launch_arnoldi(bt, ctx->fe, j, s, nl, pf);
+    lt::launch_shift_ls(bt, j, s);
+    ++*nl;
+    CK(cudaGetLastError());
+    if ((j + 1) % o.check_every == 0 || j + 1 == o.maxit) {
+      CK(cudaMemcpyAsync(act.data(), bt.active, P.nb * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      bool any = false;
+      for (int b = 0; b < P.nb; ++b) any |= act[b] != 0;
+      if (!any) { ++j; break; }
+    }
+  }
+  // y per shift
+  int* d_shb = nullptr;
+  std::vector<void*> tmp;
+  if ((rc = dalloc(ctx, tmp, &d_shb, P.nsh))) return rc;
+  CK(cudaMemcpyAsync(d_shb, P.sh_basis.data(), P.nsh * sizeof(int), cudaMemcpyHostToDevice, s));
+  lt::launch_backsolve_map(bt, d_shb, s);
+  ++*nl;
+  true_res.assign(P.nsh, -1.0);
+  if (o.true_residual) {
+    Workspace& ws = ctx->ws;
+    size_t need = (size_t)P.nsh * ctx->N;
+    if (ws.x_elems < need) {
+      // X buffers live in the workspace list
+      if ((rc = dalloc(ctx, ws.allocs, &ws.X_hi, need))) { free_list(tmp); return rc; }
+      if ((rc = dalloc(ctx, ws.allocs, &ws.X_lo, need))) { free_list(tmp); return rc; }
+      ws.x_elems = need;
+    }
+    double* d_res2 = nullptr;
+    if ((rc = dalloc(ctx, tmp, &d_res2, P.nsh))) { free_list(tmp); return rc; }
+    CK(cudaMemsetAsync(d_res2, 0, P.nsh * sizeof(double), s));
+    lt::launch_true_residual_map(bt, ctx->fe, d_shb, ws.X_hi, ws.X_lo, d_res2, s, nl, pf);
+    CK(cudaMemcpyAsync(true_res.data(), d_res2, P.nsh * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  // stats
+  std::vector<int> nit(P.nb), conv(P.nsh);
+  std::vector<double> pres(P.nsh), inner(P.nb);
+  CK(cudaMemcpyAsync(nit.data(), bt.nit, P.nb * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(conv.data(), bt.conv_it, P.nsh * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(pres.data(), bt.pres, P.nsh * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(inner.data(), bt.inner_max, P.nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+  unsigned long long work[16];
+  CK(cudaMemcpyAsync(work, bt.work, sizeof(work), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  free_list(tmp);
+  for (auto& r : true_res)
+    if (r >= 0) r = std::sqrt(r);
+  if (st) {
+    for (int c = 0; c < 16; ++c) st->work[c] += work[c];
+    if (pf) {
+      float tot = 0.f;
+      for (int q = 0; q < pf->n; ++q) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, pf->ev[2 * q], pf->ev[2 * q + 1]);
+        tot += ms;
+      }
+      st->timed_ms += tot;
+      st->timed_launches += pf->n;
+    }
+    st->n_bases += P.nb;
+    st->n_shift_solves += P.nsh;
+    int conv_count = 0;
+    for (int i = 0; i < P.nsh; ++i) {
+      bool ok = o.true_residual ? (true_res[i] <= o.tol) : (conv[i] > 0);
+      conv_count += ok;
+      st->max_proj_residual = std::max(st->max_proj_residual, pres[i]);
+      if (o.true_residual) st->max_true_residual = std::max(st->max_true_residual, true_res[i]);
+    }
+    st->n_converged += conv_count;
+    for (int b = 0; b < P.nb; ++b) {
+      st->outer_iters_max = std::max(st->outer_iters_max, nit[b]);
+      st->outer_iters_sum += nit[b];
+      st->max_inner_residual = std::max(st->max_inner_residual, inner[b]);
+    }
+    st->inner_cycles_total += cycles;
+  }
+  return LT_OK;
+}
+
+static void stats_reset(lt_stats* st, bool tr) {
+  if (!st) return;
+  memset(st, 0, sizeof(*st));
+  st->max_true_residual = tr ? 0.0 : -1.0;
+}
+
+static int check_times(lt_ctx* ctx, int nt, const double* times) {
+  if (!ctx->have_grid) return fail(ctx, LT_ERR_STATE, "lt_setup_grid must come first");
+  if (nt < 1 || !times) return fail(ctx, LT_ERR_INVALID_ARG, "nt=%d must be >= 1", nt);
+  for (int t = 0; t < nt; ++t)
+    if (!(times[t] > 0.0) || !std::isfinite(times[t]))
+      return fail(ctx, LT_ERR_INVALID_ARG, "times[%d]=%g must be positive and finite", t, times[t]);
+  return LT_OK;
+}
+
+// forward driver shared by lt_forward and lt_forward_fields
+static int forward_impl(lt_ctx* ctx, int nt, const double* times, double* out, int on_device, int fields,
+                        lt_stats* st) {
+  if (!ctx) return LT_ERR_INVALID_ARG;
+  int rc = check_times(ctx, nt, times);
+  if (rc) return rc;
+  if (ctx->src.empty()) return fail(ctx, LT_ERR_STATE, "no sources set");
+  if (!fields && ctx->rec.empty()) return fail(ctx, LT_ERR_STATE, "no receivers set");
+  if (!out) return fail(ctx, LT_ERR_INVALID_ARG, "output pointer is null");
+  CK(cudaSetDevice(ctx->device));
+  stats_reset(st, ctx->opts.true_residual);
+  Plan P;
+  make_plan(ctx, nt, times, ctx->src, P);
+  int nl = 0;
+  CK(cudaEventRecord(ctx->ev0, ctx->stream));
+  std::vector<double> tres;
+  rc = run_solves(ctx, P, tres, st, &nl);
+  if (rc) return rc;
+  const int ns = (int)ctx->src.size(), nr = (int)ctx->rec.size();
+  cudaStream_t s = ctx->stream;
+  // quadrature items (s, t) and weights w_k Q_s / z_k
+  std::vector<lt::QuadItem> items(ns * nt);
+  std::vector<double2> wq(P.nsh);
+  for (int si = 0; si < ns; ++si)
+    for (int t = 0; t < nt; ++t) {
+      int b = si * P.G + P.tgroup[t];
+      int sh0 = shift_of(P, b, t);
+      items[si * nt + t] = {b, sh0, P.Nk};
+      for (int k = 0; k < P.Nk; ++k) {
+        cplx v = P.w[t][k] * ctx->Q[si] / P.z[t][k];
+        wq[sh0 + k] = make_double2(v.real(), v.imag());
+      }
+    }
+  std::vector<void*> tmp;
+  lt::QuadItem* d_items;
+  double2 *d_wq, *d_C;
+  int64_t* d_rc;
+  double* d_out = nullptr;
+  const size_t out_n = fields ? (size_t)ns * nt * ctx->N : (size_t)ns * nr * nt;
+  if ((rc = dalloc(ctx, tmp, &d_items, items.size())) || (rc = dalloc(ctx, tmp, &d_wq, wq.size())) ||
+      (rc = dalloc(ctx, tmp, &d_C, items.size() * ctx->opts.maxit)) || (rc = dalloc(ctx, tmp, &d_rc, std::max(nr, 1)))) {
+    free_list(tmp);
+    return rc;
+  }
+  if (on_device) d_out = out;
+  else if ((rc = dalloc(ctx, tmp, &d_out, out_n))) { free_list(tmp); return rc; }
+  CK(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(lt::QuadItem), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_wq, wq.data(), wq.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+  if (nr) CK(cudaMemcpyAsync(d_rc, ctx->rec.data(), nr * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  lt::launch_quad_coef(ctx->ws.bt, d_items, (int)items.size(), d_wq, d_C, s);
+  if (fields) lt::launch_fields(ctx->ws.bt, d_items, d_C, (int)items.size(), d_out, s);
+  else lt::launch_measure(ctx->ws.bt, d_items, d_C, ns, nr, nt, d_rc, d_out, s);
+  nl += 2;
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(ctx->ev1, s));
+  if (!on_device) CK(cudaMemcpyAsync(out, d_out, out_n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  free_list(tmp);
+  if (st) {
+    cudaEventElapsedTime(&st->ms_total, ctx->ev0, ctx->ev1);
+    st->kernel_launches = nl;
+  }
+  bool all = true;
+  for (size_t i = 0; i < tres.size(); ++i)
+    if (ctx->opts.true_residual && !(tres[i] <= ctx->opts.tol)) all = false;
+  if (!all) return fail(ctx, LT_ERR_NOT_CONVERGED, "some shifted systems did not reach tol");
+  return LT_OK;
+}
+
+extern "C" int lt_forward(lt_ctx* ctx, int nt, const double* times, double* h, int h_on_device, lt_stats* st) {
+  return forward_impl(ctx, nt, times, h, h_on_device, 0, st);
+}
+
+extern "C" int lt_forward_fields(lt_ctx* ctx, int nt, const double* times, double* phi, int on_device,
+                                 lt_stats* st) {
+  return forward_impl(ctx, nt, times, phi, on_device, 1, st);
+}
+
+extern "C" int lt_adjoint_jacobian(lt_ctx* ctx, int nt, const double* times, double* J, lt_stats* st) {
+  (void)nt; (void)times; (void)J; (void)st;
+  return fail(ctx, LT_ERR_STATE, "adjoint Jacobian not built yet");
+}
+
+extern "C" int lt_adjoint_vjp(lt_ctx* ctx, int nt, const double* times, const double* g, double* grad, double* h,
+                              int on_device, lt_stats* st) {
+  (void)nt; (void)times; (void)g; (void)grad; (void)h; (void)on_device; (void)st;
+  return fail(ctx, LT_ERR_STATE, "adjoint VJP not built yet");
+}

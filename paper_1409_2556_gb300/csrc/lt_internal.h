@@ -1,0 +1,92 @@
+// lt_internal.h -- device data structures shared by the kernels and the
+// host driver of the Laplace-transform / flexible shifted-Krylov engine.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lt {
+
+constexpr int kMaxLevels = 16;
+constexpr int kCoarseCells = 4096;     // levels at or below this size run in one CTA per basis
+constexpr int kDirectCells = 256;      // coarsest level solved by a dense inverse if at most this size
+constexpr int kCoarseSweeps = 24;      // RB-GS sweeps at the coarsest level when it is not solved directly
+
+// One multigrid level: fp32 coefficients of K_l and M_l.
+struct Level {
+  int nx, ny, nz, N;
+  int rx, ry, rz;                  // coarsening ratio to the next level (1 or 2 per axis)
+  float* Te;                       // face (i,j,k)-(i+1,j,k), 0 on the last column
+  float* Tn;                       // face (i,j,k)-(i,j+1,k)
+  float* Tu;                       // face (i,j,k)-(i,j,k+1)
+  float* D;                        // sum of all face transmissibilities of the cell (incl. Dirichlet)
+  float* m;                        // storage S_s * volume
+  float2* u;                       // [nb][N] iterate / correction
+  float2* f;                       // [nb][N] right-hand side
+};
+
+// Fine-level operator in df32 (hi/lo float pairs) for the exact residuals.
+struct FineExact {
+  int nx, ny, nz, N;
+  const float *Te_hi, *Te_lo, *Tn_hi, *Tn_lo, *Tu_hi, *Tu_lo, *D_hi, *D_lo, *m_hi, *m_lo;
+};
+
+// Per-basis bookkeeping of a batch of Krylov bases.
+struct Batch {
+  int nb;                          // bases
+  int maxit;                       // columns of U (V has maxit + 1)
+  int64_t N;                       // fine cells
+  int rounds;                      // refinement rounds per preconditioner solve
+  double inner_tol2;               // (inner relative tolerance)^2
+  double tol;                      // outer tolerance (relative)
+  float2 *V_hi, *V_lo;             // [nb][maxit+1][N]
+  float2 *U_hi, *U_lo;             // [nb][maxit][N]
+  float2 *S_hi, *S_lo;             // [nb][N] Arnoldi work vector
+  double2* tau_grp;                // [ngroups][2] preconditioner shifts per group
+  int* group;                      // [nb]
+  int* tau_pattern;                // [5] slot per (j mod 5)
+  double2* tau_cur;                // [nb] current preconditioner shift
+  int* tau_slot;                   // [nb] current slot (0/1) for the coarse inverse
+  double* rnorm2;                  // [nb][rounds+1]
+  double2* dot;                    // [nb][2][maxit+1]
+  double2* H;                      // [nb][maxit][maxit+1], column j at H + (b*maxit + j)*(maxit+1)
+  double* snorm2;                  // [nb]
+  int* active;                     // [nb]
+  int* nit;                        // [nb] outer iterations done
+  double* inner_max;               // [nb]
+  int64_t* rhs_cell;               // [nb]
+  // shifts: basis b owns shifts [shift_off[b], shift_off[b+1])
+  int nsh;
+  int* shift_off;                  // [nb+1]
+  double2* zsh;                    // [nsh]
+  double2* R;                      // [nsh][maxit][maxit]
+  double* rc;                      // [nsh][maxit]
+  double2* rs;                     // [nsh][maxit]
+  double2* g;                      // [nsh][maxit+1]
+  int* conv_it;                    // [nsh] iterations at convergence (0 = not yet)
+  double* pres;                    // [nsh] projected residual
+  double2* Y;                      // [nsh][maxit]
+  float2* coarse_inv;              // [ngroups*2][nc*nc] dense inverses of the coarsest operator
+  int coarse_direct;               // 1 if coarse_inv is valid
+  unsigned long long* work;        // [kNumClasses] cells processed per kernel class (live roofline)
+};
+
+// kernel classes for the live per-kernel timing and work counters
+enum KernelClass {
+  KC_RBGS = 0, KC_RESTRICT, KC_PROLONG, KC_COARSE, KC_EXACT_RES, KC_UPDATE_U, KC_DOTS, KC_ORTHO, KC_NORMALIZE,
+  KC_SHIFT_LS, KC_XK, KC_TRUE_RES, KC_OTHER, kNumClasses
+};
+
+// CUDA-event timing of the launches of one kernel class (cls < 0: off)
+struct Prof {
+  int cls = -1;
+  int n = 0, cap = 0;
+  cudaEvent_t* ev = nullptr;      // 2 * cap events
+};
+inline void prof_begin(Prof* p, int cls, cudaStream_t st) {
+  if (p && p->cls == cls && p->n < p->cap) cudaEventRecord(p->ev[2 * p->n], st);
+}
+inline void prof_end(Prof* p, int cls, cudaStream_t st) {
+  if (p && p->cls == cls && p->n < p->cap) { cudaEventRecord(p->ev[2 * p->n + 1], st); ++p->n; }
+}
+
+}  // namespace lt

@@ -1,0 +1,283 @@
+// mg.cu -- geometric multigrid V-cycle for the complex-shifted operator
+// K + tau M on the cell-centred finite-volume grid, in float32 complex.
+//
+// It is the inexact shift-and-invert preconditioner (K + tau_j M)^{-1} of
+// the flexible shifted Krylov method (Sec. 3: the paper factorises these
+// systems directly; here they are solved iteratively, see krylov.cu for the
+// refinement that makes each solve accurate to the outer tolerance).
+//
+// Components:
+//   * red-black Gauss-Seidel smoother (complex diagonal D + tau m);
+//   * restriction = sum of the residual over the 2^d children;
+//   * prolongation = cell-centred multilinear interpolation (weights 3/4,
+//     1/4 per coarsened axis) with odd/even reflection across Dirichlet /
+//     Neumann faces;
+//   * coarse operators: T_coarse = (1/r) * sum of the fine faces crossing
+//     the coarse face (r = ratio along the face normal), m_coarse = sum of
+//     the children's m (built on the host);
+//   * levels at or below kCoarseCells run inside one CTA per basis
+//     (coarse_vcycle), ending in a dense inverse at the coarsest level.
+// All kernels are batched over Krylov bases (blockIdx.y = basis) and skip
+// bases that are inactive or whose preconditioner solve already converged.
+#include "lt_internal.h"
+#include "lt_kernels.h"
+
+namespace lt {
+
+__device__ __forceinline__ bool mg_skip(const Batch& bt, int b, int round) {
+  if (!bt.active[b]) return true;
+  return bt.rnorm2[b * (bt.rounds + 1) + round] <= bt.inner_tol2;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cdiv(float2 a, float2 d) {
+  float inv = 1.f / (d.x * d.x + d.y * d.y);
+  return make_float2((a.x * d.x + a.y * d.y) * inv, (a.y * d.x - a.x * d.y) * inv);
+}
+
+// sum_nb T u_nb and the cell's complex diagonal D + tau m
+__device__ __forceinline__ float2 nb_sum(const Level& L, const float2* __restrict__ u, int i, int j, int k, int c) {
+  float2 s = make_float2(0.f, 0.f);
+  if (i + 1 < L.nx) { float t = L.Te[c]; float2 v = u[c + 1]; s.x += t * v.x; s.y += t * v.y; }
+  if (i > 0) { float t = L.Te[c - 1]; float2 v = u[c - 1]; s.x += t * v.x; s.y += t * v.y; }
+  if (j + 1 < L.ny) { float t = L.Tn[c]; float2 v = u[c + L.nx]; s.x += t * v.x; s.y += t * v.y; }
+  if (j > 0) { float t = L.Tn[c - L.nx]; float2 v = u[c - L.nx]; s.x += t * v.x; s.y += t * v.y; }
+  const int pl = L.nx * L.ny;
+  if (k + 1 < L.nz) { float t = L.Tu[c]; float2 v = u[c + pl]; s.x += t * v.x; s.y += t * v.y; }
+  if (k > 0) { float t = L.Tu[c - pl]; float2 v = u[c - pl]; s.x += t * v.x; s.y += t * v.y; }
+  return s;
+}
+
+__device__ __forceinline__ float2 diag_of(const Level& L, int c, float2 tau) {
+  float m = L.m[c];
+  return make_float2(L.D[c] + tau.x * m, tau.y * m);
+}
+
+__device__ __forceinline__ void rbgs_cell(const Level& L, float2* u, const float2* f, int c, float2 tau) {
+  int i = c % L.nx, j = (c / L.nx) % L.ny, k = c / (L.nx * L.ny);
+  float2 s = nb_sum(L, u, i, j, k, c);
+  float2 r = f[c];
+  r.x += s.x; r.y += s.y;
+  u[c] = cdiv(r, diag_of(L, c, tau));
+}
+
+__device__ __forceinline__ float2 resid_cell(const Level& L, const float2* u, const float2* f, int c, float2 tau) {
+  int i = c % L.nx, j = (c / L.nx) % L.ny, k = c / (L.nx * L.ny);
+  float2 s = nb_sum(L, u, i, j, k, c);
+  float2 a = cmul(diag_of(L, c, tau), u[c]);
+  float2 fc = f[c];
+  return make_float2(fc.x - a.x + s.x, fc.y - a.y + s.y);
+}
+
+__device__ __forceinline__ float2 tau32(const Batch& bt, int b) {
+  double2 t = bt.tau_cur[b];
+  return make_float2((float)t.x, (float)t.y);
+}
+
+// ---------------------------------------------------------------- fine-level kernels
+__global__ void k_rbgs(Level L, Batch bt, int round, int color) {
+  int b = blockIdx.y;
+  if (mg_skip(bt, b, round)) return;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (threadIdx.x == 0) {
+    int n = min((int)blockDim.x, L.N - (int)(blockIdx.x * blockDim.x));
+    atomicAdd(&bt.work[KC_RBGS], (unsigned long long)n);
+  }
+  if (c >= L.N) return;
+  int i = c % L.nx, j = (c / L.nx) % L.ny, k = c / (L.nx * L.ny);
+  if (((i + j + k) & 1) != color) return;
+  rbgs_cell(L, L.u + (size_t)b * L.N, L.f + (size_t)b * L.N, c, tau32(bt, b));
+}
+
+__device__ __forceinline__ void restrict_cell(const Level& Lf, const Level& Lc, const float2* uf, const float2* ff,
+                                              float2* fc, float2* uc, int C, float2 tau) {
+  int I = C % Lc.nx, J = (C / Lc.nx) % Lc.ny, K = C / (Lc.nx * Lc.ny);
+  float2 acc = make_float2(0.f, 0.f);
+  for (int dk = 0; dk < Lf.rz; ++dk)
+    for (int dj = 0; dj < Lf.ry; ++dj)
+      for (int di = 0; di < Lf.rx; ++di) {
+        int c = ((K * Lf.rz + dk) * Lf.ny + (J * Lf.ry + dj)) * Lf.nx + (I * Lf.rx + di);
+        float2 r = resid_cell(Lf, uf, ff, c, tau);
+        acc.x += r.x; acc.y += r.y;
+      }
+  fc[C] = acc;
+  uc[C] = make_float2(0.f, 0.f);
+}
+
+__global__ void k_restrict(Level Lf, Level Lc, Batch bt, int round) {
+  int b = blockIdx.y;
+  if (mg_skip(bt, b, round)) return;
+  int C = blockIdx.x * blockDim.x + threadIdx.x;
+  if (C >= Lc.N) return;
+  restrict_cell(Lf, Lc, Lf.u + (size_t)b * Lf.N, Lf.f + (size_t)b * Lf.N, Lc.f + (size_t)b * Lc.N,
+                Lc.u + (size_t)b * Lc.N, C, tau32(bt, b));
+}
+
+// multilinear interpolation weight setup along one axis
+__device__ __forceinline__ void axis_interp(int i, int r, int nC, int lo_dir, int hi_dir, int& I0, int& I1,
+                                            float& w0, float& w1, float& s1) {
+  I0 = i / r;
+  if (r == 1) { I1 = I0; w0 = 1.f; w1 = 0.f; s1 = 1.f; return; }
+  int o = i - I0 * r;              // 0 or 1
+  int nbI = o ? I0 + 1 : I0 - 1;
+  w0 = 0.75f; w1 = 0.25f; s1 = 1.f;
+  if (nbI < 0) { nbI = I0; s1 = lo_dir ? -1.f : 1.f; }
+  else if (nbI >= nC) { nbI = I0; s1 = hi_dir ? -1.f : 1.f; }
+  I1 = nbI;
+}
+
+__device__ __forceinline__ void prolong_cell(const Level& Lf, const Level& Lc, float2* uf, const float2* uc, int c,
+                                             int dmask) {
+  int i = c % Lf.nx, j = (c / Lf.nx) % Lf.ny, k = c / (Lf.nx * Lf.ny);
+  int I[2], J[2], K[2];
+  float wi[2], wj[2], wk[2], si, sj, sk;
+  axis_interp(i, Lf.rx, Lc.nx, dmask & 1, dmask & 2, I[0], I[1], wi[0], wi[1], si);
+  axis_interp(j, Lf.ry, Lc.ny, dmask & 4, dmask & 8, J[0], J[1], wj[0], wj[1], sj);
+  axis_interp(k, Lf.rz, Lc.nz, dmask & 16, dmask & 32, K[0], K[1], wk[0], wk[1], sk);
+  wi[1] *= si; wj[1] *= sj; wk[1] *= sk;
+  float2 e = make_float2(0.f, 0.f);
+  for (int a = 0; a < 2; ++a) {
+    if (wk[a] == 0.f) continue;
+    for (int bb = 0; bb < 2; ++bb) {
+      if (wj[bb] == 0.f) continue;
+      for (int cc = 0; cc < 2; ++cc) {
+        if (wi[cc] == 0.f) continue;
+        float w = wk[a] * wj[bb] * wi[cc];
+        float2 v = uc[(K[a] * Lc.ny + J[bb]) * Lc.nx + I[cc]];
+        e.x += w * v.x; e.y += w * v.y;
+      }
+    }
+  }
+  float2 u = uf[c];
+  uf[c] = make_float2(u.x + e.x, u.y + e.y);
+}
+
+__global__ void k_prolong(Level Lf, Level Lc, Batch bt, int round, int dmask) {
+  int b = blockIdx.y;
+  if (mg_skip(bt, b, round)) return;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= Lf.N) return;
+  prolong_cell(Lf, Lc, Lf.u + (size_t)b * Lf.N, Lc.u + (size_t)b * Lc.N, c, dmask);
+}
+
+// ---------------------------------------------------------------- coarse levels in one CTA
+// levels[l0 .. nlev-1] are handled here; u at l0 is the current iterate (zero
+// when l0 > 0, set by the restriction above), f at l0 the right-hand side.
+__global__ void __launch_bounds__(1024) k_coarse_vcycle(const Level* __restrict__ levels, int l0, int nlev, Batch bt,
+                                                        int round, int npre, int npost, int dmask, int nc_direct) {
+  int b = blockIdx.x;
+  if (mg_skip(bt, b, round)) return;
+  float2 tau = tau32(bt, b);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  if (tid == 0) atomicAdd(&bt.work[KC_COARSE], (unsigned long long)levels[l0].N);
+  for (int l = l0; l < nlev - 1; ++l) {
+    const Level L = levels[l];
+    float2* u = L.u + (size_t)b * L.N;
+    const float2* f = L.f + (size_t)b * L.N;
+    for (int s = 0; s < npre; ++s)
+      for (int color = 0; color < 2; ++color) {
+        for (int c = tid; c < L.N; c += nth) {
+          int i = c % L.nx, j = (c / L.nx) % L.ny, k = c / (L.nx * L.ny);
+          if (((i + j + k) & 1) == color) rbgs_cell(L, u, f, c, tau);
+        }
+        __syncthreads();
+      }
+    const Level Lc = levels[l + 1];
+    for (int C = tid; C < Lc.N; C += nth)
+      restrict_cell(L, Lc, u, f, Lc.f + (size_t)b * Lc.N, Lc.u + (size_t)b * Lc.N, C, tau);
+    __syncthreads();
+  }
+  {  // coarsest level
+    const Level L = levels[nlev - 1];
+    float2* u = L.u + (size_t)b * L.N;
+    const float2* f = L.f + (size_t)b * L.N;
+    if (nc_direct) {
+      const float2* A = bt.coarse_inv + (size_t)bt.tau_slot[b] * L.N * L.N;
+      for (int r = tid; r < L.N; r += nth) {
+        float2 acc = make_float2(0.f, 0.f);
+        const float2* row = A + (size_t)r * L.N;
+        for (int c = 0; c < L.N; ++c) {
+          float2 a = row[c], x = f[c];
+          acc.x += a.x * x.x - a.y * x.y;
+          acc.y += a.x * x.y + a.y * x.x;
+        }
+        u[r] = acc;
+      }
+      __syncthreads();
+    } else {
+      for (int s = 0; s < kCoarseSweeps; ++s)
+        for (int color = 0; color < 2; ++color) {
+          for (int c = tid; c < L.N; c += nth) {
+            int i = c % L.nx, j = (c / L.nx) % L.ny, k = c / (L.nx * L.ny);
+            if (((i + j + k) & 1) == color) rbgs_cell(L, u, f, c, tau);
+          }
+          __syncthreads();
+        }
+    }
+  }
+  for (int l = nlev - 2; l >= l0; --l) {
+    const Level L = levels[l];
+    const Level Lc = levels[l + 1];
+    float2* u = L.u + (size_t)b * L.N;
+    const float2* f = L.f + (size_t)b * L.N;
+    for (int c = tid; c < L.N; c += nth) prolong_cell(L, Lc, u, Lc.u + (size_t)b * Lc.N, c, dmask);
+    __syncthreads();
+    for (int s = 0; s < npost; ++s)
+      for (int color = 1; color >= 0; --color) {
+        for (int c = tid; c < L.N; c += nth) {
+          int i = c % L.nx, j = (c / L.nx) % L.ny, k = c / (L.nx * L.ny);
+          if (((i + j + k) & 1) == color) rbgs_cell(L, u, f, c, tau);
+        }
+        __syncthreads();
+      }
+  }
+}
+
+// ---------------------------------------------------------------- host launcher
+int launch_vcycle(const MGHost& mg, const Batch& bt, int round, cudaStream_t st, int* nlaunch, Prof* pf) {
+  const int nb = bt.nb;
+  const int T = 256;
+  for (int l = 0; l < mg.lc; ++l) {
+    const Level& L = mg.h_levels[l];
+    dim3 g((L.N + T - 1) / T, nb);
+    for (int s = 0; s < mg.npre; ++s)
+      for (int color = 0; color < 2; ++color) {
+        prof_begin(pf, KC_RBGS, st);
+        k_rbgs<<<g, T, 0, st>>>(L, bt, round, color);
+        prof_end(pf, KC_RBGS, st);
+        ++*nlaunch;
+      }
+    const Level& Lc = mg.h_levels[l + 1];
+    dim3 gc((Lc.N + T - 1) / T, nb);
+    prof_begin(pf, KC_RESTRICT, st);
+    k_restrict<<<gc, T, 0, st>>>(L, Lc, bt, round); ++*nlaunch;
+    prof_end(pf, KC_RESTRICT, st);
+  }
+  int thr = mg.h_levels[mg.lc].N >= 1024 ? 1024 : ((mg.h_levels[mg.lc].N + 31) / 32) * 32;
+  if (thr < 64) thr = 64;
+  prof_begin(pf, KC_COARSE, st);
+  k_coarse_vcycle<<<nb, thr, 0, st>>>(mg.d_levels, mg.lc, mg.nlev, bt, round, mg.npre, mg.npost, mg.dmask,
+                                      mg.coarse_direct);
+  prof_end(pf, KC_COARSE, st);
+  ++*nlaunch;
+  for (int l = mg.lc - 1; l >= 0; --l) {
+    const Level& L = mg.h_levels[l];
+    const Level& Lc = mg.h_levels[l + 1];
+    dim3 g((L.N + T - 1) / T, nb);
+    prof_begin(pf, KC_PROLONG, st);
+    k_prolong<<<g, T, 0, st>>>(L, Lc, bt, round, mg.dmask); ++*nlaunch;
+    prof_end(pf, KC_PROLONG, st);
+    for (int s = 0; s < mg.npost; ++s)
+      for (int color = 1; color >= 0; --color) {
+        prof_begin(pf, KC_RBGS, st);
+        k_rbgs<<<g, T, 0, st>>>(L, bt, round, color);
+        prof_end(pf, KC_RBGS, st);
+        ++*nlaunch;
+      }
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+}  // namespace lt

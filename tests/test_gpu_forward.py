@@ -1,0 +1,165 @@
+"""GPU parity of the forward path (C-ABI -> CUDA kernels) against the FP64
+oracle: contour + direct LU (O1) and the eigen-expansion closed form (O2).
+
+Bar (floating point): relative L2 error <= 1e-8 over all h[s][r][t].  The
+per-shift relative residual tolerance is set tighter than that (1e-11)
+because the shifted systems amplify residuals into the solution."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import closed_form, direct
+
+pytestmark = pytest.mark.gpu
+
+TOL_H = 1e-8
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def Engine():
+    import __graft_entry__ as G
+    G.build()
+    from paper_1409_2556_gb300 import Engine
+    return Engine
+
+
+def _solve(Engine, prob, **kw):
+    eng = Engine(0)
+    eng.load_problem(prob, **kw)
+    h = eng.forward(prob.times)
+    st = eng.last_stats
+    eng.close()
+    return h, st
+
+
+def test_homogeneous_box_vs_closed_form(Engine):
+    p = W.config1(n=16, tol=1e-11)
+    h, st = _solve(Engine, p)
+    assert _rel(h, closed_form.heads(p)) < 5e-8      # includes the N_z = 16 quadrature error
+    assert _rel(h, direct.forward(p)) < TOL_H
+    assert st["n_converged"] == st["n_shift_solves"] == 64
+
+
+def test_config1_full_size_vs_closed_form(Engine):
+    """64x64 homogeneous box, 16 nodes, 8 times, single preconditioner shift."""
+    p = W.config1()
+    h, st = _solve(Engine, p, tau_policy=0, tol=1e-11)
+    ref = closed_form.heads(p)
+    for it in range(len(p.times)):
+        assert _rel(h[:, :, it], ref[:, :, it]) < 1e-8
+    assert st["max_true_residual"] <= 1e-11
+
+
+@pytest.mark.parametrize("shape,groups", [((48, 40, 1), 2), ((36, 28, 1), 1), ((64, 32, 1), 3)])
+def test_heterogeneous_2d_ragged(Engine, shape, groups):
+    nx, ny, nz = shape
+    p = W.random_problem(nx, ny, nz, variance=1.5, seed=nx, ns=3, nr=4, nt=5, Nz=16, tol=1e-11, groups=groups)
+    h, st = _solve(Engine, p)
+    assert _rel(h, direct.forward(p)) < TOL_H
+    assert st["n_converged"] == st["n_shift_solves"]
+    assert st["max_true_residual"] <= 1e-11
+
+
+def test_3d_neumann_top_bottom(Engine):
+    p = W.random_problem(16, 12, 8, variance=1.0, seed=5, ns=2, nr=3, nt=3, Nz=16, tol=1e-12,
+                         ss_variance=0.25)
+    h, st = _solve(Engine, p)
+    assert _rel(h, direct.forward(p)) < TOL_H
+
+
+@pytest.mark.parametrize("policy", [0, 1])
+def test_outer_iterations_match_algorithm1_with_exact_solves(Engine, policy):
+    """With preconditioner solves converged to 1e-13 the GPU basis follows
+    Algorithm 1 with exact LU solves: same tau sequence (projected to
+    Re >= 0), same outer iteration count (within 2)."""
+    from oracle import contour, fgmres_sh, fv
+    p = W.random_problem(64, 64, 1, variance=1.6, seed=9, ns=1, nr=2, nt=1, Nz=32, tol=1e-10)
+    p.times = np.array([300.0])
+    _, st = _solve(Engine, p, tau_policy=policy, tau_project=1, inner_tol=1e-13, inner_rounds=6)
+    K, m = fv.assemble(p)
+    z, _ = contour.nodes_weights(300.0, 32)
+    taus = contour.tau_schedule(z, "single" if policy == 0 else "flexible", 300)
+    taus = np.maximum(taus.real, 0.0) + 1j * taus.imag
+    _, it, conv = fgmres_sh.solve(K, m, fv.rhs(p, 0) / p.Q[0], z, taus, tol=1e-10, maxit=300)
+    assert abs(st["outer_iters_max"] - it) <= 2, (st["outer_iters_max"], it)
+
+
+def test_fields_match_oracle(Engine):
+    p = W.random_problem(24, 20, 1, variance=1.0, seed=4, ns=2, nr=2, nt=2, Nz=16, tol=1e-11)
+    eng = Engine(0)
+    eng.load_problem(p)
+    phi = eng.forward_fields(p.times)
+    eng.close()
+    _, F = direct.forward(p, return_fields=True)
+    assert _rel(phi, F) < TOL_H
+
+
+def test_device_output_and_stream(Engine):
+    import torch
+    p = W.random_problem(32, 32, 1, variance=1.0, seed=3, ns=2, nr=3, nt=2, Nz=16, tol=1e-11)
+    st = torch.cuda.Stream()
+    eng = Engine(0, stream=st)
+    eng.load_problem(p)
+    out = torch.zeros((2, 3, 2), dtype=torch.float64, device="cuda")
+    eng.forward(p.times, out=out)
+    st.synchronize()
+    assert _rel(out.cpu().numpy(), direct.forward(p)) < TOL_H
+    eng.close()
+
+
+def test_errors_are_status_codes(Engine):
+    from paper_1409_2556_gb300 import LtError
+    p = W.random_problem(16, 16, 1, ns=1, nr=1, nt=1)
+    eng = Engine(0)
+    with pytest.raises(LtError) as e:
+        eng.setup_grid(-p.kappa, p.Ss, p.dx, p.dy, p.dz, p.bc)
+    assert e.value.code == -1
+    bad = p.kappa.copy(); bad.ravel()[3] = np.nan
+    with pytest.raises(LtError):
+        eng.setup_grid(bad, p.Ss, p.dx, p.dy, p.dz, p.bc)
+    with pytest.raises(LtError) as e:
+        eng.forward([10.0])               # before setup_grid
+    assert e.value.code == -6
+    eng.setup_grid(p.kappa, p.Ss, p.dx, p.dy, p.dz, p.bc)
+    with pytest.raises(LtError):
+        eng.set_sources([16 * 16], [1.0])  # out of range
+    with pytest.raises(LtError):
+        eng.setup_grid(p.kappa, p.Ss, p.dx, p.dy, p.dz, (1, 1, 1, 1, 1, 1))   # no Dirichlet face
+    eng.set_sources(p.src_cells, p.Q)
+    eng.set_receivers(p.rec_cells)
+    with pytest.raises(LtError):
+        eng.forward([0.0])
+    with pytest.raises(LtError):
+        eng.set_options(Nz=7)
+    eng.close()
+
+
+def test_not_converged_is_reported_not_fatal(Engine):
+    p = W.random_problem(32, 32, 1, variance=1.0, seed=2, ns=1, nr=2, nt=1, Nz=16)
+    eng = Engine(0)
+    eng.load_problem(p, maxit=2)
+    from paper_1409_2556_gb300 import LtError
+    with pytest.raises(LtError) as e:
+        eng.forward(p.times)
+    assert e.value.code == -4
+    h = eng.forward(p.times, allow_unconverged=True)
+    assert np.all(np.isfinite(h))
+    assert eng.last_stats["n_converged"] < eng.last_stats["n_shift_solves"]
+    eng.close()
+
+
+def test_repeated_calls_are_identical_and_sizes_change(Engine):
+    p = W.random_problem(32, 24, 1, variance=1.0, seed=8, ns=2, nr=2, nt=3, Nz=16, tol=1e-11)
+    eng = Engine(0)
+    eng.load_problem(p)
+    h1 = eng.forward(p.times)
+    h2 = eng.forward(p.times)
+    assert np.array_equal(h1, h2) or _rel(h1, h2) < 1e-12
+    q = W.random_problem(40, 40, 1, variance=1.0, seed=9, ns=3, nr=2, nt=2, Nz=16, tol=1e-11)
+    eng.load_problem(q)
+    assert _rel(eng.forward(q.times), direct.forward(q)) < TOL_H
+    eng.close()
