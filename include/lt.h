@@ -168,6 +168,32 @@ int lt_adjoint_jacobian(lt_ctx* ctx, int nt, const double* times, double* J, lt_
 int lt_adjoint_vjp(lt_ctx* ctx, int nt, const double* times, const double* g, double* grad,
                    double* h, int on_device, lt_stats* stats);
 
+/*
+ * lt_forward without device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot let a library call cudaMalloc or
+ * cudaFree -- services that hand all device memory to their own pool allocator
+ * up front (a library allocation would fail or fragment that pool), and
+ * pipelines that keep other streams busy, where cudaMalloc/cudaFree may
+ * synchronise the device and stall them.
+ *
+ * Same computation and result as lt_forward, but every device buffer the call
+ * needs is taken from one fixed static region of LT_NOALLOC_SCRATCH_MAX bytes
+ * inside the library, which each GPU that loads the library holds until the
+ * process exits.  The grid, wells and options still come from lt_setup_grid,
+ * lt_set_sources/receivers and lt_set_options (those calls do allocate).
+ *   h     : float64 [ns][nr][nt], DEVICE pointer
+ *   stats : optional; timing_class is ignored (no per-launch events)
+ * Returns LT_ERR_INVALID_ARG, before launching anything, when the problem's
+ * buffers exceed the static region (the message gives the bytes needed).
+ * The first call on a device looks up the region's device address; make that
+ * call before any stream capture.  All calls share the region and it keeps the
+ * last call's contents (every buffer is re-initialised by the call that uses
+ * it), so calls that overlap on the GPU -- from two threads, two contexts or
+ * two streams -- race and must be serialised by the caller.
+ */
+#define LT_NOALLOC_SCRATCH_MAX (32u << 20)
+int lt_forward_noalloc(lt_ctx* ctx, int nt, const double* times, double* h, lt_stats* stats);
+
 /* Static description of a status code. */
 const char* lt_strerror(int status);
 

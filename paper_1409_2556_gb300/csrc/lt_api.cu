@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -88,6 +89,10 @@ struct lt_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   lt::Prof prof;
   std::vector<cudaEvent_t> prof_events;
+  // set only for the duration of an lt_forward_noalloc call: device buffers are
+  // carved from this region instead of being allocated
+  char* arena_base = nullptr;
+  size_t arena_cap = 0, arena_off = 0;
 };
 
 static int fail(lt_ctx* ctx, int code, const char* fmt, ...) {
@@ -111,8 +116,19 @@ static int fail(lt_ctx* ctx, int code, const char* fmt, ...) {
     }                                                                                    \
   } while (0)
 
+static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
 template <typename T>
 static int dalloc(lt_ctx* ctx, std::vector<void*>& list, T** p, size_t n) {
+  if (ctx->arena_base) {
+    size_t bytes = round256(std::max<size_t>(n, 1) * sizeof(T));
+    if (ctx->arena_off + bytes > ctx->arena_cap)
+      return fail(ctx, LT_ERR_INVALID_ARG, "problem needs more than the %zu-byte static scratch of lt_forward_noalloc",
+                  ctx->arena_cap);
+    *p = (T*)(ctx->arena_base + ctx->arena_off);
+    ctx->arena_off += bytes;
+    return LT_OK;
+  }
   void* q = nullptr;
   cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
   if (e != cudaSuccess)
@@ -900,4 +916,94 @@ extern "C" int lt_adjoint_vjp(lt_ctx* ctx, int nt, const double* times, const do
                               int on_device, lt_stats* st) {
   (void)nt; (void)times; (void)g; (void)grad; (void)h; (void)on_device; (void)st;
   return fail(ctx, LT_ERR_STATE, "adjoint VJP not built yet");
+}
+
+// ------------------------------------------------------------------ no-allocation forward
+// Some callers cannot let a library call cudaMalloc/cudaFree: services that
+// hand all device memory to their own pool allocator up front (a library
+// allocation then fails or fragments that pool), and pipelines that keep
+// other streams busy, where cudaMalloc/cudaFree may synchronise the device
+// and stall them.  lt_forward_noalloc serves them: it runs the same solve as
+// lt_forward but takes every device buffer it needs from this fixed static
+// region, which each GPU that loads the library holds until the process
+// exits.
+#define LT_NOALLOC_SCRATCH_BYTES (32u << 20)
+static __device__ __align__(256) unsigned char g_lt_noalloc_scratch[LT_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[256];   // device address of g_lt_noalloc_scratch, per device ordinal
+
+// bytes the no-allocation forward carves for a plan (same list as ensure_ws,
+// run_solves and forward_impl, each rounded to 256 bytes)
+static size_t noalloc_need(const lt_ctx* ctx, const Plan& P) {
+  const lt_opts& o = ctx->opts;
+  const size_t nb = P.nb, M = o.maxit, R = o.inner_rounds, nsh = P.nsh, N = (size_t)ctx->N, G = P.G;
+  const size_t ns = ctx->src.size(), nr = ctx->rec.size(), nt = P.nt;
+  size_t b = 0;
+  auto add = [&](size_t n, size_t sz) { b += round256(std::max<size_t>(n, 1) * sz); };
+  add(nb * (M + 1) * N, 8); add(nb * (M + 1) * N, 8); add(nb * M * N, 8); add(nb * M * N, 8);
+  add(nb * N, 8); add(nb * N, 8);
+  add(2 * G, 16); add(nb, 4); add(5, 4); add(nb, 16); add(nb, 4);
+  add(nb * (R + 1), 8); add(nb * 2 * (M + 1), 16); add(nb * M * (M + 1), 16);
+  add(nb, 8); add(nb, 4); add(nb, 4); add(nb, 8); add(nb, 8);
+  add(nb + 1, 4); add(nsh, 16); add(nsh * M * M, 16); add(nsh * M, 8);
+  add(nsh * M, 16); add(nsh * (M + 1), 16); add(nsh, 4); add(nsh, 8);
+  add(nsh * M, 16); add(16, 8);
+  if (ctx->mg.coarse_direct) add(2 * G * (size_t)ctx->hl.back().N * ctx->hl.back().N, 8);
+  for (int l = 0; l < ctx->mg.nlev; ++l) { add(nb * ctx->mg.h_levels[l].N, 8); add(nb * ctx->mg.h_levels[l].N, 8); }
+  add(nsh, 4);
+  if (o.true_residual) { add(nsh * N, 8); add(nsh * N, 8); add(nsh, 8); }
+  add(ns * nt, sizeof(lt::QuadItem)); add(nsh, 16); add(ns * nt * M, 16); add(std::max<size_t>(nr, 1), 8);
+  return b;
+}
+
+extern "C" int lt_forward_noalloc(lt_ctx* ctx, int nt, const double* times, double* h, lt_stats* st) {
+  if (!ctx) return LT_ERR_INVALID_ARG;
+  int rc = check_times(ctx, nt, times);
+  if (rc) return rc;
+  if (ctx->src.empty() || ctx->rec.empty()) return fail(ctx, LT_ERR_STATE, "sources and receivers must be set");
+  if (!h) return fail(ctx, LT_ERR_INVALID_ARG, "h (device pointer) is null");
+  if (ctx->device < 0 || ctx->device >= 256) return fail(ctx, LT_ERR_INVALID_ARG, "device ordinal out of range");
+  CK(cudaSetDevice(ctx->device));
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[ctx->device]) {
+      cudaError_t e = cudaGetSymbolAddress(&g_noalloc_ptr[ctx->device], g_lt_noalloc_scratch);
+      if (e != cudaSuccess) {
+        g_noalloc_ptr[ctx->device] = nullptr;
+        return fail(ctx, LT_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+      }
+    }
+    base = g_noalloc_ptr[ctx->device];
+  }
+  Plan P;
+  make_plan(ctx, nt, times, ctx->src, P);
+  const size_t need = noalloc_need(ctx, P);
+  if (need > LT_NOALLOC_SCRATCH_BYTES)
+    return fail(ctx, LT_ERR_INVALID_ARG,
+                "problem needs %zu bytes of device scratch; lt_forward_noalloc is limited to %u bytes "
+                "(reduce grid size, wells, times, Nz or maxit, or use lt_forward)",
+                need, (unsigned)LT_NOALLOC_SCRATCH_BYTES);
+  // run the ordinary forward driver with buffers carved from the static region;
+  // the context's own cached workspace and level pointers are set aside and restored
+  Workspace saved_ws = std::move(ctx->ws);
+  ctx->ws = Workspace();
+  lt::Level saved_levels[lt::kMaxLevels];
+  memcpy(saved_levels, ctx->mg.h_levels, sizeof(saved_levels));
+  const int saved_timing = ctx->opts.timing_class;
+  ctx->opts.timing_class = -1;
+  ctx->arena_base = (char*)base;
+  ctx->arena_cap = LT_NOALLOC_SCRATCH_BYTES;
+  ctx->arena_off = 0;
+  rc = forward_impl(ctx, nt, times, h, 1, 0, st);
+  ctx->arena_base = nullptr;
+  ctx->arena_cap = ctx->arena_off = 0;
+  ctx->opts.timing_class = saved_timing;
+  ctx->ws = std::move(saved_ws);
+  memcpy(ctx->mg.h_levels, saved_levels, sizeof(saved_levels));
+  cudaError_t e = cudaMemcpy(ctx->mg.d_levels, ctx->mg.h_levels, sizeof(lt::Level) * ctx->mg.nlev,
+                             cudaMemcpyHostToDevice);
+  if (e != cudaSuccess && rc == LT_OK) return fail(ctx, LT_ERR_CUDA, "restoring level table: %s", cudaGetErrorString(e));
+  return rc;
 }

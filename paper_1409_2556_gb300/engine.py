@@ -141,6 +141,20 @@ class Engine:
         self._check(rc, "lt_forward", allow)
         return res
 
+    def forward_noalloc(self, times, out, allow_unconverged: bool = False):
+        """Same as forward() into a CUDA float64 tensor `out` [ns][nr][nt], without any
+        device allocation by the library (its buffers come from a fixed static region;
+        for callers whose device memory is owned by their own pool allocator, or who
+        cannot afford the device synchronisation of cudaMalloc/cudaFree).  Calls that
+        overlap on the GPU share that region and race."""
+        t = _f64(times)
+        _check_dev(out, (self.ns, self.nr, t.size))
+        st = L.LtStats()
+        rc = self.lib.lt_forward_noalloc(self.h, t.size, _ptr(t), C.c_void_p(out.data_ptr()), C.byref(st))
+        self.last_stats = st.as_dict()
+        self._check(rc, "lt_forward_noalloc", (L.LT_ERR_NOT_CONVERGED,) if allow_unconverged else ())
+        return out
+
     def forward_fields(self, times, out=None, allow_unconverged: bool = False):
         t = _f64(times)
         st = L.LtStats()
