@@ -634,17 +634,19 @@ __global__ void k_true_res(Batch bt, FineExact fe, const int* sh_basis, const fl
   if (threadIdx.x == 0) atomicAdd(&res2[sh], (double)acc[0]);
 }
 
-void launch_true_residual_map(const Batch& bt, const FineExact& fe, const int* sh_basis, float2* X_hi, float2* X_lo,
-                              double* res2, cudaStream_t st, int* nlaunch, Prof* pf) {
+void launch_xk(const Batch& bt, float2* X_hi, float2* X_lo, cudaStream_t st, Prof* pf) {
   dim3 g((unsigned)((bt.N + 255) / 256), bt.nb);
   prof_begin(pf, KC_XK, st);
   k_xk<<<g, 256, 0, st>>>(bt, X_hi, X_lo);
   prof_end(pf, KC_XK, st);
+}
+
+void launch_true_res(const Batch& bt, const FineExact& fe, const int* sh_basis, const float2* X_hi,
+                     const float2* X_lo, double* res2, cudaStream_t st, Prof* pf) {
   dim3 g2((unsigned)((bt.N + 255) / 256), bt.nsh);
   prof_begin(pf, KC_TRUE_RES, st);
   k_true_res<<<g2, 256, 0, st>>>(bt, fe, sh_basis, X_hi, X_lo, res2);
   prof_end(pf, KC_TRUE_RES, st);
-  *nlaunch += 2;
 }
 
 }  // namespace lt

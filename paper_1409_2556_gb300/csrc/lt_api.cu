@@ -82,6 +82,8 @@ struct lt_ctx {
   lt::MGHost mg{};
   std::vector<void*> grid_allocs;
   lt::FineExact fe{};
+  // float64 fine-level geometry for the sensitivity assembly
+  double *g_Te = nullptr, *g_Tn = nullptr, *g_Tu = nullptr, *g_kap = nullptr, *g_Bd = nullptr, *g_m = nullptr;
   // wells
   std::vector<int64_t> src, rec;
   std::vector<double> Q;
@@ -458,6 +460,20 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
   if ((rc = upload_df(ctx, ctx->grid_allocs, &fe.Tu_hi, &fe.Tu_lo, L0.Tu))) return rc;
   if ((rc = upload_df(ctx, ctx->grid_allocs, &fe.D_hi, &fe.D_lo, ctx->hl[0].D))) return rc;
   if ((rc = upload_df(ctx, ctx->grid_allocs, &fe.m_hi, &fe.m_lo, L0.m))) return rc;
+  {
+    std::vector<double> Bd(N, 0.0);
+    for (int64_t c = 0; c < N; ++c)
+      for (int d = 0; d < 6; ++d) Bd[c] += bfs[0].b[d][c];
+    auto up = [&](double** dst, const std::vector<double>& v) -> int {
+      int r = dalloc(ctx, ctx->grid_allocs, dst, v.size());
+      if (r) return r;
+      CK(cudaMemcpy(*dst, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice));
+      return LT_OK;
+    };
+    if ((rc = up(&ctx->g_Te, L0.Te)) || (rc = up(&ctx->g_Tn, L0.Tn)) || (rc = up(&ctx->g_Tu, L0.Tu)) ||
+        (rc = up(&ctx->g_kap, ctx->kappa)) || (rc = up(&ctx->g_Bd, Bd)) || (rc = up(&ctx->g_m, L0.m)))
+      return rc;
+  }
   CK(cudaMalloc(&mg.d_levels, sizeof(lt::Level) * lt::kMaxLevels));
   ctx->have_grid = true;
   ctx->src.clear(); ctx->Q.clear(); ctx->rec.clear();
@@ -661,7 +677,8 @@ static int ensure_ws(lt_ctx* ctx, const Plan& P) {
 }
 
 // Runs the batched flexible shifted Krylov solves of a plan; leaves Y, U in the workspace.
-static int run_solves(lt_ctx* ctx, const Plan& P, std::vector<double>& true_res, lt_stats* st, int* nl) {
+static int run_solves(lt_ctx* ctx, const Plan& P, std::vector<double>& true_res, lt_stats* st, int* nl,
+                      bool need_x = false) {
   const lt_opts& o = ctx->opts;
   int rc = ensure_ws(ctx, P);
   if (rc) return rc;
@@ -754,7 +771,7 @@ static int run_solves(lt_ctx* ctx, const Plan& P, std::vector<double>& true_res,
   lt::launch_backsolve_map(bt, d_shb, s);
   ++*nl;
   true_res.assign(P.nsh, -1.0);
-  if (o.true_residual) {
+  if (o.true_residual || need_x) {
     Workspace& ws = ctx->ws;
     size_t need = (size_t)P.nsh * ctx->N;
     if (ws.x_elems < need) {
@@ -763,11 +780,16 @@ static int run_solves(lt_ctx* ctx, const Plan& P, std::vector<double>& true_res,
       if ((rc = dalloc(ctx, ws.allocs, &ws.X_lo, need))) { free_list(tmp); return rc; }
       ws.x_elems = need;
     }
-    double* d_res2 = nullptr;
-    if ((rc = dalloc(ctx, tmp, &d_res2, P.nsh))) { free_list(tmp); return rc; }
-    CK(cudaMemsetAsync(d_res2, 0, P.nsh * sizeof(double), s));
-    lt::launch_true_residual_map(bt, ctx->fe, d_shb, ws.X_hi, ws.X_lo, d_res2, s, nl, pf);
-    CK(cudaMemcpyAsync(true_res.data(), d_res2, P.nsh * sizeof(double), cudaMemcpyDeviceToHost, s));
+    lt::launch_xk(bt, ws.X_hi, ws.X_lo, s, pf);
+    ++*nl;
+    if (o.true_residual) {
+      double* d_res2 = nullptr;
+      if ((rc = dalloc(ctx, tmp, &d_res2, P.nsh))) { free_list(tmp); return rc; }
+      CK(cudaMemsetAsync(d_res2, 0, P.nsh * sizeof(double), s));
+      lt::launch_true_res(bt, ctx->fe, d_shb, ws.X_hi, ws.X_lo, d_res2, s, pf);
+      ++*nl;
+      CK(cudaMemcpyAsync(true_res.data(), d_res2, P.nsh * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
   }
   // stats
   std::vector<int> nit(P.nb), conv(P.nsh);
@@ -907,15 +929,132 @@ extern "C" int lt_forward_fields(lt_ctx* ctx, int nt, const double* times, doubl
   return forward_impl(ctx, nt, times, phi, on_device, 1, st);
 }
 
+// Adjoint path (Sec. 5.2): one batch of bases for the sources and the
+// receivers, solutions per shift, then the sensitivity assembly (mode 0: J,
+// mode 1: vector-Jacobian product).  h (optional) = forward measurements.
+static int adjoint_impl(lt_ctx* ctx, int nt, const double* times, double* J, const double* g, double* grad,
+                        double* h, int on_device, int mode, lt_stats* st) {
+  if (!ctx) return LT_ERR_INVALID_ARG;
+  int rc = check_times(ctx, nt, times);
+  if (rc) return rc;
+  if (ctx->src.empty() || ctx->rec.empty()) return fail(ctx, LT_ERR_STATE, "sources and receivers must be set");
+  if (mode == 0 && !J) return fail(ctx, LT_ERR_INVALID_ARG, "J is null");
+  if (mode == 1 && (!g || !grad)) return fail(ctx, LT_ERR_INVALID_ARG, "g and grad are required");
+  CK(cudaSetDevice(ctx->device));
+  stats_reset(st, ctx->opts.true_residual);
+  const int ns = (int)ctx->src.size(), nr = (int)ctx->rec.size();
+  std::vector<int64_t> rhs(ctx->src);
+  rhs.insert(rhs.end(), ctx->rec.begin(), ctx->rec.end());
+  Plan P;
+  make_plan(ctx, nt, times, rhs, P);
+  int nl = 0;
+  CK(cudaEventRecord(ctx->ev0, ctx->stream));
+  std::vector<double> tres;
+  rc = run_solves(ctx, P, tres, st, &nl, true);
+  if (rc) return rc;
+  cudaStream_t s = ctx->stream;
+  const int Nk = P.Nk;
+  std::vector<int> sh_src(nt * ns), sh_rec(nt * nr);
+  std::vector<double2> omega((size_t)nt * ns * Nk), zk((size_t)nt * Nk);
+  for (int t = 0; t < nt; ++t) {
+    for (int si = 0; si < ns; ++si) {
+      sh_src[t * ns + si] = shift_of(P, si * P.G + P.tgroup[t], t);
+      for (int k = 0; k < Nk; ++k) {
+        cplx v = P.w[t][k] * ctx->Q[si] / P.z[t][k];
+        omega[((size_t)t * ns + si) * Nk + k] = make_double2(v.real(), v.imag());
+      }
+    }
+    for (int r = 0; r < nr; ++r) sh_rec[t * nr + r] = shift_of(P, (ns + r) * P.G + P.tgroup[t], t);
+    for (int k = 0; k < Nk; ++k) zk[t * Nk + k] = make_double2(P.z[t][k].real(), P.z[t][k].imag());
+  }
+  std::vector<void*> tmp;
+  int *d_ss, *d_sr;
+  double2 *d_om, *d_zk;
+  double *d_g = nullptr, *d_grad = nullptr, *d_h = nullptr;
+  if ((rc = dalloc(ctx, tmp, &d_ss, sh_src.size())) || (rc = dalloc(ctx, tmp, &d_sr, sh_rec.size())) ||
+      (rc = dalloc(ctx, tmp, &d_om, omega.size())) || (rc = dalloc(ctx, tmp, &d_zk, zk.size()))) {
+    free_list(tmp);
+    return rc;
+  }
+  CK(cudaMemcpyAsync(d_ss, sh_src.data(), sh_src.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_sr, sh_rec.data(), sh_rec.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_om, omega.data(), omega.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_zk, zk.data(), zk.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+  const size_t nrow = (size_t)ns * nr * nt;
+  if (mode == 1) {
+    if (on_device) {
+      d_g = const_cast<double*>(g);
+      d_grad = grad;
+    } else {
+      if ((rc = dalloc(ctx, tmp, &d_g, nrow)) || (rc = dalloc(ctx, tmp, &d_grad, 2 * (size_t)ctx->N))) {
+        free_list(tmp);
+        return rc;
+      }
+      CK(cudaMemcpyAsync(d_g, g, nrow * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaMemsetAsync(d_grad, 0, 2 * (size_t)ctx->N * sizeof(double), s));
+  }
+  lt::SensLaunch L;
+  L.ns = ns; L.nr = nr; L.nt = nt; L.Nk = Nk; L.N = ctx->N;
+  L.nx = ctx->nx; L.ny = ctx->ny; L.nz = ctx->nz;
+  L.sh_src = d_ss; L.sh_rec = d_sr; L.omega = d_om; L.zk = d_zk;
+  L.X_hi = ctx->ws.X_hi; L.X_lo = ctx->ws.X_lo;
+  L.Te = ctx->g_Te; L.Tn = ctx->g_Tn; L.Tu = ctx->g_Tu; L.kap = ctx->g_kap; L.Bd = ctx->g_Bd; L.m = ctx->g_m;
+  L.J = J; L.g = d_g; L.grad = d_grad; L.mode = mode;
+  if (lt::launch_sens2(L, s)) {
+    free_list(tmp);
+    return fail(ctx, LT_ERR_INVALID_ARG, "sensitivity launch failed (too many sources/receivers for shared memory?)");
+  }
+  ++nl;
+  if (h) {   // forward measurements from the source bases
+    std::vector<lt::QuadItem> items(ns * nt);
+    std::vector<double2> wq(P.nsh, make_double2(0.0, 0.0));
+    for (int si = 0; si < ns; ++si)
+      for (int t = 0; t < nt; ++t) {
+        int b = si * P.G + P.tgroup[t];
+        int sh0 = shift_of(P, b, t);
+        items[si * nt + t] = {b, sh0, Nk};
+        for (int k = 0; k < Nk; ++k) wq[sh0 + k] = omega[((size_t)t * ns + si) * Nk + k];
+      }
+    lt::QuadItem* d_items;
+    double2 *d_wq, *d_C;
+    int64_t* d_rc;
+    if ((rc = dalloc(ctx, tmp, &d_items, items.size())) || (rc = dalloc(ctx, tmp, &d_wq, wq.size())) ||
+        (rc = dalloc(ctx, tmp, &d_C, items.size() * ctx->opts.maxit)) || (rc = dalloc(ctx, tmp, &d_rc, nr))) {
+      free_list(tmp);
+      return rc;
+    }
+    if (on_device) d_h = h;
+    else if ((rc = dalloc(ctx, tmp, &d_h, nrow))) { free_list(tmp); return rc; }
+    CK(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(lt::QuadItem), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_wq, wq.data(), wq.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_rc, ctx->rec.data(), nr * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    lt::launch_quad_coef(ctx->ws.bt, d_items, (int)items.size(), d_wq, d_C, s);
+    lt::launch_measure(ctx->ws.bt, d_items, d_C, ns, nr, nt, d_rc, d_h, s);
+    nl += 2;
+  }
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(ctx->ev1, s));
+  if (mode == 1 && !on_device) CK(cudaMemcpyAsync(grad, d_grad, 2 * (size_t)ctx->N * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (h && !on_device) CK(cudaMemcpyAsync(h, d_h, nrow * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  free_list(tmp);
+  if (st) {
+    cudaEventElapsedTime(&st->ms_total, ctx->ev0, ctx->ev1);
+    st->kernel_launches = nl;
+  }
+  for (double r : tres)
+    if (ctx->opts.true_residual && !(r <= ctx->opts.tol)) return fail(ctx, LT_ERR_NOT_CONVERGED, "some shifted systems did not reach tol");
+  return LT_OK;
+}
+
 extern "C" int lt_adjoint_jacobian(lt_ctx* ctx, int nt, const double* times, double* J, lt_stats* st) {
-  (void)nt; (void)times; (void)J; (void)st;
-  return fail(ctx, LT_ERR_STATE, "adjoint Jacobian not built yet");
+  return adjoint_impl(ctx, nt, times, J, nullptr, nullptr, nullptr, 1, 0, st);
 }
 
 extern "C" int lt_adjoint_vjp(lt_ctx* ctx, int nt, const double* times, const double* g, double* grad, double* h,
                               int on_device, lt_stats* st) {
-  (void)nt; (void)times; (void)g; (void)grad; (void)h; (void)on_device; (void)st;
-  return fail(ctx, LT_ERR_STATE, "adjoint VJP not built yet");
+  return adjoint_impl(ctx, nt, times, nullptr, g, grad, h, on_device, 1, st);
 }
 
 // ------------------------------------------------------------------ no-allocation forward

@@ -40,26 +40,26 @@ void launch_quad_coef(const Batch& bt, const QuadItem* items, int nitems, const 
 void launch_measure(const Batch& bt, const QuadItem* items, const double2* C, int ns, int nr, int nt,
                     const int64_t* rcells, double* h, cudaStream_t st);
 void launch_fields(const Batch& bt, const QuadItem* items, const double2* C, int nitems, double* phi, cudaStream_t st);
-// true residual of every shift: res2[sh] = ||e_cell - (K + z M) x_sh||^2, x_sh = U y_sh
-void launch_true_residual_map(const Batch& bt, const FineExact& fe, const int* sh_basis, float2* X_hi,
-                              float2* X_lo, double* res2, cudaStream_t st, int* nlaunch, Prof* pf);
 
 // -------- adjoint.cu
-struct SensItem {             // one Jacobian row group (s, r, t)
-  int bs, br;                 // forward basis (source) and adjoint basis (receiver)
-  int shs, shr;               // first shift of the time in each basis
-  int nk;                     // shifts of the time
-  int row;                    // output row index ((s*nr + r)*nt + t)
-  double Qs;                  // source rate
+struct SensLaunch {
+  int ns, nr, nt, Nk;
+  int64_t N;
+  int nx, ny, nz;
+  const int* sh_src;          // [nt][ns] first shift of (source s, time t)
+  const int* sh_rec;          // [nt][nr] first shift of (receiver r, time t)
+  const double2* omega;       // [nt][ns][Nk] w_k Q_s / z_k
+  const double2* zk;          // [nt][Nk]
+  const float2 *X_hi, *X_lo;  // [nsh][N] solutions per shift
+  const double *Te, *Tn, *Tu, *kap, *Bd, *m;   // float64 fine-level geometry
+  double* J;                  // mode 0: [ns][nr][nt][2][N]
+  const double* g;            // mode 1: [ns][nr][nt]
+  double* grad;               // mode 1: [2][N] (accumulated)
+  int mode;
 };
-struct SensGeom {             // fine-level derivative weights (double)
-  int nx, ny, nz, N;
-  const double *Te, *Tn, *Tu, *m;          // face transmissibilities and storage
-  const double *kap;                        // kappa per cell
-  const double *Bd;                         // Dirichlet boundary transmissibility sum per cell
-};
-void launch_sens(const Batch& fb, const Batch& rb, const SensGeom& sg, const SensItem* items, int nitems,
-                 const double2* wz, const float2* Xs_hi, const float2* Xs_lo, const float2* Xr_hi,
-                 const float2* Xr_lo, double* J, const double* g, double* grad, int mode, cudaStream_t st);
+int launch_sens2(const SensLaunch& L, cudaStream_t st);
+void launch_xk(const Batch& bt, float2* X_hi, float2* X_lo, cudaStream_t st, Prof* pf);
+void launch_true_res(const Batch& bt, const FineExact& fe, const int* sh_basis, const float2* X_hi,
+                     const float2* X_lo, double* res2, cudaStream_t st, Prof* pf);
 
 }  // namespace lt
