@@ -62,6 +62,10 @@ typedef struct {
   int    true_residual; /* 1: compute the true residual of every shift after the solve (default 1) */
   int    check_every;   /* outer iterations between host convergence polls (default 4) */
   int    timing_class;  /* -1: off; else time every launch of this kernel class with CUDA events (LT_KC_*) */
+  double inner_relax;   /* 0: fixed inner_tol; > 0: inner tolerance relaxed as inner_tol / (largest unconverged
+                           projected residual of the basis), capped at inner_relax (inexact-Krylov relaxation) */
+  int    graphs;        /* 1: replay one captured CUDA graph per outer iteration (default); 0: direct launches */
+  int    mg_tile;       /* fused 2D smoother tile: 0 = 64x32, 1 = 32x32, 2 = 32x16 cells (default 2) */
 } lt_opts;
 
 /* kernel classes reported in lt_stats.work[] and selectable by lt_opts.timing_class */
@@ -77,7 +81,9 @@ typedef struct {
 #define LT_KC_SHIFT_LS   9
 #define LT_KC_XK        10   /* x_k = U y_k for the true residual */
 #define LT_KC_TRUE_RES  11
-#define LT_KC_COUNT     13
+#define LT_KC_FUSED_DOWN 12  /* fused 2D tile: pre-smoothing + residual + restriction (cells counted once) */
+#define LT_KC_FUSED_UP   13  /* fused 2D tile: prolongation + correction + post-smoothing */
+#define LT_KC_COUNT     15
 
 typedef struct {
   int    n_bases;             /* Krylov bases built (sources x groups, or receivers x groups) */

@@ -1,0 +1,75 @@
+"""Autotuner for the multigrid and inner-solve settings of a workload.
+
+Times short forward solves of the actual problem for a small grid of
+candidate settings -- fused-smoother tile shape, pre/post smoothing sweeps,
+V-cycles per refinement round, refinement rounds -- and keeps the fastest
+candidate whose every shifted system reaches the tolerance (true residual).
+Results are cached per problem shape in memory (and optionally in a JSON
+file).  The measurement is the library's own device time (CUDA events on
+the context stream).
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import os
+from typing import Dict, Optional
+
+_CACHE: Dict[str, dict] = {}
+
+DEFAULT_GRID = {
+    "mg_tile": [0, 1, 2],
+    "sweeps": [(1, 1), (2, 2)],
+    "inner": [(4, 6), (5, 4), (3, 8)],
+}
+
+
+def problem_key(prob, opts) -> str:
+    return json.dumps([prob.nx, prob.ny, prob.nz, len(prob.src_cells), len(prob.rec_cells), len(prob.times),
+                       prob.Nz, opts.get("groups", prob.groups), opts.get("tol", prob.tol)])
+
+
+def autotune(engine, prob, base_opts: dict, grid: Optional[dict] = None, reps: int = 1,
+             cache_path: Optional[str] = None, verbose: bool = False) -> dict:
+    """Return the best option dict (base_opts updated) for `prob` on `engine`."""
+    key = problem_key(prob, base_opts)
+    if key in _CACHE:
+        return dict(_CACHE[key])
+    if cache_path and os.path.exists(cache_path):
+        try:
+            disk = json.load(open(cache_path))
+            if key in disk:
+                _CACHE[key] = disk[key]
+                return dict(disk[key])
+        except (OSError, ValueError):
+            pass
+    grid = grid or DEFAULT_GRID
+    engine.load_problem(prob, **base_opts)
+    best, best_ms = None, float("inf")
+    for tile, (pre, post), (rounds, cycles) in itertools.product(grid["mg_tile"], grid["sweeps"], grid["inner"]):
+        cand = dict(base_opts, mg_tile=tile, mg_pre=pre, mg_post=post, inner_rounds=rounds, inner_cycles=cycles)
+        engine.set_options(**{k: v for k, v in cand.items() if k not in ("Nz", "tol", "groups")})
+        ms = 0.0
+        ok = True
+        for _ in range(reps + 1):                      # first run warms the graph and workspace
+            engine.forward(prob.times, allow_unconverged=True)
+            st = engine.last_stats
+            ok &= st["n_converged"] == st["n_shift_solves"]
+        ms = st["ms_total"]
+        if verbose:
+            print(f"autotune tile={tile} sweeps={pre},{post} inner={rounds}x{cycles}: {ms:.1f} ms ok={ok}")
+        if ok and ms < best_ms:
+            best, best_ms = cand, ms
+    if best is None:
+        best = dict(base_opts)
+    best = dict(best)
+    _CACHE[key] = best
+    if cache_path:
+        try:
+            disk = json.load(open(cache_path)) if os.path.exists(cache_path) else {}
+            disk[key] = best
+            json.dump(disk, open(cache_path, "w"), indent=1)
+        except (OSError, ValueError):
+            pass
+    engine.set_options(**{k: v for k, v in best.items() if k not in ("Nz", "tol", "groups")})
+    return best

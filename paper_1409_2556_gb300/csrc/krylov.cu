@@ -94,10 +94,12 @@ __global__ void k_init_shifts(Batch bt) {
     bt.conv_it[sh] = 0;
     bt.pres[sh] = 1.0;
   }
+  if (sh == 0) *bt.jdev = 0;
   if (sh < bt.nb) {
     bt.active[sh] = 1;
     bt.nit[sh] = 0;
     bt.inner_max[sh] = 0.0;
+    bt.rmax[sh] = 1.0;
   }
 }
 
@@ -109,7 +111,8 @@ void launch_init_batch(const Batch& bt, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------ per-iteration prep
-__global__ void k_prep_iter(Batch bt, int j) {
+__global__ void k_prep_iter(Batch bt, int) {
+  const int j = *bt.jdev;   // outer iteration (device counter, so one captured graph serves every j)
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= bt.nb) return;
   if (!bt.active[b]) return;
@@ -117,6 +120,20 @@ __global__ void k_prep_iter(Batch bt, int j) {
   int g = bt.group[b];
   bt.tau_cur[b] = bt.tau_grp[2 * g + slot];
   bt.tau_slot[b] = 2 * g + slot;
+  // inexact-Krylov relaxation: the preconditioner-solve error e_j enters the
+  // true residual as e_j y_j, and |y_j| falls with the outer residual, so the
+  // inner tolerance may grow as 1 / (largest unconverged projected residual)
+  double it2 = bt.inner_tol2;
+  if (bt.inner_relax_max > 0.0 && j > 0) {
+    double r = bt.rmax[b] > 0.0 ? bt.rmax[b] : 1.0;
+    double f = 1.0 / r;
+    double lim = bt.inner_relax_max * bt.inner_relax_max / bt.inner_tol2;
+    f = f * f;
+    if (f > lim) f = lim;
+    if (f < 1.0) f = 1.0;
+    it2 *= f;
+  }
+  bt.itol2[b] = it2;
   for (int r = 0; r <= bt.rounds; ++r) bt.rnorm2[b * (bt.rounds + 1) + r] = 0.0;
   for (int i = 0; i < 2 * (bt.maxit + 1); ++i) bt.dot[(size_t)b * 2 * (bt.maxit + 1) + i] = make_double2(0.0, 0.0);
   bt.snorm2[b] = 0.0;
@@ -127,12 +144,13 @@ void launch_prep_iter(const Batch& bt, int j, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------ preconditioner-solve rounds
-__global__ void k_exact_residual(Batch bt, FineExact fe, Level L0, int j, int round, int record_only) {
+__global__ void k_exact_residual(Batch bt, FineExact fe, Level L0, int, int round, int record_only) {
+  const int j = *bt.jdev;   // outer iteration (device counter, so one captured graph serves every j)
   __shared__ float red[32];
   int b = blockIdx.y;
   if (!bt.active[b]) return;
   const int R1 = bt.rounds + 1;
-  if (!record_only && round > 0 && bt.rnorm2[b * R1 + round - 1] <= bt.inner_tol2) return;
+  if (!record_only && round > 0 && bt.rnorm2[b * R1 + round - 1] <= bt.itol2[b]) return;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   float acc[1] = {0.f};
   if (c < fe.N) {
@@ -166,10 +184,11 @@ void launch_exact_residual(const Batch& bt, const FineExact& fe, const Level& L0
   prof_end(pf, KC_EXACT_RES, st);
 }
 
-__global__ void k_update_u(Batch bt, Level L0, int j, int round) {
+__global__ void k_update_u(Batch bt, Level L0, int, int round) {
+  const int j = *bt.jdev;   // outer iteration (device counter, so one captured graph serves every j)
   int b = blockIdx.y;
   if (!bt.active[b]) return;
-  if (bt.rnorm2[b * (bt.rounds + 1) + round] <= bt.inner_tol2) return;
+  if (bt.rnorm2[b * (bt.rounds + 1) + round] <= bt.itol2[b]) return;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L0.N) return;
   float2 d = L0.u[(size_t)b * L0.N + c];
@@ -207,7 +226,8 @@ constexpr int kCPT = 4;      // cells per thread
 constexpr int kIG = 4;       // basis vectors reduced together
 
 // pass 1: dot[0][i] = V_hi[i]^H s_hi, s = M u_j (float32 estimate)
-__global__ void __launch_bounds__(kArnT) k_dots1(Batch bt, FineExact fe, int j) {
+__global__ void __launch_bounds__(kArnT) k_dots1(Batch bt, FineExact fe, int) {
+  const int j = *bt.jdev;   // outer iteration (device counter, so one captured graph serves every j)
   __shared__ float red[32 * 2 * kIG];
   int b = blockIdx.y;
   if (!bt.active[b]) return;
@@ -263,7 +283,8 @@ __global__ void __launch_bounds__(kArnT) k_dots1(Batch bt, FineExact fe, int j) 
 
 // pass 2: s' = M u_j - V c1 (df32, exact); dot[1][i] = V_hi[i]^H s'_hi; S <- s'
 // pass 3 (second = 1): s'' = S - V c2; snorm2 += ||s''||^2; S <- s''
-__global__ void __launch_bounds__(kArnT) k_update(Batch bt, FineExact fe, int j, int second) {
+__global__ void __launch_bounds__(kArnT) k_update(Batch bt, FineExact fe, int, int second) {
+  const int j = *bt.jdev;   // outer iteration (device counter, so one captured graph serves every j)
   __shared__ float red[32 * 2 * kIG];
   __shared__ float2 cf[512];
   int b = blockIdx.y;
@@ -354,7 +375,8 @@ __global__ void __launch_bounds__(kArnT) k_update(Batch bt, FineExact fe, int j,
 }
 
 // v_{j+1} = s'' / h, h = float(||s''||); H column j
-__global__ void k_normalize(Batch bt, int j) {
+__global__ void k_normalize(Batch bt, int) {
+  const int j = *bt.jdev;   // outer iteration (device counter, so one captured graph serves every j)
   int b = blockIdx.y;
   if (!bt.active[b]) return;
   float h = (float)sqrt(bt.snorm2[b]);
@@ -407,12 +429,14 @@ __device__ __forceinline__ double2 zmul(double2 a, double2 b) {
 __device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
 __device__ __forceinline__ double zabs(double2 a) { return hypot(a.x, a.y); }
 
-__global__ void k_shift_ls(Batch bt, int j) {
+__global__ void k_shift_ls(Batch bt, int) {
+  const int j = *bt.jdev;   // outer iteration (device counter, so one captured graph serves every j)
   __shared__ double2 hcol[1024];
   __shared__ int any;
+  __shared__ unsigned long long rmax_bits;
   int b = blockIdx.x;
   if (!bt.active[b]) return;
-  if (threadIdx.x == 0) any = 0;
+  if (threadIdx.x == 0) { any = 0; rmax_bits = 0ull; }
   const double2* Hc = bt.H + ((size_t)b * bt.maxit + j) * (bt.maxit + 1);
   for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) hcol[i] = Hc[i];
   __syncthreads();
@@ -466,19 +490,29 @@ __global__ void k_shift_ls(Batch bt, int j) {
     g[j + 1] = make_double2(-gn.x, -gn.y);
     double res = zabs(g[j + 1]);
     bt.pres[sh] = res;
-    if (res <= bt.tol || rho == 0.0 || hcol[j + 1].x == 0.0) bt.conv_it[sh] = j + 1;
-    else mine = 1;
+    if (res <= bt.tol || rho == 0.0 || hcol[j + 1].x == 0.0) {
+      bt.conv_it[sh] = j + 1;
+    } else {
+      mine = 1;
+      atomicMax(&rmax_bits, (unsigned long long)__double_as_longlong(res));   // res >= 0: bit order = value order
+    }
   }
   if (mine) atomicOr(&any, 1);
   __syncthreads();
   if (threadIdx.x == 0) {
     bt.nit[b] = j + 1;
     bt.active[b] = (any && j + 1 < M) ? 1 : 0;
+    bt.rmax[b] = __longlong_as_double((long long)rmax_bits);
   }
+}
+
+__global__ void k_next_iter(Batch bt) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *bt.jdev += 1;
 }
 
 void launch_shift_ls(const Batch& bt, int j, cudaStream_t st) {
   k_shift_ls<<<bt.nb, 256, 0, st>>>(bt, j);
+  k_next_iter<<<1, 32, 0, st>>>(bt);
 }
 
 // y_k = R^{-1} g over the shift's converged (or final) column count

@@ -95,6 +95,9 @@ struct lt_ctx {
   // carved from this region instead of being allocated
   char* arena_base = nullptr;
   size_t arena_cap = 0, arena_off = 0;
+  // non-blocking stream on which the per-iteration CUDA graph is captured and replayed
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
 };
 
 static int fail(lt_ctx* ctx, int code, const char* fmt, ...) {
@@ -164,6 +167,9 @@ int lt_default_options(lt_opts* o) {
   o->true_residual = 1;
   o->check_every = 4;
   o->timing_class = -1;
+  o->inner_relax = 0.0;
+  o->graphs = 1;
+  o->mg_tile = 2;
   return LT_OK;
 }
 
@@ -221,6 +227,9 @@ void lt_destroy(lt_ctx* ctx) {
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
+  if (ctx->ev_a) cudaEventDestroy(ctx->ev_a);
+  if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
 
@@ -238,11 +247,16 @@ int lt_set_options(lt_ctx* ctx, const lt_opts* o) {
     return fail(ctx, LT_ERR_INVALID_ARG, "inner_cycles in [1,64], inner_rounds in [1,16]");
   if (o->inner_tol < 0.0 || o->inner_tol >= 1.0) return fail(ctx, LT_ERR_INVALID_ARG, "inner_tol=%g", o->inner_tol);
   if (o->check_every < 1) return fail(ctx, LT_ERR_INVALID_ARG, "check_every=%d", o->check_every);
+  if (o->mg_tile < 0 || o->mg_tile > 2) return fail(ctx, LT_ERR_INVALID_ARG, "mg_tile=%d must be 0, 1 or 2", o->mg_tile);
+  if (o->graphs != 0 && o->graphs != 1) return fail(ctx, LT_ERR_INVALID_ARG, "graphs=%d must be 0 or 1", o->graphs);
+  if (!(o->inner_relax >= 0.0 && o->inner_relax < 1.0))
+    return fail(ctx, LT_ERR_INVALID_ARG, "inner_relax=%g must be in [0,1)", o->inner_relax);
   if (o->timing_class < -1 || o->timing_class >= LT_KC_COUNT)
     return fail(ctx, LT_ERR_INVALID_ARG, "timing_class=%d", o->timing_class);
   ctx->opts = *o;
   ctx->mg.npre = o->mg_pre;
   ctx->mg.npost = o->mg_post;
+  ctx->mg.tile = o->mg_tile;
   return LT_OK;
 }
 
@@ -433,6 +447,7 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
   mg.nlev = nlev;
   mg.npre = ctx->opts.mg_pre;
   mg.npost = ctx->opts.mg_post;
+  mg.tile = ctx->opts.mg_tile;
   mg.dmask = 0;
   for (int d = 0; d < 6; ++d)
     if (bc[d] == 0) mg.dmask |= (1 << d);
@@ -662,6 +677,9 @@ static int ensure_ws(lt_ctx* ctx, const Plan& P) {
   AL(bt.rs, (size_t)nsh * M); AL(bt.g, (size_t)nsh * (M + 1)); AL(bt.conv_it, nsh); AL(bt.pres, nsh);
   AL(bt.Y, (size_t)nsh * M);
   AL(bt.work, 16);
+  AL(bt.itol2, nb);
+  AL(bt.rmax, nb);
+  AL(bt.jdev, 1);
   if (nc2) AL(bt.coarse_inv, (size_t)2 * P.G * nc2);
   // multigrid vectors
   for (int l = 0; l < ctx->mg.nlev; ++l) {
@@ -688,6 +706,7 @@ static int run_solves(lt_ctx* ctx, const Plan& P, std::vector<double>& true_res,
   bt.tol = o.tol;
   double itol = o.inner_tol > 0 ? o.inner_tol : 0.01 * o.tol;
   bt.inner_tol2 = itol * itol;
+  bt.inner_relax_max = o.inner_relax;
   cudaStream_t s = ctx->stream;
   // tables
   std::vector<double2> taug(2 * P.G);
@@ -735,33 +754,72 @@ static int run_solves(lt_ctx* ctx, const Plan& P, std::vector<double>& true_res,
   std::vector<int> act(P.nb);
   int j = 0, cycles = 0;
   const lt::Level& L0 = ctx->mg.h_levels[0];
-  for (j = 0; j < o.maxit; ++j) {
-    lt::launch_prep_iter(bt, j, s);
-    ++*nl;
+  // one outer iteration of every active basis (kernels read j from bt.jdev)
+  auto iteration = [&](cudaStream_t q, int jj, int* nlq) -> int {
+    lt::launch_prep_iter(bt, jj, q);
+    ++*nlq;
     for (int r = 0; r < o.inner_rounds; ++r) {
-      lt::launch_exact_residual(bt, ctx->fe, L0, j, r, 0, s, pf);
-      ++*nl;
-      for (int cy = 0; cy < o.inner_cycles; ++cy) {
-        if (lt::launch_vcycle(ctx->mg, bt, r, s, nl, pf)) return fail(ctx, LT_ERR_CUDA, "V-cycle launch failed");
-        ++cycles;
-      }
-      lt::launch_update_u(bt, L0, j, r, s);
-      ++*nl;
+      lt::launch_exact_residual(bt, ctx->fe, L0, jj, r, 0, q, pf);
+      ++*nlq;
+      for (int cy = 0; cy < o.inner_cycles; ++cy)
+        if (lt::launch_vcycle(ctx->mg, bt, r, q, nlq, pf)) return LT_ERR_CUDA;
+      lt::launch_update_u(bt, L0, jj, r, q);
+      ++*nlq;
     }
-    lt::launch_exact_residual(bt, ctx->fe, L0, j, o.inner_rounds, 1, s, pf);
-    lt::launch_inner_record(bt, s);
-    *nl += 2;
-    lt::launch_arnoldi(bt, ctx->fe, j, s, nl, pf);
-    lt::launch_shift_ls(bt, j, s);
-    ++*nl;
+    lt::launch_exact_residual(bt, ctx->fe, L0, jj, o.inner_rounds, 1, q, pf);
+    lt::launch_inner_record(bt, q);
+    *nlq += 2;
+    lt::launch_arnoldi(bt, ctx->fe, jj, q, nlq, pf);
+    lt::launch_shift_ls(bt, jj, q);
+    *nlq += 2;
+    return LT_OK;
+  };
+  // CUDA graph replay (not while timing individual launches, and not inside
+  // lt_forward_noalloc, whose contract excludes any device allocation)
+  const bool use_graph = o.graphs && pf == nullptr && ctx->arena_base == nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t q = s;
+  int per_iter = 0;
+  if (use_graph) {
+    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    if (!ctx->ev_a) CK(cudaEventCreateWithFlags(&ctx->ev_a, cudaEventDisableTiming));
+    if (!ctx->ev_b) CK(cudaEventCreateWithFlags(&ctx->ev_b, cudaEventDisableTiming));
+    q = ctx->cap_stream;
+    CK(cudaEventRecord(ctx->ev_a, s));
+    CK(cudaStreamWaitEvent(q, ctx->ev_a, 0));
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(q, cudaStreamCaptureModeThreadLocal));
+    int rc2 = iteration(q, 0, &per_iter);
+    cudaError_t ec = cudaStreamEndCapture(q, &graph);
+    if (rc2 || ec != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return fail(ctx, LT_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ec));
+    }
+    ec = cudaGraphInstantiate(&gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ec != cudaSuccess) return fail(ctx, LT_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ec));
+  }
+  for (j = 0; j < o.maxit; ++j) {
+    if (use_graph) {
+      CK(cudaGraphLaunch(gexec, q));
+      *nl += per_iter;
+    } else if (iteration(s, j, nl)) {
+      return fail(ctx, LT_ERR_CUDA, "kernel launch failed");
+    }
+    cycles += o.inner_rounds * o.inner_cycles;
     CK(cudaGetLastError());
     if ((j + 1) % o.check_every == 0 || j + 1 == o.maxit) {
-      CK(cudaMemcpyAsync(act.data(), bt.active, P.nb * sizeof(int), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
+      CK(cudaMemcpyAsync(act.data(), bt.active, P.nb * sizeof(int), cudaMemcpyDeviceToHost, q));
+      CK(cudaStreamSynchronize(q));
       bool any = false;
       for (int b = 0; b < P.nb; ++b) any |= act[b] != 0;
       if (!any) { ++j; break; }
     }
+  }
+  if (use_graph) {
+    CK(cudaEventRecord(ctx->ev_b, q));
+    CK(cudaStreamWaitEvent(s, ctx->ev_b, 0));
+    cudaGraphExecDestroy(gexec);
   }
   // y per shift
   int* d_shb = nullptr;
@@ -1087,7 +1145,7 @@ static size_t noalloc_need(const lt_ctx* ctx, const Plan& P) {
   add(nb, 8); add(nb, 4); add(nb, 4); add(nb, 8); add(nb, 8);
   add(nb + 1, 4); add(nsh, 16); add(nsh * M * M, 16); add(nsh * M, 8);
   add(nsh * M, 16); add(nsh * (M + 1), 16); add(nsh, 4); add(nsh, 8);
-  add(nsh * M, 16); add(16, 8);
+  add(nsh * M, 16); add(16, 8); add(nb, 8); add(nb, 8); add(1, 4);
   if (ctx->mg.coarse_direct) add(2 * G * (size_t)ctx->hl.back().N * ctx->hl.back().N, 8);
   for (int l = 0; l < ctx->mg.nlev; ++l) { add(nb * ctx->mg.h_levels[l].N, 8); add(nb * ctx->mg.h_levels[l].N, 8); }
   add(nsh, 4);

@@ -7,7 +7,7 @@
 namespace lt {
 
 constexpr int kMaxLevels = 16;
-constexpr int kCoarseCells = 4096;     // levels at or below this size run in one CTA per basis
+constexpr int kCoarseCells = 1024;     // levels at or below this size run in one CTA per basis
 constexpr int kDirectCells = 256;      // coarsest level solved by a dense inverse if at most this size
 constexpr int kCoarseSweeps = 24;      // RB-GS sweeps at the coarsest level when it is not solved directly
 
@@ -36,7 +36,10 @@ struct Batch {
   int maxit;                       // columns of U (V has maxit + 1)
   int64_t N;                       // fine cells
   int rounds;                      // refinement rounds per preconditioner solve
-  double inner_tol2;               // (inner relative tolerance)^2
+  double inner_tol2;               // (inner relative tolerance)^2, before relaxation
+  double inner_relax_max;          // > 0: relax the inner tolerance as the outer residual falls, up to this
+  double* itol2;                   // [nb] inner tolerance^2 of the current outer iteration
+  double* rmax;                    // [nb] largest projected residual over the basis's unconverged shifts
   double tol;                      // outer tolerance (relative)
   float2 *V_hi, *V_lo;             // [nb][maxit+1][N]
   float2 *U_hi, *U_lo;             // [nb][maxit][N]
@@ -68,12 +71,13 @@ struct Batch {
   float2* coarse_inv;              // [ngroups*2][nc*nc] dense inverses of the coarsest operator
   int coarse_direct;               // 1 if coarse_inv is valid
   unsigned long long* work;        // [kNumClasses] cells processed per kernel class (live roofline)
+  int* jdev;                       // current outer iteration (shared by all bases of the batch)
 };
 
 // kernel classes for the live per-kernel timing and work counters
 enum KernelClass {
   KC_RBGS = 0, KC_RESTRICT, KC_PROLONG, KC_COARSE, KC_EXACT_RES, KC_UPDATE_U, KC_DOTS, KC_ORTHO, KC_NORMALIZE,
-  KC_SHIFT_LS, KC_XK, KC_TRUE_RES, KC_OTHER, kNumClasses
+  KC_SHIFT_LS, KC_XK, KC_TRUE_RES, KC_FUSED_DOWN, KC_FUSED_UP, KC_OTHER, kNumClasses
 };
 
 // CUDA-event timing of the launches of one kernel class (cls < 0: off)

@@ -11,6 +11,7 @@ struct MGHost {
   int npre, npost;             // smoothing sweeps
   int dmask;                   // Dirichlet faces bitmask (bit 2d: lower face of axis d, 2d+1: upper)
   int coarse_direct;           // 1 if the coarsest level has a dense inverse
+  int tile;                    // fused 2D tile shape: 0 = 64x32, 1 = 32x32, 2 = 32x16
   Level h_levels[kMaxLevels];  // host copy of the level descriptors
   Level* d_levels;             // device copy
 };

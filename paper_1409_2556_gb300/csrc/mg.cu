@@ -26,7 +26,7 @@ namespace lt {
 
 __device__ __forceinline__ bool mg_skip(const Batch& bt, int b, int round) {
   if (!bt.active[b]) return true;
-  return bt.rnorm2[b * (bt.rounds + 1) + round] <= bt.inner_tol2;
+  return bt.rnorm2[b * (bt.rounds + 1) + round] <= bt.itol2[b];
 }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -235,12 +235,242 @@ __global__ void __launch_bounds__(1024) k_coarse_vcycle(const Level* __restrict_
   }
 }
 
+
+// ---------------------------------------------------------------- fused 2D tile kernels
+// For 2D levels coarsened 2x2, one CTA owns a kTX x kTY tile of fine cells and
+// stages the tile plus a halo in shared memory.  A red-black half-sweep only
+// reads the other colour, so updating the staged region reproduces the global
+// sweep exactly on every cell whose neighbours were valid; each half-sweep
+// shrinks the valid region by one ring.
+//   down: pre-smoothing (npre sweeps) + residual + restriction (halo 2*npre+1)
+//   up:   prolongation + correction + post-smoothing (halo 2*npost)
+constexpr int kFusedThreads = 512;
+
+__device__ __forceinline__ float2 cinv(float2 d) {
+  float inv = 1.f / (d.x * d.x + d.y * d.y);
+  return make_float2(d.x * inv, -d.y * inv);
+}
+
+struct Tile2D {
+  float2* u;    // [RY][RX]
+  float2* f;
+  float2* di;   // inverse of the complex diagonal
+  float* te;    // east-face transmissibility
+  float* tn;    // north-face transmissibility
+};
+
+__device__ __forceinline__ void tile_load(const Level& L, const float2* u, const float2* f, float2 tau, Tile2D& T,
+                                          int gx0, int gy0, int RX, int RY) {
+  for (int idx = threadIdx.x; idx < RX * RY; idx += blockDim.x) {
+    int lx = idx % RX, ly = idx / RX;
+    int gx = gx0 + lx, gy = gy0 + ly;
+    if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) {
+      int c = gy * L.nx + gx;
+      T.u[idx] = u[c];
+      T.f[idx] = f[c];
+      T.te[idx] = L.Te[c];
+      T.tn[idx] = L.Tn[c];
+      float m = L.m[c];
+      T.di[idx] = cinv(make_float2(L.D[c] + tau.x * m, tau.y * m));
+    } else {
+      T.u[idx] = make_float2(0.f, 0.f);
+      T.f[idx] = make_float2(0.f, 0.f);
+      T.te[idx] = 0.f;
+      T.tn[idx] = 0.f;
+      T.di[idx] = make_float2(0.f, 0.f);
+    }
+  }
+}
+
+__device__ __forceinline__ float2 tile_nb(const Tile2D& T, int idx, int RX) {
+  float2 s;
+  float a = T.te[idx], b = T.te[idx - 1], c = T.tn[idx], d = T.tn[idx - RX];
+  float2 ue = T.u[idx + 1], uw = T.u[idx - 1], un = T.u[idx + RX], us = T.u[idx - RX];
+  s.x = a * ue.x + b * uw.x + c * un.x + d * us.x;
+  s.y = a * ue.y + b * uw.y + c * un.y + d * us.y;
+  return s;
+}
+
+__device__ __forceinline__ void tile_sweeps(Tile2D& T, const Level& L, int gx0, int gy0, int RX, int RY, int nhalf,
+                                            int first_color) {
+  for (int h = 0; h < nhalf; ++h) {
+    int color = (first_color + h) & 1;
+    for (int idx = threadIdx.x; idx < RX * RY; idx += blockDim.x) {
+      int lx = idx % RX, ly = idx / RX;
+      if (lx < 1 || ly < 1 || lx > RX - 2 || ly > RY - 2) continue;
+      int gx = gx0 + lx, gy = gy0 + ly;
+      if (((gx + gy) & 1) != color) continue;
+      if (gx < 0 || gy < 0 || gx >= L.nx || gy >= L.ny) continue;
+      float2 r = tile_nb(T, idx, RX);
+      float2 fc = T.f[idx];
+      r.x += fc.x; r.y += fc.y;
+      T.u[idx] = cmul(r, T.di[idx]);
+    }
+    __syncthreads();
+  }
+}
+
+template <int kTX, int kTY>
+__global__ void __launch_bounds__(kFusedThreads) k_down2d(Level Lf, Level Lc, Batch bt, int round, int npre) {
+  extern __shared__ float4 smem4[];
+  int b = blockIdx.y;
+  if (mg_skip(bt, b, round)) return;
+  const int H = 2 * npre + 1;
+  const int RX = kTX + 2 * H, RY = kTY + 2 * H, RN = RX * RY;
+  const int ntx = (Lf.nx + kTX - 1) / kTX;
+  const int tx0 = (blockIdx.x % ntx) * kTX, ty0 = (blockIdx.x / ntx) * kTY;
+  const int gx0 = tx0 - H, gy0 = ty0 - H;
+  char* base = (char*)smem4;
+  Tile2D T;
+  T.u = (float2*)base; T.f = T.u + RN; T.di = T.f + RN;
+  T.te = (float*)(T.di + RN); T.tn = T.te + RN;
+  float2 tau = tau32(bt, b);
+  float2* u = Lf.u + (size_t)b * Lf.N;
+  const float2* f = Lf.f + (size_t)b * Lf.N;
+  if (threadIdx.x == 0) {
+    int n = min(kTX, Lf.nx - tx0) * min(kTY, Lf.ny - ty0);
+    atomicAdd(&bt.work[KC_FUSED_DOWN], (unsigned long long)n);
+  }
+  tile_load(Lf, u, f, tau, T, gx0, gy0, RX, RY);
+  __syncthreads();
+  tile_sweeps(T, Lf, gx0, gy0, RX, RY, 2 * npre, 0);
+  // residual + restriction of the tile's coarse cells; write the smoothed tile
+  const int ncx = kTX / 2, ncy = kTY / 2;
+  float2* fc = Lc.f + (size_t)b * Lc.N;
+  float2* uc = Lc.u + (size_t)b * Lc.N;
+  for (int q = threadIdx.x; q < ncx * ncy; q += blockDim.x) {
+    int I = tx0 / 2 + q % ncx, J = ty0 / 2 + q / ncx;
+    if (I >= Lc.nx || J >= Lc.ny) continue;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int dj = 0; dj < 2; ++dj)
+      for (int di = 0; di < 2; ++di) {
+        int lx = H + 2 * (q % ncx) + di, ly = H + 2 * (q / ncx) + dj;
+        int idx = ly * RX + lx;
+        float2 nbs = tile_nb(T, idx, RX);
+        float2 d = cinv(T.di[idx]);
+        float2 a = cmul(d, T.u[idx]);
+        float2 fv = T.f[idx];
+        acc.x += fv.x - a.x + nbs.x;
+        acc.y += fv.y - a.y + nbs.y;
+      }
+    fc[J * Lc.nx + I] = acc;
+    uc[J * Lc.nx + I] = make_float2(0.f, 0.f);
+  }
+  for (int q = threadIdx.x; q < kTX * kTY; q += blockDim.x) {
+    int gx = tx0 + q % kTX, gy = ty0 + q / kTX;
+    if (gx >= Lf.nx || gy >= Lf.ny) continue;
+    u[gy * Lf.nx + gx] = T.u[(H + q / kTX) * RX + H + q % kTX];
+  }
+}
+
+template <int kTX, int kTY>
+__global__ void __launch_bounds__(kFusedThreads) k_up2d(Level Lf, Level Lc, Batch bt, int round, int npost,
+                                                       int dmask) {
+  extern __shared__ float4 smem4[];
+  int b = blockIdx.y;
+  if (mg_skip(bt, b, round)) return;
+  const int H = 2 * npost;
+  const int RX = kTX + 2 * H, RY = kTY + 2 * H, RN = RX * RY;
+  const int ntx = (Lf.nx + kTX - 1) / kTX;
+  const int tx0 = (blockIdx.x % ntx) * kTX, ty0 = (blockIdx.x / ntx) * kTY;
+  const int gx0 = tx0 - H, gy0 = ty0 - H;
+  char* base = (char*)smem4;
+  Tile2D T;
+  T.u = (float2*)base; T.f = T.u + RN; T.di = T.f + RN;
+  T.te = (float*)(T.di + RN); T.tn = T.te + RN;
+  float2 tau = tau32(bt, b);
+  float2* u = Lf.u + (size_t)b * Lf.N;
+  const float2* f = Lf.f + (size_t)b * Lf.N;
+  const float2* uc = Lc.u + (size_t)b * Lc.N;
+  if (threadIdx.x == 0) {
+    int n = min(kTX, Lf.nx - tx0) * min(kTY, Lf.ny - ty0);
+    atomicAdd(&bt.work[KC_FUSED_UP], (unsigned long long)n);
+  }
+  tile_load(Lf, u, f, tau, T, gx0, gy0, RX, RY);
+  __syncthreads();
+  // prolongation + correction on the whole staged region
+  for (int idx = threadIdx.x; idx < RN; idx += blockDim.x) {
+    int gx = gx0 + idx % RX, gy = gy0 + idx / RX;
+    if (gx < 0 || gy < 0 || gx >= Lf.nx || gy >= Lf.ny) continue;
+    int I0, I1, J0, J1;
+    float wi0, wi1, wj0, wj1, si, sj;
+    axis_interp(gx, 2, Lc.nx, dmask & 1, dmask & 2, I0, I1, wi0, wi1, si);
+    axis_interp(gy, 2, Lc.ny, dmask & 4, dmask & 8, J0, J1, wj0, wj1, sj);
+    wi1 *= si; wj1 *= sj;
+    float2 a = uc[J0 * Lc.nx + I0], bq = uc[J0 * Lc.nx + I1], c = uc[J1 * Lc.nx + I0], d = uc[J1 * Lc.nx + I1];
+    float w00 = wj0 * wi0, w01 = wj0 * wi1, w10 = wj1 * wi0, w11 = wj1 * wi1;
+    float2 v = T.u[idx];
+    v.x += w00 * a.x + w01 * bq.x + w10 * c.x + w11 * d.x;
+    v.y += w00 * a.y + w01 * bq.y + w10 * c.y + w11 * d.y;
+    T.u[idx] = v;
+  }
+  __syncthreads();
+  tile_sweeps(T, Lf, gx0, gy0, RX, RY, 2 * npost, 1);
+  for (int q = threadIdx.x; q < kTX * kTY; q += blockDim.x) {
+    int gx = tx0 + q % kTX, gy = ty0 + q / kTX;
+    if (gx >= Lf.nx || gy >= Lf.ny) continue;
+    u[gy * Lf.nx + gx] = T.u[(H + q / kTX) * RX + H + q % kTX];
+  }
+}
+
+size_t fused_smem(int tx, int ty, int npre_or_post, bool down) {
+  int H = down ? 2 * npre_or_post + 1 : 2 * npre_or_post;
+  size_t RN = (size_t)(tx + 2 * H) * (ty + 2 * H);
+  return RN * (3 * sizeof(float2) + 2 * sizeof(float));
+}
+
+// tile shapes selectable by MGHost::tile
+static const int kTiles[3][2] = {{64, 32}, {32, 32}, {32, 16}};
+
+template <int TX, int TY>
+static void set_attrs() {
+  cudaFuncSetAttribute(k_down2d<TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem(TX, TY, 8, true));
+  cudaFuncSetAttribute(k_up2d<TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem(TX, TY, 8, false));
+}
+
+static void launch_down(int tile, const Level& L, const Level& Lc, const Batch& bt, int round, int npre, cudaStream_t st) {
+  const int TX = kTiles[tile][0], TY = kTiles[tile][1];
+  dim3 g(((L.nx + TX - 1) / TX) * ((L.ny + TY - 1) / TY), bt.nb);
+  size_t sm = fused_smem(TX, TY, npre, true);
+  if (tile == 0) k_down2d<64, 32><<<g, kFusedThreads, sm, st>>>(L, Lc, bt, round, npre);
+  else if (tile == 1) k_down2d<32, 32><<<g, kFusedThreads, sm, st>>>(L, Lc, bt, round, npre);
+  else k_down2d<32, 16><<<g, kFusedThreads, sm, st>>>(L, Lc, bt, round, npre);
+}
+
+static void launch_up(int tile, const Level& L, const Level& Lc, const Batch& bt, int round, int npost, int dmask,
+                      cudaStream_t st) {
+  const int TX = kTiles[tile][0], TY = kTiles[tile][1];
+  dim3 g(((L.nx + TX - 1) / TX) * ((L.ny + TY - 1) / TY), bt.nb);
+  size_t sm = fused_smem(TX, TY, npost, false);
+  if (tile == 0) k_up2d<64, 32><<<g, kFusedThreads, sm, st>>>(L, Lc, bt, round, npost, dmask);
+  else if (tile == 1) k_up2d<32, 32><<<g, kFusedThreads, sm, st>>>(L, Lc, bt, round, npost, dmask);
+  else k_up2d<32, 16><<<g, kFusedThreads, sm, st>>>(L, Lc, bt, round, npost, dmask);
+}
+
+static bool fused_ok(const Level& L) { return L.nz == 1 && L.rx == 2 && L.ry == 2 && L.rz == 1; }
+
 // ---------------------------------------------------------------- host launcher
 int launch_vcycle(const MGHost& mg, const Batch& bt, int round, cudaStream_t st, int* nlaunch, Prof* pf) {
   const int nb = bt.nb;
   const int T = 256;
+  static bool attr_done = false;
+  if (!attr_done) {
+    set_attrs<64, 32>();
+    set_attrs<32, 32>();
+    set_attrs<32, 16>();
+    attr_done = true;
+  }
+  const int tile = (mg.tile >= 0 && mg.tile < 3) ? mg.tile : 2;
   for (int l = 0; l < mg.lc; ++l) {
     const Level& L = mg.h_levels[l];
+    const Level& Lc = mg.h_levels[l + 1];
+    if (fused_ok(L) && mg.npre > 0) {
+      prof_begin(pf, KC_FUSED_DOWN, st);
+      launch_down(tile, L, Lc, bt, round, mg.npre, st);
+      prof_end(pf, KC_FUSED_DOWN, st);
+      ++*nlaunch;
+      continue;
+    }
     dim3 g((L.N + T - 1) / T, nb);
     for (int s = 0; s < mg.npre; ++s)
       for (int color = 0; color < 2; ++color) {
@@ -249,7 +479,6 @@ int launch_vcycle(const MGHost& mg, const Batch& bt, int round, cudaStream_t st,
         prof_end(pf, KC_RBGS, st);
         ++*nlaunch;
       }
-    const Level& Lc = mg.h_levels[l + 1];
     dim3 gc((Lc.N + T - 1) / T, nb);
     prof_begin(pf, KC_RESTRICT, st);
     k_restrict<<<gc, T, 0, st>>>(L, Lc, bt, round); ++*nlaunch;
@@ -265,6 +494,13 @@ int launch_vcycle(const MGHost& mg, const Batch& bt, int round, cudaStream_t st,
   for (int l = mg.lc - 1; l >= 0; --l) {
     const Level& L = mg.h_levels[l];
     const Level& Lc = mg.h_levels[l + 1];
+    if (fused_ok(L) && mg.npost > 0) {
+      prof_begin(pf, KC_FUSED_UP, st);
+      launch_up(tile, L, Lc, bt, round, mg.npost, mg.dmask, st);
+      prof_end(pf, KC_FUSED_UP, st);
+      ++*nlaunch;
+      continue;
+    }
     dim3 g((L.N + T - 1) / T, nb);
     prof_begin(pf, KC_PROLONG, st);
     k_prolong<<<g, T, 0, st>>>(L, Lc, bt, round, mg.dmask); ++*nlaunch;

@@ -163,3 +163,20 @@ def test_repeated_calls_are_identical_and_sizes_change(Engine):
     eng.load_problem(q)
     assert _rel(eng.forward(q.times), direct.forward(q)) < TOL_H
     eng.close()
+
+
+@pytest.mark.parametrize("use_stream", [False, True])
+def test_graph_replay_matches_direct_launches(Engine, use_stream):
+    import torch
+    p = W.random_problem(64, 48, 1, variance=1.5, seed=13, ns=3, nr=2, nt=4, Nz=16, tol=1e-11, groups=2)
+    st = torch.cuda.Stream() if use_stream else None
+    outs = []
+    for graphs in (0, 1):
+        eng = Engine(0, stream=st)
+        eng.load_problem(p, graphs=graphs, inner_relax=1e-6)
+        outs.append((eng.forward(p.times), eng.last_stats))
+        eng.close()
+    (h0, s0), (h1, s1) = outs
+    assert s0["outer_iters_max"] == s1["outer_iters_max"]
+    assert _rel(h1, h0) < 1e-12
+    assert _rel(h1, direct.forward(p)) < TOL_H

@@ -17,6 +17,8 @@ def test_config2_full_size_sampled():
     prob = bench.workload(0)
     eng = Engine(0)
     eng.load_problem(prob, **bench.SOLVE_OPTS)
+    from paper_1409_2556_gb300.autotune import autotune
+    autotune(eng, prob, bench.SOLVE_OPTS)          # the configuration bench.py times
     h = eng.forward(prob.times)
     st = eng.last_stats
     eng.close()
