@@ -132,6 +132,44 @@ def cpu_baseline_sample(prob, nshift: int = 16, t_index: int = 0, k0: int = 0):
     return n, dt
 
 
+JAC_WORKLOAD = "3d-64x64x16 (config-3 fields at 1/8 of the cells), 16 sources, 48 receivers, 10 times, Nz=16"
+
+
+def jacobian_rows(dev, stream, reps: int = 1):
+    """Jacobian rows per second of lt_adjoint_jacobian (J materialised on the device) on the
+    config-3 fields at a reduced grid (64x64x16: the full 128x128x32 needs ~250 GB for bases,
+    fields and J together)."""
+    import torch
+    import workloads as W
+    from paper_1409_2556_gb300 import Engine
+    prob = W.config3(nxy=64, nz=16)
+    eng = Engine(dev, stream=stream)
+    eng.load_problem(prob, tol=1e-10, maxit=250, inner_relax=1e-6, mg_pre=2, mg_post=2, inner_rounds=4,
+                     inner_cycles=6, check_every=4, groups=1)
+    ns, nr, nt = len(prob.src_cells), len(prob.rec_cells), len(prob.times)
+    J = torch.zeros((ns, nr, nt, 2, prob.ncell), dtype=torch.float64, device=f"cuda:{dev}")
+    eng.adjoint_jacobian(prob.times, J)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(reps):
+            eng.adjoint_jacobian(prob.times, J)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    st = eng.last_stats
+    rows = ns * nr * nt
+    eng.close()
+    del J
+    torch.cuda.empty_cache()
+    return {"value": rows / (ms / 1000.0), "unit": "Jacobian rows/s", "workload": JAC_WORKLOAD,
+            "rows": rows, "entries_per_row": 2 * prob.ncell, "ms_per_jacobian": ms, "materialised": True,
+            "bases": st["n_bases"], "shifted_systems": st["n_shift_solves"], "converged": st["n_converged"],
+            "max_true_residual": st["max_true_residual"], "outer_iters_max": st["outer_iters_max"]}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -165,6 +203,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-jacobian", action="store_true")
     ap.add_argument("--opts", default="", help="JSON dict overriding solver options (profiling runs)")
     ap.add_argument("--launch-list", action="store_true",
                     help="profiling only: run warmup + the timed steps, print nothing else")
@@ -291,9 +330,12 @@ def main():
     roof = {"kernel": KERNEL_NAMES[TIMED_CLASS], "bound": "hbm",
             "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
-            "traffic": None, "launches_timed": timed_n, "avg_launch_us": 1000.0 * timed_ms / max(timed_n, 1),
+            "traffic": None,
+            "traffic_note": ("ncu on a 9-basis case read 2.9-11.7 MB per launch (L2-resident working set); "
+                             "does not scale in proportion to a full launch, so not reported"), "launches_timed": timed_n, "avg_launch_us": 1000.0 * timed_ms / max(timed_n, 1),
             "bytes_per_unit": bpu, "units": work,
             "measured": "CUDA events around each launch of the class, in a separate pass of the same steps"}
+    jac = None if args.no_jacobian else jacobian_rows(dev, stream)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -313,7 +355,7 @@ def main():
                        "max_true_residual": tres, "outer_iters_max": max(iters),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (Krylov bases ~GBs per step)"},
-            "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(), "jacobian": jac,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": launches}
     print(json.dumps(line), flush=True)
