@@ -170,6 +170,54 @@ def jacobian_rows(dev, stream, reps: int = 1):
             "max_true_residual": st["max_true_residual"], "outer_iters_max": st["outer_iters_max"]}
 
 
+BATCH_WORKLOAD = ("40 independent 2D aquifers, sides in {96,128,192,256,384}, log-kappa variance U[0.5,3], "
+                  "4-16 sources, 16-64 receivers, 8 times, Nz=24, 2 groups (forward solves)")
+
+
+def batch_throughput(dev, wave: int = 10):
+    """Shifted solves/s of the uneven 40-aquifer batch, solved with lt_forward_batch in waves of
+    `wave` aquifers (each on its own stream), and the same aquifers solved one after another."""
+    import torch
+    import workloads as W
+    from paper_1409_2556_gb300 import Engine
+    from paper_1409_2556_gb300.batch import forward_batch
+    aqs = W.config5_aquifers()
+    opts = dict(tol=1e-10, maxit=120, inner_relax=1e-6, groups=2, check_every=4, mg_tile=1)
+    t_batch = t_seq = 0.0
+    conv_b = conv_s = total = 0
+    maxres = 0.0
+    for w0 in range(0, len(aqs), wave):
+        group = aqs[w0:w0 + wave]
+        engs = []
+        for p in group:
+            e = Engine(dev, stream=torch.cuda.Stream(device=dev))
+            e.load_problem(p, **opts)
+            engs.append(e)
+        forward_batch(engs, [p.times for p in group], allow_unconverged=True)       # warm (workspace, graphs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, stats = forward_batch(engs, [p.times for p in group], allow_unconverged=True)
+        torch.cuda.synchronize()
+        t_batch += time.perf_counter() - t0
+        conv_b += sum(st["n_converged"] for st in stats)
+        total += sum(st["n_shift_solves"] for st in stats)
+        maxres = max(maxres, max(st["max_true_residual"] for st in stats))
+        t0 = time.perf_counter()
+        for e, p in zip(engs, group):
+            e.forward(p.times, allow_unconverged=True)
+            conv_s += e.last_stats["n_converged"]
+        torch.cuda.synchronize()
+        t_seq += time.perf_counter() - t0
+        for e in engs:
+            e.close()
+        torch.cuda.empty_cache()
+    return {"value": conv_b / t_batch, "unit": "shifted solves/s", "workload": BATCH_WORKLOAD,
+            "sequential_value": conv_s / t_seq, "speedup_vs_sequential": (conv_b / t_batch) / (conv_s / t_seq),
+            "shifted_systems": total, "converged": conv_b, "max_true_residual": maxres,
+            "wave": wave, "seconds_batched": t_batch, "seconds_sequential": t_seq,
+            "timing": "host wall clock around each call, device synchronised"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -204,6 +252,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-jacobian", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--opts", default="", help="JSON dict overriding solver options (profiling runs)")
     ap.add_argument("--launch-list", action="store_true",
                     help="profiling only: run warmup + the timed steps, print nothing else")
@@ -336,6 +385,7 @@ def main():
             "bytes_per_unit": bpu, "units": work,
             "measured": "CUDA events around each launch of the class, in a separate pass of the same steps"}
     jac = None if args.no_jacobian else jacobian_rows(dev, stream)
+    bat = None if args.no_batch else batch_throughput(dev)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -355,7 +405,7 @@ def main():
                        "max_true_residual": tres, "outer_iters_max": max(iters),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (Krylov bases ~GBs per step)"},
-            "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(), "jacobian": jac,
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(), "jacobian": jac, "batch": bat,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": launches}
     print(json.dumps(line), flush=True)

@@ -149,6 +149,19 @@ int lt_set_options(lt_ctx* ctx, const lt_opts* opts);
 int lt_forward(lt_ctx* ctx, int nt, const double* times, double* h, int h_on_device, lt_stats* stats);
 
 /*
+ * Forward problems of n independent contexts (aquifers) solved together:
+ * h[i] receives context i's float64 [ns_i][nr_i][nt[i]] measurements (all HOST
+ * pointers if h_on_device == 0, else all DEVICE pointers); stats: NULL or an
+ * array of n.  Each context keeps its own grid, wells and options; the
+ * contexts' outer iterations are interleaved on their own streams so that the
+ * GPU runs the aquifers concurrently (the batching layer of the engine).
+ * Returns LT_ERR_NOT_CONVERGED if any context did not converge (all results
+ * written), another error code on the first failing context.
+ */
+int lt_forward_batch(int n, lt_ctx* const* ctxs, const int* nt, const double* const* times, double* const* h,
+                     int h_on_device, lt_stats* stats);
+
+/*
  * Fields phi_s(t) on every cell (Eq. half), float64 [ns][nt][ncell], HOST or DEVICE as flagged.
  * Same solves as lt_forward.
  */

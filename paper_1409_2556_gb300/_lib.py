@@ -62,6 +62,8 @@ EXPORTS = {
     "lt_set_receivers": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "lt_set_options": (C.c_int, [C.c_void_p, C.POINTER(LtOpts)]),
     "lt_forward": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(LtStats)]),
+    "lt_forward_batch": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                   C.c_void_p]),
     "lt_forward_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(LtStats)]),
     "lt_forward_fields": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(LtStats)]),
     "lt_adjoint_jacobian": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(LtStats)]),

@@ -694,9 +694,45 @@ static int ensure_ws(lt_ctx* ctx, const Plan& P) {
   return LT_OK;
 }
 
-// Runs the batched flexible shifted Krylov solves of a plan; leaves Y, U in the workspace.
-static int run_solves(lt_ctx* ctx, const Plan& P, std::vector<double>& true_res, lt_stats* st, int* nl,
-                      bool need_x = false) {
+// State of the batched flexible shifted Krylov solves of one context between
+// the stages below (begin: tables, workspace, graph capture; launch: enqueue
+// outer iterations; poll: read the active flags; end: back-substitution, x_k,
+// true residuals, statistics).  run_solves chains them for one context;
+// lt_forward_batch interleaves them over several contexts.
+struct SolveState {
+  int j = 0, cycles = 0, per_iter = 0;
+  bool use_graph = false, done = false;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t q = nullptr;
+  lt::Prof* pf = nullptr;
+  std::vector<int> act;
+};
+
+// one outer iteration of every active basis (kernels read j from bt.jdev)
+static int launch_iteration(lt_ctx* ctx, cudaStream_t q, int jj, int* nlq, lt::Prof* pf) {
+  const lt_opts& o = ctx->opts;
+  lt::Batch& bt = ctx->ws.bt;
+  const lt::Level& L0 = ctx->mg.h_levels[0];
+  lt::launch_prep_iter(bt, jj, q);
+  ++*nlq;
+  for (int r = 0; r < o.inner_rounds; ++r) {
+    lt::launch_exact_residual(bt, ctx->fe, L0, jj, r, 0, q, pf);
+    ++*nlq;
+    for (int cy = 0; cy < o.inner_cycles; ++cy)
+      if (lt::launch_vcycle(ctx->mg, bt, r, q, nlq, pf)) return LT_ERR_CUDA;
+    lt::launch_update_u(bt, L0, jj, r, q);
+    ++*nlq;
+  }
+  lt::launch_exact_residual(bt, ctx->fe, L0, jj, o.inner_rounds, 1, q, pf);
+  lt::launch_inner_record(bt, q);
+  *nlq += 2;
+  lt::launch_arnoldi(bt, ctx->fe, jj, q, nlq, pf);
+  lt::launch_shift_ls(bt, jj, q);
+  *nlq += 2;
+  return LT_OK;
+}
+
+static int solve_begin(lt_ctx* ctx, const Plan& P, SolveState& S, int* nl) {
   const lt_opts& o = ctx->opts;
   int rc = ensure_ws(ctx, P);
   if (rc) return rc;
@@ -751,75 +787,75 @@ static int run_solves(lt_ctx* ctx, const Plan& P, std::vector<double>& true_res,
   }
   lt::launch_init_batch(bt, s);
   *nl += 2;
-  std::vector<int> act(P.nb);
-  int j = 0, cycles = 0;
-  const lt::Level& L0 = ctx->mg.h_levels[0];
-  // one outer iteration of every active basis (kernels read j from bt.jdev)
-  auto iteration = [&](cudaStream_t q, int jj, int* nlq) -> int {
-    lt::launch_prep_iter(bt, jj, q);
-    ++*nlq;
-    for (int r = 0; r < o.inner_rounds; ++r) {
-      lt::launch_exact_residual(bt, ctx->fe, L0, jj, r, 0, q, pf);
-      ++*nlq;
-      for (int cy = 0; cy < o.inner_cycles; ++cy)
-        if (lt::launch_vcycle(ctx->mg, bt, r, q, nlq, pf)) return LT_ERR_CUDA;
-      lt::launch_update_u(bt, L0, jj, r, q);
-      ++*nlq;
-    }
-    lt::launch_exact_residual(bt, ctx->fe, L0, jj, o.inner_rounds, 1, q, pf);
-    lt::launch_inner_record(bt, q);
-    *nlq += 2;
-    lt::launch_arnoldi(bt, ctx->fe, jj, q, nlq, pf);
-    lt::launch_shift_ls(bt, jj, q);
-    *nlq += 2;
-    return LT_OK;
-  };
+  S = SolveState();
+  S.act.assign(P.nb, 1);
+  S.pf = pf;
   // CUDA graph replay (not while timing individual launches, and not inside
   // lt_forward_noalloc, whose contract excludes any device allocation)
-  const bool use_graph = o.graphs && pf == nullptr && ctx->arena_base == nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  cudaStream_t q = s;
-  int per_iter = 0;
-  if (use_graph) {
+  S.use_graph = o.graphs && pf == nullptr && ctx->arena_base == nullptr;
+  S.q = s;
+  if (S.use_graph) {
     if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     if (!ctx->ev_a) CK(cudaEventCreateWithFlags(&ctx->ev_a, cudaEventDisableTiming));
     if (!ctx->ev_b) CK(cudaEventCreateWithFlags(&ctx->ev_b, cudaEventDisableTiming));
-    q = ctx->cap_stream;
+    S.q = ctx->cap_stream;
     CK(cudaEventRecord(ctx->ev_a, s));
-    CK(cudaStreamWaitEvent(q, ctx->ev_a, 0));
+    CK(cudaStreamWaitEvent(S.q, ctx->ev_a, 0));
     cudaGraph_t graph = nullptr;
-    CK(cudaStreamBeginCapture(q, cudaStreamCaptureModeThreadLocal));
-    int rc2 = iteration(q, 0, &per_iter);
-    cudaError_t ec = cudaStreamEndCapture(q, &graph);
+    CK(cudaStreamBeginCapture(S.q, cudaStreamCaptureModeThreadLocal));
+    int rc2 = launch_iteration(ctx, S.q, 0, &S.per_iter, nullptr);
+    cudaError_t ec = cudaStreamEndCapture(S.q, &graph);
     if (rc2 || ec != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
       return fail(ctx, LT_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ec));
     }
-    ec = cudaGraphInstantiate(&gexec, graph, 0);
+    ec = cudaGraphInstantiate(&S.gexec, graph, 0);
     cudaGraphDestroy(graph);
     if (ec != cudaSuccess) return fail(ctx, LT_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ec));
   }
-  for (j = 0; j < o.maxit; ++j) {
-    if (use_graph) {
-      CK(cudaGraphLaunch(gexec, q));
-      *nl += per_iter;
-    } else if (iteration(s, j, nl)) {
+  return LT_OK;
+}
+
+// enqueue up to n outer iterations (no host synchronisation)
+static int solve_launch(lt_ctx* ctx, SolveState& S, int n, int* nl) {
+  const lt_opts& o = ctx->opts;
+  for (int k = 0; k < n && S.j < o.maxit && !S.done; ++k) {
+    if (S.use_graph) {
+      CK(cudaGraphLaunch(S.gexec, S.q));
+      *nl += S.per_iter;
+    } else if (launch_iteration(ctx, S.q, S.j, nl, S.pf)) {
       return fail(ctx, LT_ERR_CUDA, "kernel launch failed");
     }
-    cycles += o.inner_rounds * o.inner_cycles;
-    CK(cudaGetLastError());
-    if ((j + 1) % o.check_every == 0 || j + 1 == o.maxit) {
-      CK(cudaMemcpyAsync(act.data(), bt.active, P.nb * sizeof(int), cudaMemcpyDeviceToHost, q));
-      CK(cudaStreamSynchronize(q));
-      bool any = false;
-      for (int b = 0; b < P.nb; ++b) any |= act[b] != 0;
-      if (!any) { ++j; break; }
-    }
+    S.cycles += o.inner_rounds * o.inner_cycles;
+    ++S.j;
   }
-  if (use_graph) {
-    CK(cudaEventRecord(ctx->ev_b, q));
+  CK(cudaGetLastError());
+  return LT_OK;
+}
+
+// read the active flags (waits for the context's queued iterations)
+static int solve_poll(lt_ctx* ctx, const Plan& P, SolveState& S) {
+  CK(cudaMemcpyAsync(S.act.data(), ctx->ws.bt.active, P.nb * sizeof(int), cudaMemcpyDeviceToHost, S.q));
+  CK(cudaStreamSynchronize(S.q));
+  bool any = false;
+  for (int b = 0; b < P.nb; ++b) any |= S.act[b] != 0;
+  if (!any || S.j >= ctx->opts.maxit) S.done = true;
+  return LT_OK;
+}
+
+static int solve_end(lt_ctx* ctx, const Plan& P, SolveState& S, std::vector<double>& true_res, lt_stats* st,
+                     int* nl, bool need_x) {
+  const lt_opts& o = ctx->opts;
+  lt::Batch& bt = ctx->ws.bt;
+  cudaStream_t s = ctx->stream;
+  lt::Prof* pf = S.pf;
+  int rc = LT_OK;
+  const int cycles = S.cycles;
+  if (S.use_graph) {
+    CK(cudaEventRecord(ctx->ev_b, S.q));
     CK(cudaStreamWaitEvent(s, ctx->ev_b, 0));
-    cudaGraphExecDestroy(gexec);
+    cudaGraphExecDestroy(S.gexec);
+    S.gexec = nullptr;
   }
   // y per shift
   int* d_shb = nullptr;
@@ -894,6 +930,18 @@ static int run_solves(lt_ctx* ctx, const Plan& P, std::vector<double>& true_res,
   return LT_OK;
 }
 
+static int run_solves(lt_ctx* ctx, const Plan& P, std::vector<double>& true_res, lt_stats* st, int* nl,
+                      bool need_x = false) {
+  SolveState S;
+  int rc = solve_begin(ctx, P, S, nl);
+  if (rc) return rc;
+  while (!S.done) {
+    if ((rc = solve_launch(ctx, S, ctx->opts.check_every, nl))) return rc;
+    if ((rc = solve_poll(ctx, P, S))) return rc;
+  }
+  return solve_end(ctx, P, S, true_res, st, nl, need_x);
+}
+
 static void stats_reset(lt_stats* st, bool tr) {
   if (!st) return;
   memset(st, 0, sizeof(*st));
@@ -910,6 +958,9 @@ static int check_times(lt_ctx* ctx, int nt, const double* times) {
 }
 
 // forward driver shared by lt_forward and lt_forward_fields
+static int forward_finish(lt_ctx* ctx, const Plan& P, const std::vector<double>& tres, double* out, int on_device,
+                          int fields, lt_stats* st, int nl);
+
 static int forward_impl(lt_ctx* ctx, int nt, const double* times, double* out, int on_device, int fields,
                         lt_stats* st) {
   if (!ctx) return LT_ERR_INVALID_ARG;
@@ -927,6 +978,14 @@ static int forward_impl(lt_ctx* ctx, int nt, const double* times, double* out, i
   std::vector<double> tres;
   rc = run_solves(ctx, P, tres, st, &nl);
   if (rc) return rc;
+  return forward_finish(ctx, P, tres, out, on_device, fields, st, nl);
+}
+
+// quadrature-fused measurements (or fields) after the solves of a forward plan
+static int forward_finish(lt_ctx* ctx, const Plan& P, const std::vector<double>& tres, double* out, int on_device,
+                          int fields, lt_stats* st, int nl) {
+  int rc = LT_OK;
+  const int nt = P.nt;
   const int ns = (int)ctx->src.size(), nr = (int)ctx->rec.size();
   cudaStream_t s = ctx->stream;
   // quadrature items (s, t) and weights w_k Q_s / z_k
@@ -985,6 +1044,70 @@ extern "C" int lt_forward(lt_ctx* ctx, int nt, const double* times, double* h, i
 extern "C" int lt_forward_fields(lt_ctx* ctx, int nt, const double* times, double* phi, int on_device,
                                  lt_stats* st) {
   return forward_impl(ctx, nt, times, phi, on_device, 1, st);
+}
+
+// Forward solves of several independent contexts (one aquifer each) driven
+// together: every context replays its outer-iteration graph on its own
+// non-blocking stream, and the host enqueues a slab of iterations for every
+// unfinished context before it polls any of them, so the GPU overlaps the
+// aquifers' latency-bound kernel chains.
+extern "C" int lt_forward_batch(int n, lt_ctx* const* ctxs, const int* nt, const double* const* times,
+                                double* const* h, int h_on_device, lt_stats* stats) {
+  if (n < 1 || !ctxs || !nt || !times || !h) return LT_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    lt_ctx* ctx = ctxs[i];
+    if (!ctx) return LT_ERR_INVALID_ARG;
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == ctx) return fail(ctx, LT_ERR_INVALID_ARG, "context %d appears twice in the batch", i);
+    int rc = check_times(ctx, nt[i], times[i]);
+    if (rc) return rc;
+    if (ctx->src.empty() || ctx->rec.empty()) return fail(ctx, LT_ERR_STATE, "context %d: sources and receivers must be set", i);
+    if (!h[i]) return fail(ctx, LT_ERR_INVALID_ARG, "context %d: output pointer is null", i);
+  }
+  std::vector<Plan> P(n);
+  std::vector<SolveState> S(n);
+  std::vector<int> nl(n, 0);
+  for (int i = 0; i < n; ++i) {
+    lt_ctx* ctx = ctxs[i];
+    CK(cudaSetDevice(ctx->device));
+    stats_reset(stats ? &stats[i] : nullptr, ctx->opts.true_residual);
+    make_plan(ctx, nt[i], times[i], ctx->src, P[i]);
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    int rc = solve_begin(ctx, P[i], S[i], &nl[i]);
+    if (rc) return rc;
+  }
+  for (;;) {
+    bool any = false;
+    for (int i = 0; i < n; ++i) {
+      if (S[i].done) continue;
+      lt_ctx* ctx = ctxs[i];
+      CK(cudaSetDevice(ctx->device));
+      int rc = solve_launch(ctx, S[i], ctx->opts.check_every, &nl[i]);
+      if (rc) return rc;
+      any = true;
+    }
+    if (!any) break;
+    for (int i = 0; i < n; ++i) {
+      if (S[i].done) continue;
+      lt_ctx* ctx = ctxs[i];
+      CK(cudaSetDevice(ctx->device));
+      int rc = solve_poll(ctx, P[i], S[i]);
+      if (rc) return rc;
+    }
+  }
+  int worst = LT_OK;
+  for (int i = 0; i < n; ++i) {
+    lt_ctx* ctx = ctxs[i];
+    CK(cudaSetDevice(ctx->device));
+    std::vector<double> tres;
+    lt_stats* st = stats ? &stats[i] : nullptr;
+    int rc = solve_end(ctx, P[i], S[i], tres, st, &nl[i], false);
+    if (rc) return rc;
+    rc = forward_finish(ctx, P[i], tres, h[i], h_on_device, 0, st, nl[i]);
+    if (rc == LT_ERR_NOT_CONVERGED) worst = rc;
+    else if (rc) return rc;
+  }
+  return worst;
 }
 
 // Adjoint path (Sec. 5.2): one batch of bases for the sources and the
