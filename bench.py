@@ -182,7 +182,7 @@ def batch_throughput(dev, wave: int = 10):
     from paper_1409_2556_gb300 import Engine
     from paper_1409_2556_gb300.batch import forward_batch
     aqs = W.config5_aquifers()
-    opts = dict(tol=1e-10, maxit=120, inner_relax=1e-6, groups=2, check_every=4, mg_tile=1)
+    opts = dict(tol=1e-10, maxit=250, inner_relax=1e-6, groups=2, check_every=4, mg_tile=1)
     t_batch = t_seq = 0.0
     conv_b = conv_s = total = 0
     maxres = 0.0
@@ -401,7 +401,7 @@ def main():
             "config": {"workload": WORKLOAD_NAME, "shifted_systems_per_step": ns * nt * prob.Nz // 2,
                        "solver_tol": SOLVE_OPTS["tol"], "residual_bar": RESIDUAL_BAR,
                        "autotuned": {k: tuned[k] for k in ("mg_tile", "mg_pre", "mg_post", "inner_rounds",
-                                                             "inner_cycles")},
+                                                             "inner_cycles", "inner_relax")},
                        "max_true_residual": tres, "outer_iters_max": max(iters),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (Krylov bases ~GBs per step)"},

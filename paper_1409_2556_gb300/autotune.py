@@ -21,6 +21,7 @@ DEFAULT_GRID = {
     "mg_tile": [0, 1, 2],
     "sweeps": [(1, 1), (2, 2)],
     "inner": [(4, 6), (5, 4), (3, 8)],
+    "inner_relax": [1e-6, 1e-4],
 }
 
 
@@ -46,8 +47,11 @@ def autotune(engine, prob, base_opts: dict, grid: Optional[dict] = None, reps: i
     grid = grid or DEFAULT_GRID
     engine.load_problem(prob, **base_opts)
     best, best_ms = None, float("inf")
-    for tile, (pre, post), (rounds, cycles) in itertools.product(grid["mg_tile"], grid["sweeps"], grid["inner"]):
-        cand = dict(base_opts, mg_tile=tile, mg_pre=pre, mg_post=post, inner_rounds=rounds, inner_cycles=cycles)
+    relax = grid.get("inner_relax", [base_opts.get("inner_relax", 0.0)])
+    for tile, (pre, post), (rounds, cycles), rx in itertools.product(grid["mg_tile"], grid["sweeps"], grid["inner"],
+                                                                    relax):
+        cand = dict(base_opts, mg_tile=tile, mg_pre=pre, mg_post=post, inner_rounds=rounds, inner_cycles=cycles,
+                    inner_relax=rx)
         engine.set_options(**{k: v for k, v in cand.items() if k not in ("Nz", "tol", "groups")})
         ms = 0.0
         ok = True
@@ -57,7 +61,7 @@ def autotune(engine, prob, base_opts: dict, grid: Optional[dict] = None, reps: i
             ok &= st["n_converged"] == st["n_shift_solves"]
         ms = st["ms_total"]
         if verbose:
-            print(f"autotune tile={tile} sweeps={pre},{post} inner={rounds}x{cycles}: {ms:.1f} ms ok={ok}")
+            print(f"autotune tile={tile} sweeps={pre},{post} inner={rounds}x{cycles} relax={rx}: {ms:.1f} ms ok={ok}")
         if ok and ms < best_ms:
             best, best_ms = cand, ms
     if best is None:
