@@ -66,6 +66,7 @@ typedef struct {
                            projected residual of the basis), capped at inner_relax (inexact-Krylov relaxation) */
   int    graphs;        /* 1: replay one captured CUDA graph per outer iteration (default); 0: direct launches */
   int    mg_tile;       /* fused 2D smoother tile: 0 = 64x32, 1 = 32x32, 2 = 32x16 cells (default 2) */
+  int    precond;       /* 0: multigrid (default); 1: learned initial guess + multigrid (see lt_set_learned_preconditioner) */
 } lt_opts;
 
 /* kernel classes reported in lt_stats.work[] and selectable by lt_opts.timing_class */
@@ -212,6 +213,50 @@ int lt_adjoint_vjp(lt_ctx* ctx, int nt, const double* times, const double* g, do
  */
 #define LT_NOALLOC_SCRATCH_MAX (32u << 20)
 int lt_forward_noalloc(lt_ctx* ctx, int nt, const double* times, double* h, lt_stats* stats);
+
+/* ------------------------------------------------------------------------
+ * Learned preconditioner (spec extension; no counterpart in the paper):
+ * a small 2D U-Net (bf16 activations, tensor-core 3x3 convolutions, FP32
+ * accumulation) that maps a residual of (K + tau M) u = r to an initial guess
+ * for the multigrid iteration of the preconditioner solve.
+ * Inputs of the network, float32 [nimg][H][W][5] DEVICE: Re r / s, Im r / s,
+ * normalised log kappa, Re(tau) m / D, Im(tau) m / D (s = RMS of r, D = the
+ * operator's diagonal); output float32 [nimg][H][W][2] DEVICE: the direction of
+ * D u (unit RMS); the solver rescales it by the minimal-residual coefficient.
+ * H and W must be multiples of 8.  Status: 0 or a negative LT_ERR_* code.
+ * ------------------------------------------------------------------------ */
+typedef struct lt_unet lt_unet;
+int lt_unet_create(lt_unet** out, int device, unsigned long long seed);   /* He-initialised parameters */
+int lt_unet_num_params(lt_unet* net);
+int lt_unet_get_params(lt_unet* net, float* host, int n);    /* flat FP32: per layer W[9][cout][cin], b[cout] */
+int lt_unet_set_params(lt_unet* net, const float* host, int n);
+int lt_unet_forward(lt_unet* net, int nimg, int H, int W, const float* in, float* out);
+/* loss = mean (out - target)^2 over pixels and the 2 channels; grad_host (HOST, may be NULL) receives d loss / d params */
+int lt_unet_grad(lt_unet* net, int nimg, int H, int W, const float* in, const float* target, float* grad_host,
+                 double* loss);
+/* one Adam step (beta 0.9 / 0.999) on the batch */
+int lt_unet_train_step(lt_unet* net, int nimg, int H, int W, const float* in, const float* target, float lr,
+                       double* loss);
+const char* lt_unet_last_error(lt_unet* net);
+void lt_unet_destroy(lt_unet* net);
+
+/*
+ * Multigrid solves of (K + tau_i M) e_i = r_i on the context's grid: `cycles`
+ * V-cycles from e = 0 (the preconditioner of Sec. 3's Algorithm 1 applied on
+ * its own; used to generate training pairs).  tau: HOST float64 [nimg][2];
+ * r, e: DEVICE complex float32 [nimg][ncell][2].
+ */
+int lt_precond_apply(lt_ctx* ctx, int nimg, const double* tau, const float* r, float* e, int cycles);
+
+/*
+ * Attach a trained network (NULL detaches).  With lt_opts.precond = 1 every
+ * refinement round of a preconditioner solve starts its V-cycles from the
+ * network's guess (its direction scaled by the minimal-residual coefficient)
+ * instead of zero; a guess that removes less than 5% of the residual norm is
+ * dropped (multigrid fallback).  2D grids with nx, ny
+ * multiples of 8 only.  The network must stay alive while attached.
+ */
+int lt_set_learned_preconditioner(lt_ctx* ctx, lt_unet* net);
 
 /* Static description of a status code. */
 const char* lt_strerror(int status);

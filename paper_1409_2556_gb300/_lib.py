@@ -36,7 +36,7 @@ class LtOpts(C.Structure):
                 ("tau_project", C.c_int), ("groups", C.c_int), ("mg_pre", C.c_int), ("mg_post", C.c_int),
                 ("inner_cycles", C.c_int), ("inner_rounds", C.c_int), ("inner_tol", C.c_double),
                 ("true_residual", C.c_int), ("check_every", C.c_int), ("timing_class", C.c_int),
-                ("inner_relax", C.c_double), ("graphs", C.c_int), ("mg_tile", C.c_int)]
+                ("inner_relax", C.c_double), ("graphs", C.c_int), ("mg_tile", C.c_int), ("precond", C.c_int)]
 
 
 class LtStats(C.Structure):
@@ -69,6 +69,19 @@ EXPORTS = {
     "lt_adjoint_jacobian": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(LtStats)]),
     "lt_adjoint_vjp": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                  C.POINTER(LtStats)]),
+    "lt_unet_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_ulonglong]),
+    "lt_unet_num_params": (C.c_int, [C.c_void_p]),
+    "lt_unet_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "lt_unet_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "lt_unet_forward": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "lt_unet_grad": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.POINTER(C.c_double)]),
+    "lt_unet_train_step": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_float,
+                                     C.POINTER(C.c_double)]),
+    "lt_unet_last_error": (C.c_char_p, [C.c_void_p]),
+    "lt_unet_destroy": (None, [C.c_void_p]),
+    "lt_precond_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "lt_set_learned_preconditioner": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lt_strerror": (C.c_char_p, [C.c_int]),
     "lt_last_error": (C.c_char_p, [C.c_void_p]),
     "lt_destroy": (None, [C.c_void_p]),

@@ -98,6 +98,15 @@ struct lt_ctx {
   // non-blocking stream on which the per-iteration CUDA graph is captured and replayed
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+  // learned initial guess (opts.precond = 1)
+  lt_unet* net = nullptr;
+  float *d_lk = nullptr, *d_mD = nullptr, *d_xin = nullptr, *d_gn2 = nullptr;
+  size_t xin_cap = 0;
+  // workspace of lt_precond_apply
+  std::vector<void*> pc_allocs;
+  int pc_nb = 0;
+  lt::Batch pc_bt{};
+  lt::MGHost pc_mg{};
 };
 
 static int fail(lt_ctx* ctx, int code, const char* fmt, ...) {
@@ -170,6 +179,7 @@ int lt_default_options(lt_opts* o) {
   o->inner_relax = 0.0;
   o->graphs = 1;
   o->mg_tile = 2;
+  o->precond = 0;
   return LT_OK;
 }
 
@@ -230,6 +240,11 @@ void lt_destroy(lt_ctx* ctx) {
   if (ctx->ev_a) cudaEventDestroy(ctx->ev_a);
   if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  free_list(ctx->pc_allocs);          // also holds pc_mg.d_levels
+  ctx->pc_mg.d_levels = nullptr;
+  for (float* p : {ctx->d_lk, ctx->d_mD, ctx->d_xin, ctx->d_gn2})
+    if (p) cudaFree(p);
+  cudaGetLastError();                  // leave no error state behind for other users of the runtime
   delete ctx;
 }
 
@@ -248,6 +263,7 @@ int lt_set_options(lt_ctx* ctx, const lt_opts* o) {
   if (o->inner_tol < 0.0 || o->inner_tol >= 1.0) return fail(ctx, LT_ERR_INVALID_ARG, "inner_tol=%g", o->inner_tol);
   if (o->check_every < 1) return fail(ctx, LT_ERR_INVALID_ARG, "check_every=%d", o->check_every);
   if (o->mg_tile < 0 || o->mg_tile > 2) return fail(ctx, LT_ERR_INVALID_ARG, "mg_tile=%d must be 0, 1 or 2", o->mg_tile);
+  if (o->precond != 0 && o->precond != 1) return fail(ctx, LT_ERR_INVALID_ARG, "precond=%d must be 0 or 1", o->precond);
   if (o->graphs != 0 && o->graphs != 1) return fail(ctx, LT_ERR_INVALID_ARG, "graphs=%d must be 0 or 1", o->graphs);
   if (!(o->inner_relax >= 0.0 && o->inner_relax < 1.0))
     return fail(ctx, LT_ERR_INVALID_ARG, "inner_relax=%g must be in [0,1)", o->inner_relax);
@@ -387,6 +403,13 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
   free_list(ctx->grid_allocs);
   if (ctx->mg.d_levels) { cudaFree(ctx->mg.d_levels); ctx->mg.d_levels = nullptr; }
   ctx->have_grid = false;
+  for (float** p : {&ctx->d_lk, &ctx->d_mD}) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  free_list(ctx->pc_allocs);
+  ctx->pc_mg.d_levels = nullptr;
+  ctx->pc_nb = 0;
   ctx->nx = nx; ctx->ny = ny; ctx->nz = nz; ctx->N = N;
   ctx->dx = dx; ctx->dy = dy; ctx->dz = dz;
   for (int d = 0; d < 6; ++d) ctx->bc[d] = bc[d];
@@ -718,6 +741,10 @@ static int launch_iteration(lt_ctx* ctx, cudaStream_t q, int jj, int* nlq, lt::P
   for (int r = 0; r < o.inner_rounds; ++r) {
     lt::launch_exact_residual(bt, ctx->fe, L0, jj, r, 0, q, pf);
     ++*nlq;
+    if (o.precond == 1) {
+      learned_guess(ctx->net, bt, L0, r, ctx->d_lk, ctx->d_mD, ctx->d_xin, ctx->d_gn2, q);
+      *nlq += 24;
+    }
     for (int cy = 0; cy < o.inner_cycles; ++cy)
       if (lt::launch_vcycle(ctx->mg, bt, r, q, nlq, pf)) return LT_ERR_CUDA;
     lt::launch_update_u(bt, L0, jj, r, q);
@@ -787,6 +814,38 @@ static int solve_begin(lt_ctx* ctx, const Plan& P, SolveState& S, int* nl) {
   }
   lt::launch_init_batch(bt, s);
   *nl += 2;
+  if (o.precond == 1) {
+    if (!ctx->net) return fail(ctx, LT_ERR_STATE, "precond = 1 needs lt_set_learned_preconditioner");
+    if (ctx->arena_base) return fail(ctx, LT_ERR_INVALID_ARG, "the learned preconditioner allocates; not available here");
+    if (ctx->nz != 1 || ctx->nx % 8 || ctx->ny % 8)
+      return fail(ctx, LT_ERR_INVALID_ARG, "the learned preconditioner needs a 2D grid with nx, ny multiples of 8");
+    if (learned_prepare(ctx->net, P.nb, ctx->ny, ctx->nx)) return fail(ctx, LT_ERR_OOM, "network workspace");
+    size_t need = (size_t)P.nb * ctx->N * 5;
+    if (ctx->xin_cap < need) {
+      if (ctx->d_xin) cudaFree(ctx->d_xin);
+      if (ctx->d_gn2) cudaFree(ctx->d_gn2);
+      CK(cudaMalloc(&ctx->d_xin, need * sizeof(float)));
+      CK(cudaMalloc(&ctx->d_gn2, (size_t)P.nb * 64 * sizeof(float)));
+      ctx->xin_cap = need;
+    }
+    if (!ctx->d_lk) {
+      std::vector<float> lk(ctx->N), mD(ctx->N);
+      double mu = 0, var = 0;
+      for (int64_t c = 0; c < ctx->N; ++c) mu += std::log(ctx->kappa[c]);
+      mu /= ctx->N;
+      for (int64_t c = 0; c < ctx->N; ++c) var += std::pow(std::log(ctx->kappa[c]) - mu, 2);
+      double sd = std::sqrt(var / ctx->N);
+      if (sd < 1e-12) sd = 1.0;
+      for (int64_t c = 0; c < ctx->N; ++c) {
+        lk[c] = (float)((std::log(ctx->kappa[c]) - mu) / sd);
+        mD[c] = (float)(ctx->hl[0].m[c] / ctx->hl[0].D[c]);
+      }
+      CK(cudaMalloc(&ctx->d_lk, ctx->N * sizeof(float)));
+      CK(cudaMalloc(&ctx->d_mD, ctx->N * sizeof(float)));
+      CK(cudaMemcpy(ctx->d_lk, lk.data(), ctx->N * sizeof(float), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(ctx->d_mD, mD.data(), ctx->N * sizeof(float), cudaMemcpyHostToDevice));
+    }
+  }
   S = SolveState();
   S.act.assign(P.nb, 1);
   S.pf = pf;
@@ -1238,6 +1297,81 @@ extern "C" int lt_adjoint_vjp(lt_ctx* ctx, int nt, const double* times, const do
   return adjoint_impl(ctx, nt, times, nullptr, g, grad, h, on_device, 1, st);
 }
 
+// ------------------------------------------------------------------ preconditioner apply (training pairs)
+extern "C" int lt_set_learned_preconditioner(lt_ctx* ctx, lt_unet* net) {
+  if (!ctx) return LT_ERR_INVALID_ARG;
+  ctx->net = net;
+  return LT_OK;
+}
+
+extern "C" int lt_precond_apply(lt_ctx* ctx, int nimg, const double* tau, const float* r, float* e, int cycles) {
+  if (!ctx) return LT_ERR_INVALID_ARG;
+  if (!ctx->have_grid) return fail(ctx, LT_ERR_STATE, "lt_setup_grid must come first");
+  if (nimg < 1 || nimg > 4096 || !tau || !r || !e || cycles < 1 || cycles > 1000)
+    return fail(ctx, LT_ERR_INVALID_ARG, "bad lt_precond_apply arguments");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  const HostLevel& Lc = ctx->hl.back();
+  const size_t nc2 = ctx->mg.coarse_direct ? (size_t)Lc.N * Lc.N : 0;
+  lt::Batch& bt = ctx->pc_bt;
+  lt::MGHost& mg = ctx->pc_mg;
+  if (ctx->pc_nb < nimg) {
+    CK(cudaStreamSynchronize(s));
+    free_list(ctx->pc_allocs);
+    ctx->pc_mg.d_levels = nullptr;
+    int rc;
+    auto& A = ctx->pc_allocs;
+#define AL(p, n) if ((rc = dalloc(ctx, A, &p, (size_t)(n)))) return rc
+    AL(bt.active, nimg); AL(bt.rnorm2, nimg); AL(bt.itol2, nimg); AL(bt.tau_cur, nimg); AL(bt.tau_slot, nimg);
+    AL(bt.work, 16);
+    if (nc2) AL(bt.coarse_inv, nimg * nc2);
+    mg = ctx->mg;
+    for (int l = 0; l < mg.nlev; ++l) {
+      AL(mg.h_levels[l].u, (size_t)nimg * mg.h_levels[l].N);
+      AL(mg.h_levels[l].f, (size_t)nimg * mg.h_levels[l].N);
+    }
+    lt::Level* dl = nullptr;
+    AL(dl, lt::kMaxLevels);
+#undef AL
+    mg.d_levels = nullptr;
+    CK(cudaMemcpy(dl, mg.h_levels, sizeof(lt::Level) * mg.nlev, cudaMemcpyHostToDevice));
+    mg.d_levels = dl;
+    ctx->pc_nb = nimg;
+  }
+  mg.npre = ctx->opts.mg_pre; mg.npost = ctx->opts.mg_post; mg.tile = ctx->opts.mg_tile;
+  bt.nb = nimg;
+  bt.rounds = 0;
+  bt.coarse_direct = ctx->mg.coarse_direct;
+  std::vector<int> ones(nimg, 1), slots(nimg);
+  std::vector<double> big(nimg, 1e300), zero(nimg, 0.0);
+  std::vector<double2> t2(nimg);
+  std::vector<float2> inv32(nimg * nc2);
+  for (int i = 0; i < nimg; ++i) {
+    t2[i] = make_double2(tau[2 * i], tau[2 * i + 1]);
+    slots[i] = i;
+    if (nc2) {
+      std::vector<cplx> inv;
+      if (!dense_inverse(Lc, cplx(tau[2 * i], tau[2 * i + 1]), inv)) return fail(ctx, LT_ERR_INVALID_ARG, "singular coarse operator");
+      for (size_t q = 0; q < nc2; ++q) inv32[i * nc2 + q] = make_float2((float)inv[q].real(), (float)inv[q].imag());
+    }
+  }
+  CK(cudaMemcpyAsync(bt.active, ones.data(), nimg * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(bt.rnorm2, big.data(), nimg * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(bt.itol2, zero.data(), nimg * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(bt.tau_cur, t2.data(), nimg * sizeof(double2), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(bt.tau_slot, slots.data(), nimg * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (nc2) CK(cudaMemcpyAsync(bt.coarse_inv, inv32.data(), inv32.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+  const lt::Level& L0 = mg.h_levels[0];
+  CK(cudaMemcpyAsync(L0.f, r, (size_t)nimg * L0.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(L0.u, 0, (size_t)nimg * L0.N * sizeof(float2), s));
+  int nl = 0;
+  for (int c = 0; c < cycles; ++c)
+    if (lt::launch_vcycle(mg, bt, 0, s, &nl, nullptr)) return fail(ctx, LT_ERR_CUDA, "V-cycle launch failed");
+  CK(cudaMemcpyAsync(e, L0.u, (size_t)nimg * L0.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return LT_OK;
+}
+
 // ------------------------------------------------------------------ no-allocation forward
 // Some callers cannot let a library call cudaMalloc/cudaFree: services that
 // hand all device memory to their own pool allocator up front (a library
@@ -1283,6 +1417,7 @@ extern "C" int lt_forward_noalloc(lt_ctx* ctx, int nt, const double* times, doub
   if (rc) return rc;
   if (ctx->src.empty() || ctx->rec.empty()) return fail(ctx, LT_ERR_STATE, "sources and receivers must be set");
   if (!h) return fail(ctx, LT_ERR_INVALID_ARG, "h (device pointer) is null");
+  if (ctx->opts.precond != 0) return fail(ctx, LT_ERR_INVALID_ARG, "lt_forward_noalloc supports only precond = 0");
   if (ctx->device < 0 || ctx->device >= 256) return fail(ctx, LT_ERR_INVALID_ARG, "device ordinal out of range");
   CK(cudaSetDevice(ctx->device));
   void* base = nullptr;

@@ -64,3 +64,10 @@ void launch_true_res(const Batch& bt, const FineExact& fe, const int* sh_basis, 
                      const float2* X_lo, double* res2, cudaStream_t st, Prof* pf);
 
 }  // namespace lt
+
+// -------- unet.cu (learned initial guess of the preconditioner solves)
+struct lt_unet;
+int learned_prepare(lt_unet* u, int nb, int ny, int nx);
+void learned_guess(lt_unet* u, const lt::Batch& bt, const lt::Level& L0, int round, const float* lk, const float* mD,
+                   float* xin, float* gnorm2, cudaStream_t q);
+

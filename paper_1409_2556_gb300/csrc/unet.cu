@@ -1,0 +1,712 @@
+// unet.cu -- small 2D U-Net used as a learned initial guess for the
+// preconditioner solves (K + tau M) u = r (the multigrid V-cycle stays as the
+// convergent iteration and the fallback).
+//
+// Activations are NHWC bfloat16, convolutions 3x3 (padding 1) run on the
+// tensor cores with mma.sync m16n8k16 bf16 -> f32 as implicit GEMMs
+// (M = pixels, N = output channels, K = 9 taps x input channels); the
+// backward-data pass is the same kernel with spatially flipped, transposed
+// weights; the weight gradient is an FP32 reduction over pixels.
+// Parameters are FP32 masters with Adam; bf16 copies feed the kernels.
+//
+// Network (base width c = 16, channel counts padded to multiples of 16):
+//   enc0: conv(16->c) relu, conv(c->c) relu = s0        (input: 5 channels padded to 16)
+//   enc1: pool, conv(c->2c) relu, conv(2c->2c) relu = s1
+//   enc2: pool, conv(2c->2c) relu, conv(2c->2c) relu = s2
+//   bott: pool, conv(2c->4c) relu, conv(4c->4c) relu = b
+//   dec2: up(b) ++ s2 -> conv(6c->2c) relu, conv(2c->2c) relu = d2
+//   dec1: up(d2) ++ s1 -> conv(4c->2c) relu, conv(2c->2c) relu = d1
+//   dec0: up(d1) ++ s0 -> conv(3c->c) relu, conv(c->c) relu = d0
+//   out : conv(c->16) linear (channels 0, 1 used)
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "lt_internal.h"
+
+namespace lt {
+
+using bf16 = __nv_bfloat16;
+
+// ------------------------------------------------------------------ layer table
+struct ConvSpec { int cin, cout, relu; };
+static const ConvSpec kLayers[15] = {
+    {16, 16, 1}, {16, 16, 1},      // enc0
+    {16, 32, 1}, {32, 32, 1},      // enc1
+    {32, 32, 1}, {32, 32, 1},      // enc2
+    {32, 64, 1}, {64, 64, 1},      // bottleneck
+    {96, 32, 1}, {32, 32, 1},      // dec2
+    {64, 32, 1}, {32, 32, 1},      // dec1
+    {48, 16, 1}, {16, 16, 1},      // dec0
+    {16, 16, 0}};                  // output (linear)
+constexpr int kNumLayers = 15;
+constexpr int kInChannels = 5;     // re r, im r, log kappa (normalised), Re(tau) m/D, Im(tau) m/D
+constexpr int kOutChannels = 2;
+
+// ------------------------------------------------------------------ tensor-core 3x3 convolution
+__device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// out[img][p][co] = act(bias[co] + sum_{tap,ci} in[img][p + off(tap)][ci] * W[tap][co][ci])
+// in: [nimg][H][W][cin] (cin % 16 == 0), W: [9][cout][cin], cout % 8 == 0, cout <= 64.
+// One warp = 16 consecutive pixels x all output channels; 4 warps per CTA.
+template <int NT>   // number of 8-wide output-channel tiles (cout / 8)
+__global__ void __launch_bounds__(128) k_conv3x3(const bf16* __restrict__ in, const bf16* __restrict__ Wt,
+                                                 const float* __restrict__ bias, bf16* out_bf, float* out_f,
+                                                 int H, int Wd, int cin, int relu) {
+  const int img = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tg = lane & 3;
+  const int HW = H * Wd;
+  const int p0 = (blockIdx.x * 4 + warp) * 16;
+  if (p0 >= HW) return;
+  const int cout = NT * 8;
+  const bf16* inb = in + (size_t)img * HW * cin;
+  float acc[NT][4];
+#pragma unroll
+  for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+  const int pa = p0 + g, pb = p0 + g + 8;
+  const int ya = pa / Wd, xa = pa % Wd, yb = pb / Wd, xb = pb % Wd;
+  for (int tap = 0; tap < 9; ++tap) {
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const int yya = ya + dy, xxa = xa + dx, yyb = yb + dy, xxb = xb + dx;
+    const bool va = pa < HW && yya >= 0 && yya < H && xxa >= 0 && xxa < Wd;
+    const bool vb = pb < HW && yyb >= 0 && yyb < H && xxb >= 0 && xxb < Wd;
+    const bf16* ra = inb + (size_t)(yya * Wd + xxa) * cin;
+    const bf16* rb = inb + (size_t)(yyb * Wd + xxb) * cin;
+    const bf16* wt = Wt + (size_t)tap * cout * cin;
+    for (int c0 = 0; c0 < cin; c0 += 16) {
+      uint32_t a[4];
+      a[0] = va ? ld32(ra + c0 + tg * 2) : 0u;
+      a[1] = vb ? ld32(rb + c0 + tg * 2) : 0u;
+      a[2] = va ? ld32(ra + c0 + 8 + tg * 2) : 0u;
+      a[3] = vb ? ld32(rb + c0 + 8 + tg * 2) : 0u;
+#pragma unroll
+      for (int n = 0; n < NT; ++n) {
+        const bf16* wr = wt + (size_t)(n * 8 + g) * cin + c0;
+        uint32_t b[2] = {ld32(wr + tg * 2), ld32(wr + 8 + tg * 2)};
+        mma_bf16(acc[n], a, b);
+      }
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < NT; ++n) {
+    const int co = n * 8 + tg * 2;
+    float b0 = bias ? bias[co] : 0.f, b1 = bias ? bias[co + 1] : 0.f;
+    float v[4] = {acc[n][0] + b0, acc[n][1] + b1, acc[n][2] + b0, acc[n][3] + b1};
+    if (relu)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = fmaxf(v[q], 0.f);
+    if (pa < HW) {
+      size_t o = ((size_t)img * HW + pa) * cout + co;
+      if (out_bf) { out_bf[o] = __float2bfloat16(v[0]); out_bf[o + 1] = __float2bfloat16(v[1]); }
+      if (out_f) { out_f[o] = v[0]; out_f[o + 1] = v[1]; }
+    }
+    if (pb < HW) {
+      size_t o = ((size_t)img * HW + pb) * cout + co;
+      if (out_bf) { out_bf[o] = __float2bfloat16(v[2]); out_bf[o + 1] = __float2bfloat16(v[3]); }
+      if (out_f) { out_f[o] = v[2]; out_f[o + 1] = v[3]; }
+    }
+  }
+}
+
+static void conv3x3(const bf16* in, const bf16* Wt, const float* bias, bf16* out_bf, float* out_f, int nimg, int H,
+                    int Wd, int cin, int cout, int relu, cudaStream_t st) {
+  dim3 g((H * Wd + 63) / 64, nimg);
+  switch (cout / 8) {
+    case 2: k_conv3x3<2><<<g, 128, 0, st>>>(in, Wt, bias, out_bf, out_f, H, Wd, cin, relu); break;
+    case 4: k_conv3x3<4><<<g, 128, 0, st>>>(in, Wt, bias, out_bf, out_f, H, Wd, cin, relu); break;
+    case 6: k_conv3x3<6><<<g, 128, 0, st>>>(in, Wt, bias, out_bf, out_f, H, Wd, cin, relu); break;
+    case 8: k_conv3x3<8><<<g, 128, 0, st>>>(in, Wt, bias, out_bf, out_f, H, Wd, cin, relu); break;
+    case 12: k_conv3x3<12><<<g, 128, 0, st>>>(in, Wt, bias, out_bf, out_f, H, Wd, cin, relu); break;
+    default: break;
+  }
+}
+
+// dW[tap][co][ci] += sum_p gout[p][co] * in[p + off(tap)][ci]; db[co] += sum_p gout[p][co]   (FP32)
+__global__ void k_conv_wgrad(const bf16* __restrict__ in, const bf16* __restrict__ gout, float* dW, float* db, int H,
+                             int Wd, int cin, int cout, int chunk) {
+  const int img = blockIdx.z;
+  const int HW = H * Wd;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nw = 9 * cout * cin;
+  if (idx >= nw + cout) return;
+  const int pbeg = blockIdx.y * chunk, pend = min(HW, pbeg + chunk);
+  const bf16* inb = in + (size_t)img * HW * cin;
+  const bf16* gb = gout + (size_t)img * HW * cout;
+  float acc = 0.f;
+  if (idx < nw) {
+    const int ci = idx % cin, co = (idx / cin) % cout, tap = idx / (cin * cout);
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    for (int p = pbeg; p < pend; ++p) {
+      int y = p / Wd + dy, x = p % Wd + dx;
+      if (y < 0 || y >= H || x < 0 || x >= Wd) continue;
+      acc += __bfloat162float(gb[(size_t)p * cout + co]) * __bfloat162float(inb[(size_t)(y * Wd + x) * cin + ci]);
+    }
+    atomicAdd(&dW[idx], acc);
+  } else {
+    const int co = idx - nw;
+    for (int p = pbeg; p < pend; ++p) acc += __bfloat162float(gb[(size_t)p * cout + co]);
+    atomicAdd(&db[co], acc);
+  }
+}
+
+// Wflip[tap][ci][co] = W[8 - tap][co][ci]   (backward-data weights)
+__global__ void k_flip_weights(const bf16* W, bf16* Wf, int cin, int cout) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 9 * cin * cout) return;
+  int co = idx % cout, ci = (idx / cout) % cin, tap = idx / (cout * cin);
+  Wf[idx] = W[((size_t)(8 - tap) * cout + co) * cin + ci];
+}
+
+// ------------------------------------------------------------------ elementwise helpers (NHWC)
+__global__ void k_pool2(const bf16* in, bf16* out, int H, int Wd, int C, int nimg) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int h = H / 2, w = Wd / 2;
+  size_t n = (size_t)nimg * h * w * C;
+  if (idx >= n) return;
+  int c = idx % C;
+  size_t pix = idx / C;
+  int x = pix % w, y = (pix / w) % h, img = pix / ((size_t)w * h);
+  const bf16* b = in + (size_t)img * H * Wd * C;
+  float s = __bfloat162float(b[((size_t)(2 * y) * Wd + 2 * x) * C + c]) +
+            __bfloat162float(b[((size_t)(2 * y) * Wd + 2 * x + 1) * C + c]) +
+            __bfloat162float(b[((size_t)(2 * y + 1) * Wd + 2 * x) * C + c]) +
+            __bfloat162float(b[((size_t)(2 * y + 1) * Wd + 2 * x + 1) * C + c]);
+  out[idx] = __float2bfloat16(0.25f * s);
+}
+
+// gin (fine, FP32 accumulate) += 0.25 * gout (coarse)
+__global__ void k_pool2_bwd(const float* gout, float* gin, int H, int Wd, int C, int nimg) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t n = (size_t)nimg * H * Wd * C;
+  if (idx >= n) return;
+  int c = idx % C;
+  size_t pix = idx / C;
+  int x = pix % Wd, y = (pix / Wd) % H, img = pix / ((size_t)Wd * H);
+  gin[idx] += 0.25f * gout[(((size_t)img * (H / 2) + y / 2) * (Wd / 2) + x / 2) * C + c];
+}
+
+// out[:, :, :, 0:C1] = up2(a) (coarse a, nearest), out[..., C1:C1+C2] = b
+__global__ void k_up_cat(const bf16* a, const bf16* b, bf16* out, int H, int Wd, int C1, int C2, int nimg) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int C = C1 + C2;
+  size_t n = (size_t)nimg * H * Wd * C;
+  if (idx >= n) return;
+  int c = idx % C;
+  size_t pix = idx / C;
+  int x = pix % Wd, y = (pix / Wd) % H, img = pix / ((size_t)Wd * H);
+  if (c < C1) out[idx] = a[(((size_t)img * (H / 2) + y / 2) * (Wd / 2) + x / 2) * C1 + c];
+  else out[idx] = b[pix * C2 + (c - C1)];
+}
+
+// split gradient of the concat: ga (coarse, FP32 +=) gets the up-sampled part summed, gb (fine, FP32 +=)
+__global__ void k_up_cat_bwd(const float* g, float* ga, float* gb, int H, int Wd, int C1, int C2, int nimg) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int C = C1 + C2;
+  size_t n = (size_t)nimg * H * Wd * C;
+  if (idx >= n) return;
+  int c = idx % C;
+  size_t pix = idx / C;
+  int x = pix % Wd, y = (pix / Wd) % H, img = pix / ((size_t)Wd * H);
+  if (c < C1) atomicAdd(&ga[(((size_t)img * (H / 2) + y / 2) * (Wd / 2) + x / 2) * C1 + c], g[idx]);
+  else gb[pix * C2 + (c - C1)] += g[idx];
+}
+
+// gbf = bf16(g * (y > 0)) for a ReLU output y (or plain conversion when relu == 0)
+__global__ void k_relu_mask(const float* g, const bf16* y, bf16* gbf, size_t n, int relu) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  float v = g[idx];
+  if (relu && __bfloat162float(y[idx]) <= 0.f) v = 0.f;
+  gbf[idx] = __float2bfloat16(v);
+}
+
+__global__ void k_to_f32(const float* in_dummy, const bf16* in, float* out, size_t n) {
+  (void)in_dummy;
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < n) out[idx] = __bfloat162float(in[idx]);
+}
+
+// FP32 [nimg][HW][5] -> bf16 [nimg][HW][16] (zero padded)
+__global__ void k_pack_input(const float* in, bf16* x, size_t npix) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= npix * 16) return;
+  int c = idx % 16;
+  size_t p = idx / 16;
+  x[idx] = __float2bfloat16(c < kInChannels ? in[p * kInChannels + c] : 0.f);
+}
+
+// loss = mean over pixels and the 2 used channels of (out - target)^2; grad (FP32, [npix][16]) = d loss / d out
+__global__ void k_mse(const float* out, const float* target, float* grad, double* loss, size_t npix, float scale) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float l = 0.f;
+  if (idx < npix * 16) {
+    int c = idx % 16;
+    size_t p = idx / 16;
+    float gval = 0.f;
+    if (c < kOutChannels) {
+      float d = out[idx] - target[p * kOutChannels + c];
+      l = d * d;
+      gval = 2.f * d * scale;
+    }
+    grad[idx] = gval;
+  }
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if ((threadIdx.x & 31) == 0 && l != 0.f) atomicAdd(loss, (double)l);
+}
+
+__global__ void k_adam(float* w, const float* g, float* m, float* v, bf16* wb, size_t n, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float gi = g[i];
+  float mi = b1 * m[i] + (1.f - b1) * gi;
+  float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  w[i] = wi;
+  wb[i] = __float2bfloat16(wi);
+}
+
+__global__ void k_f32_to_bf16(const float* a, bf16* b, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __float2bfloat16(a[i]);
+}
+
+}  // namespace lt
+
+// ==================================================================== host side
+using lt::bf16;
+using lt::kNumLayers;
+
+struct lt_unet {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // parameters: per layer W[9][cout][cin] then b[cout], FP32 masters
+  std::vector<size_t> woff, boff;
+  size_t nparams = 0;
+  float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+  bf16 *wb = nullptr, *wflip = nullptr;
+  int step = 0;
+  // activation workspace
+  int cap_img = 0, cap_H = 0, cap_W = 0;
+  std::vector<void*> acts;
+  bf16* A[32] = {};     // bf16 activations
+  float* G[32] = {};    // FP32 gradients
+  bf16* gbf = nullptr;  // bf16 masked gradient scratch
+  float* outf = nullptr;
+  float* gout = nullptr;
+  double* dloss = nullptr;
+};
+
+static size_t unet_npix(int nimg, int H, int W, int lvl) { return (size_t)nimg * (H >> lvl) * (W >> lvl); }
+
+// activation slots (level, channels)
+enum {
+  X0 = 0, A1, S0, P0, A3, S1, P1, A5, S2, P2, A7, BB, C2, A9, D2, C1, A11, D1, C0, A13, D0, NSLOT
+};
+static const int kSlotLvl[NSLOT] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 2, 2, 2, 1, 1, 1, 0, 0, 0};
+static const int kSlotC[NSLOT] = {16, 16, 16, 16, 32, 32, 32, 32, 32, 32, 64, 64, 96, 32, 32, 64, 32, 32, 48, 16, 16};
+
+static int unet_fail(lt_unet* u, int code, const char* msg) {
+  if (u) u->err = msg;
+  return code;
+}
+
+static int unet_ensure(lt_unet* u, int nimg, int H, int W) {
+  if (nimg <= u->cap_img && H == u->cap_H && W == u->cap_W) return 0;
+  for (void* p : u->acts) cudaFree(p);
+  u->acts.clear();
+  for (int s = 0; s < NSLOT; ++s) {
+    size_t n = unet_npix(nimg, H, W, kSlotLvl[s]) * kSlotC[s];
+    if (cudaMalloc(&u->A[s], n * sizeof(bf16)) != cudaSuccess) return -2;
+    if (cudaMalloc(&u->G[s], n * sizeof(float)) != cudaSuccess) return -2;
+    u->acts.push_back(u->A[s]);
+    u->acts.push_back(u->G[s]);
+  }
+  size_t n0 = unet_npix(nimg, H, W, 0) * 96;
+  if (cudaMalloc(&u->gbf, n0 * sizeof(bf16)) != cudaSuccess) return -2;
+  u->acts.push_back(u->gbf);
+  if (cudaMalloc(&u->outf, unet_npix(nimg, H, W, 0) * 16 * sizeof(float)) != cudaSuccess) return -2;
+  u->acts.push_back(u->outf);
+  if (cudaMalloc(&u->gout, unet_npix(nimg, H, W, 0) * 16 * sizeof(float)) != cudaSuccess) return -2;
+  u->acts.push_back(u->gout);
+  u->cap_img = nimg;
+  u->cap_H = H;
+  u->cap_W = W;
+  return 0;
+}
+
+// layer l: input slot, output slot, level
+static const int kLIn[15] = {X0, A1, P0, A3, P1, A5, P2, A7, C2, A9, C1, A11, C0, A13, D0};
+static const int kLOut[15] = {A1, S0, A3, S1, A5, S2, A7, BB, A9, D2, A11, D1, A13, D0, -1};
+static const int kLLvl[15] = {0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0, 0};
+
+static inline unsigned nblk(size_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+static void unet_forward_dev(lt_unet* u, int nimg, int H, int W) {
+  cudaStream_t st = u->stream;
+  auto conv = [&](int l) {
+    const lt::ConvSpec& c = lt::kLayers[l];
+    int h = H >> kLLvl[l], w = W >> kLLvl[l];
+    bf16* out = kLOut[l] >= 0 ? u->A[kLOut[l]] : nullptr;
+    float* outf = kLOut[l] >= 0 ? nullptr : u->outf;
+    lt::conv3x3(u->A[kLIn[l]], u->wb + u->woff[l], u->w + u->boff[l], out, outf, nimg, h, w, c.cin, c.cout, c.relu, st);
+  };
+  auto pool = [&](int src, int dst) {
+    int lv = kSlotLvl[src];
+    size_t n = unet_npix(nimg, H, W, lv + 1) * kSlotC[src];
+    lt::k_pool2<<<nblk(n), 256, 0, st>>>(u->A[src], u->A[dst], H >> lv, W >> lv, kSlotC[src], nimg);
+  };
+  auto upcat = [&](int a, int b, int dst) {
+    int lv = kSlotLvl[dst];
+    size_t n = unet_npix(nimg, H, W, lv) * kSlotC[dst];
+    lt::k_up_cat<<<nblk(n), 256, 0, st>>>(u->A[a], u->A[b], u->A[dst], H >> lv, W >> lv, kSlotC[a], kSlotC[b], nimg);
+  };
+  conv(0); conv(1); pool(S0, P0);
+  conv(2); conv(3); pool(S1, P1);
+  conv(4); conv(5); pool(S2, P2);
+  conv(6); conv(7);
+  upcat(BB, S2, C2); conv(8); conv(9);
+  upcat(D2, S1, C1); conv(10); conv(11);
+  upcat(D1, S0, C0); conv(12); conv(13);
+  conv(14);
+}
+
+// gradient of the loss w.r.t. every parameter (u->g), from u->gout (d loss / d output, FP32 [npix][16])
+static void unet_backward_dev(lt_unet* u, int nimg, int H, int W) {
+  cudaStream_t st = u->stream;
+  cudaMemsetAsync(u->g, 0, u->nparams * sizeof(float), st);
+  for (int s : {D1, D2, BB, S0, S1, S2})
+    cudaMemsetAsync(u->G[s], 0, unet_npix(nimg, H, W, kSlotLvl[s]) * kSlotC[s] * sizeof(float), st);
+  auto layer_bwd = [&](int l, const float* gy) {
+    const lt::ConvSpec& c = lt::kLayers[l];
+    int lv = kLLvl[l], h = H >> lv, w = W >> lv;
+    size_t n = unet_npix(nimg, H, W, lv) * c.cout;
+    const bf16* y = kLOut[l] >= 0 ? u->A[kLOut[l]] : nullptr;
+    lt::k_relu_mask<<<nblk(n), 256, 0, st>>>(gy, y, u->gbf, n, c.relu && y != nullptr);
+    const int nw = 9 * c.cout * c.cin;
+    const int chunk = 4096;
+    dim3 gw(nblk(nw + c.cout), (h * w + chunk - 1) / chunk, nimg);
+    lt::k_conv_wgrad<<<gw, 256, 0, st>>>(u->A[kLIn[l]], u->gbf, u->g + u->woff[l], u->g + u->boff[l], h, w, c.cin,
+                                        c.cout, chunk);
+    if (l > 0)   // backward data: conv with flipped, transposed weights, FP32 output
+      lt::conv3x3(u->gbf, u->wflip + u->woff[l], nullptr, nullptr, u->G[kLIn[l]], nimg, h, w, c.cout, c.cin, 0, st);
+  };
+  auto upcat_bwd = [&](int a, int b, int dst) {
+    int lv = kSlotLvl[dst];
+    size_t n = unet_npix(nimg, H, W, lv) * kSlotC[dst];
+    lt::k_up_cat_bwd<<<nblk(n), 256, 0, st>>>(u->G[dst], u->G[a], u->G[b], H >> lv, W >> lv, kSlotC[a], kSlotC[b],
+                                             nimg);
+  };
+  auto pool_bwd = [&](int src, int dst) {   // src = fine slot, dst = pooled slot
+    int lv = kSlotLvl[src];
+    size_t n = unet_npix(nimg, H, W, lv) * kSlotC[src];
+    lt::k_pool2_bwd<<<nblk(n), 256, 0, st>>>(u->G[dst], u->G[src], H >> lv, W >> lv, kSlotC[src], nimg);
+  };
+  layer_bwd(14, u->gout);
+  layer_bwd(13, u->G[D0]);
+  layer_bwd(12, u->G[A13]);
+  upcat_bwd(D1, S0, C0);
+  layer_bwd(11, u->G[D1]);
+  layer_bwd(10, u->G[A11]);
+  upcat_bwd(D2, S1, C1);
+  layer_bwd(9, u->G[D2]);
+  layer_bwd(8, u->G[A9]);
+  upcat_bwd(BB, S2, C2);
+  layer_bwd(7, u->G[BB]);
+  layer_bwd(6, u->G[A7]);
+  pool_bwd(S2, P2);
+  layer_bwd(5, u->G[S2]);
+  layer_bwd(4, u->G[A5]);
+  pool_bwd(S1, P1);
+  layer_bwd(3, u->G[S1]);
+  layer_bwd(2, u->G[A3]);
+  pool_bwd(S0, P0);
+  layer_bwd(1, u->G[S0]);
+  layer_bwd(0, u->G[A1]);
+}
+
+static void unet_refresh_bf16(lt_unet* u) {
+  lt::k_f32_to_bf16<<<nblk(u->nparams), 256, 0, u->stream>>>(u->w, u->wb, u->nparams);
+  for (int l = 0; l < kNumLayers; ++l) {
+    const lt::ConvSpec& c = lt::kLayers[l];
+    lt::k_flip_weights<<<nblk(9 * c.cin * c.cout), 256, 0, u->stream>>>(u->wb + u->woff[l], u->wflip + u->woff[l],
+                                                                       c.cin, c.cout);
+  }
+}
+
+static int unet_prepare(lt_unet* u, int nimg, int H, int W, const float* in) {
+  if (nimg < 1 || H < 8 || W < 8 || (H % 8) || (W % 8)) return unet_fail(u, -1, "images must be at least 8x8 with sides divisible by 8");
+  if (!in) return unet_fail(u, -1, "input is null");
+  cudaSetDevice(u->device);
+  if (unet_ensure(u, nimg, H, W)) return unet_fail(u, -2, "device allocation failed");
+  size_t npix = unet_npix(nimg, H, W, 0);
+  lt::k_pack_input<<<nblk(npix * 16), 256, 0, u->stream>>>(in, u->A[X0], npix);
+  return 0;
+}
+
+static int unet_loss_grad(lt_unet* u, int nimg, int H, int W, const float* in, const float* target, double* loss) {
+  int rc = unet_prepare(u, nimg, H, W, in);
+  if (rc) return rc;
+  if (!target) return unet_fail(u, -1, "target is null");
+  size_t npix = unet_npix(nimg, H, W, 0);
+  unet_forward_dev(u, nimg, H, W);
+  cudaMemsetAsync(u->dloss, 0, sizeof(double), u->stream);
+  float scale = 1.f / (float)(npix * lt::kOutChannels);
+  lt::k_mse<<<nblk(npix * 16), 256, 0, u->stream>>>(u->outf, target, u->gout, u->dloss, npix, scale);
+  unet_backward_dev(u, nimg, H, W);
+  double l = 0.0;
+  cudaMemcpyAsync(&l, u->dloss, sizeof(double), cudaMemcpyDeviceToHost, u->stream);
+  if (cudaStreamSynchronize(u->stream) != cudaSuccess) return unet_fail(u, -3, "CUDA error in the network step");
+  if (loss) *loss = l * scale;
+  return 0;
+}
+
+__global__ void k_take2(const float* outf, float* out, size_t npix) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < npix * 2) out[i] = outf[(i / 2) * 16 + (i % 2)];
+}
+
+extern "C" {
+
+int lt_unet_create(lt_unet** out, int device, unsigned long long seed) {
+  if (!out) return -1;
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) return -3;
+  lt_unet* u = new lt_unet();
+  u->device = device;
+  size_t off = 0;
+  for (int l = 0; l < kNumLayers; ++l) {
+    const lt::ConvSpec& c = lt::kLayers[l];
+    u->woff.push_back(off);
+    off += (size_t)9 * c.cin * c.cout;
+    u->boff.push_back(off);
+    off += c.cout;
+  }
+  u->nparams = off;
+  std::vector<float> w(off, 0.f);
+  std::mt19937_64 rng(seed);
+  std::normal_distribution<float> nd(0.f, 1.f);
+  for (int l = 0; l < kNumLayers; ++l) {
+    const lt::ConvSpec& c = lt::kLayers[l];
+    int cin_real = l == 0 ? lt::kInChannels : c.cin;
+    float sd = std::sqrt(2.f / (9.f * cin_real)) * (l == kNumLayers - 1 ? 0.1f : 1.f);
+    for (int tap = 0; tap < 9; ++tap)
+      for (int co = 0; co < c.cout; ++co)
+        for (int ci = 0; ci < c.cin; ++ci)
+          w[u->woff[l] + ((size_t)tap * c.cout + co) * c.cin + ci] = (ci < cin_real) ? sd * nd(rng) : 0.f;
+  }
+  bool ok = cudaMalloc(&u->w, off * 4) == cudaSuccess && cudaMalloc(&u->g, off * 4) == cudaSuccess &&
+            cudaMalloc(&u->m, off * 4) == cudaSuccess && cudaMalloc(&u->v, off * 4) == cudaSuccess &&
+            cudaMalloc(&u->wb, off * 2) == cudaSuccess && cudaMalloc(&u->wflip, off * 2) == cudaSuccess &&
+            cudaMalloc(&u->dloss, sizeof(double)) == cudaSuccess;
+  if (!ok) { delete u; return -2; }
+  cudaMemcpy(u->w, w.data(), off * 4, cudaMemcpyHostToDevice);
+  cudaMemset(u->m, 0, off * 4);
+  cudaMemset(u->v, 0, off * 4);
+  unet_refresh_bf16(u);
+  if (cudaStreamSynchronize(u->stream) != cudaSuccess) { delete u; return -3; }
+  *out = u;
+  return 0;
+}
+
+int lt_unet_num_params(lt_unet* u) { return u ? (int)u->nparams : -1; }
+
+int lt_unet_get_params(lt_unet* u, float* host, int n) {
+  if (!u || !host || n != (int)u->nparams) return -1;
+  cudaSetDevice(u->device);
+  return cudaMemcpy(host, u->w, n * 4, cudaMemcpyDeviceToHost) == cudaSuccess ? 0 : -3;
+}
+
+int lt_unet_set_params(lt_unet* u, const float* host, int n) {
+  if (!u || !host || n != (int)u->nparams) return -1;
+  cudaSetDevice(u->device);
+  if (cudaMemcpy(u->w, host, n * 4, cudaMemcpyHostToDevice) != cudaSuccess) return -3;
+  unet_refresh_bf16(u);
+  return cudaStreamSynchronize(u->stream) == cudaSuccess ? 0 : -3;
+}
+
+int lt_unet_forward(lt_unet* u, int nimg, int H, int W, const float* in, float* out) {
+  if (!u || !out) return -1;
+  int rc = unet_prepare(u, nimg, H, W, in);
+  if (rc) return rc;
+  unet_forward_dev(u, nimg, H, W);
+  size_t npix = unet_npix(nimg, H, W, 0);
+  k_take2<<<nblk(npix * 2), 256, 0, u->stream>>>(u->outf, out, npix);
+  return cudaStreamSynchronize(u->stream) == cudaSuccess ? 0 : unet_fail(u, -3, "CUDA error in forward");
+}
+
+int lt_unet_grad(lt_unet* u, int nimg, int H, int W, const float* in, const float* target, float* grad_host,
+                 double* loss) {
+  if (!u) return -1;
+  int rc = unet_loss_grad(u, nimg, H, W, in, target, loss);
+  if (rc) return rc;
+  if (grad_host) cudaMemcpy(grad_host, u->g, u->nparams * 4, cudaMemcpyDeviceToHost);
+  return 0;
+}
+
+int lt_unet_train_step(lt_unet* u, int nimg, int H, int W, const float* in, const float* target, float lr,
+                       double* loss) {
+  if (!u) return -1;
+  int rc = unet_loss_grad(u, nimg, H, W, in, target, loss);
+  if (rc) return rc;
+  ++u->step;
+  const float b1 = 0.9f, b2 = 0.999f;
+  float c1 = 1.f - std::pow(b1, (float)u->step), c2 = 1.f - std::pow(b2, (float)u->step);
+  lt::k_adam<<<nblk(u->nparams), 256, 0, u->stream>>>(u->w, u->g, u->m, u->v, u->wb, u->nparams, lr, b1, b2, 1e-8f,
+                                                     c1, c2);
+  for (int l = 0; l < kNumLayers; ++l) {
+    const lt::ConvSpec& c = lt::kLayers[l];
+    lt::k_flip_weights<<<nblk(9 * c.cin * c.cout), 256, 0, u->stream>>>(u->wb + u->woff[l], u->wflip + u->woff[l],
+                                                                       c.cin, c.cout);
+  }
+  return cudaStreamSynchronize(u->stream) == cudaSuccess ? 0 : unet_fail(u, -3, "CUDA error in the Adam step");
+}
+
+const char* lt_unet_last_error(lt_unet* u) { return u ? u->err.c_str() : "null network"; }
+
+void lt_unet_destroy(lt_unet* u) {
+  if (!u) return;
+  cudaSetDevice(u->device);
+  for (void* p : u->acts) cudaFree(p);
+  for (void* p : {(void*)u->w, (void*)u->g, (void*)u->m, (void*)u->v, (void*)u->wb, (void*)u->wflip, (void*)u->dloss})
+    if (p) cudaFree(p);
+  cudaGetLastError();
+  delete u;
+}
+
+}  // extern "C"
+
+// ==================================================================== use inside the preconditioner solves
+namespace lt {
+
+__device__ __forceinline__ bool lg_skip(const Batch& bt, int b, int round) {
+  if (!bt.active[b]) return true;
+  return bt.rnorm2[b * (bt.rounds + 1) + round] <= bt.itol2[b];
+}
+
+// network input from the round's float32 residual f0 = L0.f
+__global__ void k_net_pack(Batch bt, Level L0, int round, const float* lk, const float* mD, float* x) {
+  int b = blockIdx.y;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L0.N) return;
+  double rn = bt.rnorm2[b * (bt.rounds + 1) + round];
+  float s = (float)sqrt(rn / (double)L0.N);
+  float inv = s > 0.f ? 1.f / s : 0.f;
+  float2 f = L0.f[(size_t)b * L0.N + c];
+  double2 t = bt.tau_cur[b];
+  float* o = x + ((size_t)b * L0.N + c) * kInChannels;
+  o[0] = f.x * inv;
+  o[1] = f.y * inv;
+  o[2] = lk[c];
+  o[3] = (float)t.x * mD[c];
+  o[4] = (float)t.y * mD[c];
+}
+
+// w = (out0 + i out1) / D  (direction of the guess; scaled below)
+__global__ void k_net_unpack(Batch bt, Level L0, int round, const float* outf, float* gn) {
+  int b = blockIdx.y;
+  if (lg_skip(bt, b, round)) return;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L0.N) return;
+  if (c < 4) gn[b * 4 + c] = 0.f;
+  const float* o = outf + ((size_t)b * L0.N + c) * 16;
+  float Dc = L0.D[c];
+  L0.u[(size_t)b * L0.N + c] = make_float2(o[0] / Dc, o[1] / Dc);
+}
+
+// per basis: a = sum conj(A w) f (complex), q = sum |A w|^2   (float32 level-0 operator)
+__global__ void k_net_dots(Batch bt, Level L0, int round, float* gn) {
+  int b = blockIdx.y;
+  if (lg_skip(bt, b, round)) return;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  float ar = 0.f, ai = 0.f, q = 0.f;
+  if (c < L0.N) {
+    const float2* u = L0.u + (size_t)b * L0.N;
+    int i = c % L0.nx, j = c / L0.nx;
+    double2 t = bt.tau_cur[b];
+    float m = L0.m[c];
+    float2 d = make_float2(L0.D[c] + (float)t.x * m, (float)t.y * m);
+    float2 uc = u[c];
+    float ax = d.x * uc.x - d.y * uc.y, ay = d.x * uc.y + d.y * uc.x;
+    if (i + 1 < L0.nx) { ax -= L0.Te[c] * u[c + 1].x; ay -= L0.Te[c] * u[c + 1].y; }
+    if (i > 0) { ax -= L0.Te[c - 1] * u[c - 1].x; ay -= L0.Te[c - 1] * u[c - 1].y; }
+    if (j + 1 < L0.ny) { ax -= L0.Tn[c] * u[c + L0.nx].x; ay -= L0.Tn[c] * u[c + L0.nx].y; }
+    if (j > 0) { ax -= L0.Tn[c - L0.nx] * u[c - L0.nx].x; ay -= L0.Tn[c - L0.nx] * u[c - L0.nx].y; }
+    float2 f = L0.f[(size_t)b * L0.N + c];
+    ar = ax * f.x + ay * f.y;
+    ai = ax * f.y - ay * f.x;
+    q = ax * ax + ay * ay;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ar += __shfl_xor_sync(0xffffffffu, ar, o);
+    ai += __shfl_xor_sync(0xffffffffu, ai, o);
+    q += __shfl_xor_sync(0xffffffffu, q, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&gn[b * 4 + 0], ar);
+    atomicAdd(&gn[b * 4 + 1], ai);
+    atomicAdd(&gn[b * 4 + 2], q);
+  }
+}
+
+// u0 = alpha w with the minimal-residual alpha = a / q; the residual is then
+// ||f||^2 - |a|^2 / q <= ||f||^2, and a guess that removes less than 5% of the
+// residual norm is dropped in favour of the zero guess (multigrid fallback)
+__global__ void k_net_scale(Batch bt, Level L0, int round, const float* gn) {
+  int b = blockIdx.y;
+  if (lg_skip(bt, b, round)) return;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L0.N) return;
+  float ar = gn[b * 4 + 0], ai = gn[b * 4 + 1], q = gn[b * 4 + 2];
+  double f2 = bt.rnorm2[b * (bt.rounds + 1) + round];
+  double gain = q > 0.f ? ((double)ar * ar + (double)ai * ai) / q : 0.0;   // ||f||^2 - ||f - alpha A w||^2
+  bool keep = q > 0.f && gain >= (1.0 - 0.95 * 0.95) * f2;
+  float2 w = L0.u[(size_t)b * L0.N + c];
+  float2 a = keep ? make_float2(ar / q, ai / q) : make_float2(0.f, 0.f);
+  L0.u[(size_t)b * L0.N + c] = make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+  if (c == 0 && keep) atomicAdd(&bt.work[KC_OTHER], 1ull);   // guesses kept (statistics)
+}
+
+}  // namespace lt
+
+// workspace for nb images of ny x nx (call before graph capture)
+int learned_prepare(lt_unet* u, int nb, int ny, int nx) {
+  if (!u) return -1;
+  if (ny % 8 || nx % 8 || ny < 8 || nx < 8) return -1;
+  return unet_ensure(u, nb, ny, nx) ? -2 : 0;
+}
+
+// learned initial guess for round `round` of every active basis (kernels only; capturable)
+void learned_guess(lt_unet* u, const lt::Batch& bt, const lt::Level& L0, int round, const float* lk, const float* mD,
+                   float* xin, float* gnorm2, cudaStream_t q) {
+  const int nb = bt.nb;
+  dim3 g((L0.N + 255) / 256, nb);
+  lt::k_net_pack<<<g, 256, 0, q>>>(bt, L0, round, lk, mD, xin);
+  cudaStream_t saved = u->stream;
+  u->stream = q;
+  size_t npix = (size_t)nb * L0.N;
+  lt::k_pack_input<<<nblk(npix * 16), 256, 0, q>>>(xin, u->A[X0], npix);
+  unet_forward_dev(u, nb, L0.ny, L0.nx);
+  u->stream = saved;
+  lt::k_net_unpack<<<g, 256, 0, q>>>(bt, L0, round, u->outf, gnorm2);
+  lt::k_net_dots<<<g, 256, 0, q>>>(bt, L0, round, gnorm2);
+  lt::k_net_scale<<<g, 256, 0, q>>>(bt, L0, round, gnorm2);
+}
