@@ -182,7 +182,8 @@ def batch_throughput(dev, wave: int = 10):
     from paper_1409_2556_gb300 import Engine
     from paper_1409_2556_gb300.batch import forward_batch
     aqs = W.config5_aquifers()
-    opts = dict(tol=1e-10, maxit=250, inner_relax=1e-6, groups=2, check_every=4, mg_tile=1)
+    opts = dict(tol=1e-10, maxit=250, inner_relax=0.0, inner_rounds=6, inner_cycles=6, groups=2, check_every=4,
+                mg_tile=1)
     t_batch = t_seq = 0.0
     conv_b = conv_s = total = 0
     maxres = 0.0

@@ -57,7 +57,7 @@ typedef struct {
   int    mg_pre;        /* red-black Gauss-Seidel sweeps before the coarse correction (default 2) */
   int    mg_post;       /* ... and after (default 2) */
   int    inner_cycles;  /* V-cycles per refinement round of a preconditioner solve (default 6) */
-  int    inner_rounds;  /* refinement rounds per preconditioner solve (default 4) */
+  int    inner_rounds;  /* refinement rounds per preconditioner solve (default 6; finished solves skip the rest) */
   double inner_tol;     /* relative residual of each preconditioner solve (default 0.01 * tol) */
   int    true_residual; /* 1: compute the true residual of every shift after the solve (default 1) */
   int    check_every;   /* outer iterations between host convergence polls (default 4) */

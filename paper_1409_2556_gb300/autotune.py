@@ -19,7 +19,7 @@ _CACHE: Dict[str, dict] = {}
 
 DEFAULT_GRID = {
     "mg_tile": [0, 1, 2],
-    "sweeps": [(1, 1), (2, 2)],
+    "sweeps": [(1, 1), (2, 2), (3, 3)],
     "inner": [(4, 6), (5, 4), (3, 8)],
     "inner_relax": [1e-6, 1e-4],
 }

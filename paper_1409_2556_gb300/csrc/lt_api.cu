@@ -171,7 +171,7 @@ int lt_default_options(lt_opts* o) {
   o->mg_pre = 2;
   o->mg_post = 2;
   o->inner_cycles = 6;
-  o->inner_rounds = 4;
+  o->inner_rounds = 6;
   o->inner_tol = 0.0;
   o->true_residual = 1;
   o->check_every = 4;
@@ -279,35 +279,57 @@ int lt_set_options(lt_ctx* ctx, const lt_opts* o) {
 }  // extern "C"
 
 // ------------------------------------------------------------------ grid + multigrid hierarchy
-// Coarse level: T_coarse = (1/r) * sum of the fine faces crossing the coarse
-// face (r = coarsening ratio along the face normal); m_coarse = sum of the
-// children.  The Dirichlet boundary part is coarsened by coarsen_bfaces and the
-// diagonal rebuilt by level_diag.
+// Coarse level by series-parallel upscaling of the transmissibilities: along
+// the face normal (ratio r = 2) every fine row of cells is a series path
+// centre -> face -> centre crossing half the coarse cell's internal face, the
+// crossing face and half the neighbour's internal face; the parallel rows of
+// the coarse face add.  With r = 1 the coarse face is the parallel sum of the
+// fine faces.  m_coarse = sum of the children.  (For a uniform kappa this
+// reproduces the transmissibility of the coarse grid; for strongly varying
+// kappa it keeps the series resistance inside coarse cells, which the
+// multigrid coarse correction needs.)  The Dirichlet part is coarsened by
+// coarsen_bfaces and the diagonal rebuilt by level_diag.
 static HostLevel coarsen(const HostLevel& f) {
   HostLevel c;
   c.nx = f.nx / f.rx; c.ny = f.ny / f.ry; c.nz = f.nz / f.rz;
   c.N = c.nx * c.ny * c.nz;
   c.rx = c.ry = c.rz = 1;
   c.Te.assign(c.N, 0.0); c.Tn.assign(c.N, 0.0); c.Tu.assign(c.N, 0.0); c.D.assign(c.N, 0.0); c.m.assign(c.N, 0.0);
+  auto fi = [&](int i, int j, int k) { return ((size_t)k * f.ny + j) * f.nx + i; };
   for (int K = 0; K < c.nz; ++K)
     for (int J = 0; J < c.ny; ++J)
       for (int I = 0; I < c.nx; ++I) {
         size_t C = ((size_t)K * c.ny + J) * c.nx + I;
-        double te = 0, tn = 0, tu = 0, mm = 0;
+        double mm = 0, te = 0, tn = 0, tu = 0;
         for (int dk = 0; dk < f.rz; ++dk)
           for (int dj = 0; dj < f.ry; ++dj)
-            for (int di = 0; di < f.rx; ++di) {
-              int i = I * f.rx + di, j = J * f.ry + dj, k = K * f.rz + dk;
-              size_t q = ((size_t)k * f.ny + j) * f.nx + i;
-              mm += f.m[q];
-              if (di == f.rx - 1) te += f.Te[q];
-              if (dj == f.ry - 1) tn += f.Tn[q];
-              if (dk == f.rz - 1) tu += f.Tu[q];
+            for (int di = 0; di < f.rx; ++di) mm += f.m[fi(I * f.rx + di, J * f.ry + dj, K * f.rz + dk)];
+        // x faces: paths over (dj, dk)
+        if (I + 1 < c.nx)
+          for (int dk = 0; dk < f.rz; ++dk)
+            for (int dj = 0; dj < f.ry; ++dj) {
+              int j = J * f.ry + dj, k = K * f.rz + dk;
+              if (f.rx == 1) { te += f.Te[fi(I, j, k)]; continue; }
+              double a = f.Te[fi(2 * I, j, k)], x = f.Te[fi(2 * I + 1, j, k)], b = f.Te[fi(2 * I + 2, j, k)];
+              te += 1.0 / (0.5 / a + 1.0 / x + 0.5 / b);
             }
-        c.Te[C] = (I + 1 < c.nx) ? te / f.rx : 0.0;
-        c.Tn[C] = (J + 1 < c.ny) ? tn / f.ry : 0.0;
-        c.Tu[C] = (K + 1 < c.nz) ? tu / f.rz : 0.0;
-        c.m[C] = mm;
+        if (J + 1 < c.ny)
+          for (int dk = 0; dk < f.rz; ++dk)
+            for (int di = 0; di < f.rx; ++di) {
+              int i = I * f.rx + di, k = K * f.rz + dk;
+              if (f.ry == 1) { tn += f.Tn[fi(i, J, k)]; continue; }
+              double a = f.Tn[fi(i, 2 * J, k)], x = f.Tn[fi(i, 2 * J + 1, k)], b = f.Tn[fi(i, 2 * J + 2, k)];
+              tn += 1.0 / (0.5 / a + 1.0 / x + 0.5 / b);
+            }
+        if (K + 1 < c.nz)
+          for (int dj = 0; dj < f.ry; ++dj)
+            for (int di = 0; di < f.rx; ++di) {
+              int i = I * f.rx + di, j = J * f.ry + dj;
+              if (f.rz == 1) { tu += f.Tu[fi(i, j, K)]; continue; }
+              double a = f.Tu[fi(i, j, 2 * K)], x = f.Tu[fi(i, j, 2 * K + 1)], b = f.Tu[fi(i, j, 2 * K + 2)];
+              tu += 1.0 / (0.5 / a + 1.0 / x + 0.5 / b);
+            }
+        c.Te[C] = te; c.Tn[C] = tn; c.Tu[C] = tu; c.m[C] = mm;
       }
   return c;
 }
@@ -331,17 +353,31 @@ static void level_diag(HostLevel& L, const BFaces& bf) {
       }
 }
 
+// Dirichlet boundary faces of the coarse level: per parallel fine row, the
+// fine boundary transmissibility in series with half the internal face of the
+// coarse cell along the normal (ratio 2), or the fine face itself (ratio 1).
 static BFaces coarsen_bfaces(const HostLevel& f, const HostLevel& c, const BFaces& bf) {
   BFaces out;
   for (int d = 0; d < 6; ++d) out.b[d].assign(c.N, 0.0);
-  int r[3] = {f.rx, f.ry, f.rz};
+  auto fi = [&](int i, int j, int k) { return ((size_t)k * f.ny + j) * f.nx + i; };
+  const int r[3] = {f.rx, f.ry, f.rz};
   for (int k = 0; k < f.nz; ++k)
     for (int j = 0; j < f.ny; ++j)
       for (int i = 0; i < f.nx; ++i) {
-        size_t q = ((size_t)k * f.ny + j) * f.nx + i;
+        size_t q = fi(i, j, k);
         size_t C = ((size_t)(k / f.rz) * c.ny + j / f.ry) * c.nx + i / f.rx;
-        for (int d = 0; d < 6; ++d)
-          if (bf.b[d][q] != 0.0) out.b[d][C] += bf.b[d][q] / r[d / 2];
+        for (int d = 0; d < 6; ++d) {
+          double tb = bf.b[d][q];
+          if (tb == 0.0) continue;
+          int ax = d / 2;
+          if (r[ax] == 1) { out.b[d][C] += tb; continue; }
+          // internal face of the coarse cell along axis ax, in this fine row
+          double tint;
+          if (ax == 0) tint = f.Te[fi((i / 2) * 2, j, k)];
+          else if (ax == 1) tint = f.Tn[fi(i, (j / 2) * 2, k)];
+          else tint = f.Tu[fi(i, j, (k / 2) * 2)];
+          out.b[d][C] += 1.0 / (1.0 / tb + 0.5 / tint);
+        }
       }
   return out;
 }
