@@ -219,6 +219,56 @@ def batch_throughput(dev, wave: int = 10):
             "timing": "host wall clock around each call, device synchronised"}
 
 
+LEARNED_WORKLOAD = ("train: 8 seeded 64x64 aquifers (log-kappa variance 1.5), 20480 (residual, multigrid solve) "
+                    "pairs; test: unseen 512x512 aquifer, variance 2.0, 9 sources, 25 receivers, 8 times, Nz=32")
+
+
+def learned_gain(dev):
+    """Forward solve of an unseen 512x512 field with and without the learned initial guess
+    (network trained here, on the GPU, by the library's own kernels)."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_1409_2556_gb300 import Engine, learned
+    rng = np.random.default_rng(4)
+    xs, ys = [], []
+    for prob in learned.training_fields(range(8)):
+        e = Engine(dev)
+        e.setup_grid(prob.kappa, prob.Ss, prob.dx, prob.dy, prob.dz, prob.bc)
+        x, y = learned.make_pairs(e, prob, 2560, rng, cycles=30)
+        xs.append(x); ys.append(y)
+        e.close()
+    pairs = (torch.cat(xs), torch.cat(ys))
+    net = learned.UNet(dev, seed=1)
+    t0 = time.perf_counter()
+    hist = learned.train(net, pairs, steps=1500, batch=32, lr=2e-3, rng=rng)
+    t_train = time.perf_counter() - t0
+    del pairs, xs, ys
+    torch.cuda.empty_cache()
+    test = W.config2(n=512, seed=104, variance=2.0, corr=40.0, nt=8, groups=3)
+    out = {}
+    for pc in (0, 1):
+        eng = Engine(dev, stream=torch.cuda.Stream(device=dev))
+        eng.load_problem(test, tol=1e-10, maxit=200, precond=pc, inner_rounds=6, inner_cycles=6)
+        if pc:
+            eng.lib.lt_set_learned_preconditioner(eng.h, net.h)
+        eng.forward(test.times, allow_unconverged=True)          # warm
+        eng.forward(test.times, allow_unconverged=True)
+        out[pc] = dict(eng.last_stats)
+        eng.close()
+    net.close()
+    torch.cuda.empty_cache()
+    a, b = out[0], out[1]
+    return {"value": b["n_converged"] / (b["ms_total"] / 1000.0), "unit": "shifted solves/s",
+            "multigrid_value": a["n_converged"] / (a["ms_total"] / 1000.0),
+            "speedup_vs_multigrid": (b["n_converged"] / b["ms_total"]) / (a["n_converged"] / a["ms_total"]),
+            "converged": [a["n_converged"], b["n_converged"]], "shifted_systems": a["n_shift_solves"],
+            "max_true_residual": [a["max_true_residual"], b["max_true_residual"]],
+            "guesses_kept": b["work"][14], "train_seconds": t_train,
+            "train_loss_first_last": [float(np.mean(hist[:20])), float(np.mean(hist[-50:]))],
+            "workload": LEARNED_WORKLOAD}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -254,6 +304,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-jacobian", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--opts", default="", help="JSON dict overriding solver options (profiling runs)")
     ap.add_argument("--launch-list", action="store_true",
                     help="profiling only: run warmup + the timed steps, print nothing else")
@@ -387,6 +438,7 @@ def main():
             "measured": "CUDA events around each launch of the class, in a separate pass of the same steps"}
     jac = None if args.no_jacobian else jacobian_rows(dev, stream)
     bat = None if args.no_batch else batch_throughput(dev)
+    lrn = None if args.no_learned else learned_gain(dev)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -406,7 +458,7 @@ def main():
                        "max_true_residual": tres, "outer_iters_max": max(iters),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (Krylov bases ~GBs per step)"},
-            "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(), "jacobian": jac, "batch": bat,
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(), "jacobian": jac, "batch": bat, "learned": lrn,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": launches}
     print(json.dumps(line), flush=True)

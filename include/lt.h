@@ -249,9 +249,9 @@ void lt_unet_destroy(lt_unet* net);
 int lt_precond_apply(lt_ctx* ctx, int nimg, const double* tau, const float* r, float* e, int cycles);
 
 /*
- * Attach a trained network (NULL detaches).  With lt_opts.precond = 1 every
- * refinement round of a preconditioner solve starts its V-cycles from the
- * network's guess (its direction scaled by the minimal-residual coefficient)
+ * Attach a trained network (NULL detaches).  With lt_opts.precond = 1 the
+ * first refinement round of every preconditioner solve (residual = the Krylov
+ * vector v_j) starts its V-cycles from the network's guess (its direction scaled by the minimal-residual coefficient)
  * instead of zero; a guess that removes less than 5% of the residual norm is
  * dropped (multigrid fallback).  2D grids with nx, ny
  * multiples of 8 only.  The network must stay alive while attached.

@@ -777,7 +777,7 @@ static int launch_iteration(lt_ctx* ctx, cudaStream_t q, int jj, int* nlq, lt::P
   for (int r = 0; r < o.inner_rounds; ++r) {
     lt::launch_exact_residual(bt, ctx->fe, L0, jj, r, 0, q, pf);
     ++*nlq;
-    if (o.precond == 1) {
+    if (o.precond == 1 && r == 0) {   // first round: the residual is the Krylov vector v_j itself
       learned_guess(ctx->net, bt, L0, r, ctx->d_lk, ctx->d_mD, ctx->d_xin, ctx->d_gn2, q);
       *nlq += 24;
     }
