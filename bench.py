@@ -454,7 +454,7 @@ def main():
             "config": {"workload": WORKLOAD_NAME, "shifted_systems_per_step": ns * nt * prob.Nz // 2,
                        "solver_tol": SOLVE_OPTS["tol"], "residual_bar": RESIDUAL_BAR,
                        "autotuned": {k: tuned[k] for k in ("mg_tile", "mg_pre", "mg_post", "inner_rounds",
-                                                             "inner_cycles", "inner_relax")},
+                                                             "inner_cycles", "inner_relax", "mg_tma")},
                        "max_true_residual": tres, "outer_iters_max": max(iters),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (Krylov bases ~GBs per step)"},

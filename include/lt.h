@@ -67,6 +67,7 @@ typedef struct {
   int    graphs;        /* 1: replay one captured CUDA graph per outer iteration (default); 0: direct launches */
   int    mg_tile;       /* fused 2D smoother tile: 0 = 64x32, 1 = 32x32, 2 = 32x16 cells (default 2) */
   int    precond;       /* 0: multigrid (default); 1: learned initial guess + multigrid (see lt_set_learned_preconditioner) */
+  int    mg_tma;        /* 1: stage the fused 2D tiles with TMA bulk tensor copies when alignment allows (default) */
 } lt_opts;
 
 /* kernel classes reported in lt_stats.work[] and selectable by lt_opts.timing_class */

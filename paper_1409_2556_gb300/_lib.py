@@ -36,7 +36,8 @@ class LtOpts(C.Structure):
                 ("tau_project", C.c_int), ("groups", C.c_int), ("mg_pre", C.c_int), ("mg_post", C.c_int),
                 ("inner_cycles", C.c_int), ("inner_rounds", C.c_int), ("inner_tol", C.c_double),
                 ("true_residual", C.c_int), ("check_every", C.c_int), ("timing_class", C.c_int),
-                ("inner_relax", C.c_double), ("graphs", C.c_int), ("mg_tile", C.c_int), ("precond", C.c_int)]
+                ("inner_relax", C.c_double), ("graphs", C.c_int), ("mg_tile", C.c_int), ("precond", C.c_int),
+                ("mg_tma", C.c_int)]
 
 
 class LtStats(C.Structure):

@@ -19,9 +19,10 @@ _CACHE: Dict[str, dict] = {}
 
 DEFAULT_GRID = {
     "mg_tile": [0, 1, 2],
-    "sweeps": [(1, 1), (2, 2), (3, 3)],
-    "inner": [(4, 6), (5, 4), (3, 8)],
+    "sweeps": [(2, 2), (3, 3)],
+    "inner": [(4, 6), (5, 4)],
     "inner_relax": [1e-6, 1e-4],
+    "mg_tma": [1, 0],
 }
 
 
@@ -48,10 +49,11 @@ def autotune(engine, prob, base_opts: dict, grid: Optional[dict] = None, reps: i
     engine.load_problem(prob, **base_opts)
     best, best_ms = None, float("inf")
     relax = grid.get("inner_relax", [base_opts.get("inner_relax", 0.0)])
-    for tile, (pre, post), (rounds, cycles), rx in itertools.product(grid["mg_tile"], grid["sweeps"], grid["inner"],
-                                                                    relax):
+    tmas = grid.get("mg_tma", [base_opts.get("mg_tma", 1)])
+    for tile, (pre, post), (rounds, cycles), rx, tma in itertools.product(grid["mg_tile"], grid["sweeps"],
+                                                                         grid["inner"], relax, tmas):
         cand = dict(base_opts, mg_tile=tile, mg_pre=pre, mg_post=post, inner_rounds=rounds, inner_cycles=cycles,
-                    inner_relax=rx)
+                    inner_relax=rx, mg_tma=tma)
         engine.set_options(**{k: v for k, v in cand.items() if k not in ("Nz", "tol", "groups")})
         ms = 0.0
         ok = True

@@ -180,6 +180,7 @@ int lt_default_options(lt_opts* o) {
   o->graphs = 1;
   o->mg_tile = 2;
   o->precond = 0;
+  o->mg_tma = 1;
   return LT_OK;
 }
 
@@ -240,6 +241,8 @@ void lt_destroy(lt_ctx* ctx) {
   if (ctx->ev_a) cudaEventDestroy(ctx->ev_a);
   if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  lt::tma_cache_free(ctx->mg);
+  lt::tma_cache_free(ctx->pc_mg);
   free_list(ctx->pc_allocs);          // also holds pc_mg.d_levels
   ctx->pc_mg.d_levels = nullptr;
   for (float* p : {ctx->d_lk, ctx->d_mD, ctx->d_xin, ctx->d_gn2})
@@ -264,6 +267,7 @@ int lt_set_options(lt_ctx* ctx, const lt_opts* o) {
   if (o->check_every < 1) return fail(ctx, LT_ERR_INVALID_ARG, "check_every=%d", o->check_every);
   if (o->mg_tile < 0 || o->mg_tile > 2) return fail(ctx, LT_ERR_INVALID_ARG, "mg_tile=%d must be 0, 1 or 2", o->mg_tile);
   if (o->precond != 0 && o->precond != 1) return fail(ctx, LT_ERR_INVALID_ARG, "precond=%d must be 0 or 1", o->precond);
+  if (o->mg_tma != 0 && o->mg_tma != 1) return fail(ctx, LT_ERR_INVALID_ARG, "mg_tma=%d must be 0 or 1", o->mg_tma);
   if (o->graphs != 0 && o->graphs != 1) return fail(ctx, LT_ERR_INVALID_ARG, "graphs=%d must be 0 or 1", o->graphs);
   if (!(o->inner_relax >= 0.0 && o->inner_relax < 1.0))
     return fail(ctx, LT_ERR_INVALID_ARG, "inner_relax=%g must be in [0,1)", o->inner_relax);
@@ -273,6 +277,8 @@ int lt_set_options(lt_ctx* ctx, const lt_opts* o) {
   ctx->mg.npre = o->mg_pre;
   ctx->mg.npost = o->mg_post;
   ctx->mg.tile = o->mg_tile;
+  ctx->mg.tma = o->mg_tma;
+  ctx->pc_mg.tma = o->mg_tma;
   return LT_OK;
 }
 
@@ -439,6 +445,8 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
   free_list(ctx->grid_allocs);
   if (ctx->mg.d_levels) { cudaFree(ctx->mg.d_levels); ctx->mg.d_levels = nullptr; }
   ctx->have_grid = false;
+  lt::tma_cache_free(ctx->mg);
+  lt::tma_cache_free(ctx->pc_mg);
   for (float** p : {&ctx->d_lk, &ctx->d_mD}) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -507,6 +515,7 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
   mg.npre = ctx->opts.mg_pre;
   mg.npost = ctx->opts.mg_post;
   mg.tile = ctx->opts.mg_tile;
+  mg.tma = ctx->opts.mg_tma;
   mg.dmask = 0;
   for (int d = 0; d < 6; ++d)
     if (bc[d] == 0) mg.dmask |= (1 << d);
@@ -720,6 +729,7 @@ static int ensure_ws(lt_ctx* ctx, const Plan& P) {
     return LT_OK;
   CK(cudaStreamSynchronize(ctx->stream));
   free_ws(ctx);
+  lt::tma_cache_free(ctx->mg);
   lt::Batch& bt = ws.bt;
   const int nb = P.nb, M = o.maxit, R = o.inner_rounds, nsh = P.nsh;
   const size_t N = (size_t)ctx->N;
@@ -993,6 +1003,9 @@ static int solve_end(lt_ctx* ctx, const Plan& P, SolveState& S, std::vector<doub
   free_list(tmp);
   for (auto& r : true_res)
     if (r >= 0) r = std::sqrt(r);
+  if (work[lt::KC_OTHER + 1] > 0)
+    return fail(ctx, LT_ERR_TIMEOUT, "a bulk tensor copy did not complete within its bounded wait (%llu tiles)",
+                (unsigned long long)work[lt::KC_OTHER + 1]);
   if (st) {
     for (int c = 0; c < 16; ++c) st->work[c] += work[c];
     if (pf) {
@@ -1361,7 +1374,10 @@ extern "C" int lt_precond_apply(lt_ctx* ctx, int nimg, const double* tau, const 
     AL(bt.active, nimg); AL(bt.rnorm2, nimg); AL(bt.itol2, nimg); AL(bt.tau_cur, nimg); AL(bt.tau_slot, nimg);
     AL(bt.work, 16);
     if (nc2) AL(bt.coarse_inv, nimg * nc2);
+    lt::tma_cache_free(mg);
+    void* keep_none = nullptr;
     mg = ctx->mg;
+    mg.tma_cache = keep_none;
     for (int l = 0; l < mg.nlev; ++l) {
       AL(mg.h_levels[l].u, (size_t)nimg * mg.h_levels[l].N);
       AL(mg.h_levels[l].f, (size_t)nimg * mg.h_levels[l].N);
@@ -1374,7 +1390,7 @@ extern "C" int lt_precond_apply(lt_ctx* ctx, int nimg, const double* tau, const 
     mg.d_levels = dl;
     ctx->pc_nb = nimg;
   }
-  mg.npre = ctx->opts.mg_pre; mg.npost = ctx->opts.mg_post; mg.tile = ctx->opts.mg_tile;
+  mg.npre = ctx->opts.mg_pre; mg.npost = ctx->opts.mg_post; mg.tile = ctx->opts.mg_tile; mg.tma = ctx->opts.mg_tma;
   bt.nb = nimg;
   bt.rounds = 0;
   bt.coarse_direct = ctx->mg.coarse_direct;

@@ -12,12 +12,15 @@ struct MGHost {
   int dmask;                   // Dirichlet faces bitmask (bit 2d: lower face of axis d, 2d+1: upper)
   int coarse_direct;           // 1 if the coarsest level has a dense inverse
   int tile;                    // fused 2D tile shape: 0 = 64x32, 1 = 32x32, 2 = 32x16
+  int tma;                     // 1: stage fused tiles with TMA bulk tensor copies where alignment allows
+  void* tma_cache;             // host-side cache of tensor maps (owned by mg.cu)
   Level h_levels[kMaxLevels];  // host copy of the level descriptors
   Level* d_levels;             // device copy
 };
 
 // one V-cycle on every active basis of the batch whose refinement round `round` is not done
 int launch_vcycle(const MGHost& mg, const Batch& bt, int round, cudaStream_t st, int* nlaunch, Prof* pf);
+void tma_cache_free(MGHost& mg);
 
 // -------- krylov.cu
 void launch_prep_iter(const Batch& bt, int j, cudaStream_t st);

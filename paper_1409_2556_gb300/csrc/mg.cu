@@ -19,6 +19,13 @@
 //     (coarse_vcycle), ending in a dense inverse at the coarsest level.
 // All kernels are batched over Krylov bases (blockIdx.y = basis) and skip
 // bases that are inactive or whose preconditioner solve already converged.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <mutex>
+#include <vector>
+
 #include "lt_internal.h"
 #include "lt_kernels.h"
 
@@ -449,6 +456,291 @@ static void launch_up(int tile, const Level& L, const Level& Lc, const Batch& bt
 
 static bool fused_ok(const Level& L) { return L.nz == 1 && L.rx == 2 && L.ry == 2 && L.rz == 1; }
 
+
+// ---------------------------------------------------------------- TMA-staged fused tiles
+// The same fused kernels with the tile + halo brought into shared memory by
+// one cp.async.bulk.tensor box per array (out-of-domain cells zero-filled by
+// the copy engine), completing on an mbarrier.  The x origin of every box is
+// the tile origin minus 8 cells (multiple of 8 elements, so the 16-byte rule
+// holds for float and float2 planes); the y halo is what the sweeps need.
+constexpr int kTmaHx = 8;
+constexpr unsigned kTmaSpin = 1u << 26;   // bounded mbarrier wait (then an error flag is raised)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"((uint64_t)tm), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_3d(void* dst, const CUtensorMap* tm, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+struct TmaMaps { CUtensorMap u, f, te, tn, d, m; };
+
+// stage u, f, Te, Tn, D, m of the region into shared memory and build the inverse diagonal.
+// Returns false (and raises bt.work[KC_OTHER + 1] as an error flag) if the copy never completed.
+__device__ __forceinline__ bool tile_load_tma(const TmaMaps& M, Tile2D& T, float* Ds, float* ms, uint64_t* bar,
+                                              int gx0, int gy0, int b, int RX, int RY, float2 tau, const Batch& bt) {
+  const int RN = RX * RY;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(bar, (uint32_t)RN * 32u);
+    tma_3d(T.u, &M.u, gx0, gy0, b, bar);
+    tma_3d(T.f, &M.f, gx0, gy0, b, bar);
+    tma_2d(T.te, &M.te, gx0, gy0, bar);
+    tma_2d(T.tn, &M.tn, gx0, gy0, bar);
+    tma_2d(Ds, &M.d, gx0, gy0, bar);
+    tma_2d(ms, &M.m, gx0, gy0, bar);
+  }
+  bool done = false;
+  for (unsigned it = 0; it < kTmaSpin; ++it)
+    if (mbar_try_wait(bar, 0)) { done = true; break; }
+  if (!done) {
+    if (threadIdx.x == 0) atomicAdd(&bt.work[KC_OTHER + 1], 1ull);
+    for (unsigned it = 0; it < kTmaSpin; ++it)      // give copies in flight a second bounded chance to land
+      if (mbar_try_wait(bar, 0)) break;
+    return false;
+  }
+  for (int idx = threadIdx.x; idx < RN; idx += blockDim.x) {
+    float dd = Ds[idx], mm = ms[idx];
+    float2 dg = make_float2(dd + tau.x * mm, tau.y * mm);
+    T.di[idx] = (dd == 0.f && mm == 0.f) ? make_float2(0.f, 0.f) : cinv(dg);
+  }
+  __syncthreads();
+  return true;
+}
+
+template <int kTX, int kTY>
+__global__ void __launch_bounds__(kFusedThreads) k_down2d_tma(Level Lf, Level Lc, Batch bt, int round, int npre,
+                                                             const __grid_constant__ TmaMaps M) {
+  extern __shared__ __align__(128) unsigned char smem_t[];
+  int b = blockIdx.y;
+  if (mg_skip(bt, b, round)) return;
+  const int H = 2 * npre + 1;
+  const int RX = kTX + 2 * kTmaHx, RY = kTY + 2 * H, RN = RX * RY;
+  const int ntx = (Lf.nx + kTX - 1) / kTX;
+  const int tx0 = (blockIdx.x % ntx) * kTX, ty0 = (blockIdx.x / ntx) * kTY;
+  const int gx0 = tx0 - kTmaHx, gy0 = ty0 - H;
+  const size_t A = ((size_t)RN * 8 + 127) & ~(size_t)127, B4 = ((size_t)RN * 4 + 127) & ~(size_t)127;
+  Tile2D T;
+  T.u = (float2*)smem_t; T.f = (float2*)(smem_t + A); T.di = (float2*)(smem_t + 2 * A);
+  T.te = (float*)(smem_t + 3 * A); T.tn = (float*)(smem_t + 3 * A + B4);
+  float* Ds = (float*)(smem_t + 3 * A + 2 * B4);
+  float* ms = (float*)(smem_t + 3 * A + 3 * B4);
+  uint64_t& bar = *(uint64_t*)(smem_t + 3 * A + 4 * B4);
+  float2 tau = tau32(bt, b);
+  if (threadIdx.x == 0) {
+    int n = min(kTX, Lf.nx - tx0) * min(kTY, Lf.ny - ty0);
+    atomicAdd(&bt.work[KC_FUSED_DOWN], (unsigned long long)n);
+  }
+  if (!tile_load_tma(M, T, Ds, ms, &bar, gx0, gy0, b, RX, RY, tau, bt)) return;
+  tile_sweeps(T, Lf, gx0, gy0, RX, RY, 2 * npre, 0);
+  const int ncx = kTX / 2, ncy = kTY / 2;
+  float2* fc = Lc.f + (size_t)b * Lc.N;
+  float2* uc = Lc.u + (size_t)b * Lc.N;
+  for (int q = threadIdx.x; q < ncx * ncy; q += blockDim.x) {
+    int I = tx0 / 2 + q % ncx, J = ty0 / 2 + q / ncx;
+    if (I >= Lc.nx || J >= Lc.ny) continue;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int dj = 0; dj < 2; ++dj)
+      for (int di = 0; di < 2; ++di) {
+        int lx = kTmaHx + 2 * (q % ncx) + di, ly = H + 2 * (q / ncx) + dj;
+        int idx = ly * RX + lx;
+        float2 nbs = tile_nb(T, idx, RX);
+        float2 d = cinv(T.di[idx]);
+        float2 a = cmul(d, T.u[idx]);
+        float2 fv = T.f[idx];
+        acc.x += fv.x - a.x + nbs.x;
+        acc.y += fv.y - a.y + nbs.y;
+      }
+    fc[J * Lc.nx + I] = acc;
+    uc[J * Lc.nx + I] = make_float2(0.f, 0.f);
+  }
+  float2* u = Lf.u + (size_t)b * Lf.N;
+  for (int q = threadIdx.x; q < kTX * kTY; q += blockDim.x) {
+    int gx = tx0 + q % kTX, gy = ty0 + q / kTX;
+    if (gx >= Lf.nx || gy >= Lf.ny) continue;
+    u[gy * Lf.nx + gx] = T.u[(H + q / kTX) * RX + kTmaHx + q % kTX];
+  }
+}
+
+template <int kTX, int kTY>
+__global__ void __launch_bounds__(kFusedThreads) k_up2d_tma(Level Lf, Level Lc, Batch bt, int round, int npost,
+                                                           int dmask, const __grid_constant__ TmaMaps M) {
+  extern __shared__ __align__(128) unsigned char smem_t[];
+  int b = blockIdx.y;
+  if (mg_skip(bt, b, round)) return;
+  const int H = 2 * npost;
+  const int RX = kTX + 2 * kTmaHx, RY = kTY + 2 * H, RN = RX * RY;
+  const int ntx = (Lf.nx + kTX - 1) / kTX;
+  const int tx0 = (blockIdx.x % ntx) * kTX, ty0 = (blockIdx.x / ntx) * kTY;
+  const int gx0 = tx0 - kTmaHx, gy0 = ty0 - H;
+  const size_t A = ((size_t)RN * 8 + 127) & ~(size_t)127, B4 = ((size_t)RN * 4 + 127) & ~(size_t)127;
+  Tile2D T;
+  T.u = (float2*)smem_t; T.f = (float2*)(smem_t + A); T.di = (float2*)(smem_t + 2 * A);
+  T.te = (float*)(smem_t + 3 * A); T.tn = (float*)(smem_t + 3 * A + B4);
+  float* Ds = (float*)(smem_t + 3 * A + 2 * B4);
+  float* ms = (float*)(smem_t + 3 * A + 3 * B4);
+  uint64_t& bar = *(uint64_t*)(smem_t + 3 * A + 4 * B4);
+  float2 tau = tau32(bt, b);
+  const float2* ucb = Lc.u + (size_t)b * Lc.N;
+  if (threadIdx.x == 0) {
+    int n = min(kTX, Lf.nx - tx0) * min(kTY, Lf.ny - ty0);
+    atomicAdd(&bt.work[KC_FUSED_UP], (unsigned long long)n);
+  }
+  if (!tile_load_tma(M, T, Ds, ms, &bar, gx0, gy0, b, RX, RY, tau, bt)) return;
+  for (int idx = threadIdx.x; idx < RN; idx += blockDim.x) {
+    int gx = gx0 + idx % RX, gy = gy0 + idx / RX;
+    if (gx < 0 || gy < 0 || gx >= Lf.nx || gy >= Lf.ny) continue;
+    int I0, I1, J0, J1;
+    float wi0, wi1, wj0, wj1, si, sj;
+    axis_interp(gx, 2, Lc.nx, dmask & 1, dmask & 2, I0, I1, wi0, wi1, si);
+    axis_interp(gy, 2, Lc.ny, dmask & 4, dmask & 8, J0, J1, wj0, wj1, sj);
+    wi1 *= si; wj1 *= sj;
+    float2 a = ucb[J0 * Lc.nx + I0], bq = ucb[J0 * Lc.nx + I1], c = ucb[J1 * Lc.nx + I0], d = ucb[J1 * Lc.nx + I1];
+    float w00 = wj0 * wi0, w01 = wj0 * wi1, w10 = wj1 * wi0, w11 = wj1 * wi1;
+    float2 v = T.u[idx];
+    v.x += w00 * a.x + w01 * bq.x + w10 * c.x + w11 * d.x;
+    v.y += w00 * a.y + w01 * bq.y + w10 * c.y + w11 * d.y;
+    T.u[idx] = v;
+  }
+  __syncthreads();
+  tile_sweeps(T, Lf, gx0, gy0, RX, RY, 2 * npost, 1);
+  float2* u = Lf.u + (size_t)b * Lf.N;
+  for (int q = threadIdx.x; q < kTX * kTY; q += blockDim.x) {
+    int gx = tx0 + q % kTX, gy = ty0 + q / kTX;
+    if (gx >= Lf.nx || gy >= Lf.ny) continue;
+    u[gy * Lf.nx + gx] = T.u[(H + q / kTX) * RX + kTmaHx + q % kTX];
+  }
+}
+
+static size_t tma_smem(int tx, int ty, int H) {
+  size_t RN = (size_t)(tx + 2 * kTmaHx) * (ty + 2 * H);
+  size_t A = (RN * 8 + 127) & ~(size_t)127, B4 = (RN * 4 + 127) & ~(size_t)127;
+  return 3 * A + 4 * B4 + 16;   // + mbarrier
+}
+
+// ---- host: tensor maps (cached per level, tile, halo and workspace)
+struct TmaEntry {
+  const void *u, *f, *te;
+  int nb, lvl, tile, H;
+  TmaMaps maps;
+};
+struct TmaCache { std::vector<TmaEntry> e; };
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+static bool encode(CUtensorMap* tm, const void* base, CUtensorMapDataType dt, int rank, const cuuint64_t* dims,
+                   const cuuint64_t* strides, const cuuint32_t* box) {
+  auto fn = get_encoder();
+  if (!fn) return false;
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(tm, dt, rank, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// maps for level l with tile shape (tx, ty) and y-halo H, or nullptr if TMA cannot be used
+static const TmaMaps* tma_maps(const MGHost& mg, int l, int tile, int tx, int ty, int H, int nb) {
+  const Level& L = mg.h_levels[l];
+  if (!mg.tma || L.nx % 4 != 0 || H > kTmaHx || ty + 2 * H > 256) return nullptr;
+  auto* cache = (TmaCache*)mg.tma_cache;
+  if (!cache) return nullptr;
+  for (auto& e : cache->e)
+    if (e.u == L.u && e.f == L.f && e.te == L.Te && e.nb == nb && e.lvl == l && e.tile == tile && e.H == H)
+      return &e.maps;
+  TmaEntry e{L.u, L.f, L.Te, nb, l, tile, H, {}};
+  const cuuint32_t RX = tx + 2 * kTmaHx, RY = ty + 2 * H;
+  cuuint64_t d3[3] = {(cuuint64_t)L.nx, (cuuint64_t)L.ny, (cuuint64_t)nb};
+  cuuint64_t s3[2] = {(cuuint64_t)L.nx * 8, (cuuint64_t)L.nx * L.ny * 8};
+  cuuint32_t b3[3] = {RX, RY, 1};
+  cuuint64_t d2[2] = {(cuuint64_t)L.nx, (cuuint64_t)L.ny};
+  cuuint64_t s2[1] = {(cuuint64_t)L.nx * 4};
+  cuuint32_t b2[2] = {RX, RY};
+  bool ok = encode(&e.maps.u, L.u, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, d3, s3, b3) &&
+            encode(&e.maps.f, L.f, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, d3, s3, b3) &&
+            encode(&e.maps.te, L.Te, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, d2, s2, b2) &&
+            encode(&e.maps.tn, L.Tn, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, d2, s2, b2) &&
+            encode(&e.maps.d, L.D, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, d2, s2, b2) &&
+            encode(&e.maps.m, L.m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, d2, s2, b2);
+  if (!ok) return nullptr;
+  cache->e.push_back(e);
+  return &cache->e.back().maps;
+}
+
+void tma_cache_free(MGHost& mg) {
+  delete (TmaCache*)mg.tma_cache;
+  mg.tma_cache = nullptr;
+}
+
+template <int TX, int TY>
+static void set_attrs_tma() {
+  cudaFuncSetAttribute(k_down2d_tma<TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem(TX, TY, 7));
+  cudaFuncSetAttribute(k_up2d_tma<TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem(TX, TY, 8));
+}
+
+static bool launch_down_tma(const MGHost& mg, int l, int tile, const Level& L, const Level& Lc, const Batch& bt,
+                            int round, int npre, cudaStream_t st) {
+  const int TX = kTiles[tile][0], TY = kTiles[tile][1], H = 2 * npre + 1;
+  const TmaMaps* M = tma_maps(mg, l, tile, TX, TY, H, bt.nb);
+  if (!M) return false;
+  dim3 g(((L.nx + TX - 1) / TX) * ((L.ny + TY - 1) / TY), bt.nb);
+  size_t sm = tma_smem(TX, TY, H);
+  if (tile == 0) k_down2d_tma<64, 32><<<g, kFusedThreads, sm, st>>>(L, Lc, bt, round, npre, *M);
+  else if (tile == 1) k_down2d_tma<32, 32><<<g, kFusedThreads, sm, st>>>(L, Lc, bt, round, npre, *M);
+  else k_down2d_tma<32, 16><<<g, kFusedThreads, sm, st>>>(L, Lc, bt, round, npre, *M);
+  return true;
+}
+
+static bool launch_up_tma(const MGHost& mg, int l, int tile, const Level& L, const Level& Lc, const Batch& bt,
+                          int round, int npost, int dmask, cudaStream_t st) {
+  const int TX = kTiles[tile][0], TY = kTiles[tile][1], H = 2 * npost;
+  const TmaMaps* M = tma_maps(mg, l, tile, TX, TY, H, bt.nb);
+  if (!M) return false;
+  dim3 g(((L.nx + TX - 1) / TX) * ((L.ny + TY - 1) / TY), bt.nb);
+  size_t sm = tma_smem(TX, TY, H);
+  if (tile == 0) k_up2d_tma<64, 32><<<g, kFusedThreads, sm, st>>>(L, Lc, bt, round, npost, dmask, *M);
+  else if (tile == 1) k_up2d_tma<32, 32><<<g, kFusedThreads, sm, st>>>(L, Lc, bt, round, npost, dmask, *M);
+  else k_up2d_tma<32, 16><<<g, kFusedThreads, sm, st>>>(L, Lc, bt, round, npost, dmask, *M);
+  return true;
+}
+
 // ---------------------------------------------------------------- host launcher
 int launch_vcycle(const MGHost& mg, const Batch& bt, int round, cudaStream_t st, int* nlaunch, Prof* pf) {
   const int nb = bt.nb;
@@ -458,15 +750,19 @@ int launch_vcycle(const MGHost& mg, const Batch& bt, int round, cudaStream_t st,
     set_attrs<64, 32>();
     set_attrs<32, 32>();
     set_attrs<32, 16>();
+    set_attrs_tma<64, 32>();
+    set_attrs_tma<32, 32>();
+    set_attrs_tma<32, 16>();
     attr_done = true;
   }
+  if (mg.tma && !mg.tma_cache) const_cast<MGHost&>(mg).tma_cache = new TmaCache();
   const int tile = (mg.tile >= 0 && mg.tile < 3) ? mg.tile : 2;
   for (int l = 0; l < mg.lc; ++l) {
     const Level& L = mg.h_levels[l];
     const Level& Lc = mg.h_levels[l + 1];
     if (fused_ok(L) && mg.npre > 0) {
       prof_begin(pf, KC_FUSED_DOWN, st);
-      launch_down(tile, L, Lc, bt, round, mg.npre, st);
+      if (!launch_down_tma(mg, l, tile, L, Lc, bt, round, mg.npre, st)) launch_down(tile, L, Lc, bt, round, mg.npre, st);
       prof_end(pf, KC_FUSED_DOWN, st);
       ++*nlaunch;
       continue;
@@ -496,7 +792,8 @@ int launch_vcycle(const MGHost& mg, const Batch& bt, int round, cudaStream_t st,
     const Level& Lc = mg.h_levels[l + 1];
     if (fused_ok(L) && mg.npost > 0) {
       prof_begin(pf, KC_FUSED_UP, st);
-      launch_up(tile, L, Lc, bt, round, mg.npost, mg.dmask, st);
+      if (!launch_up_tma(mg, l, tile, L, Lc, bt, round, mg.npost, mg.dmask, st))
+        launch_up(tile, L, Lc, bt, round, mg.npost, mg.dmask, st);
       prof_end(pf, KC_FUSED_UP, st);
       ++*nlaunch;
       continue;
