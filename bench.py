@@ -132,20 +132,19 @@ def cpu_baseline_sample(prob, nshift: int = 16, t_index: int = 0, k0: int = 0):
     return n, dt
 
 
-JAC_WORKLOAD = "3d-64x64x16 (config-3 fields at 1/8 of the cells), 16 sources, 48 receivers, 10 times, Nz=16"
+JAC_WORKLOAD = ("3d-128x128x32 log-normal kappa (var 1.0) and Ss (var 0.25), 16 sources, 48 receivers, "
+                "10 times, Nz=16: 7680 rows x 1,048,576 entries")
 
 
 def jacobian_rows(dev, stream, reps: int = 1):
-    """Jacobian rows per second of lt_adjoint_jacobian (J materialised on the device) on the
-    config-3 fields at a reduced grid (64x64x16: the full 128x128x32 needs ~250 GB for bases,
-    fields and J together)."""
+    """Jacobian rows per second of lt_adjoint_jacobian on config 3 at full size (J materialised
+    on the device: 64 GB), timed with CUDA events after one warm-up Jacobian."""
     import torch
     import workloads as W
     from paper_1409_2556_gb300 import Engine
-    prob = W.config3(nxy=64, nz=16)
+    prob = W.config3()
     eng = Engine(dev, stream=stream)
-    eng.load_problem(prob, tol=1e-10, maxit=250, inner_relax=1e-6, mg_pre=2, mg_post=2, inner_rounds=4,
-                     inner_cycles=6, check_every=4, groups=1)
+    eng.load_problem(prob, tol=1e-10, maxit=72, inner_relax=1e-6, groups=1, check_every=4)
     ns, nr, nt = len(prob.src_cells), len(prob.rec_cells), len(prob.times)
     J = torch.zeros((ns, nr, nt, 2, prob.ncell), dtype=torch.float64, device=f"cuda:{dev}")
     eng.adjoint_jacobian(prob.times, J)
