@@ -36,21 +36,39 @@ RESIDUAL_BAR = 1e-8
 # measurements within 1e-8 (relative L2) of the FP64 oracle; the metric's
 # 1e-8 residual bar is then met with margin.
 SOLVE_OPTS = dict(tol=1e-10, maxit=160, tau_policy=1, tau_project=1, mg_pre=2, mg_post=2,
-                  inner_cycles=6, inner_rounds=4, inner_tol=0.0, inner_relax=1e-6, true_residual=1,
-                  check_every=4, graphs=1, mg_tile=2)
-TIMED_CLASS = "fused_up"    # dominant kernel class (prolongation + post-smoothing tile kernel)
-# algorithmic bytes per fine cell per launch (float32 complex vectors, float32 coefficients):
+                  inner_cycles=6, inner_rounds=8, inner_tol=0.0, inner_relax=1e-4, true_residual=1,
+                  check_every=4, graphs=1, mg_tile=2, mg_cluster=1)
+# Dominant kernel class of the step: the cluster-resident preconditioner solve when the grid splits
+# into cluster strips (config 2 does), else the fused prolongation + post-smoothing tile kernel.
+# The cluster kernel keeps every level in shared memory, so its bound is on-chip arithmetic: its
+# roofline counts float32 flops per fine cell per V-cycle of V(pre, post) against the FP32 FMA peak
+# (152 SMs x 128 lanes x 2 flops x the maximum SM clock):
+#   per cell of a level: (pre + post) red-black updates x 24 (4 complex-by-real FMAs = 16, + f = 2,
+#   x inverse diagonal = 6) + residual-and-restriction 28 + prolongation 18; levels add up to 4/3
+#   of the fine cells (2D, full coarsening).
+# The tile kernel streams its operands: algorithmic bytes per fine cell per launch (float32):
 #   fused_up  : read u, f (8+8), Te, Tn, D, m (4x4), coarse u (8/4); write u (8)        = 42
-#   fused_down: read u, f, Te, Tn, D, m (32); write u (8), coarse f and u (2 x 8/4)     = 44
-BYTES_PER_UNIT = {"fused_up": 42.0, "fused_down": 44.0}
+BYTES_PER_UNIT = {"fused_up": 42.0}
 KERNEL_NAMES = {"fused_up": "k_up2d (prolongation + correction + red-black post-smoothing, 2D tile)",
-                "fused_down": "k_down2d (red-black pre-smoothing + residual + restriction, 2D tile)"}
+                "inner": "k_inner_cluster (whole preconditioner solve per basis in one 8-CTA cluster)"}
+FP32_LANES = 152 * 128
+
+
+def inner_flops_per_unit(pre: int, post: int) -> float:
+    return (24.0 * (pre + post) + 28.0 + 18.0) * 4.0 / 3.0
 WORKLOAD_NAME = "lognormal-256x256-var1.5-9src-25rec-Nz32-12t-3groups"
 
 
 def workload(rank: int = 0):
     import workloads as W
     return W.config2(seed=2 + rank)
+
+
+def _sm_max_mhz() -> float:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p)).get("sm_max_mhz", 2070.0))
+    return 2070.0
 
 
 def _peaks():
@@ -390,14 +408,15 @@ def main():
     # roofline pass: the same K steps again, now with CUDA events around every
     # launch of the dominant kernel class (kept out of the timed region above,
     # whose value the events would slow down)
-    eng.set_options(timing_class=_lib.KC[TIMED_CLASS])
+    timed_class = "inner" if eng.last_stats["work"][_lib.KC["inner"]] > 0 else "fused_up"
+    eng.set_options(timing_class=_lib.KC[timed_class])
     timed_ms, timed_n, work = 0.0, 0, 0
     for _ in range(args.steps):
         eng.forward(prob.times, out=h)
         st = eng.last_stats
         timed_ms += st["timed_ms"]
         timed_n += st["timed_launches"]
-        work += st["work"][_lib.KC[TIMED_CLASS]]
+        work += st["work"][_lib.KC[timed_class]]
     eng.set_options(timing_class=-1)
 
     # end to end through the public API with host buffers (H2D of the
@@ -424,17 +443,30 @@ def main():
         + prob.times.nbytes + 6 * 4
     d2h = hh.nbytes
 
-    peak, peak_kind = _peaks()
-    bpu = BYTES_PER_UNIT[TIMED_CLASS]
-    achieved = (work * bpu / 1e9) / (timed_ms / 1e3) if timed_ms > 0 else None
-    roof = {"kernel": KERNEL_NAMES[TIMED_CLASS], "bound": "hbm",
-            "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
-            "traffic": None,
-            "traffic_note": ("ncu on a 9-basis case read 2.9-11.7 MB per launch (L2-resident working set); "
-                             "does not scale in proportion to a full launch, so not reported"), "launches_timed": timed_n, "avg_launch_us": 1000.0 * timed_ms / max(timed_n, 1),
-            "bytes_per_unit": bpu, "units": work,
-            "measured": "CUDA events around each launch of the class, in a separate pass of the same steps"}
+    if timed_class == "inner":
+        fpu = inner_flops_per_unit(tuned["mg_pre"], tuned["mg_post"])
+        sm_mhz = _sm_max_mhz()
+        peak = FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+        achieved = (work * fpu / 1e12) / (timed_ms / 1e3) if timed_ms > 0 else None
+        roof = {"kernel": KERNEL_NAMES["inner"], "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                "peak_kind": f"derived: 152 SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz",
+                "traffic": None,
+                "traffic_note": "iterates, right-hand sides and coarse coefficients stay in shared memory for "
+                                "the whole solve; DRAM traffic per launch is in profiles/",
+                "launches_timed": timed_n, "avg_launch_us": 1000.0 * timed_ms / max(timed_n, 1),
+                "flops_per_unit": fpu, "unit_of_work": "fine cell x V-cycle", "units": work,
+                "measured": "CUDA events around each launch of the class, in a separate pass of the same steps"}
+    else:
+        peak, peak_kind = _peaks()
+        bpu = BYTES_PER_UNIT["fused_up"]
+        achieved = (work * bpu / 1e9) / (timed_ms / 1e3) if timed_ms > 0 else None
+        roof = {"kernel": KERNEL_NAMES["fused_up"], "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
+                "traffic": None, "launches_timed": timed_n, "avg_launch_us": 1000.0 * timed_ms / max(timed_n, 1),
+                "bytes_per_unit": bpu, "units": work,
+                "measured": "CUDA events around each launch of the class, in a separate pass of the same steps"}
     jac = None if args.no_jacobian else jacobian_rows(dev, stream)
     bat = None if args.no_batch else batch_throughput(dev)
     lrn = None if args.no_learned else learned_gain(dev)
@@ -452,8 +484,9 @@ def main():
             "vs_baseline": None, "dtype": "df32+f32", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "shifted_systems_per_step": ns * nt * prob.Nz // 2,
                        "solver_tol": SOLVE_OPTS["tol"], "residual_bar": RESIDUAL_BAR,
-                       "autotuned": {k: tuned[k] for k in ("mg_tile", "mg_pre", "mg_post", "inner_rounds",
-                                                             "inner_cycles", "inner_relax", "mg_tma")},
+                       "autotuned": {k: tuned[k] for k in ("mg_cluster", "mg_tile", "mg_pre", "mg_post",
+                                                             "inner_rounds", "inner_cycles", "inner_relax",
+                                                             "mg_tma")},
                        "max_true_residual": tres, "outer_iters_max": max(iters),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (Krylov bases ~GBs per step)"},

@@ -68,6 +68,10 @@ typedef struct {
   int    mg_tile;       /* fused 2D smoother tile: 0 = 64x32, 1 = 32x32, 2 = 32x16 cells (default 2) */
   int    precond;       /* 0: multigrid (default); 1: learned initial guess + multigrid (see lt_set_learned_preconditioner) */
   int    mg_tma;        /* 1: stage the fused 2D tiles with TMA bulk tensor copies when alignment allows (default) */
+  int    mg_cluster;    /* 1: run each preconditioner solve (all rounds and V-cycles) inside one 8-CTA thread-block
+                           cluster with the multigrid levels in distributed shared memory, on grids that allow it
+                           (2D, rows divisible into 8 strips per level, levels fit in shared memory; default);
+                           0: batched multigrid launches */
 } lt_opts;
 
 /* kernel classes reported in lt_stats.work[] and selectable by lt_opts.timing_class */
@@ -85,7 +89,8 @@ typedef struct {
 #define LT_KC_TRUE_RES  11
 #define LT_KC_FUSED_DOWN 12  /* fused 2D tile: pre-smoothing + residual + restriction (cells counted once) */
 #define LT_KC_FUSED_UP   13  /* fused 2D tile: prolongation + correction + post-smoothing */
-#define LT_KC_COUNT     15
+#define LT_KC_INNER      15  /* cluster-resident preconditioner solve (fine-level cells x V-cycles) */
+#define LT_KC_COUNT     16
 
 typedef struct {
   int    n_bases;             /* Krylov bases built (sources x groups, or receivers x groups) */

@@ -26,7 +26,7 @@ LT_TAU_FLEXIBLE = 1
 
 # kernel classes (lt_stats.work, lt_opts.timing_class)
 KC_NAMES = ["rbgs", "restrict", "prolong", "coarse", "exact_res", "update_u", "dots", "ortho", "normalize",
-            "shift_ls", "xk", "true_res", "fused_down", "fused_up", "other"]
+            "shift_ls", "xk", "true_res", "fused_down", "fused_up", "other", "inner"]
 KC_COUNT = len(KC_NAMES)
 KC = {n: i for i, n in enumerate(KC_NAMES)}
 
@@ -37,7 +37,7 @@ class LtOpts(C.Structure):
                 ("inner_cycles", C.c_int), ("inner_rounds", C.c_int), ("inner_tol", C.c_double),
                 ("true_residual", C.c_int), ("check_every", C.c_int), ("timing_class", C.c_int),
                 ("inner_relax", C.c_double), ("graphs", C.c_int), ("mg_tile", C.c_int), ("precond", C.c_int),
-                ("mg_tma", C.c_int)]
+                ("mg_tma", C.c_int), ("mg_cluster", C.c_int)]
 
 
 class LtStats(C.Structure):

@@ -1,9 +1,11 @@
 """Autotuner for the multigrid and inner-solve settings of a workload.
 
 Times short forward solves of the actual problem for a small grid of
-candidate settings -- fused-smoother tile shape, pre/post smoothing sweeps,
-V-cycles per refinement round, refinement rounds -- and keeps the fastest
-candidate whose every shifted system reaches the tolerance (true residual).
+candidate settings -- cluster-resident or batched preconditioner solves,
+fused-smoother tile shape and TMA staging (batched only), pre/post smoothing
+sweeps, V-cycles per refinement round, refinement rounds, relaxation -- and
+keeps the fastest candidate whose every shifted system reaches the tolerance
+(true residual).
 Results are cached per problem shape in memory (and optionally in a JSON
 file).  The measurement is the library's own device time (CUDA events on
 the context stream).
@@ -15,14 +17,17 @@ import json
 import os
 from typing import Dict, Optional
 
+from ._lib import KC
+
 _CACHE: Dict[str, dict] = {}
 
 DEFAULT_GRID = {
-    "mg_tile": [0, 1, 2],
+    "mg_cluster": [1, 0],
+    "mg_tile": [1, 2],
     "sweeps": [(2, 2), (3, 3)],
-    "inner": [(4, 6), (5, 4)],
+    "inner": [(4, 6), (5, 4), (8, 6)],
     "inner_relax": [1e-6, 1e-4],
-    "mg_tma": [1, 0],
+    "mg_tma": [1],
 }
 
 
@@ -49,23 +54,33 @@ def autotune(engine, prob, base_opts: dict, grid: Optional[dict] = None, reps: i
     engine.load_problem(prob, **base_opts)
     best, best_ms = None, float("inf")
     relax = grid.get("inner_relax", [base_opts.get("inner_relax", 0.0)])
-    tmas = grid.get("mg_tma", [base_opts.get("mg_tma", 1)])
-    for tile, (pre, post), (rounds, cycles), rx, tma in itertools.product(grid["mg_tile"], grid["sweeps"],
-                                                                         grid["inner"], relax, tmas):
-        cand = dict(base_opts, mg_tile=tile, mg_pre=pre, mg_post=post, inner_rounds=rounds, inner_cycles=cycles,
-                    inner_relax=rx, mg_tma=tma)
-        engine.set_options(**{k: v for k, v in cand.items() if k not in ("Nz", "tol", "groups")})
-        ms = 0.0
-        ok = True
-        for _ in range(reps + 1):                      # first run warms the graph and workspace
-            engine.forward(prob.times, allow_unconverged=True)
-            st = engine.last_stats
-            ok &= st["n_converged"] == st["n_shift_solves"]
-        ms = st["ms_total"]
-        if verbose:
-            print(f"autotune tile={tile} sweeps={pre},{post} inner={rounds}x{cycles} relax={rx}: {ms:.1f} ms ok={ok}")
-        if ok and ms < best_ms:
-            best, best_ms = cand, ms
+    clusters = grid.get("mg_cluster", [base_opts.get("mg_cluster", 1)])
+    cluster_possible = True
+    for cl in clusters:
+        # tile shape and TMA staging only matter to the batched launches
+        tiles = grid["mg_tile"] if cl == 0 else [base_opts.get("mg_tile", 2)]
+        tmas = grid.get("mg_tma", [base_opts.get("mg_tma", 1)]) if cl == 0 else [base_opts.get("mg_tma", 1)]
+        for tile, (pre, post), (rounds, cycles), rx, tma in itertools.product(tiles, grid["sweeps"],
+                                                                             grid["inner"], relax, tmas):
+            if cl == 1 and not cluster_possible:
+                break
+            cand = dict(base_opts, mg_cluster=cl, mg_tile=tile, mg_pre=pre, mg_post=post, inner_rounds=rounds,
+                        inner_cycles=cycles, inner_relax=rx, mg_tma=tma)
+            engine.set_options(**{k: v for k, v in cand.items() if k not in ("Nz", "tol", "groups")})
+            ok = True
+            for _ in range(reps + 1):                      # first run warms the graph and workspace
+                engine.forward(prob.times, allow_unconverged=True)
+                st = engine.last_stats
+                ok &= st["n_converged"] == st["n_shift_solves"]
+            ms = st["ms_total"]
+            if cl == 1 and st["work"][KC["inner"]] == 0:   # the grid does not split into cluster strips
+                cluster_possible = False
+                continue
+            if verbose:
+                print(f"autotune cluster={cl} tile={tile} tma={tma} sweeps={pre},{post} inner={rounds}x{cycles} "
+                      f"relax={rx}: {ms:.1f} ms ok={ok}")
+            if ok and ms < best_ms:
+                best, best_ms = cand, ms
     if best is None:
         best = dict(base_opts)
     best = dict(best)

@@ -1,0 +1,638 @@
+// inner.cu -- the preconditioner solve (K + tau_j M) u_j = v_j of one Krylov
+// basis (Sec. 3: the shift-and-invert step of Algorithm 1), all refinement
+// rounds and V-cycles, inside one thread-block cluster.
+//
+// The arithmetic is that of the batched launches in krylov.cu and mg.cu:
+// rounds of  r = v_j - (K + tau M) u_j  in df32, float32 V-cycles on A d = r
+// (red-black Gauss-Seidel, sum restriction, bilinear prolongation, dense
+// inverse or sweeps at the coarsest level), u_j += d in df32, until
+// ||r||^2 <= itol2.  What changes is where the data lives:
+//   * the kCS CTAs of a cluster split every multigrid level above
+//     kCoarseCells cells into kCS strips of whole rows; each CTA keeps the
+//     iterate and right-hand side of its strips in shared memory for the
+//     whole solve and reads the row just outside a strip from the
+//     neighbouring CTA's shared memory (distributed shared memory);
+//   * the levels of at most kCoarseCells cells live in rank 0, which runs
+//     their sweeps; the dense inverse of the coarsest level is applied by all
+//     ranks, a slice of its rows each;
+//   * a cluster barrier follows every red or black half-sweep, so every
+//     half-sweep sees the other colour exactly as the global sweep does;
+//   * the squared residual norm of each round is summed over the cluster in
+//     rank order, so every CTA takes the same branch.
+// One launch replaces the (rounds x (cycles x V-cycle launches + 2)) launches
+// of the batched path.
+#include <cooperative_groups.h>
+
+#include "df32.cuh"
+#include "exact.cuh"
+#include "lt_internal.h"
+#include "lt_kernels.h"
+#include "mg_dev.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace lt {
+
+constexpr int kCS = 8;                        // CTAs per cluster (portable cluster size)
+constexpr int kIT = 512;                     // threads per CTA
+constexpr size_t kInnerSmemMax = 220 * 1024;  // dynamic shared memory per CTA
+constexpr int kL0Batch = 2;                   // finest-level cells per thread whose loads are issued together
+
+// Byte offsets of one level's arrays in dynamic shared memory.  The finest
+// level keeps only its iterate there (coefficients and right-hand side are
+// read from global memory, batched); every coarser level also keeps its
+// right-hand side, east/north face transmissibilities and the inverse of its
+// complex diagonal, staged once per launch.
+struct LevOff { int u, f, te, tn, di; };
+
+struct InnerArgs {
+  Batch bt;
+  FineExact fe;
+  const Level* levels;          // device copy of the level descriptors
+  float2* f0;                   // [nb][N] right-hand side of the finest level (global)
+  int nlev, ld;                 // levels [0, ld) in strips, [ld, nlev) in rank 0
+  int npre, npost, dmask, coarse_direct, rounds, cycles;
+  LevOff off[kMaxLevels];
+  int off_rhs;                  // byte offset of rank 0's coarsest right-hand side copy
+};
+
+// The finest level's rows [y0, y0 + h) of this CTA.
+struct L0V {
+  int nx, ny, h, y0;
+  const float* __restrict__ Te;
+  const float* __restrict__ Tn;
+  const float* __restrict__ D;
+  const float* __restrict__ m;
+  const float2* f;               // whole-level right-hand side (global cell index; rewritten every round)
+  float2* u;                     // [h][nx], shared memory
+  const float2* u_dn;            // iterate of rank - 1 (its last row lies just below y0), or null
+  const float2* u_up;            // iterate of rank + 1 (its first row lies just above y0 + h - 1), or null
+};
+
+// A staged level's rows [y0, y0 + h) (a strip of a distributed level, or a whole coarse level with y0 = 0).
+struct SV {
+  int nx, ny, h, y0;
+  float2* u;                     // [h][nx]
+  float2* f;                     // [h][nx]
+  float* te;                     // [h][nx]    face (x, y)-(x+1, y)
+  float* tn;                     // [h+1][nx]  row r: face (x, y0+r-1)-(x, y0+r)
+  float2* di;                    // [h][nx]    1 / (D + tau m)
+  const float2* u_dn;
+  const float2* u_up;
+};
+
+// Read access to the iterate of the next coarser level, for the prolongation.
+struct CoarseView {
+  int nx, ny;
+  int full;                      // 1: the whole level in one array (rank 0's), 0: strips
+  int hc, yc0;                   // own strip rows when !full
+  const float2* loc;
+  const float2* dn;
+  const float2* up;
+};
+
+__device__ __forceinline__ void axpy_c(float2& r, float t, float2 v) { r.x += t * v.x; r.y += t * v.y; }
+
+// ---------------------------------------------------------------- finest level (global coefficients)
+// loads of one cell of the finest level: the four faces, diagonal parts and right-hand side
+struct L0Cell { float te_e, te_w, tn_n, tn_s, d, m; float2 f; };
+
+__device__ __forceinline__ L0Cell l0_load(const L0V& S, int x, int y, int c) {
+  L0Cell q;
+  q.te_e = x + 1 < S.nx ? S.Te[c] : 0.f;
+  q.te_w = x > 0 ? S.Te[c - 1] : 0.f;
+  q.tn_n = y + 1 < S.ny ? S.Tn[c] : 0.f;
+  q.tn_s = y > 0 ? S.Tn[c - S.nx] : 0.f;
+  q.d = S.D[c];
+  q.m = S.m[c];
+  q.f = S.f[c];
+  return q;
+}
+
+// sum over the four neighbours of T u_nb (zero faces contribute nothing, so no boundary tests on them)
+__device__ __forceinline__ float2 l0_nb(const L0V& S, const L0Cell& q, int x, int y, int ly, int li) {
+  float2 s = make_float2(0.f, 0.f);
+  if (x + 1 < S.nx) axpy_c(s, q.te_e, S.u[li + 1]);
+  if (x > 0) axpy_c(s, q.te_w, S.u[li - 1]);
+  if (y + 1 < S.ny) axpy_c(s, q.tn_n, ly + 1 < S.h ? S.u[li + S.nx] : S.u_up[x]);
+  if (y > 0) axpy_c(s, q.tn_s, ly > 0 ? S.u[li - S.nx] : S.u_dn[(S.h - 1) * S.nx + x]);
+  return s;
+}
+
+// one red (color 0) or black (color 1) half-sweep over the strip's cells of that colour
+__device__ __forceinline__ void l0_half_sweep(const L0V& S, float2 tau, int color) {
+  const int hx = S.nx >> 1, n = S.h * hx;
+  for (int q0 = threadIdx.x; q0 < n; q0 += kL0Batch * kIT) {
+    L0Cell cq[kL0Batch];
+#pragma unroll
+    for (int k = 0; k < kL0Batch; ++k) {
+      const int q = q0 + k * kIT;
+      if (q < n) {
+        const int ly = q / hx, y = S.y0 + ly, x = 2 * (q - ly * hx) + ((color + y) & 1);
+        cq[k] = l0_load(S, x, y, y * S.nx + x);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kL0Batch; ++k) {
+      const int q = q0 + k * kIT;
+      if (q < n) {
+        const int ly = q / hx, y = S.y0 + ly, x = 2 * (q - ly * hx) + ((color + y) & 1), li = ly * S.nx + x;
+        float2 r = l0_nb(S, cq[k], x, y, ly, li);
+        r.x += cq[k].f.x; r.y += cq[k].f.y;
+        S.u[li] = cdiv(r, make_float2(cq[k].d + tau.x * cq[k].m, tau.y * cq[k].m));
+      }
+    }
+  }
+}
+
+// residual summed over 2x2 children into the coarse right-hand side (coarse row J at row J - row0 of fc);
+// returns this thread's sum of |r|^2 over the fine cells (the V-cycle's convergence monitor)
+__device__ __forceinline__ float l0_restrict(const L0V& S, float2 tau, float2* fc, int ncx, int row0) {
+  const int nch = S.h >> 1, n = nch * ncx;
+  float rr = 0.f;
+  for (int q = threadIdx.x; q < n; q += kIT) {
+    const int lJ = q / ncx, I = q - lJ * ncx;
+    L0Cell cq[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int x = 2 * I + (k & 1), ly = 2 * lJ + (k >> 1), y = S.y0 + ly;
+      cq[k] = l0_load(S, x, y, y * S.nx + x);
+    }
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int x = 2 * I + (k & 1), ly = 2 * lJ + (k >> 1), y = S.y0 + ly, li = ly * S.nx + x;
+      const float2 s = l0_nb(S, cq[k], x, y, ly, li);
+      const float2 a = cmul(make_float2(cq[k].d + tau.x * cq[k].m, tau.y * cq[k].m), S.u[li]);
+      const float rx = cq[k].f.x - a.x + s.x, ry = cq[k].f.y - a.y + s.y;
+      acc.x += rx;
+      acc.y += ry;
+      rr += rx * rx + ry * ry;
+    }
+    fc[(S.y0 / 2 + lJ - row0) * ncx + I] = acc;
+  }
+  return rr;
+}
+
+// ---------------------------------------------------------------- staged levels (shared memory)
+__device__ __forceinline__ float2 sv_nb(const SV& S, int x, int y, int ly, int li) {
+  float2 s = make_float2(0.f, 0.f);
+  if (x + 1 < S.nx) axpy_c(s, S.te[li], S.u[li + 1]);
+  if (x > 0) axpy_c(s, S.te[li - 1], S.u[li - 1]);
+  if (y + 1 < S.ny) axpy_c(s, S.tn[li + S.nx], ly + 1 < S.h ? S.u[li + S.nx] : S.u_up[x]);
+  if (y > 0) axpy_c(s, S.tn[li], ly > 0 ? S.u[li - S.nx] : S.u_dn[(S.h - 1) * S.nx + x]);
+  return s;
+}
+
+// kCompact: the level has an even number of columns, so thread q maps directly to the q-th cell of the colour
+template <bool kCompact>
+__device__ __forceinline__ void sv_half_sweep(const SV& S, int color) {
+  const int hx = S.nx >> 1;
+  const int n = kCompact ? S.h * hx : S.h * S.nx;
+  for (int q = threadIdx.x; q < n; q += kIT) {
+    int ly, x;
+    if (kCompact) {
+      ly = q / hx;
+      x = 2 * (q - ly * hx) + ((color + S.y0 + ly) & 1);
+    } else {
+      ly = q / S.nx;
+      x = q - ly * S.nx;
+      if (((x + S.y0 + ly) & 1) != color) continue;
+    }
+    const int y = S.y0 + ly, li = ly * S.nx + x;
+    float2 r = sv_nb(S, x, y, ly, li);
+    const float2 fv = S.f[li];
+    r.x += fv.x; r.y += fv.y;
+    S.u[li] = cmul(r, S.di[li]);
+  }
+}
+
+// residual of the staged level summed over rx x ry children into the coarse right-hand side;
+// zero_uc: also clear the coarse iterate (coarse levels owned by this CTA)
+__device__ __forceinline__ void sv_restrict(const SV& S, int rx, int ry, float2* fc, float2* uc, int ncx, int row0) {
+  const int nch = S.h / ry, n = nch * ncx;
+  for (int q = threadIdx.x; q < n; q += kIT) {
+    const int lJ = q / ncx, I = q - lJ * ncx;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int dj = 0; dj < ry; ++dj)
+      for (int di = 0; di < rx; ++di) {
+        const int x = I * rx + di, ly = lJ * ry + dj, y = S.y0 + ly, li = ly * S.nx + x;
+        const float2 s = sv_nb(S, x, y, ly, li);
+        const float2 a = cmul(cinv(S.di[li]), S.u[li]);
+        const float2 fv = S.f[li];
+        acc.x += fv.x - a.x + s.x;
+        acc.y += fv.y - a.y + s.y;
+      }
+    const int C = (S.y0 / ry + lJ - row0) * ncx + I;
+    fc[C] = acc;
+    if (uc) uc[C] = make_float2(0.f, 0.f);
+  }
+}
+
+__device__ __forceinline__ float2 cv_get(const CoarseView& V, int I, int J) {
+  if (V.full) return V.loc[J * V.nx + I];
+  const int lJ = J - V.yc0;
+  if (lJ < 0) return V.dn[(V.hc - 1) * V.nx + I];
+  if (lJ >= V.hc) return V.up[I];
+  return V.loc[lJ * V.nx + I];
+}
+
+// u += bilinear interpolation of the coarse correction (weights 3/4, 1/4 per axis) on rows [y0, y0 + h)
+__device__ __forceinline__ void strip_prolong(float2* u, int nx, int h, int y0, const CoarseView& V, int dmask) {
+  const int n = h * nx;
+  for (int q = threadIdx.x; q < n; q += kIT) {
+    const int ly = q / nx, x = q - ly * nx, y = y0 + ly;
+    int I0, I1, J0, J1;
+    float wi0, wi1, wj0, wj1, si, sj;
+    axis_interp(x, 2, V.nx, dmask & 1, dmask & 2, I0, I1, wi0, wi1, si);
+    axis_interp(y, 2, V.ny, dmask & 4, dmask & 8, J0, J1, wj0, wj1, sj);
+    wi1 *= si; wj1 *= sj;
+    const float2 a = cv_get(V, I0, J0), bq = cv_get(V, I1, J0), c = cv_get(V, I0, J1), d = cv_get(V, I1, J1);
+    const float w00 = wj0 * wi0, w01 = wj0 * wi1, w10 = wj1 * wi0, w11 = wj1 * wi1;
+    float2 v = u[q];
+    v.x += w00 * a.x + w01 * bq.x + w10 * c.x + w11 * d.x;
+    v.y += w00 * a.y + w01 * bq.y + w10 * c.y + w11 * d.y;
+    u[q] = v;
+  }
+}
+
+// sum of v over the CTA's threads into *dst (thread 0's view after the call)
+__device__ __forceinline__ void block_sum(float v, float* red, double* dst) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < kIT / 32 ? red[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) *dst = (double)v;
+  }
+}
+
+// sum of v over the cluster's threads; identical on every CTA (ranks added in order)
+__device__ __forceinline__ double cluster_sum(cg::cluster_group& cl, float v, float* red, double* part, int slot,
+                                              double* bcast) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < kIT / 32 ? red[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) part[slot] = (double)v;
+  }
+  cl.sync();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < kCS; ++q) s += *cl.map_shared_rank(&part[slot], q);
+    *bcast = s;
+  }
+  __syncthreads();
+  return *bcast;
+}
+
+__global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cluster(const __grid_constant__ InnerArgs a) {
+  extern __shared__ float4 dsm4[];
+  char* smb = reinterpret_cast<char*>(dsm4);
+  __shared__ Level sL[kMaxLevels];
+  __shared__ float red[32];
+  __shared__ double part[2];
+  __shared__ double bcast;
+  __shared__ double vpart[2];           // per-cycle fine residual norm^2 of this CTA's rows
+  __shared__ int vstop;                 // 1: this V-cycle ends the round
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int b = blockIdx.x / kCS;
+  const Batch& bt = a.bt;
+  if (!bt.active[b]) return;            // the same answer on every CTA of the cluster
+  const int tid = threadIdx.x;
+  if (tid < a.nlev) sL[tid] = a.levels[tid];
+  __syncthreads();
+  const int j = *bt.jdev;
+  const double2 td = bt.tau_cur[b];
+  const float2 tau = make_float2((float)td.x, (float)td.y);
+  const df taur = df_from_double(td.x), taui = df_from_double(td.y);
+  const int R = a.rounds, R1 = R + 1;
+  const double itol2 = bt.itol2[b];
+
+  // views of every level: strips [0, ld) (rows of this rank), whole coarse levels [ld, nlev) (rank 0)
+  auto sview = [&](int l) {
+    const Level& L = sL[l];
+    const LevOff& o = a.off[l];
+    SV S;
+    S.nx = L.nx; S.ny = L.ny;
+    if (l < a.ld) { S.h = L.ny / kCS; S.y0 = rank * S.h; }
+    else { S.h = L.ny; S.y0 = 0; }
+    S.u = reinterpret_cast<float2*>(smb + o.u);
+    S.f = reinterpret_cast<float2*>(smb + o.f);
+    S.te = reinterpret_cast<float*>(smb + o.te);
+    S.tn = reinterpret_cast<float*>(smb + o.tn);
+    S.di = reinterpret_cast<float2*>(smb + o.di);
+    S.u_dn = (l < a.ld && rank > 0) ? cl.map_shared_rank(S.u, rank - 1) : nullptr;
+    S.u_up = (l < a.ld && rank + 1 < kCS) ? cl.map_shared_rank(S.u, rank + 1) : nullptr;
+    return S;
+  };
+  auto cview = [&](int l) {   // view of level l + 1 from level l
+    const Level& Lc = sL[l + 1];
+    CoarseView V;
+    V.nx = Lc.nx; V.ny = Lc.ny;
+    float2* uc = reinterpret_cast<float2*>(smb + a.off[l + 1].u);
+    if (l + 1 == a.ld) {
+      V.full = 1; V.hc = Lc.ny; V.yc0 = 0;
+      V.loc = cl.map_shared_rank(uc, 0);
+      V.dn = nullptr; V.up = nullptr;
+    } else {
+      V.full = 0; V.hc = Lc.ny / kCS; V.yc0 = rank * V.hc;
+      V.loc = uc;
+      V.dn = rank > 0 ? cl.map_shared_rank(uc, rank - 1) : nullptr;
+      V.up = rank + 1 < kCS ? cl.map_shared_rank(uc, rank + 1) : nullptr;
+    }
+    return V;
+  };
+
+  // stage the coefficients of the strip levels >= 1 (own rows) and, in rank 0, of the coarse levels;
+  // clear every coarse iterate (each V-cycle clears them again after use)
+  for (int l = 1; l < a.nlev; ++l) {
+    if (l >= a.ld && rank != 0) break;
+    const Level& L = sL[l];
+    const SV S = sview(l);
+    const int n = S.h * S.nx;
+    for (int q = tid; q < n; q += kIT) {
+      const int c = S.y0 * S.nx + q;
+      S.te[q] = L.Te[c];
+      S.tn[S.nx + q] = L.Tn[c];
+      const float mm = L.m[c];
+      S.di[q] = cinv(make_float2(L.D[c] + tau.x * mm, tau.y * mm));
+      S.u[q] = make_float2(0.f, 0.f);
+    }
+    for (int x = tid; x < S.nx; x += kIT) S.tn[x] = S.y0 > 0 ? L.Tn[(S.y0 - 1) * S.nx + x] : 0.f;
+  }
+  L0V S0;
+  {
+    const Level& L = sL[0];
+    S0.nx = L.nx; S0.ny = L.ny; S0.h = L.ny / kCS; S0.y0 = rank * S0.h;
+    S0.Te = L.Te; S0.Tn = L.Tn; S0.D = L.D; S0.m = L.m;
+    S0.f = a.f0 + (size_t)b * bt.N;
+    S0.u = reinterpret_cast<float2*>(smb + a.off[0].u);
+    S0.u_dn = rank > 0 ? cl.map_shared_rank(S0.u, rank - 1) : nullptr;
+    S0.u_up = rank + 1 < kCS ? cl.map_shared_rank(S0.u, rank + 1) : nullptr;
+  }
+  float2* f0w = a.f0 + (size_t)b * bt.N;
+  __syncthreads();
+  cl.sync();   // every CTA of the cluster is running and initialised before any remote access
+
+  const int c0 = S0.y0 * S0.nx, n0 = S0.h * S0.nx;
+  const size_t vb = ((size_t)b * (bt.maxit + 1) + j) * bt.N;
+  const size_t ub = ((size_t)b * bt.maxit + j) * bt.N;
+  int slot = 0;
+  for (int r = 0; r <= R; ++r) {
+    // df32 residual of the current u_j on this CTA's rows; it is the next round's right-hand side
+    float acc = 0.f;
+    for (int q = tid; q < n0; q += kIT) {
+      const int c = c0 + q;
+      cdf rr = load_cdf(bt.V_hi, bt.V_lo, vb + c);
+      if (r > 0) rr = cdf_sub(rr, apply_exact(a.fe, bt.U_hi + ub, bt.U_lo + ub, c, taur, taui));
+      if (r < R) {
+        f0w[c] = make_float2(rr.re.hi, rr.im.hi);
+        S0.u[q] = make_float2(0.f, 0.f);
+      }
+      acc += rr.re.hi * rr.re.hi + rr.im.hi * rr.im.hi;
+    }
+    const double rn2 = cluster_sum(cl, acc, red, part, slot, &bcast);
+    slot ^= 1;
+    const bool done = (r == R) || (rn2 <= itol2);
+    if (rank == 0 && tid == 0) {
+      bt.rnorm2[b * R1 + r] = rn2;
+      if (r < R && done) bt.rnorm2[b * R1 + R] = rn2;   // u_j is final: its residual is this one
+      atomicAdd(&bt.work[KC_EXACT_RES], (unsigned long long)bt.N);
+    }
+    if (done) {
+      if (r == 0)   // v_j itself is below the tolerance: u_j = 0
+        for (int q = tid; q < n0; q += kIT) {
+          bt.U_hi[ub + c0 + q] = make_float2(0.f, 0.f);
+          bt.U_lo[ub + c0 + q] = make_float2(0.f, 0.f);
+        }
+      break;
+    }
+    // V-cycles until the fine residual after pre-smoothing is below the round's goal: the inner
+    // tolerance, or the float32 floor (1e-11 of the round's right-hand side, squared norms), at most a.cycles
+    const double goal2 = fmax(itol2, 1e-11 * rn2);
+    for (int cy = 0; cy < a.cycles; ++cy) {
+      // ---- down: pre-smoothing, residual, restriction on the strip levels
+      for (int l = 0; l < a.ld; ++l) {
+        const bool last = (l + 1 == a.ld);
+        float2* fc = reinterpret_cast<float2*>(smb + a.off[l + 1].f);
+        if (last) fc = cl.map_shared_rank(fc, 0);
+        const int ncx = sL[l + 1].nx;
+        if (l == 0) {
+          for (int h = 0; h < 2 * a.npre; ++h) {
+            l0_half_sweep(S0, tau, h & 1);
+            cl.sync();
+          }
+          const float rr = l0_restrict(S0, tau, fc, ncx, last ? 0 : S0.y0 / 2);
+          block_sum(rr, red, &vpart[cy & 1]);
+        } else {
+          const SV S = sview(l);
+          for (int h = 0; h < 2 * a.npre; ++h) {
+            sv_half_sweep<true>(S, h & 1);
+            cl.sync();
+          }
+          sv_restrict(S, 2, 2, fc, nullptr, ncx, last ? 0 : S.y0 / 2);
+        }
+        __syncthreads();   // the next level's sweeps read right-hand sides written by other threads
+      }
+      cl.sync();   // rank 0 holds the whole restricted residual of level ld
+      if (tid == 0) {
+        double s2 = 0.0;
+        for (int q = 0; q < kCS; ++q) s2 += *cl.map_shared_rank(&vpart[cy & 1], q);
+        vstop = s2 <= goal2;
+        if (rank == 0) atomicAdd(&bt.work[KC_INNER], (unsigned long long)bt.N);
+      }
+      // ---- coarse levels in rank 0
+      if (rank == 0)
+        for (int l = a.ld; l < a.nlev - 1; ++l) {
+          const SV S = sview(l);
+          for (int h = 0; h < 2 * a.npre; ++h) {
+            sv_half_sweep<false>(S, h & 1);
+            __syncthreads();
+          }
+          const Level& Lc = sL[l + 1];
+          sv_restrict(S, sL[l].rx, sL[l].ry, reinterpret_cast<float2*>(smb + a.off[l + 1].f),
+                      reinterpret_cast<float2*>(smb + a.off[l + 1].u), Lc.nx, 0);
+          __syncthreads();
+        }
+      if (a.coarse_direct) {
+        // u_c = A_c^{-1} f_c; every rank takes a slice of the rows of the dense inverse
+        cl.sync();
+        const int lc = a.nlev - 1, N = sL[lc].N;
+        const float2* fr = cl.map_shared_rank(reinterpret_cast<float2*>(smb + a.off[lc].f), 0);
+        float2* ur = cl.map_shared_rank(reinterpret_cast<float2*>(smb + a.off[lc].u), 0);
+        float2* rhs = reinterpret_cast<float2*>(smb + a.off_rhs);
+        for (int i = tid; i < N; i += kIT) rhs[i] = fr[i];
+        __syncthreads();
+        const float2* A = bt.coarse_inv + (size_t)bt.tau_slot[b] * N * N;
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int row = rank * (kIT / 32) + warp; row < N; row += kCS * (kIT / 32)) {
+          const float2* Ar = A + (size_t)row * N;
+          float sx = 0.f, sy = 0.f;
+          for (int c = lane; c < N; c += 32) {
+            const float2 av = Ar[c], x = rhs[c];
+            sx += av.x * x.x - av.y * x.y;
+            sy += av.x * x.y + av.y * x.x;
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+          }
+          if (lane == 0) ur[row] = make_float2(sx, sy);
+        }
+        cl.sync();
+      } else if (rank == 0) {
+        const SV S = sview(a.nlev - 1);
+        for (int h = 0; h < 2 * kCoarseSweeps; ++h) {
+          sv_half_sweep<false>(S, h & 1);
+          __syncthreads();
+        }
+      }
+      if (rank == 0)
+        for (int l = a.nlev - 2; l >= a.ld; --l) {
+          const SV S = sview(l);
+          const float2* uc = reinterpret_cast<const float2*>(smb + a.off[l + 1].u);
+          for (int c = tid; c < sL[l].N; c += kIT) prolong_cell(sL[l], sL[l + 1], S.u, uc, c, a.dmask);
+          __syncthreads();
+          for (int h = 0; h < 2 * a.npost; ++h) {
+            sv_half_sweep<false>(S, (h + 1) & 1);
+            __syncthreads();
+          }
+        }
+      cl.sync();   // rank 0's level ld holds the coarse correction
+      // ---- up: prolongation, correction, post-smoothing on the strip levels
+      for (int l = a.ld - 1; l >= 0; --l) {
+        const CoarseView V = cview(l);
+        if (l == 0) strip_prolong(S0.u, S0.nx, S0.h, S0.y0, V, a.dmask);
+        else {
+          const SV S = sview(l);
+          strip_prolong(S.u, S.nx, S.h, S.y0, V, a.dmask);
+        }
+        cl.sync();
+        // every rank has read the coarse iterate: clear it for the next cycle
+        if (l + 1 < a.ld || rank == 0) {
+          const SV C = sview(l + 1);
+          for (int q = tid; q < C.h * C.nx; q += kIT) C.u[q] = make_float2(0.f, 0.f);
+        }
+        for (int h = 0; h < 2 * a.npost; ++h) {
+          if (l == 0) l0_half_sweep(S0, tau, (h + 1) & 1);
+          else sv_half_sweep<true>(sview(l), (h + 1) & 1);
+          cl.sync();
+        }
+      }
+      if (vstop) break;   // the same on every CTA: all read the same partial sums in the same order
+    }
+    // u_j += d (df32) on this CTA's rows; the next residual reads the neighbours' rows
+    for (int q = tid; q < n0; q += kIT) {
+      const size_t ui = ub + c0 + q;
+      const float2 d = S0.u[q];
+      if (r == 0) {
+        bt.U_hi[ui] = d;
+        bt.U_lo[ui] = make_float2(0.f, 0.f);
+      } else {
+        cdf u = load_cdf(bt.U_hi, bt.U_lo, ui);
+        u.re = df_add_f(u.re, d.x);
+        u.im = df_add_f(u.im, d.y);
+        store_cdf(bt.U_hi, bt.U_lo, ui, u);
+      }
+    }
+    cl.sync();
+  }
+  cl.sync();   // no CTA leaves while another may still read its shared memory
+}
+
+static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+int inner_cluster_plan(const MGHost& mg, InnerPlan& p) {
+  p.ok = 0;
+  const int ld = mg.lc;
+  if (ld < 1 || ld >= mg.nlev) return 0;
+  for (int l = 0; l < mg.nlev; ++l)
+    if (mg.h_levels[l].nz != 1) return 0;
+  for (int l = 0; l < ld; ++l) {
+    const Level& L = mg.h_levels[l];
+    const Level& Lc = mg.h_levels[l + 1];
+    if (L.rx != 2 || L.ry != 2 || L.rz != 1) return 0;
+    if (L.nx % 2 != 0 || L.ny % (2 * kCS) != 0) return 0;
+    if (Lc.nx * 2 != L.nx || Lc.ny * 2 != L.ny) return 0;
+  }
+  size_t cur = 0;
+  auto take = [&](size_t bytes) { const size_t o = cur; cur = align16(cur + bytes); return (int)o; };
+  for (int l = 0; l < mg.nlev; ++l) {
+    const Level& L = mg.h_levels[l];
+    const size_t h = l < ld ? (size_t)L.ny / kCS : (size_t)L.ny;
+    const size_t n = h * L.nx;
+    p.off_u[l] = take(n * sizeof(float2));
+    if (l == 0) {
+      p.off_f[l] = p.off_te[l] = p.off_tn[l] = p.off_di[l] = 0;
+      continue;
+    }
+    p.off_f[l] = take(n * sizeof(float2));
+    p.off_te[l] = take(n * sizeof(float));
+    p.off_tn[l] = take((h + 1) * L.nx * sizeof(float));
+    p.off_di[l] = take(n * sizeof(float2));
+  }
+  p.off_rhs = take(mg.coarse_direct ? (size_t)mg.h_levels[mg.nlev - 1].N * sizeof(float2) : 0);
+  p.smem = cur;
+  if (p.smem > kInnerSmemMax) return 0;
+  if (cudaFuncSetAttribute(k_inner_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  // the cluster must fit on the device (kCS SMs with this much shared memory each)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kCS);
+  cfg.blockDim = dim3(kIT);
+  cfg.dynamicSmemBytes = p.smem;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = kCS; attr.val.clusterDim.y = 1; attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, k_inner_cluster, &cfg) != cudaSuccess || nclusters < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  p.ld = ld;
+  p.max_clusters = nclusters;
+  p.ok = 1;
+  return 1;
+}
+
+int launch_inner_cluster(const MGHost& mg, const InnerPlan& p, const Batch& bt, const FineExact& fe, int cycles,
+                         cudaStream_t st, Prof* pf) {
+  InnerArgs a;
+  a.bt = bt;
+  a.fe = fe;
+  a.levels = mg.d_levels;
+  a.f0 = mg.h_levels[0].f;
+  a.nlev = mg.nlev;
+  a.ld = p.ld;
+  a.npre = mg.npre;
+  a.npost = mg.npost;
+  a.dmask = mg.dmask;
+  a.coarse_direct = mg.coarse_direct;
+  a.rounds = bt.rounds;
+  a.cycles = cycles;
+  for (int l = 0; l < kMaxLevels; ++l)
+    a.off[l] = LevOff{p.off_u[l], p.off_f[l], p.off_te[l], p.off_tn[l], p.off_di[l]};
+  a.off_rhs = p.off_rhs;
+  prof_begin(pf, KC_INNER, st);
+  k_inner_cluster<<<bt.nb * kCS, kIT, p.smem, st>>>(a);
+  prof_end(pf, KC_INNER, st);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+}  // namespace lt

@@ -20,21 +20,11 @@
 // the float32 dot products.
 #include <cstdio>
 #include "df32.cuh"
+#include "exact.cuh"
 #include "lt_internal.h"
 #include "lt_kernels.h"
 
 namespace lt {
-
-// ------------------------------------------------------------ small helpers
-__device__ __forceinline__ cdf load_cdf(const float2* hi, const float2* lo, size_t idx) {
-  float2 h = hi[idx], l = lo[idx];
-  return {{h.x, l.x}, {h.y, l.y}};
-}
-__device__ __forceinline__ void store_cdf(float2* hi, float2* lo, size_t idx, cdf v) {
-  hi[idx] = make_float2(v.re.hi, v.im.hi);
-  lo[idx] = make_float2(v.re.lo, v.im.lo);
-}
-__device__ __forceinline__ df ldf(const float* hi, const float* lo, int c) { return {hi[c], lo[c]}; }
 
 template <int NV>
 __device__ __forceinline__ void block_reduce_add(float* v, float* smem /* [32*NV] */) {
@@ -56,24 +46,6 @@ __device__ __forceinline__ void block_reduce_add(float* v, float* smem /* [32*NV
       for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
   }
   __syncthreads();
-}
-
-// (K + tau M) u at cell c, df32; u given by hi/lo planes of one vector
-__device__ __forceinline__ cdf apply_exact(const FineExact& fe, const float2* uhi, const float2* ulo, int c, df taur,
-                                           df taui) {
-  const int nx = fe.nx, ny = fe.ny, nz = fe.nz;
-  int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
-  df D = ldf(fe.D_hi, fe.D_lo, c), m = ldf(fe.m_hi, fe.m_lo, c);
-  cdf dg = {df_add(D, df_mul(taur, m)), df_mul(taui, m)};
-  cdf acc = cdf_mul(dg, load_cdf(uhi, ulo, c));
-  if (i + 1 < nx) acc = cdf_sub(acc, cdf_mul_r(load_cdf(uhi, ulo, c + 1), ldf(fe.Te_hi, fe.Te_lo, c)));
-  if (i > 0) acc = cdf_sub(acc, cdf_mul_r(load_cdf(uhi, ulo, c - 1), ldf(fe.Te_hi, fe.Te_lo, c - 1)));
-  if (j + 1 < ny) acc = cdf_sub(acc, cdf_mul_r(load_cdf(uhi, ulo, c + nx), ldf(fe.Tn_hi, fe.Tn_lo, c)));
-  if (j > 0) acc = cdf_sub(acc, cdf_mul_r(load_cdf(uhi, ulo, c - nx), ldf(fe.Tn_hi, fe.Tn_lo, c - nx)));
-  const int pl = nx * ny;
-  if (k + 1 < nz) acc = cdf_sub(acc, cdf_mul_r(load_cdf(uhi, ulo, c + pl), ldf(fe.Tu_hi, fe.Tu_lo, c)));
-  if (k > 0) acc = cdf_sub(acc, cdf_mul_r(load_cdf(uhi, ulo, c - pl), ldf(fe.Tu_hi, fe.Tu_lo, c - pl)));
-  return acc;
 }
 
 // ------------------------------------------------------------ batch init

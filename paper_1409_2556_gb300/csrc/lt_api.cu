@@ -80,6 +80,7 @@ struct lt_ctx {
   std::vector<double> kappa, Ss;
   std::vector<HostLevel> hl;
   lt::MGHost mg{};
+  lt::InnerPlan inner{};          // cluster-resident preconditioner solve on this grid (inner.ok = 0: not possible)
   std::vector<void*> grid_allocs;
   lt::FineExact fe{};
   // float64 fine-level geometry for the sensitivity assembly
@@ -181,6 +182,7 @@ int lt_default_options(lt_opts* o) {
   o->mg_tile = 2;
   o->precond = 0;
   o->mg_tma = 1;
+  o->mg_cluster = 1;
   return LT_OK;
 }
 
@@ -269,6 +271,8 @@ int lt_set_options(lt_ctx* ctx, const lt_opts* o) {
   if (o->precond != 0 && o->precond != 1) return fail(ctx, LT_ERR_INVALID_ARG, "precond=%d must be 0 or 1", o->precond);
   if (o->mg_tma != 0 && o->mg_tma != 1) return fail(ctx, LT_ERR_INVALID_ARG, "mg_tma=%d must be 0 or 1", o->mg_tma);
   if (o->graphs != 0 && o->graphs != 1) return fail(ctx, LT_ERR_INVALID_ARG, "graphs=%d must be 0 or 1", o->graphs);
+  if (o->mg_cluster != 0 && o->mg_cluster != 1)
+    return fail(ctx, LT_ERR_INVALID_ARG, "mg_cluster=%d must be 0 or 1", o->mg_cluster);
   if (!(o->inner_relax >= 0.0 && o->inner_relax < 1.0))
     return fail(ctx, LT_ERR_INVALID_ARG, "inner_relax=%g must be in [0,1)", o->inner_relax);
   if (o->timing_class < -1 || o->timing_class >= LT_KC_COUNT)
@@ -558,6 +562,7 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
       return rc;
   }
   CK(cudaMalloc(&mg.d_levels, sizeof(lt::Level) * lt::kMaxLevels));
+  lt::inner_cluster_plan(mg, ctx->inner);
   ctx->have_grid = true;
   ctx->src.clear(); ctx->Q.clear(); ctx->rec.clear();
   return LT_OK;
@@ -745,7 +750,7 @@ static int ensure_ws(lt_ctx* ctx, const Plan& P) {
   AL(bt.shift_off, nb + 1); AL(bt.zsh, nsh); AL(bt.R, (size_t)nsh * M * M); AL(bt.rc, (size_t)nsh * M);
   AL(bt.rs, (size_t)nsh * M); AL(bt.g, (size_t)nsh * (M + 1)); AL(bt.conv_it, nsh); AL(bt.pres, nsh);
   AL(bt.Y, (size_t)nsh * M);
-  AL(bt.work, 16);
+  AL(bt.work, lt::kWorkSlots);
   AL(bt.itol2, nb);
   AL(bt.rmax, nb);
   AL(bt.jdev, 1);
@@ -777,6 +782,11 @@ struct SolveState {
   std::vector<int> act;
 };
 
+// the whole preconditioner solve of each basis runs in one thread-block cluster
+static bool uses_cluster_solve(const lt_ctx* ctx) {
+  return ctx->opts.mg_cluster == 1 && ctx->opts.precond == 0 && ctx->inner.ok;
+}
+
 // one outer iteration of every active basis (kernels read j from bt.jdev)
 static int launch_iteration(lt_ctx* ctx, cudaStream_t q, int jj, int* nlq, lt::Prof* pf) {
   const lt_opts& o = ctx->opts;
@@ -784,6 +794,15 @@ static int launch_iteration(lt_ctx* ctx, cudaStream_t q, int jj, int* nlq, lt::P
   const lt::Level& L0 = ctx->mg.h_levels[0];
   lt::launch_prep_iter(bt, jj, q);
   ++*nlq;
+  if (uses_cluster_solve(ctx)) {
+    if (lt::launch_inner_cluster(ctx->mg, ctx->inner, bt, ctx->fe, o.inner_cycles, q, pf)) return LT_ERR_CUDA;
+    lt::launch_inner_record(bt, q);
+    *nlq += 2;
+    lt::launch_arnoldi(bt, ctx->fe, jj, q, nlq, pf);
+    lt::launch_shift_ls(bt, jj, q);
+    *nlq += 2;
+    return LT_OK;
+  }
   for (int r = 0; r < o.inner_rounds; ++r) {
     lt::launch_exact_residual(bt, ctx->fe, L0, jj, r, 0, q, pf);
     ++*nlq;
@@ -843,7 +862,7 @@ static int solve_begin(lt_ctx* ctx, const Plan& P, SolveState& S, int* nl) {
     CK(cudaMemcpyAsync(bt.coarse_inv, inv32.data(), inv32.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
   }
-  CK(cudaMemsetAsync(bt.work, 0, 16 * sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(bt.work, 0, lt::kWorkSlots * sizeof(unsigned long long), s));
   lt::Prof* pf = nullptr;
   if (o.timing_class >= 0) {
     const int cap = 16384;
@@ -997,17 +1016,17 @@ static int solve_end(lt_ctx* ctx, const Plan& P, SolveState& S, std::vector<doub
   CK(cudaMemcpyAsync(conv.data(), bt.conv_it, P.nsh * sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(pres.data(), bt.pres, P.nsh * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(inner.data(), bt.inner_max, P.nb * sizeof(double), cudaMemcpyDeviceToHost, s));
-  unsigned long long work[16];
+  unsigned long long work[lt::kWorkSlots];
   CK(cudaMemcpyAsync(work, bt.work, sizeof(work), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   free_list(tmp);
   for (auto& r : true_res)
     if (r >= 0) r = std::sqrt(r);
-  if (work[lt::KC_OTHER + 1] > 0)
+  if (work[lt::kTimeoutSlot] > 0)
     return fail(ctx, LT_ERR_TIMEOUT, "a bulk tensor copy did not complete within its bounded wait (%llu tiles)",
-                (unsigned long long)work[lt::KC_OTHER + 1]);
+                (unsigned long long)work[lt::kTimeoutSlot]);
   if (st) {
-    for (int c = 0; c < 16; ++c) st->work[c] += work[c];
+    for (int c = 0; c < LT_KC_COUNT; ++c) st->work[c] += work[c];
     if (pf) {
       float tot = 0.f;
       for (int q = 0; q < pf->n; ++q) {
@@ -1372,7 +1391,7 @@ extern "C" int lt_precond_apply(lt_ctx* ctx, int nimg, const double* tau, const 
     auto& A = ctx->pc_allocs;
 #define AL(p, n) if ((rc = dalloc(ctx, A, &p, (size_t)(n)))) return rc
     AL(bt.active, nimg); AL(bt.rnorm2, nimg); AL(bt.itol2, nimg); AL(bt.tau_cur, nimg); AL(bt.tau_slot, nimg);
-    AL(bt.work, 16);
+    AL(bt.work, lt::kWorkSlots);
     if (nc2) AL(bt.coarse_inv, nimg * nc2);
     lt::tma_cache_free(mg);
     void* keep_none = nullptr;

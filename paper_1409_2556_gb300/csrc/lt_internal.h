@@ -70,15 +70,19 @@ struct Batch {
   double2* Y;                      // [nsh][maxit]
   float2* coarse_inv;              // [ngroups*2][nc*nc] dense inverses of the coarsest operator
   int coarse_direct;               // 1 if coarse_inv is valid
-  unsigned long long* work;        // [kNumClasses] cells processed per kernel class (live roofline)
+  unsigned long long* work;        // [kWorkSlots] cells processed per kernel class (live roofline), flags
   int* jdev;                       // current outer iteration (shared by all bases of the batch)
 };
 
 // kernel classes for the live per-kernel timing and work counters
 enum KernelClass {
   KC_RBGS = 0, KC_RESTRICT, KC_PROLONG, KC_COARSE, KC_EXACT_RES, KC_UPDATE_U, KC_DOTS, KC_ORTHO, KC_NORMALIZE,
-  KC_SHIFT_LS, KC_XK, KC_TRUE_RES, KC_FUSED_DOWN, KC_FUSED_UP, KC_OTHER, kNumClasses
+  KC_SHIFT_LS, KC_XK, KC_TRUE_RES, KC_FUSED_DOWN, KC_FUSED_UP, KC_OTHER, KC_INNER, kNumClasses
 };
+// Batch::work holds kWorkSlots counters: one per kernel class, then the
+// error flag raised by a bounded device wait that expired.
+constexpr int kTimeoutSlot = kNumClasses;
+constexpr int kWorkSlots = 32;
 
 // CUDA-event timing of the launches of one kernel class (cls < 0: off)
 struct Prof {

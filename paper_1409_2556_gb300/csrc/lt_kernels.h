@@ -18,6 +18,21 @@ struct MGHost {
   Level* d_levels;             // device copy
 };
 
+// -------- inner.cu: the whole preconditioner solve of a basis in one thread-block cluster
+struct InnerPlan {
+  int ok = 0;                      // 1 if the grid and the device allow the cluster-resident solve
+  int ld = 0;                      // levels split into per-CTA row strips: [0, ld); [ld, nlev) in rank 0
+  int max_clusters = 0;            // clusters the device can hold at once
+  int off_u[kMaxLevels] = {}, off_f[kMaxLevels] = {};               // byte offsets in shared memory
+  int off_te[kMaxLevels] = {}, off_tn[kMaxLevels] = {}, off_di[kMaxLevels] = {}, off_rhs = 0;
+  size_t smem = 0;                 // dynamic shared memory per CTA
+};
+// fills p (p.ok = 0 when the levels do not split into 8 even row strips or do not fit); returns p.ok
+int inner_cluster_plan(const MGHost& mg, InnerPlan& p);
+// rounds x cycles V-cycles of every active basis, one cluster per basis (bt.rounds rounds)
+int launch_inner_cluster(const MGHost& mg, const InnerPlan& p, const Batch& bt, const FineExact& fe, int cycles,
+                         cudaStream_t st, Prof* pf);
+
 // one V-cycle on every active basis of the batch whose refinement round `round` is not done
 int launch_vcycle(const MGHost& mg, const Batch& bt, int round, cudaStream_t st, int* nlaunch, Prof* pf);
 void tma_cache_free(MGHost& mg);

@@ -28,54 +28,13 @@
 
 #include "lt_internal.h"
 #include "lt_kernels.h"
+#include "mg_dev.cuh"
 
 namespace lt {
 
 __device__ __forceinline__ bool mg_skip(const Batch& bt, int b, int round) {
   if (!bt.active[b]) return true;
   return bt.rnorm2[b * (bt.rounds + 1) + round] <= bt.itol2[b];
-}
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 cdiv(float2 a, float2 d) {
-  float inv = 1.f / (d.x * d.x + d.y * d.y);
-  return make_float2((a.x * d.x + a.y * d.y) * inv, (a.y * d.x - a.x * d.y) * inv);
-}
-
-// sum_nb T u_nb and the cell's complex diagonal D + tau m
-__device__ __forceinline__ float2 nb_sum(const Level& L, const float2* __restrict__ u, int i, int j, int k, int c) {
-  float2 s = make_float2(0.f, 0.f);
-  if (i + 1 < L.nx) { float t = L.Te[c]; float2 v = u[c + 1]; s.x += t * v.x; s.y += t * v.y; }
-  if (i > 0) { float t = L.Te[c - 1]; float2 v = u[c - 1]; s.x += t * v.x; s.y += t * v.y; }
-  if (j + 1 < L.ny) { float t = L.Tn[c]; float2 v = u[c + L.nx]; s.x += t * v.x; s.y += t * v.y; }
-  if (j > 0) { float t = L.Tn[c - L.nx]; float2 v = u[c - L.nx]; s.x += t * v.x; s.y += t * v.y; }
-  const int pl = L.nx * L.ny;
-  if (k + 1 < L.nz) { float t = L.Tu[c]; float2 v = u[c + pl]; s.x += t * v.x; s.y += t * v.y; }
-  if (k > 0) { float t = L.Tu[c - pl]; float2 v = u[c - pl]; s.x += t * v.x; s.y += t * v.y; }
-  return s;
-}
-
-__device__ __forceinline__ float2 diag_of(const Level& L, int c, float2 tau) {
-  float m = L.m[c];
-  return make_float2(L.D[c] + tau.x * m, tau.y * m);
-}
-
-__device__ __forceinline__ void rbgs_cell(const Level& L, float2* u, const float2* f, int c, float2 tau) {
-  int i = c % L.nx, j = (c / L.nx) % L.ny, k = c / (L.nx * L.ny);
-  float2 s = nb_sum(L, u, i, j, k, c);
-  float2 r = f[c];
-  r.x += s.x; r.y += s.y;
-  u[c] = cdiv(r, diag_of(L, c, tau));
-}
-
-__device__ __forceinline__ float2 resid_cell(const Level& L, const float2* u, const float2* f, int c, float2 tau) {
-  int i = c % L.nx, j = (c / L.nx) % L.ny, k = c / (L.nx * L.ny);
-  float2 s = nb_sum(L, u, i, j, k, c);
-  float2 a = cmul(diag_of(L, c, tau), u[c]);
-  float2 fc = f[c];
-  return make_float2(fc.x - a.x + s.x, fc.y - a.y + s.y);
 }
 
 __device__ __forceinline__ float2 tau32(const Batch& bt, int b) {
@@ -98,21 +57,6 @@ __global__ void k_rbgs(Level L, Batch bt, int round, int color) {
   rbgs_cell(L, L.u + (size_t)b * L.N, L.f + (size_t)b * L.N, c, tau32(bt, b));
 }
 
-__device__ __forceinline__ void restrict_cell(const Level& Lf, const Level& Lc, const float2* uf, const float2* ff,
-                                              float2* fc, float2* uc, int C, float2 tau) {
-  int I = C % Lc.nx, J = (C / Lc.nx) % Lc.ny, K = C / (Lc.nx * Lc.ny);
-  float2 acc = make_float2(0.f, 0.f);
-  for (int dk = 0; dk < Lf.rz; ++dk)
-    for (int dj = 0; dj < Lf.ry; ++dj)
-      for (int di = 0; di < Lf.rx; ++di) {
-        int c = ((K * Lf.rz + dk) * Lf.ny + (J * Lf.ry + dj)) * Lf.nx + (I * Lf.rx + di);
-        float2 r = resid_cell(Lf, uf, ff, c, tau);
-        acc.x += r.x; acc.y += r.y;
-      }
-  fc[C] = acc;
-  uc[C] = make_float2(0.f, 0.f);
-}
-
 __global__ void k_restrict(Level Lf, Level Lc, Batch bt, int round) {
   int b = blockIdx.y;
   if (mg_skip(bt, b, round)) return;
@@ -120,45 +64,6 @@ __global__ void k_restrict(Level Lf, Level Lc, Batch bt, int round) {
   if (C >= Lc.N) return;
   restrict_cell(Lf, Lc, Lf.u + (size_t)b * Lf.N, Lf.f + (size_t)b * Lf.N, Lc.f + (size_t)b * Lc.N,
                 Lc.u + (size_t)b * Lc.N, C, tau32(bt, b));
-}
-
-// multilinear interpolation weight setup along one axis
-__device__ __forceinline__ void axis_interp(int i, int r, int nC, int lo_dir, int hi_dir, int& I0, int& I1,
-                                            float& w0, float& w1, float& s1) {
-  I0 = i / r;
-  if (r == 1) { I1 = I0; w0 = 1.f; w1 = 0.f; s1 = 1.f; return; }
-  int o = i - I0 * r;              // 0 or 1
-  int nbI = o ? I0 + 1 : I0 - 1;
-  w0 = 0.75f; w1 = 0.25f; s1 = 1.f;
-  if (nbI < 0) { nbI = I0; s1 = lo_dir ? -1.f : 1.f; }
-  else if (nbI >= nC) { nbI = I0; s1 = hi_dir ? -1.f : 1.f; }
-  I1 = nbI;
-}
-
-__device__ __forceinline__ void prolong_cell(const Level& Lf, const Level& Lc, float2* uf, const float2* uc, int c,
-                                             int dmask) {
-  int i = c % Lf.nx, j = (c / Lf.nx) % Lf.ny, k = c / (Lf.nx * Lf.ny);
-  int I[2], J[2], K[2];
-  float wi[2], wj[2], wk[2], si, sj, sk;
-  axis_interp(i, Lf.rx, Lc.nx, dmask & 1, dmask & 2, I[0], I[1], wi[0], wi[1], si);
-  axis_interp(j, Lf.ry, Lc.ny, dmask & 4, dmask & 8, J[0], J[1], wj[0], wj[1], sj);
-  axis_interp(k, Lf.rz, Lc.nz, dmask & 16, dmask & 32, K[0], K[1], wk[0], wk[1], sk);
-  wi[1] *= si; wj[1] *= sj; wk[1] *= sk;
-  float2 e = make_float2(0.f, 0.f);
-  for (int a = 0; a < 2; ++a) {
-    if (wk[a] == 0.f) continue;
-    for (int bb = 0; bb < 2; ++bb) {
-      if (wj[bb] == 0.f) continue;
-      for (int cc = 0; cc < 2; ++cc) {
-        if (wi[cc] == 0.f) continue;
-        float w = wk[a] * wj[bb] * wi[cc];
-        float2 v = uc[(K[a] * Lc.ny + J[bb]) * Lc.nx + I[cc]];
-        e.x += w * v.x; e.y += w * v.y;
-      }
-    }
-  }
-  float2 u = uf[c];
-  uf[c] = make_float2(u.x + e.x, u.y + e.y);
 }
 
 __global__ void k_prolong(Level Lf, Level Lc, Batch bt, int round, int dmask) {
@@ -253,10 +158,6 @@ __global__ void __launch_bounds__(1024) k_coarse_vcycle(const Level* __restrict_
 //   up:   prolongation + correction + post-smoothing (halo 2*npost)
 constexpr int kFusedThreads = 512;
 
-__device__ __forceinline__ float2 cinv(float2 d) {
-  float inv = 1.f / (d.x * d.x + d.y * d.y);
-  return make_float2(d.x * inv, -d.y * inv);
-}
 
 struct Tile2D {
   float2* u;    // [RY][RX]
@@ -498,7 +399,7 @@ __device__ __forceinline__ void tma_3d(void* dst, const CUtensorMap* tm, int x, 
 struct TmaMaps { CUtensorMap u, f, te, tn, d, m; };
 
 // stage u, f, Te, Tn, D, m of the region into shared memory and build the inverse diagonal.
-// Returns false (and raises bt.work[KC_OTHER + 1] as an error flag) if the copy never completed.
+// Returns false (and raises bt.work[kTimeoutSlot] as an error flag) if the copy never completed.
 __device__ __forceinline__ bool tile_load_tma(const TmaMaps& M, Tile2D& T, float* Ds, float* ms, uint64_t* bar,
                                               int gx0, int gy0, int b, int RX, int RY, float2 tau, const Batch& bt) {
   const int RN = RX * RY;
@@ -521,7 +422,7 @@ __device__ __forceinline__ bool tile_load_tma(const TmaMaps& M, Tile2D& T, float
   for (unsigned it = 0; it < kTmaSpin; ++it)
     if (mbar_try_wait(bar, 0)) { done = true; break; }
   if (!done) {
-    if (threadIdx.x == 0) atomicAdd(&bt.work[KC_OTHER + 1], 1ull);
+    if (threadIdx.x == 0) atomicAdd(&bt.work[kTimeoutSlot], 1ull);
     for (unsigned it = 0; it < kTmaSpin; ++it)      // give copies in flight a second bounded chance to land
       if (mbar_try_wait(bar, 0)) break;
     return false;

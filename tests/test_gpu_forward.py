@@ -190,10 +190,44 @@ def test_tma_staged_tiles_match_plain_loads(Engine, tile, pre):
     outs = []
     for tma in (0, 1):
         eng = Engine(0)
-        eng.load_problem(p, mg_tile=tile, mg_pre=pre, mg_post=pre, mg_tma=tma)
+        eng.load_problem(p, mg_tile=tile, mg_pre=pre, mg_post=pre, mg_tma=tma, mg_cluster=0)
         outs.append((eng.forward(p.times), eng.last_stats))
         eng.close()
     (h0, s0), (h1, s1) = outs
     assert s0["outer_iters_max"] == s1["outer_iters_max"]
     assert _rel(h1, h0) < 1e-12
     assert _rel(h1, direct.forward(p)) < TOL_H
+
+
+@pytest.mark.parametrize("shape,pre,relax", [((64, 32), 2, 0.0), ((128, 96), 3, 1e-6), ((256, 128), 2, 1e-4)])
+def test_cluster_resident_solve_matches_batched_launches(Engine, shape, pre, relax):
+    """The preconditioner solves run inside one 8-CTA cluster per basis (levels in distributed
+    shared memory) give the solve of the batched multigrid launches: same converged set, same
+    outer iteration counts to within one, both within the bar of the direct oracle."""
+    from paper_1409_2556_gb300._lib import KC
+    nx, ny = shape
+    p = W.random_problem(nx, ny, 1, variance=1.5, seed=nx + ny, ns=2, nr=3, nt=3, Nz=16, tol=1e-11, groups=2)
+    outs = []
+    for cl in (0, 1):
+        eng = Engine(0)
+        eng.load_problem(p, mg_pre=pre, mg_post=pre, mg_cluster=cl, inner_relax=relax)
+        outs.append((eng.forward(p.times), eng.last_stats))
+        eng.close()
+    (h0, s0), (h1, s1) = outs
+    assert s0["work"][KC["inner"]] == 0 and s1["work"][KC["inner"]] > 0   # the cluster kernel ran
+    assert s1["work"][KC["fused_up"]] == 0 and s1["work"][KC["coarse"]] == 0
+    assert abs(s0["outer_iters_max"] - s1["outer_iters_max"]) <= 1
+    assert s1["n_converged"] == s1["n_shift_solves"]
+    assert s1["max_true_residual"] <= 1e-11
+    ref = direct.forward(p)
+    assert _rel(h0, ref) < TOL_H
+    assert _rel(h1, ref) < TOL_H
+
+
+def test_cluster_solve_falls_back_on_grids_that_do_not_split(Engine):
+    """40 rows do not split into 8 strips of even height: the batched launches run instead."""
+    from paper_1409_2556_gb300._lib import KC
+    p = W.random_problem(48, 40, 1, variance=1.0, seed=3, ns=2, nr=2, nt=2, Nz=16, tol=1e-11)
+    h, st = _solve(Engine, p, mg_cluster=1)
+    assert st["work"][KC["inner"]] == 0
+    assert _rel(h, direct.forward(p)) < TOL_H
