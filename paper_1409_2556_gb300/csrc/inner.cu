@@ -38,32 +38,52 @@ constexpr int kIT = 512;                     // threads per CTA
 constexpr size_t kInnerSmemMax = 220 * 1024;  // dynamic shared memory per CTA
 constexpr int kL0Batch = 2;                   // finest-level cells per thread whose loads are issued together
 
+// Division by a runtime divisor d >= 1 of a numerator below 2^31 as a multiply-high and a shift
+// (Granlund and Montgomery, "Division by invariant integers using multiplication", 1994):
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, q / d = (umulhi(q, m) + q) >> l.
+struct FastDiv {
+  uint32_t m;
+  int s;
+};
+static FastDiv make_fastdiv(uint32_t d) {
+  int l = 0;
+  while ((1u << l) < d) ++l;
+  const uint64_t m = ((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1;
+  return FastDiv{(uint32_t)m, l};
+}
+__device__ __forceinline__ int fdiv(int q, FastDiv f) {
+  const uint32_t t = __umulhi((uint32_t)q, f.m);
+  return (int)((t + (uint32_t)q) >> f.s);
+}
+
 // Byte offsets of one level's arrays in dynamic shared memory.  The finest
-// level keeps only its iterate there (coefficients and right-hand side are
-// read from global memory, batched); every coarser level also keeps its
-// right-hand side, east/north face transmissibilities and the inverse of its
-// complex diagonal, staged once per launch.
+// level keeps only its iterate there; its coefficients come from global
+// memory as two 16-byte loads per cell (the four face transmissibilities,
+// shared by all bases, and per basis the inverse complex diagonal with the
+// right-hand side), batched.  Every coarser level also keeps its right-hand
+// side, east/north face transmissibilities and the inverse of its complex
+// diagonal, staged once per launch.
 struct LevOff { int u, f, te, tn, di; };
 
 struct InnerArgs {
   Batch bt;
   FineExact fe;
   const Level* levels;          // device copy of the level descriptors
-  float2* f0;                   // [nb][N] right-hand side of the finest level (global)
+  const float4* p4;             // [N] finest level: (Te east, Te west, Tn north, Tn south) of each cell
+  float4* q4;                   // [nb][N] finest level: (1 / (D + tau m), right-hand side) per basis
   int nlev, ld;                 // levels [0, ld) in strips, [ld, nlev) in rank 0
   int npre, npost, dmask, coarse_direct, rounds, cycles;
   LevOff off[kMaxLevels];
   int off_rhs;                  // byte offset of rank 0's coarsest right-hand side copy
+  FastDiv dnx[kMaxLevels];      // divisions by the level's row length
+  FastDiv dhx[kMaxLevels];      // ... and by half of it (cells of one colour per row)
 };
 
 // The finest level's rows [y0, y0 + h) of this CTA.
 struct L0V {
   int nx, ny, h, y0;
-  const float* __restrict__ Te;
-  const float* __restrict__ Tn;
-  const float* __restrict__ D;
-  const float* __restrict__ m;
-  const float2* f;               // whole-level right-hand side (global cell index; rewritten every round)
+  const float4* __restrict__ P;  // faces (global cell index)
+  const float4* Q;               // inverse diagonal and right-hand side (global cell index; rewritten every round)
   float2* u;                     // [h][nx], shared memory
   const float2* u_dn;            // iterate of rank - 1 (its last row lies just below y0), or null
   const float2* u_up;            // iterate of rank + 1 (its first row lies just above y0 + h - 1), or null
@@ -94,33 +114,32 @@ struct CoarseView {
 __device__ __forceinline__ void axpy_c(float2& r, float t, float2 v) { r.x += t * v.x; r.y += t * v.y; }
 
 // ---------------------------------------------------------------- finest level (global coefficients)
-// loads of one cell of the finest level: the four faces, diagonal parts and right-hand side
-struct L0Cell { float te_e, te_w, tn_n, tn_s, d, m; float2 f; };
+// loads of one cell of the finest level: the four faces, inverse diagonal and right-hand side
+struct L0Cell { float4 t; float4 q; };
 
-__device__ __forceinline__ L0Cell l0_load(const L0V& S, int x, int y, int c) {
-  L0Cell q;
-  q.te_e = x + 1 < S.nx ? S.Te[c] : 0.f;
-  q.te_w = x > 0 ? S.Te[c - 1] : 0.f;
-  q.tn_n = y + 1 < S.ny ? S.Tn[c] : 0.f;
-  q.tn_s = y > 0 ? S.Tn[c - S.nx] : 0.f;
-  q.d = S.D[c];
-  q.m = S.m[c];
-  q.f = S.f[c];
-  return q;
+__device__ __forceinline__ L0Cell l0_load(const L0V& S, int c) {
+  L0Cell v;
+  v.t = S.P[c];
+  v.q = S.Q[c];
+  return v;
 }
 
-// sum over the four neighbours of T u_nb (zero faces contribute nothing, so no boundary tests on them)
-__device__ __forceinline__ float2 l0_nb(const L0V& S, const L0Cell& q, int x, int y, int ly, int li) {
-  float2 s = make_float2(0.f, 0.f);
-  if (x + 1 < S.nx) axpy_c(s, q.te_e, S.u[li + 1]);
-  if (x > 0) axpy_c(s, q.te_w, S.u[li - 1]);
-  if (y + 1 < S.ny) axpy_c(s, q.tn_n, ly + 1 < S.h ? S.u[li + S.nx] : S.u_up[x]);
-  if (y > 0) axpy_c(s, q.tn_s, ly > 0 ? S.u[li - S.nx] : S.u_dn[(S.h - 1) * S.nx + x]);
-  return s;
+// neighbour iterates of a finest-level cell (zero where the cell has no neighbour)
+__device__ __forceinline__ void l0_gather(const L0V& S, int x, int y, int ly, int li, float2* nb) {
+  const float2 z = make_float2(0.f, 0.f);
+  nb[0] = x + 1 < S.nx ? S.u[li + 1] : z;
+  nb[1] = x > 0 ? S.u[li - 1] : z;
+  nb[2] = y + 1 < S.ny ? (ly + 1 < S.h ? S.u[li + S.nx] : S.u_up[x]) : z;
+  nb[3] = y > 0 ? (ly > 0 ? S.u[li - S.nx] : S.u_dn[(S.h - 1) * S.nx + x]) : z;
+}
+
+__device__ __forceinline__ float2 nb_dot(float4 t, const float2* nb) {
+  return make_float2(t.x * nb[0].x + t.y * nb[1].x + t.z * nb[2].x + t.w * nb[3].x,
+                     t.x * nb[0].y + t.y * nb[1].y + t.z * nb[2].y + t.w * nb[3].y);
 }
 
 // one red (color 0) or black (color 1) half-sweep over the strip's cells of that colour
-__device__ __forceinline__ void l0_half_sweep(const L0V& S, float2 tau, int color) {
+__device__ __forceinline__ void l0_half_sweep(const L0V& S, FastDiv dhx, int color) {
   const int hx = S.nx >> 1, n = S.h * hx;
   for (int q0 = threadIdx.x; q0 < n; q0 += kL0Batch * kIT) {
     L0Cell cq[kL0Batch];
@@ -128,18 +147,20 @@ __device__ __forceinline__ void l0_half_sweep(const L0V& S, float2 tau, int colo
     for (int k = 0; k < kL0Batch; ++k) {
       const int q = q0 + k * kIT;
       if (q < n) {
-        const int ly = q / hx, y = S.y0 + ly, x = 2 * (q - ly * hx) + ((color + y) & 1);
-        cq[k] = l0_load(S, x, y, y * S.nx + x);
+        const int ly = fdiv(q, dhx), y = S.y0 + ly, x = 2 * (q - ly * hx) + ((color + y) & 1);
+        cq[k] = l0_load(S, y * S.nx + x);
       }
     }
 #pragma unroll
     for (int k = 0; k < kL0Batch; ++k) {
       const int q = q0 + k * kIT;
       if (q < n) {
-        const int ly = q / hx, y = S.y0 + ly, x = 2 * (q - ly * hx) + ((color + y) & 1), li = ly * S.nx + x;
-        float2 r = l0_nb(S, cq[k], x, y, ly, li);
-        r.x += cq[k].f.x; r.y += cq[k].f.y;
-        S.u[li] = cdiv(r, make_float2(cq[k].d + tau.x * cq[k].m, tau.y * cq[k].m));
+        const int ly = fdiv(q, dhx), y = S.y0 + ly, x = 2 * (q - ly * hx) + ((color + y) & 1), li = ly * S.nx + x;
+        float2 nb[4];
+        l0_gather(S, x, y, ly, li, nb);
+        float2 r = nb_dot(cq[k].t, nb);
+        r.x += cq[k].q.z; r.y += cq[k].q.w;
+        S.u[li] = cmul(r, make_float2(cq[k].q.x, cq[k].q.y));
       }
     }
   }
@@ -147,24 +168,30 @@ __device__ __forceinline__ void l0_half_sweep(const L0V& S, float2 tau, int colo
 
 // residual summed over 2x2 children into the coarse right-hand side (coarse row J at row J - row0 of fc);
 // returns this thread's sum of |r|^2 over the fine cells (the V-cycle's convergence monitor)
-__device__ __forceinline__ float l0_restrict(const L0V& S, float2 tau, float2* fc, int ncx, int row0) {
+__device__ __forceinline__ float l0_restrict(const L0V& S, float2* fc, int ncx, FastDiv dncx, int row0) {
   const int nch = S.h >> 1, n = nch * ncx;
   float rr = 0.f;
   for (int q = threadIdx.x; q < n; q += kIT) {
-    const int lJ = q / ncx, I = q - lJ * ncx;
+    const int lJ = fdiv(q, dncx), I = q - lJ * ncx;
     L0Cell cq[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int x = 2 * I + (k & 1), ly = 2 * lJ + (k >> 1), y = S.y0 + ly;
-      cq[k] = l0_load(S, x, y, y * S.nx + x);
+      cq[k] = l0_load(S, y * S.nx + x);
+    }
+    float2 nb[4][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int x = 2 * I + (k & 1), ly = 2 * lJ + (k >> 1), y = S.y0 + ly;
+      l0_gather(S, x, y, ly, ly * S.nx + x, nb[k]);
     }
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const int x = 2 * I + (k & 1), ly = 2 * lJ + (k >> 1), y = S.y0 + ly, li = ly * S.nx + x;
-      const float2 s = l0_nb(S, cq[k], x, y, ly, li);
-      const float2 a = cmul(make_float2(cq[k].d + tau.x * cq[k].m, tau.y * cq[k].m), S.u[li]);
-      const float rx = cq[k].f.x - a.x + s.x, ry = cq[k].f.y - a.y + s.y;
+      const int x = 2 * I + (k & 1), ly = 2 * lJ + (k >> 1), li = ly * S.nx + x;
+      const float2 s = nb_dot(cq[k].t, nb[k]);
+      const float2 a = cmul(cinv(make_float2(cq[k].q.x, cq[k].q.y)), S.u[li]);
+      const float rx = cq[k].q.z - a.x + s.x, ry = cq[k].q.w - a.y + s.y;
       acc.x += rx;
       acc.y += ry;
       rr += rx * rx + ry * ry;
@@ -175,32 +202,47 @@ __device__ __forceinline__ float l0_restrict(const L0V& S, float2 tau, float2* f
 }
 
 // ---------------------------------------------------------------- staged levels (shared memory)
-__device__ __forceinline__ float2 sv_nb(const SV& S, int x, int y, int ly, int li) {
-  float2 s = make_float2(0.f, 0.f);
-  if (x + 1 < S.nx) axpy_c(s, S.te[li], S.u[li + 1]);
-  if (x > 0) axpy_c(s, S.te[li - 1], S.u[li - 1]);
-  if (y + 1 < S.ny) axpy_c(s, S.tn[li + S.nx], ly + 1 < S.h ? S.u[li + S.nx] : S.u_up[x]);
-  if (y > 0) axpy_c(s, S.tn[li], ly > 0 ? S.u[li - S.nx] : S.u_dn[(S.h - 1) * S.nx + x]);
-  return s;
+// neighbour iterates and faces of a staged cell
+__device__ __forceinline__ void sv_gather(const SV& S, int x, int y, int ly, int li, float4& t, float2* nb) {
+  const float2 z = make_float2(0.f, 0.f);
+  t.x = x + 1 < S.nx ? S.te[li] : 0.f;
+  t.y = x > 0 ? S.te[li - 1] : 0.f;
+  t.z = y + 1 < S.ny ? S.tn[li + S.nx] : 0.f;
+  t.w = y > 0 ? S.tn[li] : 0.f;
+  nb[0] = x + 1 < S.nx ? S.u[li + 1] : z;
+  nb[1] = x > 0 ? S.u[li - 1] : z;
+  nb[2] = y + 1 < S.ny ? (ly + 1 < S.h ? S.u[li + S.nx] : S.u_up[x]) : z;
+  nb[3] = y > 0 ? (ly > 0 ? S.u[li - S.nx] : S.u_dn[(S.h - 1) * S.nx + x]) : z;
 }
 
-// kCompact: the level has an even number of columns, so thread q maps directly to the q-th cell of the colour
-template <bool kCompact>
-__device__ __forceinline__ void sv_half_sweep(const SV& S, int color) {
-  const int hx = S.nx >> 1;
-  const int n = kCompact ? S.h * hx : S.h * S.nx;
+// red-black half-sweep of a strip level with an even number of columns: thread q takes the q-th
+// cell of the colour
+__device__ __forceinline__ void sv_half_sweep_strip(const SV& S, FastDiv dhx, int color) {
+  const int hx = S.nx >> 1, n = S.h * hx;
   for (int q = threadIdx.x; q < n; q += kIT) {
-    int ly, x;
-    if (kCompact) {
-      ly = q / hx;
-      x = 2 * (q - ly * hx) + ((color + S.y0 + ly) & 1);
-    } else {
-      ly = q / S.nx;
-      x = q - ly * S.nx;
-      if (((x + S.y0 + ly) & 1) != color) continue;
-    }
-    const int y = S.y0 + ly, li = ly * S.nx + x;
-    float2 r = sv_nb(S, x, y, ly, li);
+    const int ly = fdiv(q, dhx), y = S.y0 + ly, x = 2 * (q - ly * hx) + ((color + y) & 1);
+    const int li = ly * S.nx + x;
+    float4 t;
+    float2 nb[4];
+    sv_gather(S, x, y, ly, li, t, nb);
+    float2 r = nb_dot(t, nb);
+    const float2 fv = S.f[li];
+    r.x += fv.x; r.y += fv.y;
+    S.u[li] = cmul(r, S.di[li]);
+  }
+}
+
+// red-black half-sweep of a whole coarse level (any shape) held by this CTA
+__device__ __forceinline__ void sv_half_sweep_full(const SV& S, FastDiv dnx, int color) {
+  const int n = S.h * S.nx;
+  for (int q = threadIdx.x; q < n; q += kIT) {
+    const int ly = fdiv(q, dnx), x = q - ly * S.nx;
+    if (((x + S.y0 + ly) & 1) != color) continue;
+    const int y = S.y0 + ly, li = q;
+    float4 t;
+    float2 nb[4];
+    sv_gather(S, x, y, ly, li, t, nb);
+    float2 r = nb_dot(t, nb);
     const float2 fv = S.f[li];
     r.x += fv.x; r.y += fv.y;
     S.u[li] = cmul(r, S.di[li]);
@@ -209,15 +251,19 @@ __device__ __forceinline__ void sv_half_sweep(const SV& S, int color) {
 
 // residual of the staged level summed over rx x ry children into the coarse right-hand side;
 // zero_uc: also clear the coarse iterate (coarse levels owned by this CTA)
-__device__ __forceinline__ void sv_restrict(const SV& S, int rx, int ry, float2* fc, float2* uc, int ncx, int row0) {
+__device__ __forceinline__ void sv_restrict(const SV& S, int rx, int ry, float2* fc, float2* uc, int ncx,
+                                            FastDiv dncx, int row0) {
   const int nch = S.h / ry, n = nch * ncx;
   for (int q = threadIdx.x; q < n; q += kIT) {
-    const int lJ = q / ncx, I = q - lJ * ncx;
+    const int lJ = fdiv(q, dncx), I = q - lJ * ncx;
     float2 acc = make_float2(0.f, 0.f);
     for (int dj = 0; dj < ry; ++dj)
       for (int di = 0; di < rx; ++di) {
         const int x = I * rx + di, ly = lJ * ry + dj, y = S.y0 + ly, li = ly * S.nx + x;
-        const float2 s = sv_nb(S, x, y, ly, li);
+        float4 t;
+        float2 nb[4];
+        sv_gather(S, x, y, ly, li, t, nb);
+        const float2 s = nb_dot(t, nb);
         const float2 a = cmul(cinv(S.di[li]), S.u[li]);
         const float2 fv = S.f[li];
         acc.x += fv.x - a.x + s.x;
@@ -238,10 +284,11 @@ __device__ __forceinline__ float2 cv_get(const CoarseView& V, int I, int J) {
 }
 
 // u += bilinear interpolation of the coarse correction (weights 3/4, 1/4 per axis) on rows [y0, y0 + h)
-__device__ __forceinline__ void strip_prolong(float2* u, int nx, int h, int y0, const CoarseView& V, int dmask) {
+__device__ __forceinline__ void strip_prolong(float2* u, int nx, FastDiv dnx, int h, int y0, const CoarseView& V,
+                                              int dmask) {
   const int n = h * nx;
   for (int q = threadIdx.x; q < n; q += kIT) {
-    const int ly = q / nx, x = q - ly * nx, y = y0 + ly;
+    const int ly = fdiv(q, dnx), x = q - ly * nx, y = y0 + ly;
     int I0, I1, J0, J1;
     float wi0, wi1, wj0, wj1, si, sj;
     axis_interp(x, 2, V.nx, dmask & 1, dmask & 2, I0, I1, wi0, wi1, si);
@@ -372,16 +419,23 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
     for (int x = tid; x < S.nx; x += kIT) S.tn[x] = S.y0 > 0 ? L.Tn[(S.y0 - 1) * S.nx + x] : 0.f;
   }
   L0V S0;
+  float4* q0 = a.q4 + (size_t)b * bt.N;
   {
     const Level& L = sL[0];
     S0.nx = L.nx; S0.ny = L.ny; S0.h = L.ny / kCS; S0.y0 = rank * S0.h;
-    S0.Te = L.Te; S0.Tn = L.Tn; S0.D = L.D; S0.m = L.m;
-    S0.f = a.f0 + (size_t)b * bt.N;
+    S0.P = a.p4;
+    S0.Q = q0;
     S0.u = reinterpret_cast<float2*>(smb + a.off[0].u);
     S0.u_dn = rank > 0 ? cl.map_shared_rank(S0.u, rank - 1) : nullptr;
     S0.u_up = rank + 1 < kCS ? cl.map_shared_rank(S0.u, rank + 1) : nullptr;
+    // inverse diagonal of this basis's shift on this CTA's rows (right-hand sides follow every round)
+    for (int q = tid; q < S0.h * S0.nx; q += kIT) {
+      const int c = S0.y0 * S0.nx + q;
+      const float mm = L.m[c];
+      const float2 di = cinv(make_float2(L.D[c] + tau.x * mm, tau.y * mm));
+      q0[c] = make_float4(di.x, di.y, 0.f, 0.f);
+    }
   }
-  float2* f0w = a.f0 + (size_t)b * bt.N;
   __syncthreads();
   cl.sync();   // every CTA of the cluster is running and initialised before any remote access
 
@@ -389,6 +443,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
   const size_t vb = ((size_t)b * (bt.maxit + 1) + j) * bt.N;
   const size_t ub = ((size_t)b * bt.maxit + j) * bt.N;
   int slot = 0;
+  unsigned long long n_res = 0, n_cyc = 0;   // rank 0, thread 0: work counters, added once at the end
   for (int r = 0; r <= R; ++r) {
     // df32 residual of the current u_j on this CTA's rows; it is the next round's right-hand side
     float acc = 0.f;
@@ -397,7 +452,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
       cdf rr = load_cdf(bt.V_hi, bt.V_lo, vb + c);
       if (r > 0) rr = cdf_sub(rr, apply_exact(a.fe, bt.U_hi + ub, bt.U_lo + ub, c, taur, taui));
       if (r < R) {
-        f0w[c] = make_float2(rr.re.hi, rr.im.hi);
+        reinterpret_cast<float2*>(q0 + c)[1] = make_float2(rr.re.hi, rr.im.hi);
         S0.u[q] = make_float2(0.f, 0.f);
       }
       acc += rr.re.hi * rr.re.hi + rr.im.hi * rr.im.hi;
@@ -408,7 +463,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
     if (rank == 0 && tid == 0) {
       bt.rnorm2[b * R1 + r] = rn2;
       if (r < R && done) bt.rnorm2[b * R1 + R] = rn2;   // u_j is final: its residual is this one
-      atomicAdd(&bt.work[KC_EXACT_RES], (unsigned long long)bt.N);
+      n_res += (unsigned long long)bt.N;
     }
     if (done) {
       if (r == 0)   // v_j itself is below the tolerance: u_j = 0
@@ -430,18 +485,18 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
         const int ncx = sL[l + 1].nx;
         if (l == 0) {
           for (int h = 0; h < 2 * a.npre; ++h) {
-            l0_half_sweep(S0, tau, h & 1);
+            l0_half_sweep(S0, a.dhx[0], h & 1);
             cl.sync();
           }
-          const float rr = l0_restrict(S0, tau, fc, ncx, last ? 0 : S0.y0 / 2);
+          const float rr = l0_restrict(S0, fc, ncx, a.dnx[1], last ? 0 : S0.y0 / 2);
           block_sum(rr, red, &vpart[cy & 1]);
         } else {
           const SV S = sview(l);
           for (int h = 0; h < 2 * a.npre; ++h) {
-            sv_half_sweep<true>(S, h & 1);
+            sv_half_sweep_strip(S, a.dhx[l], h & 1);
             cl.sync();
           }
-          sv_restrict(S, 2, 2, fc, nullptr, ncx, last ? 0 : S.y0 / 2);
+          sv_restrict(S, 2, 2, fc, nullptr, ncx, a.dnx[l + 1], last ? 0 : S.y0 / 2);
         }
         __syncthreads();   // the next level's sweeps read right-hand sides written by other threads
       }
@@ -450,19 +505,19 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
         double s2 = 0.0;
         for (int q = 0; q < kCS; ++q) s2 += *cl.map_shared_rank(&vpart[cy & 1], q);
         vstop = s2 <= goal2;
-        if (rank == 0) atomicAdd(&bt.work[KC_INNER], (unsigned long long)bt.N);
+        n_cyc += (unsigned long long)bt.N;
       }
       // ---- coarse levels in rank 0
       if (rank == 0)
         for (int l = a.ld; l < a.nlev - 1; ++l) {
           const SV S = sview(l);
           for (int h = 0; h < 2 * a.npre; ++h) {
-            sv_half_sweep<false>(S, h & 1);
+            sv_half_sweep_full(S, a.dnx[l], h & 1);
             __syncthreads();
           }
           const Level& Lc = sL[l + 1];
           sv_restrict(S, sL[l].rx, sL[l].ry, reinterpret_cast<float2*>(smb + a.off[l + 1].f),
-                      reinterpret_cast<float2*>(smb + a.off[l + 1].u), Lc.nx, 0);
+                      reinterpret_cast<float2*>(smb + a.off[l + 1].u), Lc.nx, a.dnx[l + 1], 0);
           __syncthreads();
         }
       if (a.coarse_direct) {
@@ -495,7 +550,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
       } else if (rank == 0) {
         const SV S = sview(a.nlev - 1);
         for (int h = 0; h < 2 * kCoarseSweeps; ++h) {
-          sv_half_sweep<false>(S, h & 1);
+          sv_half_sweep_full(S, a.dnx[a.nlev - 1], h & 1);
           __syncthreads();
         }
       }
@@ -506,7 +561,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
           for (int c = tid; c < sL[l].N; c += kIT) prolong_cell(sL[l], sL[l + 1], S.u, uc, c, a.dmask);
           __syncthreads();
           for (int h = 0; h < 2 * a.npost; ++h) {
-            sv_half_sweep<false>(S, (h + 1) & 1);
+            sv_half_sweep_full(S, a.dnx[l], (h + 1) & 1);
             __syncthreads();
           }
         }
@@ -514,10 +569,10 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
       // ---- up: prolongation, correction, post-smoothing on the strip levels
       for (int l = a.ld - 1; l >= 0; --l) {
         const CoarseView V = cview(l);
-        if (l == 0) strip_prolong(S0.u, S0.nx, S0.h, S0.y0, V, a.dmask);
+        if (l == 0) strip_prolong(S0.u, S0.nx, a.dnx[0], S0.h, S0.y0, V, a.dmask);
         else {
           const SV S = sview(l);
-          strip_prolong(S.u, S.nx, S.h, S.y0, V, a.dmask);
+          strip_prolong(S.u, S.nx, a.dnx[l], S.h, S.y0, V, a.dmask);
         }
         cl.sync();
         // every rank has read the coarse iterate: clear it for the next cycle
@@ -526,8 +581,8 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
           for (int q = tid; q < C.h * C.nx; q += kIT) C.u[q] = make_float2(0.f, 0.f);
         }
         for (int h = 0; h < 2 * a.npost; ++h) {
-          if (l == 0) l0_half_sweep(S0, tau, (h + 1) & 1);
-          else sv_half_sweep<true>(sview(l), (h + 1) & 1);
+          if (l == 0) l0_half_sweep(S0, a.dhx[0], (h + 1) & 1);
+          else sv_half_sweep_strip(sview(l), a.dhx[l], (h + 1) & 1);
           cl.sync();
         }
       }
@@ -548,6 +603,10 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
       }
     }
     cl.sync();
+  }
+  if (rank == 0 && tid == 0) {
+    atomicAdd(&bt.work[KC_EXACT_RES], n_res);
+    atomicAdd(&bt.work[KC_INNER], n_cyc);
   }
   cl.sync();   // no CTA leaves while another may still read its shared memory
 }
@@ -611,13 +670,14 @@ int inner_cluster_plan(const MGHost& mg, InnerPlan& p) {
   return 1;
 }
 
-int launch_inner_cluster(const MGHost& mg, const InnerPlan& p, const Batch& bt, const FineExact& fe, int cycles,
-                         cudaStream_t st, Prof* pf) {
+int launch_inner_cluster(const MGHost& mg, const InnerPlan& p, const Batch& bt, const FineExact& fe, float4* q4,
+                         int cycles, cudaStream_t st, Prof* pf) {
   InnerArgs a;
   a.bt = bt;
   a.fe = fe;
   a.levels = mg.d_levels;
-  a.f0 = mg.h_levels[0].f;
+  a.p4 = p.p4;
+  a.q4 = q4;
   a.nlev = mg.nlev;
   a.ld = p.ld;
   a.npre = mg.npre;
@@ -629,6 +689,11 @@ int launch_inner_cluster(const MGHost& mg, const InnerPlan& p, const Batch& bt, 
   for (int l = 0; l < kMaxLevels; ++l)
     a.off[l] = LevOff{p.off_u[l], p.off_f[l], p.off_te[l], p.off_tn[l], p.off_di[l]};
   a.off_rhs = p.off_rhs;
+  for (int l = 0; l < kMaxLevels; ++l) {
+    const int nx = l < mg.nlev ? mg.h_levels[l].nx : 2;
+    a.dnx[l] = make_fastdiv((uint32_t)nx);
+    a.dhx[l] = make_fastdiv((uint32_t)(nx / 2 > 0 ? nx / 2 : 1));
+  }
   prof_begin(pf, KC_INNER, st);
   k_inner_cluster<<<bt.nb * kCS, kIT, p.smem, st>>>(a);
   prof_end(pf, KC_INNER, st);

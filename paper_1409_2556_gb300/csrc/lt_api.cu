@@ -64,6 +64,7 @@ struct Workspace {
   float2* X_hi = nullptr;
   float2* X_lo = nullptr;
   size_t x_elems = 0;
+  float4* l0q = nullptr;          // [nb][N] finest-level scratch of the cluster-resident solve
 };
 
 struct lt_ctx {
@@ -562,7 +563,20 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
       return rc;
   }
   CK(cudaMalloc(&mg.d_levels, sizeof(lt::Level) * lt::kMaxLevels));
-  lt::inner_cluster_plan(mg, ctx->inner);
+  if (lt::inner_cluster_plan(mg, ctx->inner)) {
+    // the four faces of every finest-level cell in one 16-byte record (zero across domain edges)
+    const HostLevel& h0 = ctx->hl[0];
+    std::vector<float4> p4(N);
+    for (int64_t c = 0; c < N; ++c) {
+      const int x = (int)(c % nx), y = (int)(c / nx);
+      p4[c] = make_float4(x + 1 < nx ? (float)h0.Te[c] : 0.f, x > 0 ? (float)h0.Te[c - 1] : 0.f,
+                          y + 1 < ny ? (float)h0.Tn[c] : 0.f, y > 0 ? (float)h0.Tn[c - nx] : 0.f);
+    }
+    float4* d4 = nullptr;
+    if ((rc = dalloc(ctx, ctx->grid_allocs, &d4, (size_t)N))) return rc;
+    CK(cudaMemcpy(d4, p4.data(), N * sizeof(float4), cudaMemcpyHostToDevice));
+    ctx->inner.p4 = d4;
+  }
   ctx->have_grid = true;
   ctx->src.clear(); ctx->Q.clear(); ctx->rec.clear();
   return LT_OK;
@@ -755,6 +769,7 @@ static int ensure_ws(lt_ctx* ctx, const Plan& P) {
   AL(bt.rmax, nb);
   AL(bt.jdev, 1);
   if (nc2) AL(bt.coarse_inv, (size_t)2 * P.G * nc2);
+  if (ctx->inner.ok) AL(ws.l0q, (size_t)nb * N);
   // multigrid vectors
   for (int l = 0; l < ctx->mg.nlev; ++l) {
     lt::Level& L = ctx->mg.h_levels[l];
@@ -795,7 +810,8 @@ static int launch_iteration(lt_ctx* ctx, cudaStream_t q, int jj, int* nlq, lt::P
   lt::launch_prep_iter(bt, jj, q);
   ++*nlq;
   if (uses_cluster_solve(ctx)) {
-    if (lt::launch_inner_cluster(ctx->mg, ctx->inner, bt, ctx->fe, o.inner_cycles, q, pf)) return LT_ERR_CUDA;
+    if (lt::launch_inner_cluster(ctx->mg, ctx->inner, bt, ctx->fe, ctx->ws.l0q, o.inner_cycles, q, pf))
+      return LT_ERR_CUDA;
     lt::launch_inner_record(bt, q);
     *nlq += 2;
     lt::launch_arnoldi(bt, ctx->fe, jj, q, nlq, pf);

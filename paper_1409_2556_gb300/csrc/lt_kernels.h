@@ -26,12 +26,14 @@ struct InnerPlan {
   int off_u[kMaxLevels] = {}, off_f[kMaxLevels] = {};               // byte offsets in shared memory
   int off_te[kMaxLevels] = {}, off_tn[kMaxLevels] = {}, off_di[kMaxLevels] = {}, off_rhs = 0;
   size_t smem = 0;                 // dynamic shared memory per CTA
+  const float4* p4 = nullptr;      // [N] finest-level faces (Te east, Te west, Tn north, Tn south), set by the host
 };
 // fills p (p.ok = 0 when the levels do not split into 8 even row strips or do not fit); returns p.ok
 int inner_cluster_plan(const MGHost& mg, InnerPlan& p);
 // rounds x cycles V-cycles of every active basis, one cluster per basis (bt.rounds rounds)
-int launch_inner_cluster(const MGHost& mg, const InnerPlan& p, const Batch& bt, const FineExact& fe, int cycles,
-                         cudaStream_t st, Prof* pf);
+// q4: [nb][N] float4 scratch of the finest level (inverse diagonal, right-hand side)
+int launch_inner_cluster(const MGHost& mg, const InnerPlan& p, const Batch& bt, const FineExact& fe, float4* q4,
+                         int cycles, cudaStream_t st, Prof* pf);
 
 // one V-cycle on every active basis of the batch whose refinement round `round` is not done
 int launch_vcycle(const MGHost& mg, const Batch& bt, int round, cudaStream_t st, int* nlaunch, Prof* pf);
