@@ -488,6 +488,8 @@ void launch_shift_ls(const Batch& bt, int j, cudaStream_t st) {
   k_shift_ls<<<bt.nb, 256, 0, st>>>(bt, j);
   k_next_iter<<<1, 32, 0, st>>>(bt);
 }
+void launch_shift_ls_only(const Batch& bt, int j, cudaStream_t st) { k_shift_ls<<<bt.nb, 256, 0, st>>>(bt, j); }
+void launch_next_iter(const Batch& bt, cudaStream_t st) { k_next_iter<<<1, 32, 0, st>>>(bt); }
 
 // y_k = R^{-1} g over the shift's converged (or final) column count
 __global__ void k_backsolve(Batch bt, const int* sh_basis) {

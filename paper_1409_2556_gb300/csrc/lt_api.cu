@@ -100,6 +100,9 @@ struct lt_ctx {
   // non-blocking stream on which the per-iteration CUDA graph is captured and replayed
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+  // second branch of an outer iteration whose bases are split in two (cluster-resident solves)
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // learned initial guess (opts.precond = 1)
   lt_unet* net = nullptr;
   float *d_lk = nullptr, *d_mD = nullptr, *d_xin = nullptr, *d_gn2 = nullptr;
@@ -244,6 +247,9 @@ void lt_destroy(lt_ctx* ctx) {
   if (ctx->ev_a) cudaEventDestroy(ctx->ev_a);
   if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
   lt::tma_cache_free(ctx->mg);
   lt::tma_cache_free(ctx->pc_mg);
   free_list(ctx->pc_allocs);          // also holds pc_mg.d_levels
@@ -802,23 +808,76 @@ static bool uses_cluster_solve(const lt_ctx* ctx) {
   return ctx->opts.mg_cluster == 1 && ctx->opts.precond == 0 && ctx->inner.ok;
 }
 
+// The bases [b0, b0 + n) of a batch as a batch of their own: per-basis arrays
+// offset by b0; shift indices (shift_off) stay global, so per-shift arrays
+// are shared; the outer-iteration counter is shared too.
+static lt::Batch sub_batch(const lt::Batch& bt, int b0, int n) {
+  lt::Batch v = bt;
+  const size_t N = (size_t)bt.N, M = (size_t)bt.maxit;
+  v.nb = n;
+  v.itol2 += b0; v.rmax += b0;
+  v.V_hi += b0 * (M + 1) * N; v.V_lo += b0 * (M + 1) * N;
+  v.U_hi += b0 * M * N; v.U_lo += b0 * M * N;
+  v.S_hi += b0 * N; v.S_lo += b0 * N;
+  v.group += b0; v.tau_cur += b0; v.tau_slot += b0;
+  v.rnorm2 += (size_t)b0 * (bt.rounds + 1);
+  v.dot += (size_t)b0 * 2 * (M + 1);
+  v.H += (size_t)b0 * M * (M + 1);
+  v.snorm2 += b0; v.active += b0; v.nit += b0; v.inner_max += b0; v.rhs_cell += b0;
+  v.shift_off += b0;
+  return v;
+}
+
+// One outer iteration with cluster-resident preconditioner solves.  When the
+// bases outnumber the clusters the device holds at once, they are split in
+// two halves issued as two independent branches (the second on side_stream):
+// while one half's second wave of clusters runs, the other half's
+// Gram-Schmidt and least squares use the SMs the clusters leave idle.
+static int launch_iteration_cluster(lt_ctx* ctx, cudaStream_t q, int jj, int* nlq, lt::Prof* pf) {
+  const lt_opts& o = ctx->opts;
+  lt::Batch& bt = ctx->ws.bt;
+  const int nb = bt.nb;
+  // (not inside lt_forward_noalloc, which creates no streams or events)
+  const int parts = (nb > ctx->inner.max_clusters && nb >= 2 && ctx->arena_base == nullptr) ? 2 : 1;
+  if (parts == 2) {
+    if (!ctx->side_stream) CK(cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking));
+    if (!ctx->ev_fork) CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    if (!ctx->ev_join) CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    CK(cudaEventRecord(ctx->ev_fork, q));
+    CK(cudaStreamWaitEvent(ctx->side_stream, ctx->ev_fork, 0));
+  }
+  const int half = (nb + 1) / 2;
+  for (int part = 0; part < parts; ++part) {
+    const int b0 = part == 0 ? 0 : half;
+    const int n = parts == 1 ? nb : (part == 0 ? half : nb - half);
+    cudaStream_t qs = part == 0 ? q : ctx->side_stream;
+    const lt::Batch v = parts == 1 ? bt : sub_batch(bt, b0, n);
+    lt::launch_prep_iter(v, jj, qs);
+    if (lt::launch_inner_cluster(ctx->mg, ctx->inner, v, ctx->fe, ctx->ws.l0q + (size_t)b0 * ctx->N,
+                                 o.inner_cycles, qs, pf))
+      return LT_ERR_CUDA;
+    lt::launch_inner_record(v, qs);
+    lt::launch_arnoldi(v, ctx->fe, jj, qs, nlq, pf);
+    lt::launch_shift_ls_only(v, jj, qs);
+    *nlq += 4;
+  }
+  if (parts == 2) {
+    CK(cudaEventRecord(ctx->ev_join, ctx->side_stream));
+    CK(cudaStreamWaitEvent(q, ctx->ev_join, 0));
+  }
+  lt::launch_next_iter(bt, q);
+  *nlq += 1;
+  return LT_OK;
+}
+
 // one outer iteration of every active basis (kernels read j from bt.jdev)
 static int launch_iteration(lt_ctx* ctx, cudaStream_t q, int jj, int* nlq, lt::Prof* pf) {
   const lt_opts& o = ctx->opts;
   lt::Batch& bt = ctx->ws.bt;
   const lt::Level& L0 = ctx->mg.h_levels[0];
+  if (uses_cluster_solve(ctx)) return launch_iteration_cluster(ctx, q, jj, nlq, pf);
   lt::launch_prep_iter(bt, jj, q);
   ++*nlq;
-  if (uses_cluster_solve(ctx)) {
-    if (lt::launch_inner_cluster(ctx->mg, ctx->inner, bt, ctx->fe, ctx->ws.l0q, o.inner_cycles, q, pf))
-      return LT_ERR_CUDA;
-    lt::launch_inner_record(bt, q);
-    *nlq += 2;
-    lt::launch_arnoldi(bt, ctx->fe, jj, q, nlq, pf);
-    lt::launch_shift_ls(bt, jj, q);
-    *nlq += 2;
-    return LT_OK;
-  }
   for (int r = 0; r < o.inner_rounds; ++r) {
     lt::launch_exact_residual(bt, ctx->fe, L0, jj, r, 0, q, pf);
     ++*nlq;

@@ -46,7 +46,9 @@ void launch_exact_residual(const Batch& bt, const FineExact& fe, const Level& L0
 void launch_update_u(const Batch& bt, const Level& L0, int j, int round, cudaStream_t st);
 void launch_inner_record(const Batch& bt, cudaStream_t st);
 void launch_arnoldi(const Batch& bt, const FineExact& fe, int j, cudaStream_t st, int* nlaunch, Prof* pf);
-void launch_shift_ls(const Batch& bt, int j, cudaStream_t st);
+void launch_shift_ls(const Batch& bt, int j, cudaStream_t st);   // least squares, then the iteration counter
+void launch_shift_ls_only(const Batch& bt, int j, cudaStream_t st);
+void launch_next_iter(const Batch& bt, cudaStream_t st);
 void launch_init_batch(const Batch& bt, cudaStream_t st);
 void launch_backsolve_map(const Batch& bt, const int* sh_basis, cudaStream_t st);
 
