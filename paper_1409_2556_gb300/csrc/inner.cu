@@ -69,8 +69,8 @@ struct InnerArgs {
   Batch bt;
   FineExact fe;
   const Level* levels;          // device copy of the level descriptors
-  const float4* p4;             // [N] finest level: (Te east, Te west, Tn north, Tn south) of each cell
-  float4* q4;                   // [nb][N] finest level: (1 / (D + tau m), right-hand side) per basis
+  const float4* p4;             // [N] finest level: (Te east, Te west, Tn north, Tn south), red-black order
+  float4* q4;                   // [nb][N] finest level: (1 / (D + tau m), right-hand side) per basis, same order
   int nlev, ld;                 // levels [0, ld) in strips, [ld, nlev) in rank 0
   int npre, npost, dmask, coarse_direct, rounds, cycles;
   LevOff off[kMaxLevels];
@@ -114,13 +114,20 @@ struct CoarseView {
 __device__ __forceinline__ void axpy_c(float2& r, float t, float2 v) { r.x += t * v.x; r.y += t * v.y; }
 
 // ---------------------------------------------------------------- finest level (global coefficients)
+// The finest level's per-cell records are stored in red-black order: all cells of colour 0,
+// then all of colour 1, each colour row by row, so that the cells one half-sweep visits are
+// contiguous (cell (x, y) of an nx-wide level at  ((x + y) & 1) * N/2 + y * nx/2 + x/2).
+__device__ __forceinline__ int rb_index(int x, int y, int nx, int nhalf) {
+  return ((x + y) & 1) * nhalf + y * (nx >> 1) + (x >> 1);
+}
+
 // loads of one cell of the finest level: the four faces, inverse diagonal and right-hand side
 struct L0Cell { float4 t; float4 q; };
 
-__device__ __forceinline__ L0Cell l0_load(const L0V& S, int c) {
+__device__ __forceinline__ L0Cell l0_load(const L0V& S, int r) {
   L0Cell v;
-  v.t = S.P[c];
-  v.q = S.Q[c];
+  v.t = S.P[r];
+  v.q = S.Q[r];
   return v;
 }
 
@@ -147,8 +154,7 @@ __device__ __forceinline__ void l0_half_sweep(const L0V& S, FastDiv dhx, int col
     for (int k = 0; k < kL0Batch; ++k) {
       const int q = q0 + k * kIT;
       if (q < n) {
-        const int ly = fdiv(q, dhx), y = S.y0 + ly, x = 2 * (q - ly * hx) + ((color + y) & 1);
-        cq[k] = l0_load(S, y * S.nx + x);
+        cq[k] = l0_load(S, color * (S.ny * hx) + S.y0 * hx + q);   // red-black order: contiguous in q
       }
     }
 #pragma unroll
@@ -177,7 +183,7 @@ __device__ __forceinline__ float l0_restrict(const L0V& S, float2* fc, int ncx, 
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int x = 2 * I + (k & 1), ly = 2 * lJ + (k >> 1), y = S.y0 + ly;
-      cq[k] = l0_load(S, y * S.nx + x);
+      cq[k] = l0_load(S, rb_index(x, y, S.nx, S.ny * (S.nx >> 1)));
     }
     float2 nb[4][4];
 #pragma unroll
@@ -433,7 +439,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
       const int c = S0.y0 * S0.nx + q;
       const float mm = L.m[c];
       const float2 di = cinv(make_float2(L.D[c] + tau.x * mm, tau.y * mm));
-      q0[c] = make_float4(di.x, di.y, 0.f, 0.f);
+      q0[rb_index(c % S0.nx, c / S0.nx, S0.nx, (int)(bt.N >> 1))] = make_float4(di.x, di.y, 0.f, 0.f);
     }
   }
   __syncthreads();
@@ -452,7 +458,8 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
       cdf rr = load_cdf(bt.V_hi, bt.V_lo, vb + c);
       if (r > 0) rr = cdf_sub(rr, apply_exact(a.fe, bt.U_hi + ub, bt.U_lo + ub, c, taur, taui));
       if (r < R) {
-        reinterpret_cast<float2*>(q0 + c)[1] = make_float2(rr.re.hi, rr.im.hi);
+        const int x = q % S0.nx, y = S0.y0 + q / S0.nx;
+        reinterpret_cast<float2*>(q0 + rb_index(x, y, S0.nx, (int)(bt.N >> 1)))[1] = make_float2(rr.re.hi, rr.im.hi);
         S0.u[q] = make_float2(0.f, 0.f);
       }
       acc += rr.re.hi * rr.re.hi + rr.im.hi * rr.im.hi;

@@ -570,12 +570,13 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
   }
   CK(cudaMalloc(&mg.d_levels, sizeof(lt::Level) * lt::kMaxLevels));
   if (lt::inner_cluster_plan(mg, ctx->inner)) {
-    // the four faces of every finest-level cell in one 16-byte record (zero across domain edges)
+    // the four faces of every finest-level cell in one 16-byte record (zero across domain edges),
+    // in red-black order: colour (x + y) & 1 first, then row by row, x / 2 within the row
     const HostLevel& h0 = ctx->hl[0];
     std::vector<float4> p4(N);
     for (int64_t c = 0; c < N; ++c) {
       const int x = (int)(c % nx), y = (int)(c / nx);
-      p4[c] = make_float4(x + 1 < nx ? (float)h0.Te[c] : 0.f, x > 0 ? (float)h0.Te[c - 1] : 0.f,
+      p4[((x + y) & 1) * (N / 2) + (int64_t)y * (nx / 2) + x / 2] = make_float4(x + 1 < nx ? (float)h0.Te[c] : 0.f, x > 0 ? (float)h0.Te[c - 1] : 0.f,
                           y + 1 < ny ? (float)h0.Tn[c] : 0.f, y > 0 ? (float)h0.Tn[c - nx] : 0.f);
     }
     float4* d4 = nullptr;
