@@ -172,32 +172,27 @@ __device__ __forceinline__ void l0_half_sweep(const L0V& S, FastDiv dhx, int col
   }
 }
 
-// residual summed over 2x2 children into the coarse right-hand side (coarse row J at row J - row0 of fc);
-// returns this thread's sum of |r|^2 over the fine cells (the V-cycle's convergence monitor)
-__device__ __forceinline__ float l0_restrict(const L0V& S, float2* fc, int ncx, FastDiv dncx, int row0) {
+// Residual summed over the 2x2 children into the coarse right-hand side (coarse row J at row J - row0
+// of fc); returns this thread's sum of |r|^2 over the fine cells (the V-cycle's convergence monitor).
+// After a red-black sweep ending with the black half-sweep every black cell satisfies its equation, so
+// its residual is zero up to rounding and only the two red children (the diagonal ones, as strips start
+// on even rows) are evaluated; red_only = false evaluates all four.
+__device__ __forceinline__ float l0_restrict(const L0V& S, float2* fc, int ncx, FastDiv dncx, int row0,
+                                             bool red_only) {
   const int nch = S.h >> 1, n = nch * ncx;
+  const int kstep = red_only ? 3 : 1;
   float rr = 0.f;
   for (int q = threadIdx.x; q < n; q += kIT) {
     const int lJ = fdiv(q, dncx), I = q - lJ * ncx;
-    L0Cell cq[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int x = 2 * I + (k & 1), ly = 2 * lJ + (k >> 1), y = S.y0 + ly;
-      cq[k] = l0_load(S, rb_index(x, y, S.nx, S.ny * (S.nx >> 1)));
-    }
-    float2 nb[4][4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int x = 2 * I + (k & 1), ly = 2 * lJ + (k >> 1), y = S.y0 + ly;
-      l0_gather(S, x, y, ly, ly * S.nx + x, nb[k]);
-    }
     float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int x = 2 * I + (k & 1), ly = 2 * lJ + (k >> 1), li = ly * S.nx + x;
-      const float2 s = nb_dot(cq[k].t, nb[k]);
-      const float2 a = cmul(cinv(make_float2(cq[k].q.x, cq[k].q.y)), S.u[li]);
-      const float rx = cq[k].q.z - a.x + s.x, ry = cq[k].q.w - a.y + s.y;
+    for (int k = 0; k < 4; k += kstep) {
+      const int x = 2 * I + (k & 1), ly = 2 * lJ + (k >> 1), y = S.y0 + ly, li = ly * S.nx + x;
+      const L0Cell cq = l0_load(S, rb_index(x, y, S.nx, S.ny * (S.nx >> 1)));
+      float2 nb[4];
+      l0_gather(S, x, y, ly, li, nb);
+      const float2 s = nb_dot(cq.t, nb);
+      const float2 a = cmul(cinv(make_float2(cq.q.x, cq.q.y)), S.u[li]);
+      const float rx = cq.q.z - a.x + s.x, ry = cq.q.w - a.y + s.y;
       acc.x += rx;
       acc.y += ry;
       rr += rx * rx + ry * ry;
@@ -257,14 +252,16 @@ __device__ __forceinline__ void sv_half_sweep_full(const SV& S, FastDiv dnx, int
 
 // residual of the staged level summed over rx x ry children into the coarse right-hand side;
 // zero_uc: also clear the coarse iterate (coarse levels owned by this CTA)
+// red_only (2x2 coarsening, even first row, sweep ended black): only the red children, see l0_restrict
 __device__ __forceinline__ void sv_restrict(const SV& S, int rx, int ry, float2* fc, float2* uc, int ncx,
-                                            FastDiv dncx, int row0) {
+                                            FastDiv dncx, int row0, bool red_only) {
   const int nch = S.h / ry, n = nch * ncx;
   for (int q = threadIdx.x; q < n; q += kIT) {
     const int lJ = fdiv(q, dncx), I = q - lJ * ncx;
     float2 acc = make_float2(0.f, 0.f);
     for (int dj = 0; dj < ry; ++dj)
       for (int di = 0; di < rx; ++di) {
+        if (red_only && di != dj) continue;
         const int x = I * rx + di, ly = lJ * ry + dj, y = S.y0 + ly, li = ly * S.nx + x;
         float4 t;
         float2 nb[4];
@@ -289,23 +286,47 @@ __device__ __forceinline__ float2 cv_get(const CoarseView& V, int I, int J) {
   return V.loc[lJ * V.nx + I];
 }
 
-// u += bilinear interpolation of the coarse correction (weights 3/4, 1/4 per axis) on rows [y0, y0 + h)
-__device__ __forceinline__ void strip_prolong(float2* u, int nx, FastDiv dnx, int h, int y0, const CoarseView& V,
+// u += bilinear interpolation of the coarse correction (weights 3/4 and 1/4 per axis) on rows
+// [y0, y0 + h), one thread per 2x2 block of fine cells: the block's four cells interpolate from the
+// same 3x3 coarse neighbourhood, read once.  Across a domain face the coarse neighbour is the cell
+// itself, negated for a Dirichlet face (odd reflection) and kept for a Neumann face (even).
+__device__ __forceinline__ void strip_prolong(float2* u, int nx, FastDiv dhx, int h, int y0, const CoarseView& V,
                                               int dmask) {
-  const int n = h * nx;
+  const int ncx = nx >> 1, n = (h >> 1) * ncx;
+  const float sxl = (dmask & 1) ? -1.f : 1.f, sxh = (dmask & 2) ? -1.f : 1.f;
+  const float syl = (dmask & 4) ? -1.f : 1.f, syh = (dmask & 8) ? -1.f : 1.f;
   for (int q = threadIdx.x; q < n; q += kIT) {
-    const int ly = fdiv(q, dnx), x = q - ly * nx, y = y0 + ly;
-    int I0, I1, J0, J1;
-    float wi0, wi1, wj0, wj1, si, sj;
-    axis_interp(x, 2, V.nx, dmask & 1, dmask & 2, I0, I1, wi0, wi1, si);
-    axis_interp(y, 2, V.ny, dmask & 4, dmask & 8, J0, J1, wj0, wj1, sj);
-    wi1 *= si; wj1 *= sj;
-    const float2 a = cv_get(V, I0, J0), bq = cv_get(V, I1, J0), c = cv_get(V, I0, J1), d = cv_get(V, I1, J1);
-    const float w00 = wj0 * wi0, w01 = wj0 * wi1, w10 = wj1 * wi0, w11 = wj1 * wi1;
-    float2 v = u[q];
-    v.x += w00 * a.x + w01 * bq.x + w10 * c.x + w11 * d.x;
-    v.y += w00 * a.y + w01 * bq.y + w10 * c.y + w11 * d.y;
-    u[q] = v;
+    const int lJ = fdiv(q, dhx), I = q - lJ * ncx, J = (y0 >> 1) + lJ;
+    float2 c[3][3];
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy) {
+      int Jq = J + dy - 1;
+      float sy = 1.f;
+      if (Jq < 0) { Jq = J; sy = syl; }
+      else if (Jq >= V.ny) { Jq = J; sy = syh; }
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        int Iq = I + dx - 1;
+        float sx = 1.f;
+        if (Iq < 0) { Iq = I; sx = sxl; }
+        else if (Iq >= V.nx) { Iq = I; sx = sxh; }
+        const float2 v = cv_get(V, Iq, Jq);
+        c[dy][dx] = make_float2(sx * sy * v.x, sx * sy * v.y);
+      }
+    }
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+      for (int aa = 0; aa < 2; ++aa) {
+        // along each axis: the own coarse cell (index 1) with 3/4, the nearer neighbour (0 or 2) with 1/4
+        const int ny_ = bb ? 2 : 0, nx_ = aa ? 2 : 0;
+        const float2 e = make_float2(
+            0.5625f * c[1][1].x + 0.1875f * (c[1][nx_].x + c[ny_][1].x) + 0.0625f * c[ny_][nx_].x,
+            0.5625f * c[1][1].y + 0.1875f * (c[1][nx_].y + c[ny_][1].y) + 0.0625f * c[ny_][nx_].y);
+        float2& v = u[(2 * lJ + bb) * nx + 2 * I + aa];
+        v.x += e.x;
+        v.y += e.y;
+      }
   }
 }
 
@@ -495,7 +516,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
             l0_half_sweep(S0, a.dhx[0], h & 1);
             cl.sync();
           }
-          const float rr = l0_restrict(S0, fc, ncx, a.dnx[1], last ? 0 : S0.y0 / 2);
+          const float rr = l0_restrict(S0, fc, ncx, a.dnx[1], last ? 0 : S0.y0 / 2, a.npre > 0);
           block_sum(rr, red, &vpart[cy & 1]);
         } else {
           const SV S = sview(l);
@@ -503,7 +524,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
             sv_half_sweep_strip(S, a.dhx[l], h & 1);
             cl.sync();
           }
-          sv_restrict(S, 2, 2, fc, nullptr, ncx, a.dnx[l + 1], last ? 0 : S.y0 / 2);
+          sv_restrict(S, 2, 2, fc, nullptr, ncx, a.dnx[l + 1], last ? 0 : S.y0 / 2, a.npre > 0);
         }
         __syncthreads();   // the next level's sweeps read right-hand sides written by other threads
       }
@@ -524,7 +545,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
           }
           const Level& Lc = sL[l + 1];
           sv_restrict(S, sL[l].rx, sL[l].ry, reinterpret_cast<float2*>(smb + a.off[l + 1].f),
-                      reinterpret_cast<float2*>(smb + a.off[l + 1].u), Lc.nx, a.dnx[l + 1], 0);
+                      reinterpret_cast<float2*>(smb + a.off[l + 1].u), Lc.nx, a.dnx[l + 1], 0, false);
           __syncthreads();
         }
       if (a.coarse_direct) {
@@ -576,10 +597,10 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
       // ---- up: prolongation, correction, post-smoothing on the strip levels
       for (int l = a.ld - 1; l >= 0; --l) {
         const CoarseView V = cview(l);
-        if (l == 0) strip_prolong(S0.u, S0.nx, a.dnx[0], S0.h, S0.y0, V, a.dmask);
+        if (l == 0) strip_prolong(S0.u, S0.nx, a.dhx[0], S0.h, S0.y0, V, a.dmask);
         else {
           const SV S = sview(l);
-          strip_prolong(S.u, S.nx, a.dnx[l], S.h, S.y0, V, a.dmask);
+          strip_prolong(S.u, S.nx, a.dhx[l], S.h, S.y0, V, a.dmask);
         }
         cl.sync();
         // every rank has read the coarse iterate: clear it for the next cycle
