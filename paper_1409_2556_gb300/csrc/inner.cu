@@ -473,17 +473,32 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
   unsigned long long n_res = 0, n_cyc = 0;   // rank 0, thread 0: work counters, added once at the end
   for (int r = 0; r <= R; ++r) {
     // df32 residual of the current u_j on this CTA's rows; it is the next round's right-hand side
+    // (two cells per pass, both evaluated before either is stored, so their loads overlap)
     float acc = 0.f;
-    for (int q = tid; q < n0; q += kIT) {
-      const int c = c0 + q;
-      cdf rr = load_cdf(bt.V_hi, bt.V_lo, vb + c);
-      if (r > 0) rr = cdf_sub(rr, apply_exact(a.fe, bt.U_hi + ub, bt.U_lo + ub, c, taur, taui));
-      if (r < R) {
-        const int x = q % S0.nx, y = S0.y0 + q / S0.nx;
-        reinterpret_cast<float2*>(q0 + rb_index(x, y, S0.nx, (int)(bt.N >> 1)))[1] = make_float2(rr.re.hi, rr.im.hi);
-        S0.u[q] = make_float2(0.f, 0.f);
+    for (int q0i = tid; q0i < n0; q0i += 2 * kIT) {
+      cdf rr[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int q = q0i + k * kIT;
+        if (q < n0) {
+          const int c = c0 + q;
+          rr[k] = load_cdf(bt.V_hi, bt.V_lo, vb + c);
+          if (r > 0) rr[k] = cdf_sub(rr[k], apply_exact(a.fe, bt.U_hi + ub, bt.U_lo + ub, c, taur, taui));
+        }
       }
-      acc += rr.re.hi * rr.re.hi + rr.im.hi * rr.im.hi;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int q = q0i + k * kIT;
+        if (q < n0) {
+          if (r < R) {
+            const int ly = fdiv(q, a.dnx[0]), x = q - ly * S0.nx;
+            reinterpret_cast<float2*>(q0 + rb_index(x, S0.y0 + ly, S0.nx, (int)(bt.N >> 1)))[1] =
+                make_float2(rr[k].re.hi, rr[k].im.hi);
+            S0.u[q] = make_float2(0.f, 0.f);
+          }
+          acc += rr[k].re.hi * rr[k].re.hi + rr[k].im.hi * rr[k].im.hi;
+        }
+      }
     }
     const double rn2 = cluster_sum(cl, acc, red, part, slot, &bcast);
     slot ^= 1;
@@ -536,16 +551,20 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
         n_cyc += (unsigned long long)bt.N;
       }
       // ---- coarse levels in rank 0
+      // (levels coarsened 2x2 use the colour-compact sweep, red-only restriction and block prolongation)
       if (rank == 0)
         for (int l = a.ld; l < a.nlev - 1; ++l) {
           const SV S = sview(l);
+          const bool q22 = sL[l].rx == 2 && sL[l].ry == 2;
           for (int h = 0; h < 2 * a.npre; ++h) {
-            sv_half_sweep_full(S, a.dnx[l], h & 1);
+            if (q22) sv_half_sweep_strip(S, a.dhx[l], h & 1);
+            else sv_half_sweep_full(S, a.dnx[l], h & 1);
             __syncthreads();
           }
           const Level& Lc = sL[l + 1];
           sv_restrict(S, sL[l].rx, sL[l].ry, reinterpret_cast<float2*>(smb + a.off[l + 1].f),
-                      reinterpret_cast<float2*>(smb + a.off[l + 1].u), Lc.nx, a.dnx[l + 1], 0, false);
+                      reinterpret_cast<float2*>(smb + a.off[l + 1].u), Lc.nx, a.dnx[l + 1], 0,
+                      q22 && a.npre > 0);
           __syncthreads();
         }
       if (a.coarse_direct) {
@@ -585,11 +604,21 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
       if (rank == 0)
         for (int l = a.nlev - 2; l >= a.ld; --l) {
           const SV S = sview(l);
+          const bool q22 = sL[l].rx == 2 && sL[l].ry == 2;
           const float2* uc = reinterpret_cast<const float2*>(smb + a.off[l + 1].u);
-          for (int c = tid; c < sL[l].N; c += kIT) prolong_cell(sL[l], sL[l + 1], S.u, uc, c, a.dmask);
+          if (q22) {
+            CoarseView V;
+            V.nx = sL[l + 1].nx; V.ny = sL[l + 1].ny;
+            V.full = 1; V.hc = V.ny; V.yc0 = 0;
+            V.loc = uc; V.dn = nullptr; V.up = nullptr;
+            strip_prolong(S.u, S.nx, a.dhx[l], S.h, 0, V, a.dmask);
+          } else {
+            for (int c = tid; c < sL[l].N; c += kIT) prolong_cell(sL[l], sL[l + 1], S.u, uc, c, a.dmask);
+          }
           __syncthreads();
           for (int h = 0; h < 2 * a.npost; ++h) {
-            sv_half_sweep_full(S, a.dnx[l], (h + 1) & 1);
+            if (q22) sv_half_sweep_strip(S, a.dhx[l], (h + 1) & 1);
+            else sv_half_sweep_full(S, a.dnx[l], (h + 1) & 1);
             __syncthreads();
           }
         }
