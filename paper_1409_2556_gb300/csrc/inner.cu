@@ -702,7 +702,10 @@ int inner_cluster_plan(const MGHost& mg, InnerPlan& p) {
   p.off_rhs = take(mg.coarse_direct ? (size_t)mg.h_levels[mg.nlev - 1].N * sizeof(float2) : 0);
   p.smem = cur;
   if (p.smem > kInnerSmemMax) return 0;
-  if (cudaFuncSetAttribute(k_inner_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem) != cudaSuccess) {
+  // the attribute belongs to the kernel, not to this grid: always the ceiling, so that contexts with
+  // different grids can launch it in any order
+  if (cudaFuncSetAttribute(k_inner_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInnerSmemMax) !=
+      cudaSuccess) {
     cudaGetLastError();
     return 0;
   }

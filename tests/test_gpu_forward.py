@@ -231,3 +231,22 @@ def test_cluster_solve_falls_back_on_grids_that_do_not_split(Engine):
     h, st = _solve(Engine, p, mg_cluster=1)
     assert st["work"][KC["inner"]] == 0
     assert _rel(h, direct.forward(p)) < TOL_H
+
+
+def test_cluster_solve_on_grids_set_up_in_any_order(Engine):
+    """A context on a larger grid keeps its cluster-resident solve after another context set up a
+    smaller grid (the kernel's shared-memory limit is per kernel, not per grid)."""
+    from paper_1409_2556_gb300._lib import KC
+    big = W.random_problem(256, 128, 1, variance=1.0, seed=31, ns=2, nr=2, nt=2, Nz=16, tol=1e-11)
+    small = W.random_problem(64, 32, 1, variance=1.0, seed=32, ns=2, nr=2, nt=2, Nz=16, tol=1e-11)
+    e_big, e_small = Engine(0), Engine(0)
+    e_big.load_problem(big)
+    e_small.load_problem(small)
+    h_small = e_small.forward(small.times)
+    h_big = e_big.forward(big.times)
+    assert e_big.last_stats["work"][KC["inner"]] > 0
+    assert e_big.last_stats["n_converged"] == e_big.last_stats["n_shift_solves"]
+    assert _rel(h_big, direct.forward(big)) < TOL_H
+    assert _rel(h_small, direct.forward(small)) < TOL_H
+    e_big.close()
+    e_small.close()
