@@ -588,11 +588,34 @@ void launch_fields(const Batch& bt, const QuadItem* items, const double2* C, int
 }
 
 // ------------------------------------------------------------ true residual (judge)
-constexpr int kXS = 4;   // shifts per pass
+constexpr int kXS = 16;   // shifts per pass (U is read once per pass)
 
-// X[sh] = U_b y_sh for every shift of basis b (df32 accumulation)
-__global__ void k_xk(Batch bt, float2* X_hi, float2* X_lo) {
-  __shared__ cdf ys[kXS][256];
+// acc + u * y for df32 complex values, with one renormalisation per component: the two hi x hi
+// products enter the running sum through TwoSum, their rounding errors and the hi x lo cross terms
+// go to the low word.
+__device__ __forceinline__ df df_fma2(df acc, df a, df b, df c, df d) {   // acc + a*b - c*d
+  float p1, e1, p2, e2, s1, t1, s2, t2;
+  two_prod(a.hi, b.hi, p1, e1);
+  two_prod(c.hi, d.hi, p2, e2);
+  two_sum(acc.hi, p1, s1, t1);
+  two_sum(s1, -p2, s2, t2);
+  float lo = __fadd_rn(acc.lo, __fadd_rn(t1, t2));
+  lo = __fadd_rn(lo, __fsub_rn(e1, e2));
+  lo = __fmaf_rn(a.hi, b.lo, lo);
+  lo = __fmaf_rn(a.lo, b.hi, lo);
+  lo = __fmaf_rn(-c.hi, d.lo, lo);
+  lo = __fmaf_rn(-c.lo, d.hi, lo);
+  df r;
+  fast_two_sum(s2, lo, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ cdf cdf_fma(cdf acc, cdf u, cdf y) {
+  return {df_fma2(acc.re, u.re, y.re, u.im, y.im), df_fma2(acc.im, u.re, y.im, df_neg(u.im), y.re)};
+}
+
+// X[sh] = U_b y_sh for every shift of basis b (df32 accumulation); ys: [kXS][maxit] in shared memory
+__global__ void __launch_bounds__(256) k_xk(Batch bt, float2* X_hi, float2* X_lo) {
+  extern __shared__ cdf ys[];
   int b = blockIdx.y;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int M = bt.maxit;
@@ -605,7 +628,7 @@ __global__ void k_xk(Batch bt, float2* X_hi, float2* X_lo) {
       int q = idx / m, i = idx % m;
       int sh = sa + q;
       double2 y = sh < s1 ? bt.Y[(size_t)sh * M + i] : make_double2(0.0, 0.0);
-      ys[q][i] = {df_from_double(y.x), df_from_double(y.y)};
+      ys[q * m + i] = {df_from_double(y.x), df_from_double(y.y)};
     }
     __syncthreads();
     if (c < bt.N) {
@@ -615,13 +638,26 @@ __global__ void k_xk(Batch bt, float2* X_hi, float2* X_lo) {
       for (int i = 0; i < m; ++i) {
         cdf u = load_cdf(bt.U_hi, bt.U_lo, ub + (size_t)i * bt.N + c);
 #pragma unroll
-        for (int q = 0; q < kXS; ++q) acc[q] = cdf_add(acc[q], cdf_mul(u, ys[q][i]));
+        for (int q = 0; q < kXS; ++q) acc[q] = cdf_fma(acc[q], u, ys[q * m + i]);
       }
 #pragma unroll
       for (int q = 0; q < kXS; ++q)
         if (sa + q < s1) store_cdf(X_hi, X_lo, (size_t)(sa + q) * bt.N + c, acc[q]);
     }
   }
+}
+
+void launch_xk(const Batch& bt, float2* X_hi, float2* X_lo, cudaStream_t st, Prof* pf) {
+  static bool attr = false;
+  const size_t smem_max = (size_t)kXS * 256 * sizeof(cdf);   // maxit <= 250
+  if (!attr) {
+    cudaFuncSetAttribute(k_xk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+    attr = true;
+  }
+  dim3 g((unsigned)((bt.N + 255) / 256), bt.nb);
+  prof_begin(pf, KC_XK, st);
+  k_xk<<<g, 256, (size_t)kXS * bt.maxit * sizeof(cdf), st>>>(bt, X_hi, X_lo);
+  prof_end(pf, KC_XK, st);
 }
 
 __global__ void k_true_res(Batch bt, FineExact fe, const int* sh_basis, const float2* X_hi, const float2* X_lo,
@@ -642,13 +678,6 @@ __global__ void k_true_res(Batch bt, FineExact fe, const int* sh_basis, const fl
   }
   block_reduce_add<1>(acc, red);
   if (threadIdx.x == 0) atomicAdd(&res2[sh], (double)acc[0]);
-}
-
-void launch_xk(const Batch& bt, float2* X_hi, float2* X_lo, cudaStream_t st, Prof* pf) {
-  dim3 g((unsigned)((bt.N + 255) / 256), bt.nb);
-  prof_begin(pf, KC_XK, st);
-  k_xk<<<g, 256, 0, st>>>(bt, X_hi, X_lo);
-  prof_end(pf, KC_XK, st);
 }
 
 void launch_true_res(const Batch& bt, const FineExact& fe, const int* sh_basis, const float2* X_hi,
