@@ -79,14 +79,33 @@ struct InnerArgs {
   FastDiv dhx[kMaxLevels];      // ... and by half of it (cells of one colour per row)
 };
 
+// Strip levels keep their shared-memory arrays in red-black order too: colour c = (x + y) & 1, then
+// the strip's rows, then x / 2 ([2][h][nx/2]; strips start on even rows, so the colour of local row
+// ly is (x + ly) & 1).  A half-sweep's own cells and each of its four neighbour streams are then
+// contiguous across a warp (no shared-memory bank conflicts).  For a cell of colour c in local row
+// ly at position k (x = 2k + p, p = (c + ly) & 1) the neighbours have colour 1 - c and positions
+// k + p (east), k - 1 + p (west), k (north, south).
+
 // The finest level's rows [y0, y0 + h) of this CTA.
 struct L0V {
-  int nx, ny, h, y0;
-  const float4* __restrict__ P;  // faces (global cell index)
-  const float4* Q;               // inverse diagonal and right-hand side (global cell index; rewritten every round)
-  float2* u;                     // [h][nx], shared memory
+  int nx, ny, h, y0, hx, plane;  // hx = nx / 2, plane = h hx (cells of one colour in the strip)
+  const float4* __restrict__ P;  // faces (red-black order over the whole level)
+  const float4* Q;               // inverse diagonal and right-hand side (same order; rewritten every round)
+  float2* u;                     // [2][h][hx], shared memory
   const float2* u_dn;            // iterate of rank - 1 (its last row lies just below y0), or null
   const float2* u_up;            // iterate of rank + 1 (its first row lies just above y0 + h - 1), or null
+};
+
+// A strip level below the finest, staged in shared memory in red-black order.
+struct RBV {
+  int nx, ny, h, y0, hx, plane;
+  float2* u;                     // [2][h][hx]
+  float2* f;                     // [2][h][hx]
+  float* te;                     // [2][h][hx]     east face of the cell
+  float* ts;                     // [2][h+1][hx]   south face of the cell in local row r (r = h: the row above)
+  float2* di;                    // [2][h][hx]     1 / (D + tau m)
+  const float2* u_dn;
+  const float2* u_up;
 };
 
 // A staged level's rows [y0, y0 + h) (a strip of a distributed level, or a whole coarse level with y0 = 0).
@@ -104,8 +123,8 @@ struct SV {
 // Read access to the iterate of the next coarser level, for the prolongation.
 struct CoarseView {
   int nx, ny;
-  int full;                      // 1: the whole level in one array (rank 0's), 0: strips
-  int hc, yc0;                   // own strip rows when !full
+  int full;                      // 1: the whole level in one array (rank 0's, natural order), 0: red-black strips
+  int hc, yc0, hxc, planec;      // own strip rows, half row length and cells per colour when !full
   const float2* loc;
   const float2* dn;
   const float2* up;
@@ -131,13 +150,20 @@ __device__ __forceinline__ L0Cell l0_load(const L0V& S, int r) {
   return v;
 }
 
-// neighbour iterates of a finest-level cell (zero where the cell has no neighbour)
-__device__ __forceinline__ void l0_gather(const L0V& S, int x, int y, int ly, int li, float2* nb) {
+// neighbour iterates (red-black strip order) of the colour-c cell at local row ly, position k (zero where
+// the cell has no neighbour); u, u_dn, u_up: this strip's and the neighbour ranks' arrays
+__device__ __forceinline__ void rb_gather(const float2* u, const float2* u_dn, const float2* u_up, int nx, int ny,
+                                          int h, int y0, int hx, int plane, int c, int ly, int k, float2* nb) {
   const float2 z = make_float2(0.f, 0.f);
-  nb[0] = x + 1 < S.nx ? S.u[li + 1] : z;
-  nb[1] = x > 0 ? S.u[li - 1] : z;
-  nb[2] = y + 1 < S.ny ? (ly + 1 < S.h ? S.u[li + S.nx] : S.u_up[x]) : z;
-  nb[3] = y > 0 ? (ly > 0 ? S.u[li - S.nx] : S.u_dn[(S.h - 1) * S.nx + x]) : z;
+  const int p = (c + ly) & 1, x = 2 * k + p, y = y0 + ly;
+  const int ob = (c ^ 1) * plane, row = ob + ly * hx;
+  nb[0] = x + 1 < nx ? u[row + k + p] : z;
+  nb[1] = x > 0 ? u[row + k - 1 + p] : z;
+  nb[2] = y + 1 < ny ? (ly + 1 < h ? u[row + hx + k] : u_up[ob + k]) : z;
+  nb[3] = y > 0 ? (ly > 0 ? u[row - hx + k] : u_dn[ob + (h - 1) * hx + k]) : z;
+}
+__device__ __forceinline__ void l0_gather(const L0V& S, int c, int ly, int k, float2* nb) {
+  rb_gather(S.u, S.u_dn, S.u_up, S.nx, S.ny, S.h, S.y0, S.hx, S.plane, c, ly, k, nb);
 }
 
 __device__ __forceinline__ float2 nb_dot(float4 t, const float2* nb) {
@@ -161,45 +187,102 @@ __device__ __forceinline__ void l0_half_sweep(const L0V& S, FastDiv dhx, int col
     for (int k = 0; k < kL0Batch; ++k) {
       const int q = q0 + k * kIT;
       if (q < n) {
-        const int ly = fdiv(q, dhx), y = S.y0 + ly, x = 2 * (q - ly * hx) + ((color + y) & 1), li = ly * S.nx + x;
+        const int ly = fdiv(q, dhx);
         float2 nb[4];
-        l0_gather(S, x, y, ly, li, nb);
+        l0_gather(S, color, ly, q - ly * hx, nb);
         float2 r = nb_dot(cq[k].t, nb);
         r.x += cq[k].q.z; r.y += cq[k].q.w;
-        S.u[li] = cmul(r, make_float2(cq[k].q.x, cq[k].q.y));
+        S.u[color * S.plane + q] = cmul(r, make_float2(cq[k].q.x, cq[k].q.y));
       }
     }
   }
 }
 
-// Residual summed over the 2x2 children into the coarse right-hand side (coarse row J at row J - row0
-// of fc); returns this thread's sum of |r|^2 over the fine cells (the V-cycle's convergence monitor).
-// After a red-black sweep ending with the black half-sweep every black cell satisfies its equation, so
-// its residual is zero up to rounding and only the two red children (the diagonal ones, as strips start
-// on even rows) are evaluated; red_only = false evaluates all four.
-__device__ __forceinline__ float l0_restrict(const L0V& S, float2* fc, int ncx, FastDiv dncx, int row0,
-                                             bool red_only) {
+// Where the restriction writes coarse cell (I, row J of the strip): the next strip level's red-black
+// arrays (fc_planec > 0: cells per colour of its strip, half row length fc_hx), or rank 0's whole
+// level in natural order (fc_planec = 0: row J + rowoff, ncx columns).
+__device__ __forceinline__ int coarse_slot(int I, int lJ, int ncx, int rowoff, int fc_hx, int fc_planec) {
+  return fc_planec > 0 ? ((I + lJ) & 1) * fc_planec + lJ * fc_hx + (I >> 1) : (lJ + rowoff) * ncx + I;
+}
+
+// Residual summed over the 2x2 children into the coarse right-hand side; returns this thread's sum of
+// |r|^2 over the fine cells (the V-cycle's convergence monitor).  After a red-black sweep ending with
+// the black half-sweep every black cell satisfies its equation, so its residual is zero up to rounding
+// and only the two red children are evaluated; red_only = false evaluates all four.  The children of
+// coarse cell I all sit at position k = I of their colour and row (strips start on even rows).
+__device__ __forceinline__ float l0_restrict(const L0V& S, float2* fc, int ncx, FastDiv dncx, int rowoff, int fc_hx,
+                                             int fc_planec, bool red_only) {
   const int nch = S.h >> 1, n = nch * ncx;
-  const int kstep = red_only ? 3 : 1;
+  const int nchild = red_only ? 2 : 4;
   float rr = 0.f;
   for (int q = threadIdx.x; q < n; q += kIT) {
     const int lJ = fdiv(q, dncx), I = q - lJ * ncx;
     float2 acc = make_float2(0.f, 0.f);
-    for (int k = 0; k < 4; k += kstep) {
-      const int x = 2 * I + (k & 1), ly = 2 * lJ + (k >> 1), y = S.y0 + ly, li = ly * S.nx + x;
-      const L0Cell cq = l0_load(S, rb_index(x, y, S.nx, S.ny * (S.nx >> 1)));
+    for (int ch = 0; ch < nchild; ++ch) {
+      const int c = ch >> 1, ly = 2 * lJ + (ch & 1);
+      const L0Cell cq = l0_load(S, c * (S.ny * S.hx) + (S.y0 + ly) * S.hx + I);
       float2 nb[4];
-      l0_gather(S, x, y, ly, li, nb);
+      l0_gather(S, c, ly, I, nb);
       const float2 s = nb_dot(cq.t, nb);
-      const float2 a = cmul(cinv(make_float2(cq.q.x, cq.q.y)), S.u[li]);
+      const float2 a = cmul(cinv(make_float2(cq.q.x, cq.q.y)), S.u[c * S.plane + ly * S.hx + I]);
       const float rx = cq.q.z - a.x + s.x, ry = cq.q.w - a.y + s.y;
       acc.x += rx;
       acc.y += ry;
       rr += rx * rx + ry * ry;
     }
-    fc[(S.y0 / 2 + lJ - row0) * ncx + I] = acc;
+    fc[coarse_slot(I, lJ, ncx, rowoff, fc_hx, fc_planec)] = acc;
   }
   return rr;
+}
+
+// ---------------------------------------------------------------- staged strip levels (red-black)
+__device__ __forceinline__ void rbv_cell(const RBV& S, int c, int ly, int k, float4& t, float2* nb) {
+  const int p = (c + ly) & 1, x = 2 * k + p, y = S.y0 + ly;
+  const int o = c ^ 1;
+  t.x = x + 1 < S.nx ? S.te[c * S.plane + ly * S.hx + k] : 0.f;
+  t.y = x > 0 ? S.te[o * S.plane + ly * S.hx + k - 1 + p] : 0.f;
+  const int tplane = (S.h + 1) * S.hx;
+  t.z = y + 1 < S.ny ? S.ts[o * tplane + (ly + 1) * S.hx + k] : 0.f;
+  t.w = y > 0 ? S.ts[c * tplane + ly * S.hx + k] : 0.f;
+  rb_gather(S.u, S.u_dn, S.u_up, S.nx, S.ny, S.h, S.y0, S.hx, S.plane, c, ly, k, nb);
+}
+
+__device__ __forceinline__ void rbv_half_sweep(const RBV& S, FastDiv dhx, int color) {
+  const int n = S.plane;
+  for (int q = threadIdx.x; q < n; q += kIT) {
+    const int ly = fdiv(q, dhx), k = q - ly * S.hx;
+    float4 t;
+    float2 nb[4];
+    rbv_cell(S, color, ly, k, t, nb);
+    float2 r = nb_dot(t, nb);
+    const int own = color * S.plane + q;
+    const float2 fv = S.f[own];
+    r.x += fv.x; r.y += fv.y;
+    S.u[own] = cmul(r, S.di[own]);
+  }
+}
+
+__device__ __forceinline__ void rbv_restrict(const RBV& S, float2* fc, int ncx, FastDiv dncx, int rowoff, int fc_hx,
+                                             int fc_planec, bool red_only) {
+  const int nch = S.h >> 1, n = nch * ncx;
+  const int nchild = red_only ? 2 : 4;
+  for (int q = threadIdx.x; q < n; q += kIT) {
+    const int lJ = fdiv(q, dncx), I = q - lJ * ncx;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int ch = 0; ch < nchild; ++ch) {
+      const int c = ch >> 1, ly = 2 * lJ + (ch & 1);
+      float4 t;
+      float2 nb[4];
+      rbv_cell(S, c, ly, I, t, nb);
+      const float2 s = nb_dot(t, nb);
+      const int own = c * S.plane + ly * S.hx + I;
+      const float2 a = cmul(cinv(S.di[own]), S.u[own]);
+      const float2 fv = S.f[own];
+      acc.x += fv.x - a.x + s.x;
+      acc.y += fv.y - a.y + s.y;
+    }
+    fc[coarse_slot(I, lJ, ncx, rowoff, fc_hx, fc_planec)] = acc;
+  }
 }
 
 // ---------------------------------------------------------------- staged levels (shared memory)
@@ -280,18 +363,19 @@ __device__ __forceinline__ void sv_restrict(const SV& S, int rx, int ry, float2*
 
 __device__ __forceinline__ float2 cv_get(const CoarseView& V, int I, int J) {
   if (V.full) return V.loc[J * V.nx + I];
-  const int lJ = J - V.yc0;
-  if (lJ < 0) return V.dn[(V.hc - 1) * V.nx + I];
-  if (lJ >= V.hc) return V.up[I];
-  return V.loc[lJ * V.nx + I];
+  const int lJ = J - V.yc0, slot = ((I + J) & 1) * V.planec + (I >> 1);
+  if (lJ < 0) return V.dn[slot + (V.hc - 1) * V.hxc];
+  if (lJ >= V.hc) return V.up[slot];
+  return V.loc[slot + lJ * V.hxc];
 }
 
 // u += bilinear interpolation of the coarse correction (weights 3/4 and 1/4 per axis) on rows
 // [y0, y0 + h), one thread per 2x2 block of fine cells: the block's four cells interpolate from the
 // same 3x3 coarse neighbourhood, read once.  Across a domain face the coarse neighbour is the cell
 // itself, negated for a Dirichlet face (odd reflection) and kept for a Neumann face (even).
+// rb: the fine level's arrays are in red-black strip order (strip levels), else natural (rank 0's levels)
 __device__ __forceinline__ void strip_prolong(float2* u, int nx, FastDiv dhx, int h, int y0, const CoarseView& V,
-                                              int dmask) {
+                                              int dmask, bool rb) {
   const int ncx = nx >> 1, n = (h >> 1) * ncx;
   const float sxl = (dmask & 1) ? -1.f : 1.f, sxh = (dmask & 2) ? -1.f : 1.f;
   const float syl = (dmask & 4) ? -1.f : 1.f, syh = (dmask & 8) ? -1.f : 1.f;
@@ -323,7 +407,7 @@ __device__ __forceinline__ void strip_prolong(float2* u, int nx, FastDiv dhx, in
         const float2 e = make_float2(
             0.5625f * c[1][1].x + 0.1875f * (c[1][nx_].x + c[ny_][1].x) + 0.0625f * c[ny_][nx_].x,
             0.5625f * c[1][1].y + 0.1875f * (c[1][nx_].y + c[ny_][1].y) + 0.0625f * c[ny_][nx_].y);
-        float2& v = u[(2 * lJ + bb) * nx + 2 * I + aa];
+        float2& v = rb ? u[((aa + bb) & 1) * (h * ncx) + (2 * lJ + bb) * ncx + I] : u[(2 * lJ + bb) * nx + 2 * I + aa];
         v.x += e.x;
         v.y += e.y;
       }
@@ -393,21 +477,34 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
   const int R = a.rounds, R1 = R + 1;
   const double itol2 = bt.itol2[b];
 
-  // views of every level: strips [0, ld) (rows of this rank), whole coarse levels [ld, nlev) (rank 0)
+  // views of the levels: strips [1, ld) in red-black order (rows of this rank), whole coarse levels
+  // [ld, nlev) in natural order (rank 0)
+  auto rbview = [&](int l) {
+    const Level& L = sL[l];
+    const LevOff& o = a.off[l];
+    RBV S;
+    S.nx = L.nx; S.ny = L.ny; S.h = L.ny / kCS; S.y0 = rank * S.h; S.hx = L.nx >> 1; S.plane = S.h * S.hx;
+    S.u = reinterpret_cast<float2*>(smb + o.u);
+    S.f = reinterpret_cast<float2*>(smb + o.f);
+    S.te = reinterpret_cast<float*>(smb + o.te);
+    S.ts = reinterpret_cast<float*>(smb + o.tn);
+    S.di = reinterpret_cast<float2*>(smb + o.di);
+    S.u_dn = rank > 0 ? cl.map_shared_rank(S.u, rank - 1) : nullptr;
+    S.u_up = rank + 1 < kCS ? cl.map_shared_rank(S.u, rank + 1) : nullptr;
+    return S;
+  };
   auto sview = [&](int l) {
     const Level& L = sL[l];
     const LevOff& o = a.off[l];
     SV S;
-    S.nx = L.nx; S.ny = L.ny;
-    if (l < a.ld) { S.h = L.ny / kCS; S.y0 = rank * S.h; }
-    else { S.h = L.ny; S.y0 = 0; }
+    S.nx = L.nx; S.ny = L.ny; S.h = L.ny; S.y0 = 0;
     S.u = reinterpret_cast<float2*>(smb + o.u);
     S.f = reinterpret_cast<float2*>(smb + o.f);
     S.te = reinterpret_cast<float*>(smb + o.te);
     S.tn = reinterpret_cast<float*>(smb + o.tn);
     S.di = reinterpret_cast<float2*>(smb + o.di);
-    S.u_dn = (l < a.ld && rank > 0) ? cl.map_shared_rank(S.u, rank - 1) : nullptr;
-    S.u_up = (l < a.ld && rank + 1 < kCS) ? cl.map_shared_rank(S.u, rank + 1) : nullptr;
+    S.u_dn = nullptr;
+    S.u_up = nullptr;
     return S;
   };
   auto cview = [&](int l) {   // view of level l + 1 from level l
@@ -416,11 +513,11 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
     V.nx = Lc.nx; V.ny = Lc.ny;
     float2* uc = reinterpret_cast<float2*>(smb + a.off[l + 1].u);
     if (l + 1 == a.ld) {
-      V.full = 1; V.hc = Lc.ny; V.yc0 = 0;
+      V.full = 1; V.hc = Lc.ny; V.yc0 = 0; V.hxc = 0; V.planec = 0;
       V.loc = cl.map_shared_rank(uc, 0);
       V.dn = nullptr; V.up = nullptr;
     } else {
-      V.full = 0; V.hc = Lc.ny / kCS; V.yc0 = rank * V.hc;
+      V.full = 0; V.hc = Lc.ny / kCS; V.yc0 = rank * V.hc; V.hxc = Lc.nx >> 1; V.planec = V.hc * V.hxc;
       V.loc = uc;
       V.dn = rank > 0 ? cl.map_shared_rank(uc, rank - 1) : nullptr;
       V.up = rank + 1 < kCS ? cl.map_shared_rank(uc, rank + 1) : nullptr;
@@ -428,28 +525,45 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
     return V;
   };
 
-  // stage the coefficients of the strip levels >= 1 (own rows) and, in rank 0, of the coarse levels;
-  // clear every coarse iterate (each V-cycle clears them again after use)
-  for (int l = 1; l < a.nlev; ++l) {
-    if (l >= a.ld && rank != 0) break;
+  // stage the coefficients of the strip levels >= 1 (own rows, red-black order) and, in rank 0, of the
+  // coarse levels (natural order); clear every coarse iterate (each V-cycle clears them again after use)
+  for (int l = 1; l < a.ld; ++l) {
     const Level& L = sL[l];
-    const SV S = sview(l);
-    const int n = S.h * S.nx;
-    for (int q = tid; q < n; q += kIT) {
-      const int c = S.y0 * S.nx + q;
-      S.te[q] = L.Te[c];
-      S.tn[S.nx + q] = L.Tn[c];
+    const RBV S = rbview(l);
+    const int tplane = (S.h + 1) * S.hx;
+    for (int q = tid; q < S.h * S.nx; q += kIT) {
+      const int ly = q / S.nx, x = q - ly * S.nx, c = (S.y0 + ly) * S.nx + x;
+      const int rbi = ((x + ly) & 1) * S.plane + ly * S.hx + (x >> 1);
+      S.te[rbi] = L.Te[c];
       const float mm = L.m[c];
-      S.di[q] = cinv(make_float2(L.D[c] + tau.x * mm, tau.y * mm));
-      S.u[q] = make_float2(0.f, 0.f);
+      S.di[rbi] = cinv(make_float2(L.D[c] + tau.x * mm, tau.y * mm));
+      S.u[rbi] = make_float2(0.f, 0.f);
     }
-    for (int x = tid; x < S.nx; x += kIT) S.tn[x] = S.y0 > 0 ? L.Tn[(S.y0 - 1) * S.nx + x] : 0.f;
+    for (int q = tid; q < (S.h + 1) * S.nx; q += kIT) {   // south faces of local rows 0 .. h
+      const int r = q / S.nx, x = q - r * S.nx, y = S.y0 + r;
+      S.ts[((x + r) & 1) * tplane + r * S.hx + (x >> 1)] = (y >= 1 && y - 1 < S.ny) ? L.Tn[(y - 1) * S.nx + x] : 0.f;
+    }
   }
+  if (rank == 0)
+    for (int l = a.ld; l < a.nlev; ++l) {
+      const Level& L = sL[l];
+      const SV S = sview(l);
+      const int n = S.h * S.nx;
+      for (int q = tid; q < n; q += kIT) {
+        S.te[q] = L.Te[q];
+        S.tn[S.nx + q] = L.Tn[q];
+        const float mm = L.m[q];
+        S.di[q] = cinv(make_float2(L.D[q] + tau.x * mm, tau.y * mm));
+        S.u[q] = make_float2(0.f, 0.f);
+      }
+      for (int x = tid; x < S.nx; x += kIT) S.tn[x] = 0.f;
+    }
   L0V S0;
   float4* q0 = a.q4 + (size_t)b * bt.N;
   {
     const Level& L = sL[0];
     S0.nx = L.nx; S0.ny = L.ny; S0.h = L.ny / kCS; S0.y0 = rank * S0.h;
+    S0.hx = L.nx >> 1; S0.plane = S0.h * S0.hx;
     S0.P = a.p4;
     S0.Q = q0;
     S0.u = reinterpret_cast<float2*>(smb + a.off[0].u);
@@ -531,15 +645,17 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
             l0_half_sweep(S0, a.dhx[0], h & 1);
             cl.sync();
           }
-          const float rr = l0_restrict(S0, fc, ncx, a.dnx[1], last ? 0 : S0.y0 / 2, a.npre > 0);
+          const int fhx = last ? 0 : sL[1].nx >> 1, fplane = last ? 0 : (sL[1].ny / kCS) * fhx;
+          const float rr = l0_restrict(S0, fc, ncx, a.dnx[1], S0.y0 / 2, fhx, fplane, a.npre > 0);
           block_sum(rr, red, &vpart[cy & 1]);
         } else {
-          const SV S = sview(l);
+          const RBV S = rbview(l);
           for (int h = 0; h < 2 * a.npre; ++h) {
-            sv_half_sweep_strip(S, a.dhx[l], h & 1);
+            rbv_half_sweep(S, a.dhx[l], h & 1);
             cl.sync();
           }
-          sv_restrict(S, 2, 2, fc, nullptr, ncx, a.dnx[l + 1], last ? 0 : S.y0 / 2, a.npre > 0);
+          const int fhx = last ? 0 : sL[l + 1].nx >> 1, fplane = last ? 0 : (sL[l + 1].ny / kCS) * fhx;
+          rbv_restrict(S, fc, ncx, a.dnx[l + 1], S.y0 / 2, fhx, fplane, a.npre > 0);
         }
         __syncthreads();   // the next level's sweeps read right-hand sides written by other threads
       }
@@ -609,9 +725,9 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
           if (q22) {
             CoarseView V;
             V.nx = sL[l + 1].nx; V.ny = sL[l + 1].ny;
-            V.full = 1; V.hc = V.ny; V.yc0 = 0;
+            V.full = 1; V.hc = V.ny; V.yc0 = 0; V.hxc = 0; V.planec = 0;
             V.loc = uc; V.dn = nullptr; V.up = nullptr;
-            strip_prolong(S.u, S.nx, a.dhx[l], S.h, 0, V, a.dmask);
+            strip_prolong(S.u, S.nx, a.dhx[l], S.h, 0, V, a.dmask, false);
           } else {
             for (int c = tid; c < sL[l].N; c += kIT) prolong_cell(sL[l], sL[l + 1], S.u, uc, c, a.dmask);
           }
@@ -626,20 +742,23 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
       // ---- up: prolongation, correction, post-smoothing on the strip levels
       for (int l = a.ld - 1; l >= 0; --l) {
         const CoarseView V = cview(l);
-        if (l == 0) strip_prolong(S0.u, S0.nx, a.dhx[0], S0.h, S0.y0, V, a.dmask);
+        if (l == 0) strip_prolong(S0.u, S0.nx, a.dhx[0], S0.h, S0.y0, V, a.dmask, true);
         else {
-          const SV S = sview(l);
-          strip_prolong(S.u, S.nx, a.dhx[l], S.h, S.y0, V, a.dmask);
+          const RBV S = rbview(l);
+          strip_prolong(S.u, S.nx, a.dhx[l], S.h, S.y0, V, a.dmask, true);
         }
         cl.sync();
         // every rank has read the coarse iterate: clear it for the next cycle
-        if (l + 1 < a.ld || rank == 0) {
+        if (l + 1 < a.ld) {
+          const RBV C = rbview(l + 1);
+          for (int q = tid; q < C.h * C.nx; q += kIT) C.u[q] = make_float2(0.f, 0.f);
+        } else if (rank == 0) {
           const SV C = sview(l + 1);
           for (int q = tid; q < C.h * C.nx; q += kIT) C.u[q] = make_float2(0.f, 0.f);
         }
         for (int h = 0; h < 2 * a.npost; ++h) {
           if (l == 0) l0_half_sweep(S0, a.dhx[0], (h + 1) & 1);
-          else sv_half_sweep_strip(sview(l), a.dhx[l], (h + 1) & 1);
+          else rbv_half_sweep(rbview(l), a.dhx[l], (h + 1) & 1);
           cl.sync();
         }
       }
@@ -648,7 +767,8 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
     // u_j += d (df32) on this CTA's rows; the next residual reads the neighbours' rows
     for (int q = tid; q < n0; q += kIT) {
       const size_t ui = ub + c0 + q;
-      const float2 d = S0.u[q];
+      const int ly = fdiv(q, a.dnx[0]), x = q - ly * S0.nx;
+      const float2 d = S0.u[((x + ly) & 1) * S0.plane + ly * S0.hx + (x >> 1)];
       if (r == 0) {
         bt.U_hi[ui] = d;
         bt.U_lo[ui] = make_float2(0.f, 0.f);
