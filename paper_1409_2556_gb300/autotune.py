@@ -24,9 +24,9 @@ _CACHE: Dict[str, dict] = {}
 DEFAULT_GRID = {
     "mg_cluster": [1, 0],
     "mg_tile": [1, 2],
-    "sweeps": [(2, 2), (3, 3)],
+    "sweeps": [(1, 2), (2, 2), (3, 3)],
     "inner": [(4, 6), (5, 4), (8, 6)],
-    "inner_relax": [1e-6, 1e-4],
+    "inner_relax": [1e-4, 1e-3],
     "mg_tma": [1],
 }
 
