@@ -452,7 +452,16 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
   if (!any_dirichlet) return fail(ctx, LT_ERR_INVALID_ARG, "at least one Dirichlet face is required (K must be nonsingular)");
   CK(cudaSetDevice(ctx->device));
   CK(cudaStreamSynchronize(ctx->stream));
-  free_ws(ctx);
+  // A new aquifer on a grid of the same dimensions keeps the Krylov workspace (its sizes depend only
+  // on the dimensions, the level structure and the plan): only the coefficients are replaced.
+  const bool keep_ws = ctx->have_grid && ctx->ws.nb > 0 && nx == ctx->nx && ny == ctx->ny && nz == ctx->nz;
+  float2* keep_u[lt::kMaxLevels] = {};
+  float2* keep_f[lt::kMaxLevels] = {};
+  const int keep_nlev = ctx->mg.nlev;
+  if (keep_ws)
+    for (int l = 0; l < keep_nlev; ++l) { keep_u[l] = ctx->mg.h_levels[l].u; keep_f[l] = ctx->mg.h_levels[l].f; }
+  else
+    free_ws(ctx);
   free_list(ctx->grid_allocs);
   if (ctx->mg.d_levels) { cudaFree(ctx->mg.d_levels); ctx->mg.d_levels = nullptr; }
   ctx->have_grid = false;
@@ -546,6 +555,13 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
     if ((rc = upload_f32(ctx, ctx->grid_allocs, &L.m, h.m))) return rc;
     L.u = L.f = nullptr;   // per-batch vectors, set when a workspace is sized
   }
+  if (keep_ws) {
+    if (nlev == keep_nlev) {
+      for (int l = 0; l < nlev; ++l) { mg.h_levels[l].u = keep_u[l]; mg.h_levels[l].f = keep_f[l]; }
+    } else {
+      free_ws(ctx);   // (cannot happen for equal dimensions; kept as a guard)
+    }
+  }
   lt::FineExact& fe = ctx->fe;
   fe.nx = nx; fe.ny = ny; fe.nz = nz; fe.N = (int)N;
   int rc;
@@ -569,6 +585,8 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
       return rc;
   }
   CK(cudaMalloc(&mg.d_levels, sizeof(lt::Level) * lt::kMaxLevels));
+  if (ctx->ws.nb > 0)   // kept workspace: the device level table must point at the new coefficients
+    CK(cudaMemcpy(mg.d_levels, mg.h_levels, sizeof(lt::Level) * nlev, cudaMemcpyHostToDevice));
   if (lt::inner_cluster_plan(mg, ctx->inner)) {
     // the four faces of every finest-level cell in one 16-byte record (zero across domain edges),
     // in red-black order: colour (x + y) & 1 first, then row by row, x / 2 within the row
@@ -1549,8 +1567,9 @@ static size_t noalloc_need(const lt_ctx* ctx, const Plan& P) {
   add(nb, 8); add(nb, 4); add(nb, 4); add(nb, 8); add(nb, 8);
   add(nb + 1, 4); add(nsh, 16); add(nsh * M * M, 16); add(nsh * M, 8);
   add(nsh * M, 16); add(nsh * (M + 1), 16); add(nsh, 4); add(nsh, 8);
-  add(nsh * M, 16); add(16, 8); add(nb, 8); add(nb, 8); add(1, 4);
+  add(nsh * M, 16); add(lt::kWorkSlots, 8); add(nb, 8); add(nb, 8); add(1, 4);
   if (ctx->mg.coarse_direct) add(2 * G * (size_t)ctx->hl.back().N * ctx->hl.back().N, 8);
+  if (ctx->inner.ok) add(nb * N, 16);
   for (int l = 0; l < ctx->mg.nlev; ++l) { add(nb * ctx->mg.h_levels[l].N, 8); add(nb * ctx->mg.h_levels[l].N, 8); }
   add(nsh, 4);
   if (o.true_residual) { add(nsh * N, 8); add(nsh * N, 8); add(nsh, 8); }

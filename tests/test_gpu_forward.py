@@ -250,3 +250,19 @@ def test_cluster_solve_on_grids_set_up_in_any_order(Engine):
     assert _rel(h_small, direct.forward(small)) < TOL_H
     e_big.close()
     e_small.close()
+
+
+def test_new_aquifer_on_same_grid_reuses_workspace_correctly(Engine):
+    """setup_grid with the same dimensions keeps the Krylov workspace; the second aquifer's heads must
+    be its own (oracle), not the first one's."""
+    p1 = W.random_problem(64, 32, 1, variance=1.0, seed=41, ns=2, nr=2, nt=2, Nz=16, tol=1e-11)
+    p2 = W.random_problem(64, 32, 1, variance=2.0, seed=42, ns=2, nr=2, nt=2, Nz=16, tol=1e-11)
+    for cl in (1, 0):
+        eng = Engine(0)
+        eng.load_problem(p1, mg_cluster=cl)
+        h1 = eng.forward(p1.times)
+        eng.load_problem(p2, mg_cluster=cl)
+        h2 = eng.forward(p2.times)
+        assert _rel(h1, direct.forward(p1)) < TOL_H
+        assert _rel(h2, direct.forward(p2)) < TOL_H
+        eng.close()
