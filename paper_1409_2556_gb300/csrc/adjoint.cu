@@ -12,8 +12,10 @@
 //   A_f[s] = W_f omega_{s,k} (x_c - x_o)   (f = 6 faces),  A_b[s] = Bd_c omega x_c,  A_z[s] = m_c omega z_k x_c
 //   B_f[r] = psi_c - psi_o,                                B_0[r] = psi_c
 // in shared memory (df32), omega_{s,k} = w_k Q_s / z_k, and every thread
-// accumulates Re sum A B for its (cell, s, r) pairs in df32 (the quadrature
-// sum cancels strongly, so float32 products would not reach 1e-8).
+// accumulates Re sum A B in df32 (the quadrature sum cancels strongly, so
+// float32 products would not reach 1e-8) for a block of kSB sources x kRB
+// receivers of one cell: per face it loads kSB + kRB staged values and forms
+// kSB kRB products (the per-cell sum is a small complex matrix product).
 // mode 0 writes J; mode 1 accumulates grad[p][c] += sum g[s][r][t] J[s][r][t][p][c].
 #include "df32.cuh"
 #include "lt_internal.h"
@@ -22,7 +24,9 @@
 namespace lt {
 
 constexpr int kTC = 8;       // cells per CTA
-constexpr int kPairs = 8;    // (s, r) pairs per thread per pass
+constexpr int kSB = 2;       // sources per thread block of pairs
+constexpr int kRB = 4;       // receivers per thread block of pairs
+constexpr int kSensThreads = 768;
 
 struct SensArgs {
   int ns, nr, nt, Nk;
@@ -54,7 +58,7 @@ __device__ __forceinline__ df re_mul_acc(df acc, const cdf& a, const cdf& b) {
   return df_sub(acc, df_mul(a.im, b.im));
 }
 
-__global__ void __launch_bounds__(256) k_sens(SensArgs a) {
+__global__ void __launch_bounds__(kSensThreads) k_sens(SensArgs a) {
   extern __shared__ cdf smem[];
   const int t = blockIdx.y;
   const int64_t c0 = (int64_t)blockIdx.x * kTC;
@@ -89,11 +93,17 @@ __global__ void __launch_bounds__(256) k_sens(SensArgs a) {
     }
   }
   __syncthreads();
-  const int npairs = kTC * ns * nr;
-  for (int p0 = 0; p0 < npairs; p0 += blockDim.x * kPairs) {
-    df acc0[kPairs], acc1[kPairs];
+  const int nsb = (ns + kSB - 1) / kSB, nrb = (nr + kRB - 1) / kRB;
+  const int nblk = kTC * nsb * nrb;
+  for (int p0 = 0; p0 < nblk; p0 += blockDim.x) {
+    const int pb = p0 + threadIdx.x;
+    const bool act = pb < nblk;
+    const int rb = pb % nrb, sb = (pb / nrb) % nsb, cl = pb / (nrb * nsb);
+    df acc0[kSB][kRB], acc1[kSB][kRB];
 #pragma unroll
-    for (int q = 0; q < kPairs; ++q) { acc0[q] = {0.f, 0.f}; acc1[q] = {0.f, 0.f}; }
+    for (int i = 0; i < kSB; ++i)
+#pragma unroll
+      for (int q = 0; q < kRB; ++q) { acc0[i][q] = {0.f, 0.f}; acc1[i][q] = {0.f, 0.f}; }
     for (int kk = 0; kk < a.Nk; ++kk) {
       __syncthreads();
       // stage A
@@ -136,39 +146,59 @@ __global__ void __launch_bounds__(256) k_sens(SensArgs a) {
         B[idx] = v;
       }
       __syncthreads();
-#pragma unroll
-      for (int q = 0; q < kPairs; ++q) {
-        int p = p0 + q * blockDim.x + threadIdx.x;
-        if (p >= npairs) break;
-        int r = p % nr, s = (p / nr) % ns, cl = p / (nr * ns);
+      if (act) {
         const cdf* Ap = A + (size_t)cl * 8 * ns;
         const cdf* Bp = B + (size_t)cl * 7 * nr;
-        df a0 = acc0[q];
+        for (int f = 0; f < 7; ++f) {
+          cdf av[kSB], bv[kRB];
 #pragma unroll
-        for (int f = 0; f < 6; ++f) a0 = re_mul_acc(a0, Ap[f * ns + s], Bp[f * nr + r]);
-        a0 = re_mul_acc(a0, Ap[6 * ns + s], Bp[6 * nr + r]);
-        acc0[q] = a0;
-        acc1[q] = re_mul_acc(acc1[q], Ap[7 * ns + s], Bp[6 * nr + r]);
+          for (int i = 0; i < kSB; ++i) {
+            const int s = sb * kSB + i;
+            av[i] = s < ns ? Ap[f * ns + s] : cdf_zero();
+          }
+#pragma unroll
+          for (int q = 0; q < kRB; ++q) {
+            const int r = rb * kRB + q;
+            bv[q] = r < nr ? Bp[f * nr + r] : cdf_zero();
+          }
+#pragma unroll
+          for (int i = 0; i < kSB; ++i)
+#pragma unroll
+            for (int q = 0; q < kRB; ++q) acc0[i][q] = re_mul_acc(acc0[i][q], av[i], bv[q]);
+          if (f == 6) {   // storage term: A_z with the cell's own adjoint value (B_0 = bv here)
+#pragma unroll
+            for (int i = 0; i < kSB; ++i) {
+              const int s = sb * kSB + i;
+              const cdf az = s < ns ? Ap[7 * ns + s] : cdf_zero();
+#pragma unroll
+              for (int q = 0; q < kRB; ++q) acc1[i][q] = re_mul_acc(acc1[i][q], az, bv[q]);
+            }
+          }
+        }
       }
     }
     // write / reduce
+    if (act) {
+      const int64_t c = c0 + cl;
+      if (c < a.N) {
 #pragma unroll
-    for (int q = 0; q < kPairs; ++q) {
-      int p = p0 + q * blockDim.x + threadIdx.x;
-      if (p >= npairs) break;
-      int r = p % nr, s = (p / nr) % ns, cl = p / (nr * ns);
-      int64_t c = c0 + cl;
-      if (c >= a.N) continue;
-      double j0 = -2.0 * df_to_double(acc0[q]);
-      double j1 = -2.0 * df_to_double(acc1[q]);
-      if (a.mode == 0) {
-        size_t row = ((size_t)s * nr + r) * a.nt + t;
-        a.J[(row * 2 + 0) * a.N + c] = j0;
-        a.J[(row * 2 + 1) * a.N + c] = j1;
-      } else {
-        double gv = a.g[((size_t)s * nr + r) * a.nt + t];
-        atomicAdd(&a.grad[c], gv * j0);
-        atomicAdd(&a.grad[a.N + c], gv * j1);
+        for (int i = 0; i < kSB; ++i)
+#pragma unroll
+          for (int q = 0; q < kRB; ++q) {
+            const int s = sb * kSB + i, r = rb * kRB + q;
+            if (s >= ns || r >= nr) continue;
+            double j0 = -2.0 * df_to_double(acc0[i][q]);
+            double j1 = -2.0 * df_to_double(acc1[i][q]);
+            if (a.mode == 0) {
+              size_t row = ((size_t)s * nr + r) * a.nt + t;
+              a.J[(row * 2 + 0) * a.N + c] = j0;
+              a.J[(row * 2 + 1) * a.N + c] = j1;
+            } else {
+              double gv = a.g[((size_t)s * nr + r) * a.nt + t];
+              atomicAdd(&a.grad[c], gv * j0);
+              atomicAdd(&a.grad[a.N + c], gv * j1);
+            }
+          }
       }
     }
   }
@@ -188,7 +218,9 @@ int launch_sens2(const SensLaunch& L, cudaStream_t st) {
   if (smem > 200 * 1024) return -1;
   cudaFuncSetAttribute(k_sens, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 g((unsigned)((L.N + kTC - 1) / kTC), L.nt);
-  k_sens<<<g, 256, smem, st>>>(a);
+  const int nblk = kTC * ((L.ns + kSB - 1) / kSB) * ((L.nr + kRB - 1) / kRB);
+  const int threads = nblk >= kSensThreads ? kSensThreads : ((nblk + 31) / 32) * 32;
+  k_sens<<<g, threads, smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
