@@ -18,7 +18,11 @@
 //   * a cluster barrier follows every red or black half-sweep, so every
 //     half-sweep sees the other colour exactly as the global sweep does;
 //   * the squared residual norm of each round is summed over the cluster in
-//     rank order, so every CTA takes the same branch.
+//     rank order, so every CTA takes the same branch;
+//   * the V-cycles of a round stop once the fine residual the restriction
+//     computes anyway is below the round's goal (at most `cycles`);
+//   * per-cell records and strip arrays are kept in red-black order, so a
+//     half-sweep reads contiguous runs (global loads and shared-memory banks).
 // One launch replaces the (rounds x (cycles x V-cycle launches + 2)) launches
 // of the batched path.
 #include <cooperative_groups.h>
@@ -34,7 +38,7 @@ namespace cg = cooperative_groups;
 namespace lt {
 
 constexpr int kCS = 8;                        // CTAs per cluster (portable cluster size)
-constexpr int kIT = 512;                     // threads per CTA
+constexpr int kIT = 512;                      // threads per CTA
 constexpr size_t kInnerSmemMax = 220 * 1024;  // dynamic shared memory per CTA
 constexpr int kL0Batch = 2;                   // finest-level cells per thread whose loads are issued together
 
@@ -108,7 +112,8 @@ struct RBV {
   const float2* u_up;
 };
 
-// A staged level's rows [y0, y0 + h) (a strip of a distributed level, or a whole coarse level with y0 = 0).
+// A whole coarse level held by rank 0, staged in shared memory in natural order (y0 = 0, h = ny; the
+// neighbour pointers stay null, as no row lies outside the level).
 struct SV {
   int nx, ny, h, y0;
   float2* u;                     // [h][nx]
@@ -299,9 +304,9 @@ __device__ __forceinline__ void sv_gather(const SV& S, int x, int y, int ly, int
   nb[3] = y > 0 ? (ly > 0 ? S.u[li - S.nx] : S.u_dn[(S.h - 1) * S.nx + x]) : z;
 }
 
-// red-black half-sweep of a strip level with an even number of columns: thread q takes the q-th
+// red-black half-sweep of a natural-order level with an even number of columns: thread q takes the q-th
 // cell of the colour
-__device__ __forceinline__ void sv_half_sweep_strip(const SV& S, FastDiv dhx, int color) {
+__device__ __forceinline__ void sv_half_sweep_even(const SV& S, FastDiv dhx, int color) {
   const int hx = S.nx >> 1, n = S.h * hx;
   for (int q = threadIdx.x; q < n; q += kIT) {
     const int ly = fdiv(q, dhx), y = S.y0 + ly, x = 2 * (q - ly * hx) + ((color + y) & 1);
@@ -333,9 +338,9 @@ __device__ __forceinline__ void sv_half_sweep_full(const SV& S, FastDiv dnx, int
   }
 }
 
-// residual of the staged level summed over rx x ry children into the coarse right-hand side;
-// zero_uc: also clear the coarse iterate (coarse levels owned by this CTA)
-// red_only (2x2 coarsening, even first row, sweep ended black): only the red children, see l0_restrict
+// residual of a coarse level (rank 0, natural order) summed over rx x ry children into the next level's
+// right-hand side fc (coarse row J at row J - row0); uc non-null: also clear the next level's iterate;
+// red_only (2x2 coarsening, sweep ended black): only the red children, see l0_restrict
 __device__ __forceinline__ void sv_restrict(const SV& S, int rx, int ry, float2* fc, float2* uc, int ncx,
                                             FastDiv dncx, int row0, bool red_only) {
   const int nch = S.h / ry, n = nch * ncx;
@@ -673,7 +678,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
           const SV S = sview(l);
           const bool q22 = sL[l].rx == 2 && sL[l].ry == 2;
           for (int h = 0; h < 2 * a.npre; ++h) {
-            if (q22) sv_half_sweep_strip(S, a.dhx[l], h & 1);
+            if (q22) sv_half_sweep_even(S, a.dhx[l], h & 1);
             else sv_half_sweep_full(S, a.dnx[l], h & 1);
             __syncthreads();
           }
@@ -733,7 +738,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
           }
           __syncthreads();
           for (int h = 0; h < 2 * a.npost; ++h) {
-            if (q22) sv_half_sweep_strip(S, a.dhx[l], (h + 1) & 1);
+            if (q22) sv_half_sweep_even(S, a.dhx[l], (h + 1) & 1);
             else sv_half_sweep_full(S, a.dnx[l], (h + 1) & 1);
             __syncthreads();
           }
