@@ -23,6 +23,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -85,7 +86,8 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples go to the LT_CLOCKS_DIR directory if set (kept for inspection), else to a temp file
+        self.path = os.path.join(os.environ.get("LT_CLOCKS_DIR", tempfile.gettempdir()), f"lt_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
