@@ -25,8 +25,8 @@ namespace lt {
 
 constexpr int kTC = 8;       // cells per CTA
 constexpr int kSB = 2;       // sources per thread block of pairs
-constexpr int kRB = 4;       // receivers per thread block of pairs
-constexpr int kSensThreads = 768;
+constexpr int kRB = 6;       // receivers per thread block of pairs
+constexpr int kSensThreads = 512;
 
 struct SensArgs {
   int ns, nr, nt, Nk;
