@@ -40,7 +40,7 @@ namespace lt {
 constexpr int kCS = 8;                        // CTAs per cluster (portable cluster size)
 constexpr int kIT = 512;                      // threads per CTA
 constexpr size_t kInnerSmemMax = 220 * 1024;  // dynamic shared memory per CTA
-constexpr int kL0Batch = 2;                   // finest-level cells per thread whose loads are issued together
+constexpr int kL0Batch = 1;                   // finest-level cells per thread whose loads are issued together
 
 // Division by a runtime divisor d >= 1 of a numerator below 2^31 as a multiply-high and a shift
 // (Granlund and Montgomery, "Division by invariant integers using multiplication", 1994):
