@@ -47,6 +47,10 @@ class Problem:
     Nz: int                      # contour nodes (full contour; Nz/2 shifts solved)
     tol: float
     groups: int = 1              # preconditioner-shift groups over the times
+    phi0: Optional[np.ndarray] = None   # [ncell] float64 initial head (None: phi(0) = 0)
+    # per source: (amplitudes a_j [m^3/s], decay rates lambda_j >= 0 [1/s]) of the rate
+    # q_s(t) = sum_j a_j exp(-lambda_j t); None: the constant rate Q_s switched on at t = 0
+    rate_terms: Optional[List[Tuple[np.ndarray, np.ndarray]]] = None
     name: str = ""
     meta: dict = field(default_factory=dict)
 
@@ -209,3 +213,33 @@ def random_problem(nx: int, ny: int, nz: int = 1, variance: float = 1.0, seed: i
                    cells[:ns].astype(np.int64), rng.uniform(0.5, 1.5, ns) * Q_RATE,
                    cells[ns:].astype(np.int64), times, Nz, tol, groups=groups,
                    name=f"random-{nx}x{ny}x{nz}")
+
+
+def with_initial_state_and_rates(prob: Problem, seed: int = 0, phi0_amp: float = 0.05,
+                                 n_terms: int = 3, rates: bool = True, initial: bool = True) -> Problem:
+    """The same aquifer with a non-zero initial head and time-varying pumping rates.
+
+    phi0: a smooth seeded Gaussian field (correlation a quarter of the grid) scaled to an RMS of
+    `phi0_amp` m.  Rates: per source, its constant rate Q_s plus n_terms - 1 decaying terms
+    a_j exp(-lambda_j t) with |a_j| <= Q_s and 1/lambda_j log-uniform in [30, 3000] s (within the
+    output times), so that q_s(t) stays positive."""
+    import copy
+    rng = np.random.default_rng(seed + 104729)
+    out = copy.copy(prob)
+    if initial:
+        shape = (prob.nz, prob.ny, prob.nx)
+        corr = tuple(max(1.0, s / 4.0) for s in shape)
+        f = gaussian_field(shape, 1.0, corr, seed + 17).ravel()
+        out.phi0 = np.ascontiguousarray(phi0_amp * f / max(np.sqrt(np.mean(f * f)), 1e-300))
+    if rates:
+        terms = []
+        for s in range(len(prob.src_cells)):
+            a = [float(prob.Q[s])]
+            lam = [0.0]
+            for _ in range(n_terms - 1):
+                a.append(float(rng.uniform(-0.4, 0.8)) * float(prob.Q[s]))
+                lam.append(1.0 / float(np.exp(rng.uniform(np.log(30.0), np.log(3000.0)))))
+            terms.append((np.array(a), np.array(lam)))
+        out.rate_terms = terms
+    out.name = prob.name + ("-phi0" if initial else "") + ("-rates" if rates else "")
+    return out
