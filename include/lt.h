@@ -72,7 +72,39 @@ typedef struct {
                            cluster with the multigrid levels in distributed shared memory, on grids that allow it
                            (2D, rows divisible into 8 strips per level, levels fit in shared memory; default);
                            0: batched multigrid launches */
+  int    precision;     /* LT_PREC_FP64 (default) or LT_PREC_FP32 (reduced precision, tolerances down to 2e-6) */
+  int    krylov;        /* LT_KRYLOV_GMRES (default): minimal-residual coefficients per shift (FGMRES-Sh);
+                           LT_KRYLOV_FOM: Petrov-Galerkin coefficients H_j(z_k; T_j) y = beta e_1 (FFOM-Sh),
+                           both from Algorithm 1 of Sec. 3 */
+  int    stop_rule;     /* LT_STOP_SHIFT (default): each shift stops on its own relative residual <= tol;
+                           LT_STOP_QUADRATURE: all shifts of an output time stop together once the
+                           quadrature-weighted residual sum_k |w_k qhat(z_k)| rho_k <= tol sum_k |w_k qhat(z_k)|
+                           (the a-posteriori bound of Sec. 3.1, Proposition 1; rho_k = |eta_k| for FOM) */
+  int    tma_wait_polls;/* polls of the mbarrier before a TMA tile load counts as timed out (default 1 << 26);
+                           0 makes every TMA tile load time out at once, which exercises the
+                           LT_ERR_TIMEOUT path without a fault */
+  int    gram_schmidt;  /* orthogonalisation of s_j = M u_j against V_j (Algorithm 1's inner loop):
+                           2 = classical Gram-Schmidt twice, coefficients from float32 dots (default);
+                           1 = one classical pass whose coefficients come from df32 dots (V read twice
+                           instead of four times per column) */
 } lt_opts;
+
+/* arithmetic of the outer Krylov method (lt_opts.precision) */
+#define LT_PREC_FP64    0         /* basis, solutions and residuals carried in double-float32 pairs (about
+                                     48 significant bits; every relation checked to ~1e-13): results within
+                                     1e-8 of an FP64 solve */
+#define LT_PREC_FP32    1         /* single float32 planes for the basis, the preconditioner solutions and x_k
+                                     (half the Krylov memory and traffic); tol >= 2e-6, for results within
+                                     1e-5 of an FP64 solve.  Rounding a solution to float32 alone leaves a true
+                                     residual of about cond(K + z M) * 6e-8 (near 2e-7 for point sources, far
+                                     more for smooth right-hand sides such as M phi_0), so in this mode set
+                                     true_residual = 0 and judge convergence by the projected residual */
+/* coefficient rule of Algorithm 1 (lt_opts.krylov) */
+#define LT_KRYLOV_GMRES 0
+#define LT_KRYLOV_FOM   1
+/* stopping rule (lt_opts.stop_rule) */
+#define LT_STOP_SHIFT      0
+#define LT_STOP_QUADRATURE 1
 
 /* kernel classes reported in lt_stats.work[] and selectable by lt_opts.timing_class */
 #define LT_KC_RBGS       0   /* red-black Gauss-Seidel half-sweep on a fine multigrid level */
@@ -133,9 +165,33 @@ int lt_set_stream(lt_ctx* ctx, void* stream);
 int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, double dy, double dz,
                   const double* kappa, const double* Ss, const int* bc, const double* Sy);
 
-/* Point sources b_s = Q_s e_{cell_s}, constant rate switched on at t = 0, phi_0 = 0 (Sec. 2.1).
- * cells: HOST int64 [ns], each in [0, ncell); Q: HOST float64 [ns]. */
+/* Point sources b_s = Q_s e_{cell_s}, constant rate Q_s switched on at t = 0 (Sec. 2.1).
+ * cells: HOST int64 [ns], each in [0, ncell); Q: HOST float64 [ns].  Clears any rates set by
+ * lt_set_source_rates. */
 int lt_set_sources(lt_ctx* ctx, int ns, const int64_t* cells, const double* Q);
+
+/*
+ * Time-varying pumping rates (Sec. 2.1-2.2: sources separable in space and time, q(t) with a
+ * known Laplace transform; Sec. 2.2 names exponential sums, fitted by Prony's method, for a
+ * general q): source s pumps
+ *     q_s(t) = sum_{j < nterm[s]} a_j exp(-lambda_j t),   qhat_s(z) = sum_j a_j / (z + lambda_j),
+ * which replaces Q_s / z in every quadrature weight (forward and adjoint).
+ *   ns     : must equal the number of sources set by lt_set_sources
+ *   nterm  : HOST int [ns], each in [1, 64]; NULL restores the constant rates Q_s
+ *   a      : HOST float64 [sum nterm], amplitudes (m^3/s), source by source
+ *   lambda : HOST float64 [sum nterm], decay rates (1/s), each finite and >= 0 (0 = a constant term)
+ * Copied at the call.  LT_ERR_INVALID_ARG on a count mismatch or a bad value.
+ */
+int lt_set_source_rates(lt_ctx* ctx, int ns, const int* nterm, const double* a, const double* lambda);
+
+/*
+ * Initial head phi(0) = phi_0 (Sec. 2.2, F(z) = (K + z M)^{-1} (M phi_0 + qhat(z) b); Sec. 3, the
+ * two right-hand sides [b, M phi_0]).  The forward calls then add, for every source, the
+ * response to phi_0, solved as one more Krylov basis per time group with the right-hand side
+ * M phi_0.  phi0: HOST float64 [ncell], finite; NULL (or all zeros) restores phi_0 = 0.
+ * lt_setup_grid clears it.  The adjoint entry points need phi_0 = 0 (LT_ERR_STATE otherwise).
+ */
+int lt_set_initial_state(lt_ctx* ctx, const double* phi0);
 
 /* Point receivers (measurement cells, Sec. 5.2 functional I(t)).  cells: HOST int64 [nr]. */
 int lt_set_receivers(lt_ctx* ctx, int nr, const int64_t* cells);
@@ -146,8 +202,10 @@ int lt_set_options(lt_ctx* ctx, const lt_opts* opts);
 /*
  * Forward problem (Sec. 2.2 Eq. half and Sec. 3 Algorithm 1): for every
  * source s, receiver r and time t,
- *   h[s][r][t] = 2 Re sum_k w_k(t) (Q_s / z_k) x_{s,k}[cell_r],   (K + z_k M) x_{s,k} = e_{cell_s}
- * over the N_z/2 upper-half Talbot nodes of each time.
+ *   h[s][r][t] = 2 Re sum_k w_k(t) (qhat_s(z_k) x_{s,k}[cell_r] + beta0 x_{0,k}[cell_r]),
+ *   (K + z_k M) x_{s,k} = e_{cell_s},  (K + z_k M) x_{0,k} = M phi_0 / beta0,  beta0 = ||M phi_0||
+ * over the N_z/2 upper-half Talbot nodes of each time (qhat_s = Q_s / z without lt_set_source_rates;
+ * the x_0 term only with an initial state).
  *   times : HOST float64 [nt], each > 0
  *   h     : float64 [ns][nr][nt], HOST pointer if h_on_device == 0, else a DEVICE pointer
  *   stats : optional (may be NULL)
@@ -193,6 +251,22 @@ int lt_adjoint_jacobian(lt_ctx* ctx, int nt, const double* times, double* J, lt_
  */
 int lt_adjoint_vjp(lt_ctx* ctx, int nt, const double* times, const double* g, double* grad,
                    double* h, int on_device, lt_stats* stats);
+
+/*
+ * Adjoint Jacobians (or vector-Jacobian products) of n independent contexts solved together, the
+ * adjoint counterpart of lt_forward_batch: every context's source and receiver bases are built
+ * with their outer iterations interleaved on the contexts' own streams, then each context's
+ * sensitivities are assembled (Sec. 5.2, the formula of lt_adjoint_jacobian).  All pointers are
+ * DEVICE pointers.  For context i:
+ *   J[i] non-NULL (J itself non-NULL): the Jacobian float64 [ns][nr][nt][2][ncell] is written;
+ *   otherwise the VJP: g[i] float64 [ns][nr][nt] in, grad[i] float64 [2][ncell] out.
+ *   h: NULL or an array of n (entries may be NULL): the measurements float64 [ns][nr][nt].
+ *   stats: NULL or an array of n.
+ * Returns LT_ERR_NOT_CONVERGED if any context did not converge (all results written), another
+ * error code on the first failing context.
+ */
+int lt_adjoint_batch(int n, lt_ctx* const* ctxs, const int* nt, const double* const* times, double* const* J,
+                     const double* const* g, double* const* grad, double* const* h, lt_stats* stats);
 
 /*
  * lt_forward without device allocation.  The paper has no counterpart: this
@@ -253,6 +327,35 @@ void lt_unet_destroy(lt_unet* net);
  * r, e: DEVICE complex float32 [nimg][ncell][2].
  */
 int lt_precond_apply(lt_ctx* ctx, int nimg, const double* tau, const float* r, float* e, int cycles);
+
+/*
+ * Talbot nodes and weights of one output time (Sec. 2.2, Eq. half): the N_z/2 upper-half nodes
+ * z_k and weights w_k, phi(t) = 2 Re sum_k w_k F(z_k).  project = 1 replaces Re z_k by
+ * max(Re z_k, 0) (the rule lt_opts.tau_project applies to preconditioner shifts).
+ *   z, w : HOST float64 [Nz/2][2] (re, im); w may be NULL.  No context, no device work.
+ * LT_ERR_INVALID_ARG if t <= 0 or Nz is not even in [4, 128].
+ */
+int lt_contour_nodes(double t, int Nz, int project, double* z, double* w);
+
+/*
+ * Training pairs of the learned preconditioner on the context's grid: for residuals r_i and
+ * shifts tau_i, the multigrid solution e_i of (K + tau_i M) e_i = r_i (`cycles` V-cycles, as
+ * lt_precond_apply), then the network input x_i (the five channels listed above, the residual at
+ * unit RMS) and the target y_i = D e_i at unit RMS, all computed on the device.
+ *   tau : HOST float64 [nimg][2];  r : DEVICE complex float32 [nimg][ncell][2]
+ *   x   : DEVICE float32 [nimg][ncell][5];  y : DEVICE float32 [nimg][ncell][2]
+ */
+int lt_learned_pairs(lt_ctx* ctx, int nimg, const double* tau, const float* r, int cycles, float* x, float* y);
+
+/*
+ * The Krylov vectors v_j of the context's last forward or adjoint solve, with the preconditioner
+ * shift tau_j each was solved with (Algorithm 1: (K + tau_j M) u_j = v_j): these are the
+ * residuals the preconditioner sees, used as training inputs.  Bases in order, j = 0 .. (outer
+ * iterations of the basis) - 1, at most max_n vectors (the float32 hi plane of each).
+ *   r   : DEVICE complex float32 [max_n][ncell][2];  tau : HOST float64 [max_n][2]
+ *   n_out : number written.  LT_ERR_STATE if the context has not solved yet.
+ */
+int lt_krylov_vectors(lt_ctx* ctx, int max_n, float* r, double* tau, int* n_out);
 
 /*
  * Attach a trained network (NULL detaches).  With lt_opts.precond = 1 the

@@ -1,11 +1,16 @@
 """O4: Laplace-domain adjoint Jacobian of the measurements (Sec. 5.2).
 
-Measurement h_{s,r}(t) = e_r^T phi_s(t), phi_s(t) = 2 Re sum_k w_k (Q_s / z_k)
-xhat_{s,k}, xhat_{s,k} = A_k^{-1} e_{cell(s)}, A_k = K + z_k M.  Since w_k,
+Test infrastructure: only the tests, the smoke check and the benchmark's CPU
+baseline use this package.
+
+Measurement h_{s,r}(t) = e_r^T phi_s(t), phi_s(t) = 2 Re sum_k w_k qhat_s(z_k)
+xhat_{s,k}, xhat_{s,k} = A_k^{-1} e_{cell(s)}, A_k = K + z_k M, with
+qhat_s(z) = Q_s / z for a constant rate (oracle/source.py for exponential
+sums) and phi_0 = 0.  Since w_k,
 z_k do not depend on the parameters, and A_k is complex symmetric (so the
 adjoint field uses a transpose, not a conjugate transpose):
 
-  dh_{s,r}(t)/dp = -2 Re sum_k w_k (Q_s / z_k) psi_{r,k}^T (dK/dp + z_k dM/dp) xhat_{s,k},
+  dh_{s,r}(t)/dp = -2 Re sum_k w_k qhat_s(z_k) psi_{r,k}^T (dK/dp + z_k dM/dp) xhat_{s,k},
   psi_{r,k} = A_k^{-1} e_{cell(r)}
 
 (the discrete counterpart of the sensitivity formula of Sec. 5.2 with the
@@ -25,7 +30,7 @@ import copy
 
 import numpy as np
 
-from . import contour, direct, fv
+from . import contour, direct, fv, source
 
 
 def face_weights(prob):
@@ -68,6 +73,7 @@ def _bilinear_terms(prob, fw, psi, x):
 
 def jacobian(prob):
     """J[ns][nr][nt][2][N]: d h / d log kappa (index 0), d h / d log Ss (1)."""
+    assert not np.any(source.initial_state(prob)), "the adjoint here assumes phi_0 = 0"
     K, m = fv.assemble(prob)
     N = prob.ncell
     ns, nr, nt = len(prob.src_cells), len(prob.rec_cells), len(prob.times)
@@ -81,7 +87,7 @@ def jacobian(prob):
             Xs = direct.shifted_solve(K, m, zk, E_s)      # [N, ns]
             Ps = direct.shifted_solve(K, m, zk, E_r)      # [N, nr]
             for s in range(ns):
-                coef = wk * prob.Q[s] / zk
+                coef = wk * source.q_hat(prob, s, zk)
                 for r in range(nr):
                     gk = _bilinear_terms(prob, fw, Ps[:, r], Xs[:, s])
                     gs = zk * m * Ps[:, r] * Xs[:, s]

@@ -23,6 +23,12 @@ LT_BC_DIRICHLET = 0
 LT_BC_NEUMANN = 1
 LT_TAU_SINGLE = 0
 LT_TAU_FLEXIBLE = 1
+LT_PREC_FP64 = 0
+LT_PREC_FP32 = 1
+LT_KRYLOV_GMRES = 0
+LT_KRYLOV_FOM = 1
+LT_STOP_SHIFT = 0
+LT_STOP_QUADRATURE = 1
 
 # kernel classes (lt_stats.work, lt_opts.timing_class)
 KC_NAMES = ["rbgs", "restrict", "prolong", "coarse", "exact_res", "update_u", "dots", "ortho", "normalize",
@@ -37,7 +43,8 @@ class LtOpts(C.Structure):
                 ("inner_cycles", C.c_int), ("inner_rounds", C.c_int), ("inner_tol", C.c_double),
                 ("true_residual", C.c_int), ("check_every", C.c_int), ("timing_class", C.c_int),
                 ("inner_relax", C.c_double), ("graphs", C.c_int), ("mg_tile", C.c_int), ("precond", C.c_int),
-                ("mg_tma", C.c_int), ("mg_cluster", C.c_int)]
+                ("mg_tma", C.c_int), ("mg_cluster", C.c_int), ("precision", C.c_int), ("krylov", C.c_int),
+                ("stop_rule", C.c_int), ("tma_wait_polls", C.c_int), ("gram_schmidt", C.c_int)]
 
 
 class LtStats(C.Structure):
@@ -61,10 +68,14 @@ EXPORTS = {
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "lt_set_sources": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "lt_set_receivers": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "lt_set_source_rates": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lt_set_initial_state": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lt_set_options": (C.c_int, [C.c_void_p, C.POINTER(LtOpts)]),
     "lt_forward": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(LtStats)]),
     "lt_forward_batch": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                    C.c_void_p]),
+    "lt_adjoint_batch": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p, C.c_void_p]),
     "lt_forward_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(LtStats)]),
     "lt_forward_fields": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(LtStats)]),
     "lt_adjoint_jacobian": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(LtStats)]),
@@ -83,6 +94,9 @@ EXPORTS = {
     "lt_unet_destroy": (None, [C.c_void_p]),
     "lt_precond_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "lt_set_learned_preconditioner": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lt_contour_nodes": (C.c_int, [C.c_double, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "lt_learned_pairs": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "lt_krylov_vectors": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
     "lt_strerror": (C.c_char_p, [C.c_int]),
     "lt_last_error": (C.c_char_p, [C.c_void_p]),
     "lt_destroy": (None, [C.c_void_p]),

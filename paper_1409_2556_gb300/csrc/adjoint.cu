@@ -46,7 +46,7 @@ struct SensArgs {
 
 __device__ __forceinline__ cdf ldx(const SensArgs& a, int sh, int64_t c) {
   size_t i = (size_t)sh * a.N + c;
-  float2 h = a.X_hi[i], l = a.X_lo[i];
+  float2 h = a.X_hi[i], l = a.X_lo ? a.X_lo[i] : make_float2(0.f, 0.f);
   return {{h.x, l.x}, {h.y, l.y}};
 }
 __device__ __forceinline__ cdf cdf_from_d2(double2 v) { return {df_from_double(v.x), df_from_double(v.y)}; }

@@ -8,13 +8,20 @@
 
 namespace lt {
 
+// A vector is a hi plane and a lo plane of float2 (df32 complex).  With reduced precision
+// (LT_PREC_FP32) the lo planes are not allocated: a null lo plane reads as zero and is not
+// written, so the same kernels carry float32 vectors.
 __device__ __forceinline__ cdf load_cdf(const float2* hi, const float2* lo, size_t idx) {
-  float2 h = hi[idx], l = lo[idx];
+  float2 h = hi[idx], l = lo ? lo[idx] : make_float2(0.f, 0.f);
   return {{h.x, l.x}, {h.y, l.y}};
 }
 __device__ __forceinline__ void store_cdf(float2* hi, float2* lo, size_t idx, cdf v) {
-  hi[idx] = make_float2(v.re.hi, v.im.hi);
-  lo[idx] = make_float2(v.re.lo, v.im.lo);
+  if (lo) {
+    hi[idx] = make_float2(v.re.hi, v.im.hi);
+    lo[idx] = make_float2(v.re.lo, v.im.lo);
+  } else {
+    hi[idx] = make_float2(v.re.hi + v.re.lo, v.im.hi + v.im.lo);
+  }
 }
 __device__ __forceinline__ df ldf(const float* hi, const float* lo, int c) { return {hi[c], lo[c]}; }
 

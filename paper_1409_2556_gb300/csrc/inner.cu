@@ -602,7 +602,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
         if (q < n0) {
           const int c = c0 + q;
           rr[k] = load_cdf(bt.V_hi, bt.V_lo, vb + c);
-          if (r > 0) rr[k] = cdf_sub(rr[k], apply_exact(a.fe, bt.U_hi + ub, bt.U_lo + ub, c, taur, taui));
+          if (r > 0) rr[k] = cdf_sub(rr[k], apply_exact(a.fe, bt.U_hi + ub, lo_at(bt.U_lo, ub), c, taur, taui));
         }
       }
 #pragma unroll
@@ -631,7 +631,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
       if (r == 0)   // v_j itself is below the tolerance: u_j = 0
         for (int q = tid; q < n0; q += kIT) {
           bt.U_hi[ub + c0 + q] = make_float2(0.f, 0.f);
-          bt.U_lo[ub + c0 + q] = make_float2(0.f, 0.f);
+          if (bt.U_lo) bt.U_lo[ub + c0 + q] = make_float2(0.f, 0.f);
         }
       break;
     }
@@ -776,7 +776,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
       const float2 d = S0.u[((x + ly) & 1) * S0.plane + ly * S0.hx + (x >> 1)];
       if (r == 0) {
         bt.U_hi[ui] = d;
-        bt.U_lo[ui] = make_float2(0.f, 0.f);
+        if (bt.U_lo) bt.U_lo[ui] = make_float2(0.f, 0.f);
       } else {
         cdf u = load_cdf(bt.U_hi, bt.U_lo, ui);
         u.re = df_add_f(u.re, d.x);

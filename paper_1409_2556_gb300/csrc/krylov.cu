@@ -54,9 +54,15 @@ __global__ void k_init_vectors(Batch bt) {
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= bt.N) return;
   size_t idx = (size_t)b * (bt.maxit + 1) * bt.N + c;
-  float one = (c == bt.rhs_cell[b]) ? 1.f : 0.f;
-  bt.V_hi[idx] = make_float2(one, 0.f);
-  bt.V_lo[idx] = make_float2(0.f, 0.f);
+  const int64_t rc = bt.rhs_cell[b];
+  float hi = (c == rc) ? 1.f : 0.f, lo = 0.f;
+  if (rc < 0) { hi = bt.rhs_hi[c]; lo = bt.rhs_lo[c]; }    // dense right-hand side (initial state)
+  if (bt.V_lo) {
+    bt.V_hi[idx] = make_float2(hi, 0.f);
+    bt.V_lo[idx] = make_float2(lo, 0.f);
+  } else {
+    bt.V_hi[idx] = make_float2(hi + lo, 0.f);
+  }
 }
 
 __global__ void k_init_shifts(Batch bt) {
@@ -132,7 +138,7 @@ __global__ void k_exact_residual(Batch bt, FineExact fe, Level L0, int, int roun
       double2 t = bt.tau_cur[b];
       df taur = df_from_double(t.x), taui = df_from_double(t.y);
       size_t ub = ((size_t)b * bt.maxit + j) * bt.N;
-      cdf au = apply_exact(fe, bt.U_hi + ub, bt.U_lo + ub, c, taur, taui);
+      cdf au = apply_exact(fe, bt.U_hi + ub, lo_at(bt.U_lo, ub), c, taur, taui);
       r = cdf_sub(r, au);
     }
     if (!record_only) {
@@ -167,7 +173,7 @@ __global__ void k_update_u(Batch bt, Level L0, int, int round) {
   size_t ui = ((size_t)b * bt.maxit + j) * bt.N + c;
   if (round == 0) {
     bt.U_hi[ui] = d;
-    bt.U_lo[ui] = make_float2(0.f, 0.f);
+    if (bt.U_lo) bt.U_lo[ui] = make_float2(0.f, 0.f);
   } else {
     cdf u = load_cdf(bt.U_hi, bt.U_lo, ui);
     u.re = df_add_f(u.re, d.x);
@@ -253,17 +259,25 @@ __global__ void __launch_bounds__(kArnT) k_dots1(Batch bt, FineExact fe, int) {
   }
 }
 
-// pass 2: s' = M u_j - V c1 (df32, exact); dot[1][i] = V_hi[i]^H s'_hi; S <- s'
-// pass 3 (second = 1): s'' = S - V c2; snorm2 += ||s''||^2; S <- s''
-__global__ void __launch_bounds__(kArnT) k_update(Batch bt, FineExact fe, int, int second) {
+// mode 0 (pass 2): s' = M u_j - V c1 (df32, exact); dot[1][i] = V_hi[i]^H s'_hi; S <- s'
+// mode 1 (pass 3): s'' = S - V c2; snorm2 += ||s''||^2; S <- s''
+// mode 2 (the one-pass form): s' = M u_j - V c1 with c1 from the df32 dots; snorm2 += ||s'||^2; S <- s'
+__global__ void __launch_bounds__(kArnT) k_update(Batch bt, FineExact fe, int, int mode) {
+  const bool from_u = mode != 1, do_dots = mode == 0;
+  const int second = mode == 1;
   const int j = *bt.jdev;   // outer iteration (device counter, so one captured graph serves every j)
   __shared__ float red[32 * 2 * kIG];
   __shared__ float2 cf[512];
+  __shared__ float2 cl[512];     // mode 2: the low words of the df32-accurate coefficients
   int b = blockIdx.y;
   if (!bt.active[b]) return;
   const int N = fe.N;
   const double2* dsrc = bt.dot + (size_t)b * 2 * (bt.maxit + 1) + (second ? (bt.maxit + 1) : 0);
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) cf[i] = make_float2((float)dsrc[i].x, (float)dsrc[i].y);
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    const float hx = (float)dsrc[i].x, hy = (float)dsrc[i].y;
+    cf[i] = make_float2(hx, hy);
+    cl[i] = make_float2((float)(dsrc[i].x - (double)hx), (float)(dsrc[i].y - (double)hy));
+  }
   __syncthreads();
   int c0 = blockIdx.x * kArnT * kCPT + threadIdx.x;
   cdf s[kCPT];
@@ -273,7 +287,7 @@ __global__ void __launch_bounds__(kArnT) k_update(Batch bt, FineExact fe, int, i
   for (int q = 0; q < kCPT; ++q) {
     int c = c0 + q * kArnT;
     if (c < N) {
-      if (!second) {
+      if (from_u) {
         df m = ldf(fe.m_hi, fe.m_lo, c);
         s[q] = cdf_mul_r(load_cdf(bt.U_hi, bt.U_lo, ub + c), m);
       } else {
@@ -286,15 +300,20 @@ __global__ void __launch_bounds__(kArnT) k_update(Batch bt, FineExact fe, int, i
   size_t vb = (size_t)b * (bt.maxit + 1) * bt.N;
   for (int i = 0; i <= j; ++i) {
     float2 ci = cf[i];
+    const float2 cli = cl[i];
     const float2* vh = bt.V_hi + vb + (size_t)i * bt.N;
-    const float2* vl = bt.V_lo + vb + (size_t)i * bt.N;
+    const float2* vl = lo_at(bt.V_lo, vb + (size_t)i * bt.N);
 #pragma unroll
     for (int q = 0; q < kCPT; ++q) {
       int c = c0 + q * kArnT;
       if (c < N) {
-        float2 h = vh[c], l = vl[c];
+        float2 h = vh[c], l = vl ? vl[c] : make_float2(0.f, 0.f);
         cdf v = {{h.x, l.x}, {h.y, l.y}};
         s[q] = cdf_sub(s[q], cdf_mul_cf(v, ci.x, ci.y));
+        if (mode == 2) {   // - V_hi c_lo: the rest of the coefficient (V_lo c_lo is below 1e-14 |c|)
+          s[q].re = df_add_f(s[q].re, -(h.x * cli.x - h.y * cli.y));
+          s[q].im = df_add_f(s[q].im, -(h.x * cli.y + h.y * cli.x));
+        }
       }
     }
   }
@@ -303,7 +322,7 @@ __global__ void __launch_bounds__(kArnT) k_update(Batch bt, FineExact fe, int, i
     int c = c0 + q * kArnT;
     if (c < N) store_cdf(bt.S_hi, bt.S_lo, sb + c, s[q]);
   }
-  if (!second) {
+  if (do_dots) {
     for (int i0 = 0; i0 <= j; i0 += kIG) {
       float acc[2 * kIG];
 #pragma unroll
@@ -370,8 +389,16 @@ __global__ void k_normalize(Batch bt, int) {
     double2* Hc = bt.H + ((size_t)b * bt.maxit + j) * (bt.maxit + 1);
     for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) {
       if (i <= j) {
+        // exactly the coefficients the updates subtracted: float c1 + float c2 (two passes), or the
+        // hi + lo float pair of the df32-accurate c1 (one pass)
         double2 a = d[i], a2 = d[bt.maxit + 1 + i];
-        Hc[i] = make_double2((double)(float)a.x + (double)(float)a2.x, (double)(float)a.y + (double)(float)a2.y);
+        if (bt.gs_passes == 1) {
+          const float hx = (float)a.x, hy = (float)a.y;
+          Hc[i] = make_double2((double)hx + (double)(float)(a.x - (double)hx),
+                               (double)hy + (double)(float)(a.y - (double)hy));
+        } else {
+          Hc[i] = make_double2((double)(float)a.x + (double)(float)a2.x, (double)(float)a.y + (double)(float)a2.y);
+        }
       } else {
         Hc[i] = make_double2((double)h, 0.0);
       }
@@ -379,15 +406,28 @@ __global__ void k_normalize(Batch bt, int) {
   }
 }
 
+void launch_dots_df(const Batch& bt, const FineExact& fe, dim3 g, cudaStream_t st);
+
 void launch_arnoldi(const Batch& bt, const FineExact& fe, int j, cudaStream_t st, int* nlaunch, Prof* pf) {
   dim3 g((fe.N + kArnT * kCPT - 1) / (kArnT * kCPT), bt.nb);
-  prof_begin(pf, KC_DOTS, st);
-  k_dots1<<<g, kArnT, 0, st>>>(bt, fe, j);
-  prof_end(pf, KC_DOTS, st);
-  for (int second = 0; second < 2; ++second) {
+  if (bt.gs_passes == 1) {
+    // one classical pass whose coefficients come from df32 dots (V read twice per column)
+    prof_begin(pf, KC_DOTS, st);
+    launch_dots_df(bt, fe, g, st);
+    prof_end(pf, KC_DOTS, st);
     prof_begin(pf, KC_ORTHO, st);
-    k_update<<<g, kArnT, 0, st>>>(bt, fe, j, second);
+    k_update<<<g, kArnT, 0, st>>>(bt, fe, j, 2);
     prof_end(pf, KC_ORTHO, st);
+    *nlaunch -= 1;
+  } else {
+    prof_begin(pf, KC_DOTS, st);
+    k_dots1<<<g, kArnT, 0, st>>>(bt, fe, j);
+    prof_end(pf, KC_DOTS, st);
+    for (int mode = 0; mode < 2; ++mode) {
+      prof_begin(pf, KC_ORTHO, st);
+      k_update<<<g, kArnT, 0, st>>>(bt, fe, j, mode);
+      prof_end(pf, KC_ORTHO, st);
+    }
   }
   dim3 gn((fe.N + 255) / 256, bt.nb);
   k_normalize<<<gn, 256, 0, st>>>(bt, j);
@@ -460,15 +500,44 @@ __global__ void k_shift_ls(Batch bt, int) {
     g[j] = make_double2(c * gj.x, c * gj.y);
     double2 gn = zmul(zconj(s), gj);
     g[j + 1] = make_double2(-gn.x, -gn.y);
+    // GMRES-Sh: the least-squares residual |g_{j+1}|.  FOM-Sh: the square system H_j(z; T_j) y = e_1
+    // is the Givens-reduced one without the last rotation, whose residual is
+    // |eta_k| = |h_{j+1,j} (z - tau_j) y_j| = |g_{j+1}| / c_j (Sec. 3.1, Proposition 1); c_j = 0 means
+    // H_j(z; T_j) is singular and the FOM coefficients do not exist at this j.
     double res = zabs(g[j + 1]);
+    if (bt.krylov == 1) res = c > 0.0 ? res / c : INFINITY;
     bt.pres[sh] = res;
-    // stop at half the tolerance: the true residual adds the (relaxed) inner-solve
-    // error e_j y_j and the float32 loss of orthogonality on top of the projected one
-    if (res <= 0.5 * bt.tol || rho == 0.0 || hcol[j + 1].x == 0.0) {
-      bt.conv_it[sh] = j + 1;
-    } else {
-      mine = 1;
-      atomicMax(&rmax_bits, (unsigned long long)__double_as_longlong(res));   // res >= 0: bit order = value order
+    if (bt.stop_rule == 0) {
+      // stop at half the tolerance: the true residual adds the (relaxed) inner-solve
+      // error e_j y_j and the float32 loss of orthogonality on top of the projected one
+      if (res <= 0.5 * bt.tol || rho == 0.0 || hcol[j + 1].x == 0.0) {
+        bt.conv_it[sh] = j + 1;
+      } else {
+        mine = 1;
+        atomicMax(&rmax_bits, (unsigned long long)__double_as_longlong(res));   // res >= 0: bit order = value order
+      }
+    }
+  }
+  if (bt.stop_rule == 1) {
+    // quadrature-weighted rule: the nk shifts of one output time stop together once
+    // sum_k |w_k qhat_k| rho_k <= tol/2 sum_k |w_k qhat_k| (the bound of Proposition 1 on the
+    // residual of the quadrature sum, relative to that of its right-hand side)
+    __syncthreads();
+    const int s0 = bt.shift_off[b], s1 = bt.shift_off[b + 1], nk = bt.nk;
+    for (int t0 = s0 + threadIdx.x * nk; t0 < s1; t0 += blockDim.x * nk) {
+      if (bt.conv_it[t0] > 0) continue;
+      double num = 0.0, den = 0.0, worst = 0.0;
+      for (int sh = t0; sh < t0 + nk; ++sh) {
+        num += bt.wabs[sh] * bt.pres[sh];
+        den += bt.wabs[sh];
+        worst = fmax(worst, bt.pres[sh]);
+      }
+      if (num <= 0.5 * bt.tol * den || hcol[j + 1].x == 0.0) {
+        for (int sh = t0; sh < t0 + nk; ++sh) bt.conv_it[sh] = j + 1;
+      } else {
+        mine = 1;
+        atomicMax(&rmax_bits, (unsigned long long)__double_as_longlong(worst));
+      }
     }
   }
   if (mine) atomicOr(&any, 1);
@@ -501,8 +570,15 @@ __global__ void k_backsolve(Batch bt, const int* sh_basis) {
   const double2* g = bt.g + (size_t)sh * (M + 1);
   double2* y = bt.Y + (size_t)sh * M;
   for (int i = m; i < M; ++i) y[i] = make_double2(0.0, 0.0);
+  // FOM-Sh: the last equation of the square system takes the pre-rotation entries, which
+  // amounts to g_{m-1} / c_{m-1}^2 against the rotated R (the other rows are the same)
+  const double cl = bt.rc[(size_t)sh * M + (m > 0 ? m - 1 : 0)];
   for (int i = m - 1; i >= 0; --i) {
     double2 acc = g[i];
+    if (bt.krylov == 1 && i == m - 1) {
+      const double f = cl > 0.0 ? 1.0 / (cl * cl) : 0.0;
+      acc.x *= f; acc.y *= f;
+    }
     for (int l = i + 1; l < m; ++l) {
       double2 t = zmul(R[(size_t)l * M + i], y[l]);
       acc.x -= t.x; acc.y -= t.y;
@@ -539,52 +615,61 @@ void launch_quad_coef(const Batch& bt, const QuadItem* items, int nitems, const 
   k_quad_coef<<<nitems, 128, 0, st>>>(bt, items, nitems, wq, C);
 }
 
+// Re (U_b[cell] . C_q) over the basis's columns, df32 U read as double
+__device__ __forceinline__ double quad_dot(const Batch& bt, const QuadItem& it, const double2* C, int q, int64_t cell,
+                                           int m) {
+  const int M = bt.maxit;
+  double acc = 0.0;
+  for (int i = 0; i < m; ++i) {
+    size_t ui = ((size_t)it.basis * M + i) * bt.N + cell;
+    float2 hi = bt.U_hi[ui], lo = bt.U_lo ? bt.U_lo[ui] : make_float2(0.f, 0.f);
+    double2 c = C[(size_t)q * M + i];
+    acc += ((double)hi.x + (double)lo.x) * c.x - ((double)hi.y + (double)lo.y) * c.y;
+  }
+  return acc;
+}
+
+// h[s][r][t] = 2 Re (U[rcell] . C_{s,t}) (+ the initial-state item dense_q0 + t, the same for every s)
 __global__ void k_measure(Batch bt, const QuadItem* items, const double2* C, int ns, int nr, int nt,
-                          const int64_t* rcells, double* h) {
+                          const int64_t* rcells, double* h, int dense_q0) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= ns * nr * nt) return;
   int t = idx % nt, r = (idx / nt) % nr, s = idx / (nt * nr);
   int q = s * nt + t;
-  QuadItem it = items[q];
-  const int M = bt.maxit;
   int64_t cell = rcells[r];
-  double acc = 0.0;
-  for (int i = 0; i < M; ++i) {
-    size_t ui = ((size_t)it.basis * M + i) * bt.N + cell;
-    float2 hi = bt.U_hi[ui], lo = bt.U_lo[ui];
-    double2 c = C[(size_t)q * M + i];
-    acc += ((double)hi.x + (double)lo.x) * c.x - ((double)hi.y + (double)lo.y) * c.y;
+  const QuadItem it = items[q];
+  double acc = quad_dot(bt, it, C, q, cell, bt.nit[it.basis]);
+  if (dense_q0 >= 0) {
+    const QuadItem id = items[dense_q0 + t];
+    acc += quad_dot(bt, id, C, dense_q0 + t, cell, bt.nit[id.basis]);
   }
   h[idx] = 2.0 * acc;
 }
 
 void launch_measure(const Batch& bt, const QuadItem* items, const double2* C, int ns, int nr, int nt,
-                    const int64_t* rcells, double* h, cudaStream_t st) {
+                    const int64_t* rcells, double* h, cudaStream_t st, int dense_q0) {
   int n = ns * nr * nt;
-  k_measure<<<(n + 127) / 128, 128, 0, st>>>(bt, items, C, ns, nr, nt, rcells, h);
+  k_measure<<<(n + 127) / 128, 128, 0, st>>>(bt, items, C, ns, nr, nt, rcells, h, dense_q0);
 }
 
-__global__ void k_fields(Batch bt, const QuadItem* items, const double2* C, double* phi) {
+// phi[q][c] for the items q = s * nt + t (+ the initial-state item dense_q0 + t)
+__global__ void k_fields(Batch bt, const QuadItem* items, const double2* C, double* phi, int nt, int dense_q0) {
   int q = blockIdx.y;
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= bt.N) return;
   QuadItem it = items[q];
-  const int M = bt.maxit;
-  int m = bt.nit[it.basis];
-  double acc = 0.0;
-  for (int i = 0; i < m; ++i) {
-    size_t ui = ((size_t)it.basis * M + i) * bt.N + c;
-    float2 hi = bt.U_hi[ui], lo = bt.U_lo[ui];
-    double2 cc = C[(size_t)q * M + i];
-    acc += ((double)hi.x + (double)lo.x) * cc.x - ((double)hi.y + (double)lo.y) * cc.y;
+  double acc = quad_dot(bt, it, C, q, c, bt.nit[it.basis]);
+  if (dense_q0 >= 0) {
+    const int qd = dense_q0 + q % nt;
+    acc += quad_dot(bt, items[qd], C, qd, c, bt.nit[items[qd].basis]);
   }
   phi[(size_t)q * bt.N + c] = 2.0 * acc;
 }
 
 void launch_fields(const Batch& bt, const QuadItem* items, const double2* C, int nitems, double* phi,
-                   cudaStream_t st) {
+                   cudaStream_t st, int nt, int dense_q0) {
   dim3 g((unsigned)((bt.N + 255) / 256), nitems);
-  k_fields<<<g, 256, 0, st>>>(bt, items, C, phi);
+  k_fields<<<g, 256, 0, st>>>(bt, items, C, phi, nt, dense_q0);
 }
 
 // ------------------------------------------------------------ true residual (judge)
@@ -609,6 +694,73 @@ __device__ __forceinline__ df df_fma2(df acc, df a, df b, df c, df d) {   // acc
   fast_two_sum(s2, lo, r.hi, r.lo);
   return r;
 }
+// one-pass Gram-Schmidt: dot[0][i] = V_i^H (M u_j) with V and M u_j in df32; each thread sums its
+// cells in df32, the block and the grid in double (a few additions per block)
+__global__ void __launch_bounds__(kArnT) k_dots_df(Batch bt, FineExact fe) {
+  const int j = *bt.jdev;
+  __shared__ double red[32 * 2 * kIG];
+  const int b = blockIdx.y;
+  if (!bt.active[b]) return;
+  const int N = fe.N;
+  const int c0 = blockIdx.x * kArnT * kCPT + threadIdx.x;
+  cdf s[kCPT];
+  const size_t ub = ((size_t)b * bt.maxit + j) * bt.N;
+#pragma unroll
+  for (int q = 0; q < kCPT; ++q) {
+    const int c = c0 + q * kArnT;
+    s[q] = c < N ? cdf_mul_r(load_cdf(bt.U_hi, bt.U_lo, ub + c), ldf(fe.m_hi, fe.m_lo, c))
+                 : cdf{{0.f, 0.f}, {0.f, 0.f}};
+  }
+  const size_t vb = (size_t)b * (bt.maxit + 1) * bt.N;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i0 = 0; i0 <= j; i0 += kIG) {
+    double acc[2 * kIG];
+#pragma unroll
+    for (int ii = 0; ii < kIG; ++ii) {
+      acc[2 * ii] = acc[2 * ii + 1] = 0.0;
+      const int i = i0 + ii;
+      if (i > j) continue;
+      const float2* vh = bt.V_hi + vb + (size_t)i * bt.N;
+      const float2* vl = lo_at(bt.V_lo, vb + (size_t)i * bt.N);
+      df re = {0.f, 0.f}, im = {0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < kCPT; ++q) {
+        const int c = c0 + q * kArnT;
+        if (c < N) {
+          const cdf v = load_cdf(vh, vl, c);
+          re = df_fma2(re, v.re, s[q].re, df_neg(v.im), s[q].im);   // + vr sr + vi si
+          im = df_fma2(im, v.re, s[q].im, v.im, s[q].re);           // + vr si - vi sr
+        }
+      }
+      acc[2 * ii] = (double)re.hi + (double)re.lo;
+      acc[2 * ii + 1] = (double)im.hi + (double)im.lo;
+    }
+#pragma unroll
+    for (int q = 0; q < 2 * kIG; ++q)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < 2 * kIG; ++q) red[warp * 2 * kIG + q] = acc[q];
+    __syncthreads();
+    if (threadIdx.x < 2 * kIG && i0 + (int)threadIdx.x / 2 <= j) {
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t += red[w * 2 * kIG + threadIdx.x];
+      double* d = (double*)(bt.dot + (size_t)b * 2 * (bt.maxit + 1) + i0 + threadIdx.x / 2);
+      atomicAdd(d + (threadIdx.x & 1), t);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int n = min(kArnT * kCPT, N - (int)(blockIdx.x * kArnT * kCPT));
+    atomicAdd(&bt.work[KC_DOTS], (unsigned long long)n * (unsigned long long)(j + 1));
+  }
+}
+
+void launch_dots_df(const Batch& bt, const FineExact& fe, dim3 g, cudaStream_t st) {
+  k_dots_df<<<g, kArnT, 0, st>>>(bt, fe);
+}
+
 __device__ __forceinline__ cdf cdf_fma(cdf acc, cdf u, cdf y) {
   return {df_fma2(acc.re, u.re, y.re, u.im, y.im), df_fma2(acc.im, u.re, y.im, df_neg(u.im), y.re)};
 }
@@ -670,10 +822,12 @@ __global__ void k_true_res(Batch bt, FineExact fe, const int* sh_basis, const fl
     double2 z = bt.zsh[sh];
     df zr = df_from_double(z.x), zi = df_from_double(z.y);
     const float2* xh = X_hi + (size_t)sh * bt.N;
-    const float2* xl = X_lo + (size_t)sh * bt.N;
+    const float2* xl = lo_at(X_lo, (size_t)sh * bt.N);
     cdf ax = apply_exact(fe, xh, xl, c, zr, zi);
-    float e = (c == bt.rhs_cell[sh_basis[sh]]) ? 1.f : 0.f;
-    cdf r = cdf_sub({{e, 0.f}, {0.f, 0.f}}, ax);
+    const int64_t rc = bt.rhs_cell[sh_basis[sh]];
+    df e = {(c == rc) ? 1.f : 0.f, 0.f};
+    if (rc < 0) e = {bt.rhs_hi[c], bt.rhs_lo[c]};
+    cdf r = cdf_sub({e, {0.f, 0.f}}, ax);
     acc[0] = r.re.hi * r.re.hi + r.im.hi * r.im.hi;
   }
   block_reduce_add<1>(acc, red);

@@ -57,7 +57,7 @@ struct HostLevel {
 };
 
 struct Workspace {
-  int nb = 0, maxit = 0, nsh = 0, rounds = 0, ngroups = 0, nc2 = 0;
+  int nb = 0, maxit = 0, nsh = 0, rounds = 0, ngroups = 0, nc2 = 0, prec = -1;
   int64_t N = 0;
   std::vector<void*> allocs;
   lt::Batch bt{};
@@ -89,6 +89,10 @@ struct lt_ctx {
   // wells
   std::vector<int64_t> src, rec;
   std::vector<double> Q;
+  // per source: rate q_s(t) = sum_j rate_a[s][j] exp(-rate_l[s][j] t) (empty: the constant Q[s])
+  std::vector<std::vector<double>> rate_a, rate_l;
+  // initial head phi_0 (empty: zero)
+  std::vector<double> phi0;
   Workspace ws;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   lt::Prof prof;
@@ -105,7 +109,11 @@ struct lt_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // learned initial guess (opts.precond = 1)
   lt_unet* net = nullptr;
-  float *d_lk = nullptr, *d_mD = nullptr, *d_xin = nullptr, *d_gn2 = nullptr;
+  float *d_lk = nullptr, *d_mD = nullptr, *d_xin = nullptr, *d_gn2 = nullptr, *d_D32 = nullptr;
+  // the last solve's bases (lt_krylov_vectors): group, outer iterations, shifts per group, tau pattern
+  std::vector<int> last_group, last_nit;
+  std::vector<cplx> last_tau;
+  int last_single = 0;
   size_t xin_cap = 0;
   // workspace of lt_precond_apply
   std::vector<void*> pc_allocs;
@@ -187,6 +195,11 @@ int lt_default_options(lt_opts* o) {
   o->precond = 0;
   o->mg_tma = 1;
   o->mg_cluster = 1;
+  o->precision = LT_PREC_FP64;
+  o->krylov = LT_KRYLOV_GMRES;
+  o->stop_rule = LT_STOP_SHIFT;
+  o->tma_wait_polls = 1 << 26;
+  o->gram_schmidt = 2;
   return LT_OK;
 }
 
@@ -254,7 +267,7 @@ void lt_destroy(lt_ctx* ctx) {
   lt::tma_cache_free(ctx->pc_mg);
   free_list(ctx->pc_allocs);          // also holds pc_mg.d_levels
   ctx->pc_mg.d_levels = nullptr;
-  for (float* p : {ctx->d_lk, ctx->d_mD, ctx->d_xin, ctx->d_gn2})
+  for (float* p : {ctx->d_lk, ctx->d_mD, ctx->d_xin, ctx->d_gn2, ctx->d_D32})
     if (p) cudaFree(p);
   cudaGetLastError();                  // leave no error state behind for other users of the runtime
   delete ctx;
@@ -284,6 +297,17 @@ int lt_set_options(lt_ctx* ctx, const lt_opts* o) {
     return fail(ctx, LT_ERR_INVALID_ARG, "inner_relax=%g must be in [0,1)", o->inner_relax);
   if (o->timing_class < -1 || o->timing_class >= LT_KC_COUNT)
     return fail(ctx, LT_ERR_INVALID_ARG, "timing_class=%d", o->timing_class);
+  if (o->precision != LT_PREC_FP64 && o->precision != LT_PREC_FP32)
+    return fail(ctx, LT_ERR_INVALID_ARG, "precision=%d must be LT_PREC_FP64 or LT_PREC_FP32", o->precision);
+  if (o->precision == LT_PREC_FP32 && o->tol < 2e-6)
+    return fail(ctx, LT_ERR_INVALID_ARG, "tol=%g is below the float32 floor (2e-6) of LT_PREC_FP32", o->tol);
+  if (o->krylov != LT_KRYLOV_GMRES && o->krylov != LT_KRYLOV_FOM)
+    return fail(ctx, LT_ERR_INVALID_ARG, "krylov=%d must be LT_KRYLOV_GMRES or LT_KRYLOV_FOM", o->krylov);
+  if (o->stop_rule != LT_STOP_SHIFT && o->stop_rule != LT_STOP_QUADRATURE)
+    return fail(ctx, LT_ERR_INVALID_ARG, "stop_rule=%d must be LT_STOP_SHIFT or LT_STOP_QUADRATURE", o->stop_rule);
+  if (o->tma_wait_polls < 0) return fail(ctx, LT_ERR_INVALID_ARG, "tma_wait_polls=%d must be >= 0", o->tma_wait_polls);
+  if (o->gram_schmidt != 1 && o->gram_schmidt != 2)
+    return fail(ctx, LT_ERR_INVALID_ARG, "gram_schmidt=%d must be 1 or 2", o->gram_schmidt);
   ctx->opts = *o;
   ctx->mg.npre = o->mg_pre;
   ctx->mg.npost = o->mg_post;
@@ -467,10 +491,11 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
   ctx->have_grid = false;
   lt::tma_cache_free(ctx->mg);
   lt::tma_cache_free(ctx->pc_mg);
-  for (float** p : {&ctx->d_lk, &ctx->d_mD}) {
+  for (float** p : {&ctx->d_lk, &ctx->d_mD, &ctx->d_D32}) {
     if (*p) cudaFree(*p);
     *p = nullptr;
   }
+  ctx->last_group.clear(); ctx->last_nit.clear(); ctx->last_tau.clear();
   free_list(ctx->pc_allocs);
   ctx->pc_mg.d_levels = nullptr;
   ctx->pc_nb = 0;
@@ -604,6 +629,7 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
   }
   ctx->have_grid = true;
   ctx->src.clear(); ctx->Q.clear(); ctx->rec.clear();
+  ctx->rate_a.clear(); ctx->rate_l.clear(); ctx->phi0.clear();
   return LT_OK;
 }
 
@@ -619,7 +645,61 @@ extern "C" int lt_set_sources(lt_ctx* ctx, int ns, const int64_t* cells, const d
   }
   ctx->src.assign(cells, cells + ns);
   ctx->Q.assign(Q, Q + ns);
+  ctx->rate_a.clear(); ctx->rate_l.clear();
   return LT_OK;
+}
+
+extern "C" int lt_set_source_rates(lt_ctx* ctx, int ns, const int* nterm, const double* a, const double* lambda) {
+  if (!ctx) return LT_ERR_INVALID_ARG;
+  if (!ctx->have_grid) return fail(ctx, LT_ERR_STATE, "lt_setup_grid must come first");
+  if (!nterm) {
+    ctx->rate_a.clear(); ctx->rate_l.clear();
+    return LT_OK;
+  }
+  if (ns != (int)ctx->src.size())
+    return fail(ctx, LT_ERR_INVALID_ARG, "ns=%d must equal the %d sources set by lt_set_sources", ns,
+                (int)ctx->src.size());
+  if (!a || !lambda) return fail(ctx, LT_ERR_INVALID_ARG, "a and lambda must not be null");
+  std::vector<std::vector<double>> A(ns), L(ns);
+  size_t off = 0;
+  for (int s = 0; s < ns; ++s) {
+    if (nterm[s] < 1 || nterm[s] > 64) return fail(ctx, LT_ERR_INVALID_ARG, "nterm[%d]=%d must be in [1,64]", s, nterm[s]);
+    for (int j = 0; j < nterm[s]; ++j, ++off) {
+      if (!std::isfinite(a[off])) return fail(ctx, LT_ERR_INVALID_ARG, "a[%zu] is not finite", off);
+      if (!(lambda[off] >= 0.0) || !std::isfinite(lambda[off]))
+        return fail(ctx, LT_ERR_INVALID_ARG, "lambda[%zu]=%g must be finite and >= 0", off, lambda[off]);
+      A[s].push_back(a[off]);
+      L[s].push_back(lambda[off]);
+    }
+  }
+  ctx->rate_a.swap(A);
+  ctx->rate_l.swap(L);
+  return LT_OK;
+}
+
+extern "C" int lt_set_initial_state(lt_ctx* ctx, const double* phi0) {
+  if (!ctx) return LT_ERR_INVALID_ARG;
+  if (!ctx->have_grid) return fail(ctx, LT_ERR_STATE, "lt_setup_grid must come first");
+  if (!phi0) {
+    ctx->phi0.clear();
+    return LT_OK;
+  }
+  bool any = false;
+  for (int64_t c = 0; c < ctx->N; ++c) {
+    if (!std::isfinite(phi0[c])) return fail(ctx, LT_ERR_INVALID_ARG, "phi0[%lld] is not finite", (long long)c);
+    any |= phi0[c] != 0.0;
+  }
+  if (any) ctx->phi0.assign(phi0, phi0 + ctx->N);
+  else ctx->phi0.clear();
+  return LT_OK;
+}
+
+// Laplace transform of source s's rate at z (Sec. 2.1-2.2): sum_j a_j / (z + lambda_j), or Q_s / z
+static cplx qhat(const lt_ctx* ctx, int s, cplx z) {
+  if (ctx->rate_a.empty()) return ctx->Q[s] / z;
+  cplx v(0.0, 0.0);
+  for (size_t j = 0; j < ctx->rate_a[s].size(); ++j) v += ctx->rate_a[s][j] / (z + ctx->rate_l[s][j]);
+  return v;
 }
 
 extern "C" int lt_set_receivers(lt_ctx* ctx, int nr, const int64_t* cells) {
@@ -649,9 +729,17 @@ struct Plan {
   std::vector<int> shift_off;           // nb + 1
   std::vector<int> sh_basis;
   std::vector<cplx> zsh;
+  // bases [dense_b0, nb) (one per group) solve for the dense right-hand side M phi_0 / beta0
+  int dense_b0 = -1;
+  double beta0 = 0.0;
+  std::vector<double> wabs;             // [nsh] |w_k qhat(z_k)| (quadrature stopping rule)
 };
 
-static int make_plan(lt_ctx* ctx, int nt, const double* times, const std::vector<int64_t>& rhs, Plan& P) {
+// rhs: one point right-hand side per entry; the first n_src of them are sources (weights of the
+// quadrature stopping rule use their rate transforms).  dense: one more basis per group for the
+// initial-state right-hand side M phi_0.
+static int make_plan(lt_ctx* ctx, int nt, const double* times, const std::vector<int64_t>& rhs, Plan& P,
+                     int n_src = 0, bool dense = false) {
   const lt_opts& o = ctx->opts;
   P.nt = nt;
   P.times.assign(times, times + nt);
@@ -690,21 +778,31 @@ static int make_plan(lt_ctx* ctx, int nt, const double* times, const std::vector
     P.tau[2 * g] = lo;
     P.tau[2 * g + 1] = (o.tau_policy == LT_TAU_SINGLE) ? lo : hi;
   }
-  P.nb = (int)rhs.size() * P.G;
+  const int nrhs = (int)rhs.size() + (dense ? 1 : 0);
+  P.nb = nrhs * P.G;
+  P.dense_b0 = dense ? (int)rhs.size() * P.G : -1;
+  P.beta0 = 0.0;
+  if (dense) {   // beta0 = ||M phi_0||_2
+    for (int64_t c = 0; c < ctx->N; ++c) P.beta0 += std::pow(ctx->hl[0].m[c] * ctx->phi0[c], 2);
+    P.beta0 = std::sqrt(P.beta0);
+  }
   P.rhs_cell.resize(P.nb);
   P.group.resize(P.nb);
   P.shift_off.assign(P.nb + 1, 0);
   P.zsh.clear();
   P.sh_basis.clear();
-  for (size_t s = 0; s < rhs.size(); ++s)
+  P.wabs.clear();
+  for (int s = 0; s < nrhs; ++s)
     for (int g = 0; g < P.G; ++g) {
-      int b = (int)s * P.G + g;
-      P.rhs_cell[b] = rhs[s];
+      int b = s * P.G + g;
+      P.rhs_cell[b] = s < (int)rhs.size() ? rhs[s] : -1;
       P.group[b] = g;
       for (int t : gtimes[g])
-        for (const cplx& z : P.z[t]) {
+        for (int k = 0; k < P.Nk; ++k) {
+          const cplx z = P.z[t][k];
           P.zsh.push_back(z);
           P.sh_basis.push_back(b);
+          P.wabs.push_back(std::abs(P.w[t][k] * (s < n_src ? qhat(ctx, s, z) : cplx(1.0, 0.0))));
         }
       P.shift_off[b + 1] = (int)P.zsh.size();
     }
@@ -769,7 +867,7 @@ static int ensure_ws(lt_ctx* ctx, const Plan& P) {
   const int nc = ctx->hl.back().N;
   const int nc2 = ctx->mg.coarse_direct ? nc * nc : 0;
   if (ws.nb >= P.nb && ws.maxit == o.maxit && ws.nsh >= P.nsh && ws.rounds == o.inner_rounds && ws.N == ctx->N &&
-      ws.ngroups >= P.G && ws.nc2 >= nc2)
+      ws.ngroups >= P.G && ws.nc2 >= nc2 && ws.prec == o.precision)
     return LT_OK;
   CK(cudaStreamSynchronize(ctx->stream));
   free_ws(ctx);
@@ -780,9 +878,17 @@ static int ensure_ws(lt_ctx* ctx, const Plan& P) {
   auto& A = ws.allocs;
   int rc = 0;
 #define AL(p, n) if ((rc = dalloc(ctx, A, &p, (size_t)(n)))) return rc
-  AL(bt.V_hi, (size_t)nb * (M + 1) * N); AL(bt.V_lo, (size_t)nb * (M + 1) * N);
-  AL(bt.U_hi, (size_t)nb * M * N); AL(bt.U_lo, (size_t)nb * M * N);
-  AL(bt.S_hi, (size_t)nb * N); AL(bt.S_lo, (size_t)nb * N);
+  // reduced precision keeps one float32 plane per vector (the lo planes stay null)
+  const bool df = o.precision == LT_PREC_FP64;
+  AL(bt.V_hi, (size_t)nb * (M + 1) * N);
+  AL(bt.U_hi, (size_t)nb * M * N);
+  AL(bt.S_hi, (size_t)nb * N);
+  bt.V_lo = bt.U_lo = bt.S_lo = nullptr;
+  if (df) {
+    AL(bt.V_lo, (size_t)nb * (M + 1) * N);
+    AL(bt.U_lo, (size_t)nb * M * N);
+    AL(bt.S_lo, (size_t)nb * N);
+  }
   AL(bt.tau_grp, 2 * P.G); AL(bt.group, nb); AL(bt.tau_pattern, 5); AL(bt.tau_cur, nb); AL(bt.tau_slot, nb);
   AL(bt.rnorm2, (size_t)nb * (R + 1)); AL(bt.dot, (size_t)nb * 2 * (M + 1)); AL(bt.H, (size_t)nb * M * (M + 1));
   AL(bt.snorm2, nb); AL(bt.active, nb); AL(bt.nit, nb); AL(bt.inner_max, nb); AL(bt.rhs_cell, nb);
@@ -793,6 +899,12 @@ static int ensure_ws(lt_ctx* ctx, const Plan& P) {
   AL(bt.itol2, nb);
   AL(bt.rmax, nb);
   AL(bt.jdev, 1);
+  {
+    double* w = nullptr;
+    float *rh = nullptr, *rl = nullptr;
+    AL(w, nsh); AL(rh, N); AL(rl, N);
+    bt.wabs = w; bt.rhs_hi = rh; bt.rhs_lo = rl;
+  }
   if (nc2) AL(bt.coarse_inv, (size_t)2 * P.G * nc2);
   if (ctx->inner.ok) AL(ws.l0q, (size_t)nb * N);
   // multigrid vectors
@@ -804,6 +916,7 @@ static int ensure_ws(lt_ctx* ctx, const Plan& P) {
 #undef AL
   CK(cudaMemcpy(ctx->mg.d_levels, ctx->mg.h_levels, sizeof(lt::Level) * ctx->mg.nlev, cudaMemcpyHostToDevice));
   ws.nb = nb; ws.maxit = M; ws.nsh = nsh; ws.rounds = R; ws.N = ctx->N; ws.ngroups = P.G; ws.nc2 = nc2;
+  ws.prec = o.precision;
   bt.nb = nb; bt.maxit = M; bt.N = ctx->N; bt.rounds = R; bt.nsh = nsh;
   return LT_OK;
 }
@@ -835,9 +948,9 @@ static lt::Batch sub_batch(const lt::Batch& bt, int b0, int n) {
   const size_t N = (size_t)bt.N, M = (size_t)bt.maxit;
   v.nb = n;
   v.itol2 += b0; v.rmax += b0;
-  v.V_hi += b0 * (M + 1) * N; v.V_lo += b0 * (M + 1) * N;
-  v.U_hi += b0 * M * N; v.U_lo += b0 * M * N;
-  v.S_hi += b0 * N; v.S_lo += b0 * N;
+  v.V_hi += b0 * (M + 1) * N; v.V_lo = lt::lo_at(bt.V_lo, b0 * (M + 1) * N);
+  v.U_hi += b0 * M * N; v.U_lo = lt::lo_at(bt.U_lo, b0 * M * N);
+  v.S_hi += b0 * N; v.S_lo = lt::lo_at(bt.S_lo, b0 * N);
   v.group += b0; v.tau_cur += b0; v.tau_slot += b0;
   v.rnorm2 += (size_t)b0 * (bt.rounds + 1);
   v.dot += (size_t)b0 * 2 * (M + 1);
@@ -869,7 +982,10 @@ static int launch_iteration_cluster(lt_ctx* ctx, cudaStream_t q, int jj, int* nl
   for (int part = 0; part < parts; ++part) {
     const int b0 = part == 0 ? 0 : half;
     const int n = parts == 1 ? nb : (part == 0 ? half : nb - half);
-    cudaStream_t qs = part == 0 ? q : ctx->side_stream;
+    // with per-launch CUDA-event timing on, both halves go to one stream so that the timed
+    // windows of different launches never overlap
+    const bool timing = pf && pf->cls >= 0;
+    cudaStream_t qs = (part == 0 || timing) ? q : ctx->side_stream;
     const lt::Batch v = parts == 1 ? bt : sub_batch(bt, b0, n);
     lt::launch_prep_iter(v, jj, qs);
     if (lt::launch_inner_cluster(ctx->mg, ctx->inner, v, ctx->fe, ctx->ws.l0q + (size_t)b0 * ctx->N,
@@ -918,6 +1034,31 @@ static int launch_iteration(lt_ctx* ctx, cudaStream_t q, int jj, int* nlq, lt::P
   return LT_OK;
 }
 
+// per-cell tables of the learned preconditioner's input channels (normalised log kappa, m / D) and
+// the float32 diagonal D of the fine operator; built once per grid
+static int learned_tables(lt_ctx* ctx) {
+  if (ctx->d_lk) return LT_OK;
+  std::vector<float> lk(ctx->N), mD(ctx->N), D(ctx->N);
+  double mu = 0, var = 0;
+  for (int64_t c = 0; c < ctx->N; ++c) mu += std::log(ctx->kappa[c]);
+  mu /= ctx->N;
+  for (int64_t c = 0; c < ctx->N; ++c) var += std::pow(std::log(ctx->kappa[c]) - mu, 2);
+  double sd = std::sqrt(var / ctx->N);
+  if (sd < 1e-12) sd = 1.0;
+  for (int64_t c = 0; c < ctx->N; ++c) {
+    lk[c] = (float)((std::log(ctx->kappa[c]) - mu) / sd);
+    mD[c] = (float)(ctx->hl[0].m[c] / ctx->hl[0].D[c]);
+    D[c] = (float)ctx->hl[0].D[c];
+  }
+  CK(cudaMalloc(&ctx->d_lk, ctx->N * sizeof(float)));
+  CK(cudaMalloc(&ctx->d_mD, ctx->N * sizeof(float)));
+  CK(cudaMalloc(&ctx->d_D32, ctx->N * sizeof(float)));
+  CK(cudaMemcpy(ctx->d_lk, lk.data(), ctx->N * sizeof(float), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_mD, mD.data(), ctx->N * sizeof(float), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_D32, D.data(), ctx->N * sizeof(float), cudaMemcpyHostToDevice));
+  return LT_OK;
+}
+
 static int solve_begin(lt_ctx* ctx, const Plan& P, SolveState& S, int* nl) {
   const lt_opts& o = ctx->opts;
   int rc = ensure_ws(ctx, P);
@@ -927,9 +1068,30 @@ static int solve_begin(lt_ctx* ctx, const Plan& P, SolveState& S, int* nl) {
   bt.nsh = P.nsh;
   bt.tol = o.tol;
   double itol = o.inner_tol > 0 ? o.inner_tol : 0.01 * o.tol;
+  // float32 solution vectors: the residual of a rounded u_j stalls near 2e-7 (relative), so
+  // refinement rounds below that would not make progress
+  if (o.precision == LT_PREC_FP32) itol = std::max(itol, 3e-7);
   bt.inner_tol2 = itol * itol;
   bt.inner_relax_max = o.inner_relax;
+  bt.tma_polls = (unsigned)o.tma_wait_polls;
+  bt.krylov = o.krylov;
+  bt.stop_rule = o.stop_rule;
+  bt.gs_passes = o.gram_schmidt;
+  bt.nk = P.Nk;
   cudaStream_t s = ctx->stream;
+  CK(cudaMemcpyAsync(const_cast<double*>(bt.wabs), P.wabs.data(), P.nsh * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (P.dense_b0 >= 0) {
+    // dense right-hand side M phi_0 / beta0 (Sec. 3: the second system [b, M phi_0]), df32 split
+    std::vector<float> hi(ctx->N), lo(ctx->N);
+    for (int64_t c = 0; c < ctx->N; ++c) {
+      const double x = ctx->hl[0].m[c] * ctx->phi0[c] / P.beta0;
+      hi[c] = (float)x;
+      lo[c] = (float)(x - (double)hi[c]);
+    }
+    CK(cudaMemcpyAsync(const_cast<float*>(bt.rhs_hi), hi.data(), ctx->N * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(const_cast<float*>(bt.rhs_lo), lo.data(), ctx->N * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));    // host vectors go out of scope
+  }
   // tables
   std::vector<double2> taug(2 * P.G);
   for (int i = 0; i < 2 * P.G; ++i) taug[i] = make_double2(P.tau[i].real(), P.tau[i].imag());
@@ -987,23 +1149,7 @@ static int solve_begin(lt_ctx* ctx, const Plan& P, SolveState& S, int* nl) {
       CK(cudaMalloc(&ctx->d_gn2, (size_t)P.nb * 64 * sizeof(float)));
       ctx->xin_cap = need;
     }
-    if (!ctx->d_lk) {
-      std::vector<float> lk(ctx->N), mD(ctx->N);
-      double mu = 0, var = 0;
-      for (int64_t c = 0; c < ctx->N; ++c) mu += std::log(ctx->kappa[c]);
-      mu /= ctx->N;
-      for (int64_t c = 0; c < ctx->N; ++c) var += std::pow(std::log(ctx->kappa[c]) - mu, 2);
-      double sd = std::sqrt(var / ctx->N);
-      if (sd < 1e-12) sd = 1.0;
-      for (int64_t c = 0; c < ctx->N; ++c) {
-        lk[c] = (float)((std::log(ctx->kappa[c]) - mu) / sd);
-        mD[c] = (float)(ctx->hl[0].m[c] / ctx->hl[0].D[c]);
-      }
-      CK(cudaMalloc(&ctx->d_lk, ctx->N * sizeof(float)));
-      CK(cudaMalloc(&ctx->d_mD, ctx->N * sizeof(float)));
-      CK(cudaMemcpy(ctx->d_lk, lk.data(), ctx->N * sizeof(float), cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(ctx->d_mD, mD.data(), ctx->N * sizeof(float), cudaMemcpyHostToDevice));
-    }
+    if ((rc = learned_tables(ctx))) return rc;
   }
   S = SolveState();
   S.act.assign(P.nb, 1);
@@ -1061,6 +1207,28 @@ static int solve_poll(lt_ctx* ctx, const Plan& P, SolveState& S) {
   return LT_OK;
 }
 
+// Which shifted systems count as solved.  Per-shift rule: the shift's true relative residual is at
+// most tol (without true residuals: it stopped on its projected residual).  Quadrature rule: the
+// shifts of one output time of a basis count together when their |w_k qhat(z_k)|-weighted true
+// residual is at most tol times the sum of the weights.
+static void converged_flags(const lt_ctx* ctx, const Plan& P, const std::vector<double>& tres, const int* conv,
+                            std::vector<char>& ok) {
+  const lt_opts& o = ctx->opts;
+  ok.assign(P.nsh, 0);
+  for (int i = 0; i < P.nsh; ++i) ok[i] = o.true_residual ? (tres[i] >= 0 && tres[i] <= o.tol) : (conv && conv[i] > 0);
+  if (o.stop_rule != LT_STOP_QUADRATURE || !o.true_residual) return;
+  for (int b = 0; b < P.nb; ++b)
+    for (int t0 = P.shift_off[b]; t0 < P.shift_off[b + 1]; t0 += P.Nk) {
+      double num = 0.0, den = 0.0;
+      for (int i = t0; i < t0 + P.Nk; ++i) {
+        num += P.wabs[i] * (tres[i] >= 0 ? tres[i] : INFINITY);
+        den += P.wabs[i];
+      }
+      const char v = num <= o.tol * den;
+      for (int i = t0; i < t0 + P.Nk; ++i) ok[i] = v;
+    }
+}
+
 static int solve_end(lt_ctx* ctx, const Plan& P, SolveState& S, std::vector<double>& true_res, lt_stats* st,
                      int* nl, bool need_x) {
   const lt_opts& o = ctx->opts;
@@ -1089,7 +1257,8 @@ static int solve_end(lt_ctx* ctx, const Plan& P, SolveState& S, std::vector<doub
     if (ws.x_elems < need) {
       // X buffers live in the workspace list
       if ((rc = dalloc(ctx, ws.allocs, &ws.X_hi, need))) { free_list(tmp); return rc; }
-      if ((rc = dalloc(ctx, ws.allocs, &ws.X_lo, need))) { free_list(tmp); return rc; }
+      ws.X_lo = nullptr;
+      if (o.precision == LT_PREC_FP64 && (rc = dalloc(ctx, ws.allocs, &ws.X_lo, need))) { free_list(tmp); return rc; }
       ws.x_elems = need;
     }
     lt::launch_xk(bt, ws.X_hi, ws.X_lo, s, pf);
@@ -1134,9 +1303,10 @@ static int solve_end(lt_ctx* ctx, const Plan& P, SolveState& S, std::vector<doub
     st->n_bases += P.nb;
     st->n_shift_solves += P.nsh;
     int conv_count = 0;
+    std::vector<char> okv;
+    converged_flags(ctx, P, true_res, conv.data(), okv);
     for (int i = 0; i < P.nsh; ++i) {
-      bool ok = o.true_residual ? (true_res[i] <= o.tol) : (conv[i] > 0);
-      conv_count += ok;
+      conv_count += okv[i];
       st->max_proj_residual = std::max(st->max_proj_residual, pres[i]);
       if (o.true_residual) st->max_true_residual = std::max(st->max_true_residual, true_res[i]);
     }
@@ -1148,6 +1318,10 @@ static int solve_end(lt_ctx* ctx, const Plan& P, SolveState& S, std::vector<doub
     }
     st->inner_cycles_total += cycles;
   }
+  ctx->last_group = P.group;
+  ctx->last_nit = nit;
+  ctx->last_tau = P.tau;
+  ctx->last_single = o.tau_policy == LT_TAU_SINGLE;
   return LT_OK;
 }
 
@@ -1193,7 +1367,7 @@ static int forward_impl(lt_ctx* ctx, int nt, const double* times, double* out, i
   CK(cudaSetDevice(ctx->device));
   stats_reset(st, ctx->opts.true_residual);
   Plan P;
-  make_plan(ctx, nt, times, ctx->src, P);
+  make_plan(ctx, nt, times, ctx->src, P, (int)ctx->src.size(), !ctx->phi0.empty());
   int nl = 0;
   CK(cudaEventRecord(ctx->ev0, ctx->stream));
   std::vector<double> tres;
@@ -1209,8 +1383,10 @@ static int forward_finish(lt_ctx* ctx, const Plan& P, const std::vector<double>&
   const int nt = P.nt;
   const int ns = (int)ctx->src.size(), nr = (int)ctx->rec.size();
   cudaStream_t s = ctx->stream;
-  // quadrature items (s, t) and weights w_k Q_s / z_k
-  std::vector<lt::QuadItem> items(ns * nt);
+  // quadrature items (s, t) and weights w_k qhat_s(z_k); with an initial state, items
+  // (dense, t) with weights beta0 w_k (its basis solves for M phi_0 / beta0)
+  const int dense_q0 = P.dense_b0 >= 0 ? ns * nt : -1;
+  std::vector<lt::QuadItem> items(ns * nt + (dense_q0 >= 0 ? nt : 0));
   std::vector<double2> wq(P.nsh);
   for (int si = 0; si < ns; ++si)
     for (int t = 0; t < nt; ++t) {
@@ -1218,7 +1394,17 @@ static int forward_finish(lt_ctx* ctx, const Plan& P, const std::vector<double>&
       int sh0 = shift_of(P, b, t);
       items[si * nt + t] = {b, sh0, P.Nk};
       for (int k = 0; k < P.Nk; ++k) {
-        cplx v = P.w[t][k] * ctx->Q[si] / P.z[t][k];
+        cplx v = P.w[t][k] * qhat(ctx, si, P.z[t][k]);
+        wq[sh0 + k] = make_double2(v.real(), v.imag());
+      }
+    }
+  if (dense_q0 >= 0)
+    for (int t = 0; t < nt; ++t) {
+      int b = P.dense_b0 + P.tgroup[t];
+      int sh0 = shift_of(P, b, t);
+      items[dense_q0 + t] = {b, sh0, P.Nk};
+      for (int k = 0; k < P.Nk; ++k) {
+        cplx v = P.w[t][k] * P.beta0;
         wq[sh0 + k] = make_double2(v.real(), v.imag());
       }
     }
@@ -1239,8 +1425,8 @@ static int forward_finish(lt_ctx* ctx, const Plan& P, const std::vector<double>&
   CK(cudaMemcpyAsync(d_wq, wq.data(), wq.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
   if (nr) CK(cudaMemcpyAsync(d_rc, ctx->rec.data(), nr * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   lt::launch_quad_coef(ctx->ws.bt, d_items, (int)items.size(), d_wq, d_C, s);
-  if (fields) lt::launch_fields(ctx->ws.bt, d_items, d_C, (int)items.size(), d_out, s);
-  else lt::launch_measure(ctx->ws.bt, d_items, d_C, ns, nr, nt, d_rc, d_out, s);
+  if (fields) lt::launch_fields(ctx->ws.bt, d_items, d_C, ns * nt, d_out, s, nt, dense_q0);
+  else lt::launch_measure(ctx->ws.bt, d_items, d_C, ns, nr, nt, d_rc, d_out, s, dense_q0);
   nl += 2;
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev1, s));
@@ -1251,10 +1437,12 @@ static int forward_finish(lt_ctx* ctx, const Plan& P, const std::vector<double>&
     cudaEventElapsedTime(&st->ms_total, ctx->ev0, ctx->ev1);
     st->kernel_launches = nl;
   }
-  bool all = true;
-  for (size_t i = 0; i < tres.size(); ++i)
-    if (ctx->opts.true_residual && !(tres[i] <= ctx->opts.tol)) all = false;
-  if (!all) return fail(ctx, LT_ERR_NOT_CONVERGED, "some shifted systems did not reach tol");
+  if (ctx->opts.true_residual) {
+    std::vector<char> ok;
+    converged_flags(ctx, P, tres, nullptr, ok);
+    for (char c : ok)
+      if (!c) return fail(ctx, LT_ERR_NOT_CONVERGED, "some shifted systems did not reach tol");
+  }
   return LT_OK;
 }
 
@@ -1292,7 +1480,7 @@ extern "C" int lt_forward_batch(int n, lt_ctx* const* ctxs, const int* nt, const
     lt_ctx* ctx = ctxs[i];
     CK(cudaSetDevice(ctx->device));
     stats_reset(stats ? &stats[i] : nullptr, ctx->opts.true_residual);
-    make_plan(ctx, nt[i], times[i], ctx->src, P[i]);
+    make_plan(ctx, nt[i], times[i], ctx->src, P[i], (int)ctx->src.size(), !ctx->phi0.empty());
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     int rc = solve_begin(ctx, P[i], S[i], &nl[i]);
     if (rc) return rc;
@@ -1334,26 +1522,51 @@ extern "C" int lt_forward_batch(int n, lt_ctx* const* ctxs, const int* nt, const
 // Adjoint path (Sec. 5.2): one batch of bases for the sources and the
 // receivers, solutions per shift, then the sensitivity assembly (mode 0: J,
 // mode 1: vector-Jacobian product).  h (optional) = forward measurements.
-static int adjoint_impl(lt_ctx* ctx, int nt, const double* times, double* J, const double* g, double* grad,
-                        double* h, int on_device, int mode, lt_stats* st) {
+static int adjoint_check(lt_ctx* ctx, int nt, const double* times, double* J, const double* g, double* grad,
+                         int mode) {
   if (!ctx) return LT_ERR_INVALID_ARG;
   int rc = check_times(ctx, nt, times);
   if (rc) return rc;
   if (ctx->src.empty() || ctx->rec.empty()) return fail(ctx, LT_ERR_STATE, "sources and receivers must be set");
   if (mode == 0 && !J) return fail(ctx, LT_ERR_INVALID_ARG, "J is null");
   if (mode == 1 && (!g || !grad)) return fail(ctx, LT_ERR_INVALID_ARG, "g and grad are required");
-  CK(cudaSetDevice(ctx->device));
-  stats_reset(st, ctx->opts.true_residual);
-  const int ns = (int)ctx->src.size(), nr = (int)ctx->rec.size();
+  if (!ctx->phi0.empty())
+    return fail(ctx, LT_ERR_STATE, "the adjoint Jacobian is implemented for phi_0 = 0; clear the initial state "
+                                   "(lt_set_initial_state(ctx, NULL))");
+  return LT_OK;
+}
+
+// the adjoint plan: one basis per (source or receiver, time group)
+static void adjoint_plan(lt_ctx* ctx, int nt, const double* times, Plan& P) {
   std::vector<int64_t> rhs(ctx->src);
   rhs.insert(rhs.end(), ctx->rec.begin(), ctx->rec.end());
+  make_plan(ctx, nt, times, rhs, P, (int)ctx->src.size(), false);
+}
+
+static int adjoint_finish(lt_ctx* ctx, const Plan& P, const std::vector<double>& tres, double* J, const double* g,
+                          double* grad, double* h, int on_device, int mode, lt_stats* st, int nl);
+
+static int adjoint_impl(lt_ctx* ctx, int nt, const double* times, double* J, const double* g, double* grad,
+                        double* h, int on_device, int mode, lt_stats* st) {
+  int rc = adjoint_check(ctx, nt, times, J, g, grad, mode);
+  if (rc) return rc;
+  CK(cudaSetDevice(ctx->device));
+  stats_reset(st, ctx->opts.true_residual);
   Plan P;
-  make_plan(ctx, nt, times, rhs, P);
+  adjoint_plan(ctx, nt, times, P);
   int nl = 0;
   CK(cudaEventRecord(ctx->ev0, ctx->stream));
   std::vector<double> tres;
   rc = run_solves(ctx, P, tres, st, &nl, true);
   if (rc) return rc;
+  return adjoint_finish(ctx, P, tres, J, g, grad, h, on_device, mode, st, nl);
+}
+
+// sensitivity assembly (J or the VJP) and the measurements, after the solves of an adjoint plan
+static int adjoint_finish(lt_ctx* ctx, const Plan& P, const std::vector<double>& tres, double* J, const double* g,
+                          double* grad, double* h, int on_device, int mode, lt_stats* st, int nl) {
+  int rc = LT_OK;
+  const int ns = (int)ctx->src.size(), nr = (int)ctx->rec.size(), nt = P.nt;
   cudaStream_t s = ctx->stream;
   const int Nk = P.Nk;
   std::vector<int> sh_src(nt * ns), sh_rec(nt * nr);
@@ -1362,7 +1575,7 @@ static int adjoint_impl(lt_ctx* ctx, int nt, const double* times, double* J, con
     for (int si = 0; si < ns; ++si) {
       sh_src[t * ns + si] = shift_of(P, si * P.G + P.tgroup[t], t);
       for (int k = 0; k < Nk; ++k) {
-        cplx v = P.w[t][k] * ctx->Q[si] / P.z[t][k];
+        cplx v = P.w[t][k] * qhat(ctx, si, P.z[t][k]);
         omega[((size_t)t * ns + si) * Nk + k] = make_double2(v.real(), v.imag());
       }
     }
@@ -1445,9 +1658,75 @@ static int adjoint_impl(lt_ctx* ctx, int nt, const double* times, double* J, con
     cudaEventElapsedTime(&st->ms_total, ctx->ev0, ctx->ev1);
     st->kernel_launches = nl;
   }
-  for (double r : tres)
-    if (ctx->opts.true_residual && !(r <= ctx->opts.tol)) return fail(ctx, LT_ERR_NOT_CONVERGED, "some shifted systems did not reach tol");
+  if (ctx->opts.true_residual) {
+    std::vector<char> ok;
+    converged_flags(ctx, P, tres, nullptr, ok);
+    for (char c : ok)
+      if (!c) return fail(ctx, LT_ERR_NOT_CONVERGED, "some shifted systems did not reach tol");
+  }
   return LT_OK;
+}
+
+extern "C" int lt_adjoint_batch(int n, lt_ctx* const* ctxs, const int* nt, const double* const* times,
+                                double* const* J, const double* const* g, double* const* grad, double* const* h,
+                                lt_stats* stats) {
+  if (n < 1 || !ctxs || !nt || !times) return LT_ERR_INVALID_ARG;
+  std::vector<int> mode(n);
+  for (int i = 0; i < n; ++i) {
+    lt_ctx* ctx = ctxs[i];
+    if (!ctx) return LT_ERR_INVALID_ARG;
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == ctx) return fail(ctx, LT_ERR_INVALID_ARG, "context %d appears twice in the batch", i);
+    mode[i] = (J && J[i]) ? 0 : 1;
+    int rc = adjoint_check(ctx, nt[i], times[i], J ? J[i] : nullptr, g ? g[i] : nullptr, grad ? grad[i] : nullptr,
+                           mode[i]);
+    if (rc) return rc;
+  }
+  std::vector<Plan> P(n);
+  std::vector<SolveState> S(n);
+  std::vector<int> nl(n, 0);
+  for (int i = 0; i < n; ++i) {
+    lt_ctx* ctx = ctxs[i];
+    CK(cudaSetDevice(ctx->device));
+    stats_reset(stats ? &stats[i] : nullptr, ctx->opts.true_residual);
+    adjoint_plan(ctx, nt[i], times[i], P[i]);
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    int rc = solve_begin(ctx, P[i], S[i], &nl[i]);
+    if (rc) return rc;
+  }
+  for (;;) {
+    bool any = false;
+    for (int i = 0; i < n; ++i) {
+      if (S[i].done) continue;
+      lt_ctx* ctx = ctxs[i];
+      CK(cudaSetDevice(ctx->device));
+      int rc = solve_launch(ctx, S[i], ctx->opts.check_every, &nl[i]);
+      if (rc) return rc;
+      any = true;
+    }
+    if (!any) break;
+    for (int i = 0; i < n; ++i) {
+      if (S[i].done) continue;
+      lt_ctx* ctx = ctxs[i];
+      CK(cudaSetDevice(ctx->device));
+      int rc = solve_poll(ctx, P[i], S[i]);
+      if (rc) return rc;
+    }
+  }
+  int worst = LT_OK;
+  for (int i = 0; i < n; ++i) {
+    lt_ctx* ctx = ctxs[i];
+    CK(cudaSetDevice(ctx->device));
+    std::vector<double> tres;
+    lt_stats* st = stats ? &stats[i] : nullptr;
+    int rc = solve_end(ctx, P[i], S[i], tres, st, &nl[i], true);
+    if (rc) return rc;
+    rc = adjoint_finish(ctx, P[i], tres, mode[i] == 0 ? J[i] : nullptr, mode[i] == 1 ? g[i] : nullptr,
+                        mode[i] == 1 ? grad[i] : nullptr, h ? h[i] : nullptr, 1, mode[i], st, nl[i]);
+    if (rc == LT_ERR_NOT_CONVERGED) worst = rc;
+    else if (rc) return rc;
+  }
+  return worst;
 }
 
 extern "C" int lt_adjoint_jacobian(lt_ctx* ctx, int nt, const double* times, double* J, lt_stats* st) {
@@ -1506,6 +1785,7 @@ extern "C" int lt_precond_apply(lt_ctx* ctx, int nimg, const double* tau, const 
   mg.npre = ctx->opts.mg_pre; mg.npost = ctx->opts.mg_post; mg.tile = ctx->opts.mg_tile; mg.tma = ctx->opts.mg_tma;
   bt.nb = nimg;
   bt.rounds = 0;
+  bt.tma_polls = (unsigned)ctx->opts.tma_wait_polls;
   bt.coarse_direct = ctx->mg.coarse_direct;
   std::vector<int> ones(nimg, 1), slots(nimg);
   std::vector<double> big(nimg, 1e300), zero(nimg, 0.0);
@@ -1529,11 +1809,86 @@ extern "C" int lt_precond_apply(lt_ctx* ctx, int nimg, const double* tau, const 
   const lt::Level& L0 = mg.h_levels[0];
   CK(cudaMemcpyAsync(L0.f, r, (size_t)nimg * L0.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemsetAsync(L0.u, 0, (size_t)nimg * L0.N * sizeof(float2), s));
+  CK(cudaMemsetAsync(bt.work, 0, lt::kWorkSlots * sizeof(unsigned long long), s));
   int nl = 0;
   for (int c = 0; c < cycles; ++c)
     if (lt::launch_vcycle(mg, bt, 0, s, &nl, nullptr)) return fail(ctx, LT_ERR_CUDA, "V-cycle launch failed");
   CK(cudaMemcpyAsync(e, L0.u, (size_t)nimg * L0.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  unsigned long long flag = 0;
+  CK(cudaMemcpyAsync(&flag, bt.work + lt::kTimeoutSlot, sizeof(flag), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (flag) return fail(ctx, LT_ERR_TIMEOUT, "a bulk tensor copy did not complete within its bounded wait");
+  return LT_OK;
+}
+
+// ------------------------------------------------------------------ learned preconditioner: data
+extern "C" int lt_contour_nodes(double t, int Nz, int project, double* z, double* w) {
+  if (!(t > 0.0) || !std::isfinite(t) || Nz < 4 || Nz > 128 || (Nz & 1) || !z) return LT_ERR_INVALID_ARG;
+  std::vector<cplx> zz, ww;
+  talbot_half(t, Nz, zz, ww);
+  for (int k = 0; k < Nz / 2; ++k) {
+    cplx v = zz[k];
+    if (project) v = cplx(std::max(v.real(), 0.0), v.imag());
+    z[2 * k] = v.real();
+    z[2 * k + 1] = v.imag();
+    if (w) {
+      w[2 * k] = ww[k].real();
+      w[2 * k + 1] = ww[k].imag();
+    }
+  }
+  return LT_OK;
+}
+
+extern "C" int lt_learned_pairs(lt_ctx* ctx, int nimg, const double* tau, const float* r, int cycles, float* x,
+                                float* y) {
+  if (!ctx) return LT_ERR_INVALID_ARG;
+  if (!ctx->have_grid) return fail(ctx, LT_ERR_STATE, "lt_setup_grid must come first");
+  if (nimg < 1 || !tau || !r || !x || !y) return fail(ctx, LT_ERR_INVALID_ARG, "nimg >= 1 and non-null buffers");
+  CK(cudaSetDevice(ctx->device));
+  int rc = learned_tables(ctx);
+  if (rc) return rc;
+  std::vector<void*> tmp;
+  float2* e = nullptr;
+  double2* dtau = nullptr;
+  double* acc = nullptr;
+  if ((rc = dalloc(ctx, tmp, &e, (size_t)nimg * ctx->N)) || (rc = dalloc(ctx, tmp, &dtau, nimg)) ||
+      (rc = dalloc(ctx, tmp, &acc, 2 * (size_t)nimg))) {
+    free_list(tmp);
+    return rc;
+  }
+  rc = lt_precond_apply(ctx, nimg, tau, r, (float*)e, cycles);
+  if (rc) { free_list(tmp); return rc; }
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemcpyAsync(dtau, tau, nimg * sizeof(double2), cudaMemcpyHostToDevice, s));
+  learned_pair_features(nimg, (int)ctx->N, (const float2*)r, e, dtau, ctx->d_lk, ctx->d_mD, ctx->d_D32, acc, x, y, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  free_list(tmp);
+  return LT_OK;
+}
+
+extern "C" int lt_krylov_vectors(lt_ctx* ctx, int max_n, float* r, double* tau, int* n_out) {
+  if (!ctx || !n_out) return LT_ERR_INVALID_ARG;
+  *n_out = 0;
+  if (ctx->last_nit.empty() || !ctx->ws.bt.V_hi) return fail(ctx, LT_ERR_STATE, "no forward solve to take vectors from");
+  if (max_n < 0 || (max_n > 0 && (!r || !tau))) return fail(ctx, LT_ERR_INVALID_ARG, "max_n >= 0 and non-null buffers");
+  CK(cudaSetDevice(ctx->device));
+  const lt::Batch& bt = ctx->ws.bt;
+  const size_t N = (size_t)ctx->N;
+  static const int pat_flex[5] = {0, 0, 0, 1, 1};
+  int n = 0;
+  cudaStream_t s = ctx->stream;
+  for (size_t b = 0; b < ctx->last_nit.size() && n < max_n; ++b)
+    for (int j = 0; j < ctx->last_nit[b] && n < max_n; ++j, ++n) {
+      const float2* v = bt.V_hi + (b * (size_t)(bt.maxit + 1) + j) * N;
+      CK(cudaMemcpyAsync(r + (size_t)n * N * 2, v, N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+      const int slot = ctx->last_single ? 0 : pat_flex[j % 5];
+      const cplx t = ctx->last_tau[2 * ctx->last_group[b] + slot];
+      tau[2 * n] = t.real();
+      tau[2 * n + 1] = t.imag();
+    }
+  CK(cudaStreamSynchronize(s));
+  *n_out = n;
   return LT_OK;
 }
 
@@ -1560,8 +1915,10 @@ static size_t noalloc_need(const lt_ctx* ctx, const Plan& P) {
   const size_t ns = ctx->src.size(), nr = ctx->rec.size(), nt = P.nt;
   size_t b = 0;
   auto add = [&](size_t n, size_t sz) { b += round256(std::max<size_t>(n, 1) * sz); };
-  add(nb * (M + 1) * N, 8); add(nb * (M + 1) * N, 8); add(nb * M * N, 8); add(nb * M * N, 8);
-  add(nb * N, 8); add(nb * N, 8);
+  const bool df = o.precision == LT_PREC_FP64;   // lo planes only in df32
+  add(nb * (M + 1) * N, 8); add(nb * M * N, 8); add(nb * N, 8);
+  if (df) { add(nb * (M + 1) * N, 8); add(nb * M * N, 8); add(nb * N, 8); }
+  add(nsh, 8); add(N, 4); add(N, 4);
   add(2 * G, 16); add(nb, 4); add(5, 4); add(nb, 16); add(nb, 4);
   add(nb * (R + 1), 8); add(nb * 2 * (M + 1), 16); add(nb * M * (M + 1), 16);
   add(nb, 8); add(nb, 4); add(nb, 4); add(nb, 8); add(nb, 8);
@@ -1572,8 +1929,9 @@ static size_t noalloc_need(const lt_ctx* ctx, const Plan& P) {
   if (ctx->inner.ok) add(nb * N, 16);
   for (int l = 0; l < ctx->mg.nlev; ++l) { add(nb * ctx->mg.h_levels[l].N, 8); add(nb * ctx->mg.h_levels[l].N, 8); }
   add(nsh, 4);
-  if (o.true_residual) { add(nsh * N, 8); add(nsh * N, 8); add(nsh, 8); }
-  add(ns * nt, sizeof(lt::QuadItem)); add(nsh, 16); add(ns * nt * M, 16); add(std::max<size_t>(nr, 1), 8);
+  if (o.true_residual) { add(nsh * N, 8); if (df) add(nsh * N, 8); add(nsh, 8); }
+  const size_t nitems = ns * nt + (P.dense_b0 >= 0 ? nt : 0);
+  add(nitems, sizeof(lt::QuadItem)); add(nsh, 16); add(nitems * M, 16); add(std::max<size_t>(nr, 1), 8);
   return b;
 }
 
@@ -1599,7 +1957,7 @@ extern "C" int lt_forward_noalloc(lt_ctx* ctx, int nt, const double* times, doub
     base = g_noalloc_ptr[ctx->device];
   }
   Plan P;
-  make_plan(ctx, nt, times, ctx->src, P);
+  make_plan(ctx, nt, times, ctx->src, P, (int)ctx->src.size(), !ctx->phi0.empty());
   const size_t need = noalloc_need(ctx, P);
   if (need > LT_NOALLOC_SCRATCH_BYTES)
     return fail(ctx, LT_ERR_INVALID_ARG,
@@ -1618,13 +1976,18 @@ extern "C" int lt_forward_noalloc(lt_ctx* ctx, int nt, const double* times, doub
   ctx->arena_cap = LT_NOALLOC_SCRATCH_BYTES;
   ctx->arena_off = 0;
   rc = forward_impl(ctx, nt, times, h, 1, 0, st);
+  // an error return can leave kernels of this call queued on the caller's stream; they read the
+  // level table that points into the static region, so let them finish before it is restored
+  cudaError_t es = cudaStreamSynchronize(ctx->stream);
   ctx->arena_base = nullptr;
   ctx->arena_cap = ctx->arena_off = 0;
   ctx->opts.timing_class = saved_timing;
   ctx->ws = std::move(saved_ws);
+  ctx->last_nit.clear();          // the bases of this call lived in the static region
   memcpy(ctx->mg.h_levels, saved_levels, sizeof(saved_levels));
   cudaError_t e = cudaMemcpy(ctx->mg.d_levels, ctx->mg.h_levels, sizeof(lt::Level) * ctx->mg.nlev,
                              cudaMemcpyHostToDevice);
   if (e != cudaSuccess && rc == LT_OK) return fail(ctx, LT_ERR_CUDA, "restoring level table: %s", cudaGetErrorString(e));
+  if (es != cudaSuccess && rc == LT_OK) return fail(ctx, LT_ERR_CUDA, "stream synchronize: %s", cudaGetErrorString(es));
   return rc;
 }

@@ -7,6 +7,10 @@
 namespace lt {
 
 constexpr int kMaxLevels = 16;
+
+// offset into a df32 lo plane that may be absent (reduced precision: null stays null)
+template <class T>
+__host__ __device__ __forceinline__ T* lo_at(T* p, size_t off) { return p ? p + off : nullptr; }
 constexpr int kCoarseCells = 1024;     // levels at or below this size run in one CTA per basis
 constexpr int kDirectCells = 256;      // coarsest level solved by a dense inverse if at most this size
 constexpr int kCoarseSweeps = 24;      // RB-GS sweeps at the coarsest level when it is not solved directly
@@ -72,6 +76,16 @@ struct Batch {
   int coarse_direct;               // 1 if coarse_inv is valid
   unsigned long long* work;        // [kWorkSlots] cells processed per kernel class (live roofline), flags
   int* jdev;                       // current outer iteration (shared by all bases of the batch)
+  unsigned tma_polls;              // mbarrier polls of a TMA tile load before it counts as timed out
+  int krylov;                      // 0: GMRES-Sh coefficients, 1: FOM-Sh (Algorithm 1)
+  int stop_rule;                   // 0: per shift; 1: per output time, quadrature-weighted residual
+  int nk;                          // shifts per output time (a basis's shifts are nk per time, contiguous)
+  int gs_passes;                   // Gram-Schmidt: 2 = CGS2 with float32 dots, 1 = one pass with df32 dots
+  const double* wabs;              // [nsh] |w_k qhat(z_k)| of each shift (quadrature stopping rule)
+  // right-hand side of the bases whose rhs_cell is negative: one dense vector of unit 2-norm
+  // (M phi_0 / ||M phi_0||), df32 real
+  const float* rhs_hi;
+  const float* rhs_lo;
 };
 
 // kernel classes for the live per-kernel timing and work counters

@@ -59,10 +59,12 @@ struct QuadItem {            // one (source-or-receiver, time) pair
 };
 void launch_quad_coef(const Batch& bt, const QuadItem* items, int nitems, const double2* wq, double2* C,
                       cudaStream_t st);
-// h[s][r][t]: item index q = s*nt + t
+// h[s][r][t]: item index q = s*nt + t; dense_q0 >= 0: items dense_q0 + t (the initial-state basis)
+// are added to every source's measurements (fields)
 void launch_measure(const Batch& bt, const QuadItem* items, const double2* C, int ns, int nr, int nt,
-                    const int64_t* rcells, double* h, cudaStream_t st);
-void launch_fields(const Batch& bt, const QuadItem* items, const double2* C, int nitems, double* phi, cudaStream_t st);
+                    const int64_t* rcells, double* h, cudaStream_t st, int dense_q0 = -1);
+void launch_fields(const Batch& bt, const QuadItem* items, const double2* C, int nitems, double* phi, cudaStream_t st,
+                   int nt = 1, int dense_q0 = -1);
 
 // -------- adjoint.cu
 struct SensLaunch {
@@ -92,4 +94,6 @@ struct lt_unet;
 int learned_prepare(lt_unet* u, int nb, int ny, int nx);
 void learned_guess(lt_unet* u, const lt::Batch& bt, const lt::Level& L0, int round, const float* lk, const float* mD,
                    float* xin, float* gnorm2, cudaStream_t q);
+void learned_pair_features(int nimg, int N, const float2* r, const float2* e, const double2* tau, const float* lk,
+                           const float* mD, const float* D, double* acc, float* x, float* y, cudaStream_t q);
 

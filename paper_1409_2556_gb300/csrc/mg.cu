@@ -399,9 +399,14 @@ __device__ __forceinline__ void tma_3d(void* dst, const CUtensorMap* tm, int x, 
 struct TmaMaps { CUtensorMap u, f, te, tn, d, m; };
 
 // stage u, f, Te, Tn, D, m of the region into shared memory and build the inverse diagonal.
-// Returns false (and raises bt.work[kTimeoutSlot] as an error flag) if the copy never completed.
+// Returns false (and raises bt.work[kTimeoutSlot] as an error flag) if the copy did not complete
+// within bt.tma_polls polls of the mbarrier.  Thread 0 alone polls and publishes the outcome in
+// shared memory, so every thread of the block takes the same branch.  On a timeout thread 0
+// keeps polling for up to kTmaSpin more tries before the block returns, so that copies still in
+// flight land in shared memory that the block still owns.
 __device__ __forceinline__ bool tile_load_tma(const TmaMaps& M, Tile2D& T, float* Ds, float* ms, uint64_t* bar,
                                               int gx0, int gy0, int b, int RX, int RY, float2 tau, const Batch& bt) {
+  __shared__ int s_landed;
   const int RN = RX * RY;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
@@ -417,16 +422,18 @@ __device__ __forceinline__ bool tile_load_tma(const TmaMaps& M, Tile2D& T, float
     tma_2d(T.tn, &M.tn, gx0, gy0, bar);
     tma_2d(Ds, &M.d, gx0, gy0, bar);
     tma_2d(ms, &M.m, gx0, gy0, bar);
+    int landed = 0;
+    for (unsigned it = 0; it < bt.tma_polls; ++it)
+      if (mbar_try_wait(bar, 0)) { landed = 1; break; }
+    if (!landed) {
+      atomicAdd(&bt.work[kTimeoutSlot], 1ull);
+      for (unsigned it = 0; it < kTmaSpin; ++it)    // drain: let the copies in flight land
+        if (mbar_try_wait(bar, 0)) break;
+    }
+    s_landed = landed;
   }
-  bool done = false;
-  for (unsigned it = 0; it < kTmaSpin; ++it)
-    if (mbar_try_wait(bar, 0)) { done = true; break; }
-  if (!done) {
-    if (threadIdx.x == 0) atomicAdd(&bt.work[kTimeoutSlot], 1ull);
-    for (unsigned it = 0; it < kTmaSpin; ++it)      // give copies in flight a second bounded chance to land
-      if (mbar_try_wait(bar, 0)) break;
-    return false;
-  }
+  __syncthreads();
+  if (!s_landed) return false;
   for (int idx = threadIdx.x; idx < RN; idx += blockDim.x) {
     float dd = Ds[idx], mm = ms[idx];
     float2 dg = make_float2(dd + tau.x * mm, tau.y * mm);

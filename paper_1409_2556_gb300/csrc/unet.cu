@@ -685,7 +685,54 @@ __global__ void k_net_scale(Batch bt, Level L0, int round, const float* gn) {
   if (c == 0 && keep) atomicAdd(&bt.work[KC_OTHER], 1ull);   // guesses kept (statistics)
 }
 
+// ---- training pairs (residual r, multigrid solution e of (K + tau M) e = r) -> (input, target)
+// acc[img] += sum_c |v_c|^2 (scale_c = 1) or |scale_c v_c|^2
+__global__ void k_img_norm2(const float2* v, const float* scale, int N, double* acc) {
+  const int img = blockIdx.y;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  float q = 0.f;
+  if (c < N) {
+    float2 a = v[(size_t)img * N + c];
+    float f = scale ? scale[c] : 1.f;
+    q = f * f * (a.x * a.x + a.y * a.y);
+  }
+  for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&acc[img], (double)q);
+}
+
+// network input (the same channels as k_net_pack) and target: D e at unit RMS
+__global__ void k_pair_pack(const float2* r, const float2* e, const double2* tau, const float* lk, const float* mD,
+                            const float* D, const double* rn2, const double* en2, int N, float* x, float* y) {
+  const int img = blockIdx.y;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  const size_t i = (size_t)img * N + c;
+  const float rs = (float)sqrt(rn2[img] / N), es = (float)sqrt(en2[img] / N);
+  const float ir = rs > 0.f ? 1.f / rs : 0.f, ie = es > 0.f ? 1.f / es : 0.f;
+  const float2 f = r[i], u = e[i];
+  const double2 t = tau[img];
+  float* o = x + i * kInChannels;
+  o[0] = f.x * ir;
+  o[1] = f.y * ir;
+  o[2] = lk[c];
+  o[3] = (float)t.x * mD[c];
+  o[4] = (float)t.y * mD[c];
+  y[2 * i] = D[c] * u.x * ie;
+  y[2 * i + 1] = D[c] * u.y * ie;
+}
+
 }  // namespace lt
+
+// inputs x [nimg][N][5] and targets y [nimg][N][2] of training pairs from residuals r and their
+// multigrid solutions e (all DEVICE); tau: DEVICE [nimg]; lk, mD, D: DEVICE [N]; acc: DEVICE [2 nimg]
+void learned_pair_features(int nimg, int N, const float2* r, const float2* e, const double2* tau, const float* lk,
+                           const float* mD, const float* D, double* acc, float* x, float* y, cudaStream_t q) {
+  cudaMemsetAsync(acc, 0, 2 * (size_t)nimg * sizeof(double), q);
+  dim3 g((N + 255) / 256, nimg);
+  lt::k_img_norm2<<<g, 256, 0, q>>>(r, nullptr, N, acc);
+  lt::k_img_norm2<<<g, 256, 0, q>>>(e, D, N, acc + nimg);
+  lt::k_pair_pack<<<g, 256, 0, q>>>(r, e, tau, lk, mD, D, acc, acc + nimg, N, x, y);
+}
 
 // workspace for nb images of ny x nx (call before graph capture)
 int learned_prepare(lt_unet* u, int nb, int ny, int nx) {

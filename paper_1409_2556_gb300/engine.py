@@ -99,6 +99,28 @@ class Engine:
         self._check(self.lib.lt_set_sources(self.h, c.size, _ptr(c), _ptr(q)), "lt_set_sources")
         self.ns = c.size
 
+    def set_source_rates(self, terms):
+        """terms: per source (amplitudes, decay rates) of q_s(t) = sum_j a_j exp(-lambda_j t);
+        None restores the constant rates."""
+        if terms is None:
+            self._check(self.lib.lt_set_source_rates(self.h, 0, None, None, None), "lt_set_source_rates")
+            return
+        n = np.ascontiguousarray([len(np.atleast_1d(a)) for a, _ in terms], dtype=np.int32)
+        a = _f64(np.concatenate([np.atleast_1d(a) for a, _ in terms]))
+        lam = _f64(np.concatenate([np.atleast_1d(l) for _, l in terms]))
+        self._check(self.lib.lt_set_source_rates(self.h, len(terms), _ptr(n), _ptr(a), _ptr(lam)),
+                    "lt_set_source_rates")
+
+    def set_initial_state(self, phi0):
+        """phi0: float64 [ncell] initial head, or None for phi(0) = 0."""
+        if phi0 is None:
+            self._check(self.lib.lt_set_initial_state(self.h, None), "lt_set_initial_state")
+            return
+        p = _f64(phi0).ravel()
+        if p.size != self.ncell:
+            raise ValueError(f"phi0 needs {self.ncell} entries")
+        self._check(self.lib.lt_set_initial_state(self.h, _ptr(p)), "lt_set_initial_state")
+
     def set_receivers(self, cells):
         c = _i64(cells)
         self._check(self.lib.lt_set_receivers(self.h, c.size, _ptr(c)), "lt_set_receivers")
@@ -119,6 +141,10 @@ class Engine:
         self.setup_grid(prob.kappa, prob.Ss, prob.dx, prob.dy, prob.dz, prob.bc)
         self.set_sources(prob.src_cells, prob.Q)
         self.set_receivers(prob.rec_cells)
+        if getattr(prob, "rate_terms", None) is not None:
+            self.set_source_rates(prob.rate_terms)
+        if getattr(prob, "phi0", None) is not None:
+            self.set_initial_state(prob.phi0)
         o = dict(Nz=prob.Nz, tol=prob.tol, groups=prob.groups)
         o.update(opts)
         self.set_options(**o)

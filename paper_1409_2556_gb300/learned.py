@@ -2,7 +2,8 @@
 training-pair generation with the library's own multigrid, and training.
 
 Everything numerical runs in liblt.so (tensor-core U-Net kernels, Adam,
-multigrid); this module prepares tensors and drives the loop.
+multigrid, the contour nodes, the network's input channels and targets);
+this module draws synthetic residuals, moves tensors and drives the loop.
 """
 from __future__ import annotations
 
@@ -79,9 +80,9 @@ class UNet:
 
 
 def precond_apply(engine: Engine, tau, r, cycles: int):
-    """e = multigrid solve of (K + tau_i M) e_i = r_i (r: CUDA complex64 [n, ncell])."""
+    """e = multigrid solve of (K + tau_i M) e_i = r_i (r: CUDA complex64 [n, ncell] viewed as float32 pairs)."""
     import torch
-    t = np.ascontiguousarray(np.asarray([[complex(v).real, complex(v).imag] for v in tau], dtype=np.float64))
+    t = _tau_array(tau)
     e = torch.zeros_like(r)
     rc = engine.lib.lt_precond_apply(engine.h, len(t), t.ctypes.data_as(C.c_void_p), C.c_void_p(r.data_ptr()),
                                      C.c_void_p(e.data_ptr()), int(cycles))
@@ -89,58 +90,56 @@ def precond_apply(engine: Engine, tau, r, cycles: int):
     return e
 
 
-def features(prob, r, tau):
-    """Network input [n, ny, nx, 5] and per-image scale s for residuals r (complex [n, ncell]) of
-    shifts tau (n values): Re r/s, Im r/s, normalised log kappa, Re(tau) m/D, Im(tau) m/D."""
-    import torch
-    n = r.shape[0]
-    ny, nx = prob.ny, prob.nx
-    dev = r.device
-    s = torch.sqrt(torch.mean(torch.abs(r) ** 2, dim=1)).clamp_min(1e-30)
-    lk = np.log(prob.kappa[0])
-    lk = (lk - lk.mean()) / max(lk.std(), 1e-12)
-    D, m = operator_diag(prob)
-    x = torch.zeros((n, ny, nx, IN_CHANNELS), dtype=torch.float32, device=dev)
-    rr = (r / s[:, None]).reshape(n, ny, nx)
-    x[..., 0] = rr.real
-    x[..., 1] = rr.imag
-    x[..., 2] = torch.tensor(lk, dtype=torch.float32, device=dev)[None]
-    ratio = torch.tensor((m / D).reshape(ny, nx), dtype=torch.float32, device=dev)
-    tau_t = torch.tensor(np.asarray(tau, dtype=np.complex128), device=dev)
-    x[..., 3] = tau_t.real.float()[:, None, None] * ratio[None]
-    x[..., 4] = tau_t.imag.float()[:, None, None] * ratio[None]
-    return x, s
+def _tau_array(tau):
+    return np.ascontiguousarray(np.asarray([[complex(v).real, complex(v).imag] for v in tau], dtype=np.float64))
 
 
-def operator_diag(prob):
-    """Diagonal D (sum of face transmissibilities incl. Dirichlet) and m of the 2D FV operator."""
-    k = prob.kappa[0]
-    ny, nx = k.shape
-    ax, ay = prob.dy * prob.dz / prob.dx, prob.dx * prob.dz / prob.dy
-    harm = lambda a, b: 2 * a * b / (a + b)
-    D = np.zeros((ny, nx))
-    tx = ax * harm(k[:, :-1], k[:, 1:])
-    ty = ay * harm(k[:-1, :], k[1:, :])
-    D[:, :-1] += tx; D[:, 1:] += tx; D[:-1, :] += ty; D[1:, :] += ty
-    bc = prob.bc
-    if bc[0] == 0: D[:, 0] += 2 * k[:, 0] * ax
-    if bc[1] == 0: D[:, -1] += 2 * k[:, -1] * ax
-    if bc[2] == 0: D[0, :] += 2 * k[0, :] * ay
-    if bc[3] == 0: D[-1, :] += 2 * k[-1, :] * ay
-    m = prob.Ss[0] * prob.dx * prob.dy * prob.dz
-    return D.ravel(), m.ravel()
-
-
-# modified Talbot contour (Sec. 2.2): shifts of the training pairs are drawn from it
-_SIGMA, _MU, _ALPHA, _NU = -0.6122, 0.5017, 0.6407, 0.2645
+def contour_nodes(t: float, Nz: int, project: bool = True):
+    """Talbot nodes of time t from the library (upper half, Re projected to >= 0 if asked)."""
+    lib = L.load()
+    z = np.zeros((Nz // 2, 2))
+    rc = lib.lt_contour_nodes(float(t), int(Nz), int(project), z.ctypes.data_as(C.c_void_p), None)
+    if rc != 0:
+        raise LtError(rc, f"lt_contour_nodes(t={t}, Nz={Nz})")
+    return z[:, 0] + 1j * z[:, 1]
 
 
 def sample_shifts(rng, n: int, Nz: int = 32, t_range=(10.0, 1e4)):
-    """Preconditioner-style shifts: a Talbot node of a random time, Re projected to >= 0."""
+    """Preconditioner-style shifts: a random Talbot node of a random time, Re projected to >= 0."""
     t = np.exp(rng.uniform(np.log(t_range[0]), np.log(t_range[1]), n))
-    th = rng.uniform(0.05, np.pi - 0.05, n)
-    z = (Nz / t) * (_SIGMA + _MU * th / np.tan(_ALPHA * th) + 1j * _NU * th)
-    return np.maximum(z.real, 0.0) + 1j * z.imag
+    k = rng.integers(0, Nz // 2, n)
+    return np.array([contour_nodes(ti, Nz)[ki] for ti, ki in zip(t, k)])
+
+
+def pairs_from_residuals(engine: Engine, tau, r, cycles: int = 40):
+    """Network inputs [n, ncell, 5] and targets [n, ncell, 2] for residuals r (CUDA complex64
+    [n, ncell]) and shifts tau: the library solves (K + tau M) e = r by multigrid and forms the
+    channels and the unit-RMS target D e on the device (lt_learned_pairs)."""
+    import torch
+    n = r.shape[0]
+    N = r.shape[1]
+    t = _tau_array(tau)
+    rr = torch.view_as_real(r).contiguous()
+    x = torch.empty((n, N, IN_CHANNELS), dtype=torch.float32, device=r.device)
+    y = torch.empty((n, N, 2), dtype=torch.float32, device=r.device)
+    rc = engine.lib.lt_learned_pairs(engine.h, n, t.ctypes.data_as(C.c_void_p), C.c_void_p(rr.data_ptr()),
+                                     int(cycles), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()))
+    engine._check(rc, "lt_learned_pairs")
+    return x, y
+
+
+def krylov_residuals(engine: Engine, max_n: int):
+    """The Krylov vectors v_j (and their shifts tau_j) of the engine's last solve: the residuals the
+    preconditioner actually receives inside Algorithm 1 (lt_krylov_vectors)."""
+    import torch
+    r = torch.zeros((max_n, engine.ncell), dtype=torch.complex64, device=f"cuda:{engine.device}")
+    tau = np.zeros((max_n, 2))
+    n = C.c_int()
+    rr = torch.view_as_real(r)
+    engine._check(engine.lib.lt_krylov_vectors(engine.h, max_n, C.c_void_p(rr.data_ptr()),
+                                               tau.ctypes.data_as(C.c_void_p), C.byref(n)), "lt_krylov_vectors")
+    k = n.value
+    return r[:k].contiguous(), tau[:k, 0] + 1j * tau[:k, 1]
 
 
 def random_residuals(rng, n: int, ny: int, nx: int, device):
@@ -163,27 +162,34 @@ def random_residuals(rng, n: int, ny: int, nx: int, device):
     return torch.tensor(r.reshape(n, ny * nx), dtype=torch.complex64, device=device)
 
 
-def make_pairs(engine: Engine, prob, n: int, rng, cycles: int = 40, batch: int = 256):
-    """(input features, target) pairs on the engine's grid: residuals r, shifts tau,
-    targets D e normalised to unit RMS, e the multigrid solution of (K + tau M) e = r
-    (the solver rescales the network's direction by a minimal-residual coefficient)."""
+def make_pairs(engine: Engine, prob, n: int, rng, cycles: int = 40, batch: int = 256, krylov: bool = True):
+    """(input, target) pairs on the engine's grid, reshaped to [n, ny, nx, C].  With krylov=True
+    the residuals are the Krylov vectors of a forward solve of `prob` on this engine (the vectors
+    the preconditioner solves inside Algorithm 1), topped up with synthetic residuals if the solve
+    produced fewer than n; else all residuals are synthetic (point sources, smooth fields, noise)."""
     import torch
     dev = torch.device("cuda", engine.device)
-    D, _ = operator_diag(prob)
-    Dt = torch.tensor(D, dtype=torch.float32, device=dev)
+    rs, taus = [], []
+    if krylov:
+        engine.set_sources(prob.src_cells, prob.Q)
+        engine.set_receivers(prob.rec_cells)
+        engine.set_options(Nz=prob.Nz, tol=prob.tol, groups=prob.groups)
+        engine.forward(prob.times, allow_unconverged=True)
+        r, tau = krylov_residuals(engine, n)
+        rs.append(r)
+        taus.append(tau)
+    have = sum(x.shape[0] for x in rs)
+    if have < n:
+        rs.append(random_residuals(rng, n - have, prob.ny, prob.nx, dev))
+        taus.append(sample_shifts(rng, n - have))
+    r = torch.cat(rs)
+    tau = np.concatenate(taus)
     xs, ys = [], []
     for i0 in range(0, n, batch):
         k = min(batch, n - i0)
-        tau = sample_shifts(rng, k)
-        r = random_residuals(rng, k, prob.ny, prob.nx, dev)
-        e = precond_apply(engine, tau, torch.view_as_real(r).contiguous(), cycles)
-        e = torch.view_as_complex(e)
-        x, s = features(prob, r, tau)
-        de = e * Dt[None]
-        nrm = torch.sqrt(torch.mean(torch.abs(de) ** 2, dim=1)).clamp_min(1e-30)
-        tgt = (de / nrm[:, None].to(torch.complex64)).reshape(k, prob.ny, prob.nx)
-        ys.append(torch.stack([tgt.real, tgt.imag], -1).float().contiguous())
-        xs.append(x)
+        x, y = pairs_from_residuals(engine, tau[i0:i0 + k], r[i0:i0 + k].contiguous(), cycles)
+        xs.append(x.reshape(k, prob.ny, prob.nx, IN_CHANNELS))
+        ys.append(y.reshape(k, prob.ny, prob.nx, 2))
     return torch.cat(xs), torch.cat(ys)
 
 

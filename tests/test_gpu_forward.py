@@ -71,15 +71,15 @@ def test_3d_neumann_top_bottom(Engine):
     assert _rel(h, direct.forward(p)) < TOL_H
 
 
-@pytest.mark.parametrize("policy", [0, 1])
-def test_outer_iterations_match_algorithm1_with_exact_solves(Engine, policy):
+@pytest.mark.parametrize("policy,gs", [(0, 2), (1, 2), (1, 1)])
+def test_outer_iterations_match_algorithm1_with_exact_solves(Engine, policy, gs):
     """With preconditioner solves converged to 1e-13 the GPU basis follows
     Algorithm 1 with exact LU solves: same tau sequence (projected to
     Re >= 0), same outer iteration count (within 2)."""
     from oracle import contour, fgmres_sh, fv
     p = W.random_problem(64, 64, 1, variance=1.6, seed=9, ns=1, nr=2, nt=1, Nz=32, tol=1e-10)
     p.times = np.array([300.0])
-    _, st = _solve(Engine, p, tau_policy=policy, tau_project=1, inner_tol=1e-13, inner_rounds=6)
+    _, st = _solve(Engine, p, tau_policy=policy, tau_project=1, inner_tol=1e-13, inner_rounds=6, gram_schmidt=gs)
     K, m = fv.assemble(p)
     z, _ = contour.nodes_weights(300.0, 32)
     taus = contour.tau_schedule(z, "single" if policy == 0 else "flexible", 300)
@@ -294,3 +294,16 @@ def test_cluster_solve_semicoarsened_levels_and_neumann_faces(Engine, shape, bc)
         assert _rel(h, ref) < TOL_H
         hs.append(h)
     assert _rel(hs[0], hs[1]) < 1e-9
+
+
+@pytest.mark.parametrize("cluster", [1, 0])
+def test_one_pass_gram_schmidt_with_df32_dots_matches_oracle(Engine, cluster):
+    """gram_schmidt = 1: one classical pass with df32-accurate coefficients keeps the basis
+    orthogonal enough that the projected residual stays the judge (true = projected to rounding)."""
+    p = W.random_problem(64, 64, 1, variance=1.5, seed=41, ns=3, nr=4, nt=6, Nz=32, tol=1e-11, groups=3)
+    h, st = _solve(Engine, p, gram_schmidt=1, mg_cluster=cluster)
+    assert _rel(h, direct.forward(p)) < TOL_H
+    assert st["n_converged"] == st["n_shift_solves"]
+    assert st["max_true_residual"] <= 1e-11
+    h2, st2 = _solve(Engine, p, gram_schmidt=2, mg_cluster=cluster)
+    assert abs(st["outer_iters_max"] - st2["outer_iters_max"]) <= 2

@@ -65,3 +65,15 @@ def test_symmetry_homogeneous_source_receiver_swap():
     # mirror symmetry about the source-receiver axis (row c)
     m = J1[0, 0, 0, 0].reshape(n, n)
     assert np.abs(m[c - 2] - m[c + 2]).max() / np.abs(m).max() < 1e-12
+
+
+def test_fd_with_exponential_sum_rates():
+    """O4 with time-varying rates (qhat in place of Q / z) against central differences of O1."""
+    p = W.random_problem(6, 5, 1, variance=1.0, seed=11, ns=2, nr=2, nt=2, Nz=24)
+    p = W.with_initial_state_and_rates(p, seed=11, initial=False)
+    J = adjoint.jacobian(p)
+    cells = [0, 7, 13, 29]
+    for which in (0, 1):
+        fd = adjoint.fd_jacobian(p, cells, which)
+        an = J[:, :, :, which, :][..., cells]
+        assert np.linalg.norm(an - fd) / np.linalg.norm(fd) < 1e-6

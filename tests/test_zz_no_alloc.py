@@ -51,6 +51,42 @@ def test_noalloc_matches_forward_on_two_calls():
     eng.close()
 
 
+def test_noalloc_cluster_path_matches_forward_and_allocates_nothing():
+    """64 x 32 splits into the cluster-resident preconditioner solve (its finest-level
+    scratch then also comes from the static region); after a warm-up call, a call
+    leaves the device's free memory unchanged."""
+    import torch
+
+    import __graft_entry__ as G
+    G.build()
+    from paper_1409_2556_gb300 import Engine
+    p = W.random_problem(64, 32, 1, variance=1.0, seed=22, ns=2, nr=3, nt=2, Nz=16, tol=1e-11)
+    eng = Engine(0)
+    eng.load_problem(p, maxit=64)
+    shape = (2, 3, 2)
+    ref = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    eng.forward(p.times, out=ref)
+    torch.cuda.synchronize()
+    ref = ref.cpu().numpy()
+    out = torch.full(shape, float("nan"), dtype=torch.float64, device="cuda")
+    eng.forward_noalloc(p.times, out)          # warm-up: loads every kernel module it uses
+    torch.cuda.synchronize()
+    assert eng.last_stats["work"][15] > 0      # the cluster-resident solve ran
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        out.fill_(float("nan"))
+        eng.forward_noalloc(p.times, out)
+        torch.cuda.synchronize()
+        assert eng.last_stats["work"][15] > 0
+        assert eng.last_stats["n_converged"] == eng.last_stats["n_shift_solves"] == 2 * 2 * 8
+        o = out.cpu().numpy()
+        assert np.all(np.isfinite(o))
+        assert _rel(o, ref) < TOL_H
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    eng.close()
+
+
 def test_noalloc_rejects_problems_larger_than_its_region():
     import torch
 
