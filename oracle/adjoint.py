@@ -18,7 +18,8 @@ adjoint problem driven by the point measurement).  With p = log kappa_c:
   psi^T dK x = sum over interior faces f of c:
                  T_f kappa_o / (kappa_c + kappa_o) (psi_c - psi_o)(x_c - x_o)
              + sum over Dirichlet faces of c: T_f psi_c x_c
-and with p = log Ss_c:  psi^T z dM x = z m_c psi_c x_c.
+and with p = log Ss_c:  psi^T z dM x = z Ss_c V_c psi_c x_c (the storage of a water-table face,
+S_y A_f, does not depend on Ss).
 
 Pinned by tests/test_oracle_adjoint.py: central finite differences of O1 on
 tiny grids, the scale invariant sum_c (dh/dlog kappa_c + dh/dlog Ss_c) = -h,
@@ -75,6 +76,7 @@ def jacobian(prob):
     """J[ns][nr][nt][2][N]: d h / d log kappa (index 0), d h / d log Ss (1)."""
     assert not np.any(source.initial_state(prob)), "the adjoint here assumes phi_0 = 0"
     K, m = fv.assemble(prob)
+    mss = (np.asarray(prob.Ss, dtype=np.float64) * (prob.dx * prob.dy * prob.dz)).ravel()   # dM / dlog Ss
     N = prob.ncell
     ns, nr, nt = len(prob.src_cells), len(prob.rec_cells), len(prob.times)
     fw = face_weights(prob)
@@ -90,7 +92,7 @@ def jacobian(prob):
                 coef = wk * source.q_hat(prob, s, zk)
                 for r in range(nr):
                     gk = _bilinear_terms(prob, fw, Ps[:, r], Xs[:, s])
-                    gs = zk * m * Ps[:, r] * Xs[:, s]
+                    gs = zk * mss * Ps[:, r] * Xs[:, s]
                     J[s, r, it, 0] += -2.0 * np.real(coef * gk)
                     J[s, r, it, 1] += -2.0 * np.real(coef * gs)
     return J

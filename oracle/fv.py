@@ -9,8 +9,10 @@ path) uses the cell-centred two-point-flux finite-volume scheme:
 * Dirichlet boundary face (ghost half a cell away, phi = 0 there):
   T_f = 2 kappa_c area / dist
 * Neumann face: T_f = 0
+* linearised water-table face (Sec. 2.1, the boundary term (S_y d phi/dt, psi) of the weak
+  form): no flux, T_f = 0, and S_y,c times the face area joins the cell's storage
 * K = sum_f T_f (e_a - e_b)(e_a - e_b)^T + sum_{Dirichlet f} T_f e_c e_c^T
-* M = diag(Ss_c * V_c),  b = Q e_source.
+* M = diag(Ss_c * V_c + sum_{water-table f of c} Sy_c A_f),  b = Q e_source.
 
 Pinned by: the eigen-expansion closed form (tests/test_oracle_forward.py),
 symmetry/positivity of K, and the row-sum identity (K 1 = boundary terms).
@@ -74,7 +76,25 @@ def assemble(prob):
     rows.append(idx.ravel()); cols.append(idx.ravel()); vals.append(diag.ravel())
     K = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(N, N))
     m = (np.asarray(prob.Ss, dtype=np.float64) * (prob.dx * prob.dy * prob.dz)).ravel()
+    m = m + water_table_storage(prob)
     return K, m
+
+
+def water_table_storage(prob):
+    """Per cell: sum over its water-table faces of S_y,c times the face area (zeros if none)."""
+    nx, ny, nz = prob.nx, prob.ny, prob.nz
+    add = np.zeros((nz, ny, nx))
+    if not any(code == 2 for code in prob.bc):
+        return add.ravel()
+    sy = np.asarray(prob.Sy, dtype=np.float64).reshape(nz, ny, nx)
+    ax, ay, az = prob.dy * prob.dz, prob.dx * prob.dz, prob.dx * prob.dy
+    sel = [(0, (slice(None), slice(None), 0), ax), (1, (slice(None), slice(None), -1), ax),
+           (2, (slice(None), 0, slice(None)), ay), (3, (slice(None), -1, slice(None)), ay),
+           (4, (0, slice(None), slice(None)), az), (5, (-1, slice(None), slice(None)), az)]
+    for face, idx, area in sel:
+        if prob.bc[face] == 2:
+            add[idx] += sy[idx] * area
+    return add.ravel()
 
 
 def rhs(prob, s):

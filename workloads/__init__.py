@@ -26,6 +26,7 @@ SS_CONST = 1e-5           # 1/m (2D: storativity), Sec. 4.1
 # boundary codes per face (x-, x+, y-, y+, z-, z+)
 BC_DIRICHLET = 0
 BC_NEUMANN = 1
+BC_WATERTABLE = 2        # linearised water table (no flux; storage S_y per unit face area)
 
 
 @dataclass
@@ -48,6 +49,7 @@ class Problem:
     tol: float
     groups: int = 1              # preconditioner-shift groups over the times
     phi0: Optional[np.ndarray] = None   # [ncell] float64 initial head (None: phi(0) = 0)
+    Sy: Optional[np.ndarray] = None     # [ncell] float64 specific yield, used on water-table faces
     # per source: (amplitudes a_j [m^3/s], decay rates lambda_j >= 0 [1/s]) of the rate
     # q_s(t) = sum_j a_j exp(-lambda_j t); None: the constant rate Q_s switched on at t = 0
     rate_terms: Optional[List[Tuple[np.ndarray, np.ndarray]]] = None
@@ -242,4 +244,23 @@ def with_initial_state_and_rates(prob: Problem, seed: int = 0, phi0_amp: float =
             terms.append((np.array(a), np.array(lam)))
         out.rate_terms = terms
     out.name = prob.name + ("-phi0" if initial else "") + ("-rates" if rates else "")
+    return out
+
+
+def with_water_table(prob: Problem, face: int = 5, sy: float = 0.2, seed: int = 0,
+                     variance: float = 0.0) -> Problem:
+    """The same aquifer with a linearised water table on one face (default z+, the top):
+    specific yield sy (times a log-normal factor of the given variance, seeded) per cell."""
+    import copy
+    out = copy.copy(prob)
+    bc = list(prob.bc)
+    bc[face] = BC_WATERTABLE
+    out.bc = tuple(bc)
+    f = np.ones(prob.ncell)
+    if variance > 0:
+        shape = (prob.nz, prob.ny, prob.nx)
+        corr = tuple(max(1.0, s / 4.0) for s in shape)
+        f = np.exp(gaussian_field(shape, variance, corr, seed + 29).ravel())
+    out.Sy = np.ascontiguousarray(sy * f)
+    out.name = prob.name + "-watertable"
     return out
