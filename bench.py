@@ -58,9 +58,12 @@ BYTES_PER_UNIT = {"fused_up": 42.0}
 KERNEL_NAMES = {"fused_up": "k_up2d (prolongation + correction + red-black post-smoothing, 2D tile)",
                 "inner": "k_inner_cluster (whole preconditioner solve per basis in one 8-CTA cluster)"}
 # DRAM bytes (read + write) per fine cell x V-cycle of k_inner_cluster, from the ncu launch list of
-# `bench.py --launch-list --sources 2` with dram__bytes_{read,write}.sum (all launches of the kernel
-# summed, divided by the work units the same command prints); None when the kernel changed since.
-INNER_TRAFFIC_PER_UNIT = None
+# `bench.py --launch-list --sources 2 --steps 1 --warmup 1 --no-autotune` with
+# dram__bytes_{read,write}.sum: 0.943 GB over its 120 launches (two forward solves, warm-up and
+# timed) / (2 x 151.5e6 units) = 3.11 B; the 2-source case has 6 bases per launch, config 2 has 13-14
+# (the per-basis records dominate, so the per-unit figure carries over).  Set to None when the
+# kernel changes until it is captured again.
+INNER_TRAFFIC_PER_UNIT = 3.11
 
 
 def vcycle_bytes_per_unit(R: int) -> float:

@@ -203,10 +203,87 @@ constexpr int kArnT = 256;   // threads per block
 constexpr int kCPT = 4;      // cells per thread
 constexpr int kIG = 4;       // basis vectors reduced together
 
+constexpr int kWarps = kArnT / 32;
+constexpr int kMaxCol = 256;   // columns of V (maxit + 1 <= 251)
+
+// Sum 8 values over the 32 lanes of a warp in 9 shuffles: each step trades half of the lane's
+// remaining values with the partner lane (offsets 16, 8, 4), then offsets 2 and 1 finish the sum.
+// Afterwards lane 4k (k = 0..7) holds the warp's sum of value k.
+template <class T>
+__device__ __forceinline__ T warp_sum8(T (&v)[8], int lane) {
+  const bool up16 = lane & 16, up8 = lane & 8, up4 = lane & 4;
+  T a[4], b2[2], c;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T send = up16 ? v[k] : v[k + 4];
+    T keep = up16 ? v[k + 4] : v[k];
+    a[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    T send = up8 ? a[k] : a[k + 2];
+    T keep = up8 ? a[k + 2] : a[k];
+    b2[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  {
+    T send = up4 ? b2[0] : b2[1];
+    T keep = up4 ? b2[1] : b2[0];
+    c = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  c += __shfl_xor_sync(0xffffffffu, c, 2);
+  c += __shfl_xor_sync(0xffffffffu, c, 1);
+  return c;   // value index: 4 * up16 + 2 * up8 + up4 = lane >> 2
+}
+
+// Column dots conj(V_i)^T s (i = 0..j) from the hi plane over the thread's cells: four columns at a
+// time, reduced per warp into part[warp][i] without block barriers, then once across the warps
+// with one double atomicAdd per column into dst.
+__device__ __forceinline__ void column_dots(const float2* V, size_t N, int Nc, int c0, const float2 (&s)[kCPT],
+                                            int j, float2 (*part)[kMaxCol], double2* dst) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i0 = 0; i0 <= j; i0 += kIG) {
+    float acc[2 * kIG];
+#pragma unroll
+    for (int q = 0; q < 2 * kIG; ++q) acc[q] = 0.f;
+#pragma unroll
+    for (int ii = 0; ii < kIG; ++ii) {
+      const int i = i0 + ii;
+      if (i > j) break;
+      const float2* v = V + (size_t)i * N;
+#pragma unroll
+      for (int q = 0; q < kCPT; ++q) {
+        const int c = c0 + q * kArnT;
+        if (c < Nc) {
+          const float2 a = v[c];
+          acc[2 * ii] += a.x * s[q].x + a.y * s[q].y;      // conj(a) * s
+          acc[2 * ii + 1] += a.x * s[q].y - a.y * s[q].x;
+        }
+      }
+    }
+    const float r = warp_sum8(acc, lane);
+    const int k = lane >> 2;
+    if ((lane & 3) == 0 && i0 + (k >> 1) <= j) {
+      float* slot = reinterpret_cast<float*>(&part[warp][i0 + (k >> 1)]);
+      slot[k & 1] = r;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    float re = 0.f, im = 0.f;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      re += part[w][i].x;
+      im += part[w][i].y;
+    }
+    atomicAdd(&dst[i].x, (double)re);
+    atomicAdd(&dst[i].y, (double)im);
+  }
+}
+
 // pass 1: dot[0][i] = V_hi[i]^H s_hi, s = M u_j (float32 estimate)
 __global__ void __launch_bounds__(kArnT) k_dots1(Batch bt, FineExact fe, int) {
   const int j = *bt.jdev;   // outer iteration (device counter, so one captured graph serves every j)
-  __shared__ float red[32 * 2 * kIG];
+  __shared__ float2 part[kWarps][kMaxCol];
   int b = blockIdx.y;
   if (!bt.active[b]) return;
   const int N = fe.N;
@@ -224,35 +301,8 @@ __global__ void __launch_bounds__(kArnT) k_dots1(Batch bt, FineExact fe, int) {
       s[q] = make_float2(0.f, 0.f);
     }
   }
-  size_t vb = (size_t)b * (bt.maxit + 1) * bt.N;
-  for (int i0 = 0; i0 <= j; i0 += kIG) {
-    float acc[2 * kIG];
-#pragma unroll
-    for (int q = 0; q < 2 * kIG; ++q) acc[q] = 0.f;
-#pragma unroll
-    for (int ii = 0; ii < kIG; ++ii) {
-      int i = i0 + ii;
-      if (i > j) break;
-      const float2* v = bt.V_hi + vb + (size_t)i * bt.N;
-#pragma unroll
-      for (int q = 0; q < kCPT; ++q) {
-        int c = c0 + q * kArnT;
-        if (c < N) {
-          float2 a = v[c];
-          acc[2 * ii] += a.x * s[q].x + a.y * s[q].y;      // conj(a) * s
-          acc[2 * ii + 1] += a.x * s[q].y - a.y * s[q].x;
-        }
-      }
-    }
-    block_reduce_add<2 * kIG>(acc, red);
-    if (threadIdx.x == 0) {
-      for (int ii = 0; ii < kIG && i0 + ii <= j; ++ii) {
-        double2* d = bt.dot + (size_t)b * 2 * (bt.maxit + 1) + (i0 + ii);
-        atomicAdd(&d->x, (double)acc[2 * ii]);
-        atomicAdd(&d->y, (double)acc[2 * ii + 1]);
-      }
-    }
-  }
+  column_dots(bt.V_hi + (size_t)b * (bt.maxit + 1) * bt.N, bt.N, N, c0, s, j, part,
+              bt.dot + (size_t)b * 2 * (bt.maxit + 1));
   if (threadIdx.x == 0) {
     int n = min(kArnT * kCPT, N - (int)(blockIdx.x * kArnT * kCPT));
     atomicAdd(&bt.work[KC_DOTS], (unsigned long long)n * (unsigned long long)(j + 1));
@@ -267,8 +317,9 @@ __global__ void __launch_bounds__(kArnT) k_update(Batch bt, FineExact fe, int, i
   const int second = mode == 1;
   const int j = *bt.jdev;   // outer iteration (device counter, so one captured graph serves every j)
   __shared__ float red[32 * 2 * kIG];
-  __shared__ float2 cf[512];
-  __shared__ float2 cl[512];     // mode 2: the low words of the df32-accurate coefficients
+  __shared__ float2 part[kWarps][kMaxCol];
+  __shared__ float2 cf[kMaxCol];
+  __shared__ float2 cl[kMaxCol];     // mode 2: the low words of the df32-accurate coefficients
   int b = blockIdx.y;
   if (!bt.active[b]) return;
   const int N = fe.N;
@@ -298,6 +349,7 @@ __global__ void __launch_bounds__(kArnT) k_update(Batch bt, FineExact fe, int, i
     }
   }
   size_t vb = (size_t)b * (bt.maxit + 1) * bt.N;
+#pragma unroll 2
   for (int i = 0; i <= j; ++i) {
     float2 ci = cf[i];
     const float2 cli = cl[i];
@@ -323,35 +375,10 @@ __global__ void __launch_bounds__(kArnT) k_update(Batch bt, FineExact fe, int, i
     if (c < N) store_cdf(bt.S_hi, bt.S_lo, sb + c, s[q]);
   }
   if (do_dots) {
-    for (int i0 = 0; i0 <= j; i0 += kIG) {
-      float acc[2 * kIG];
+    float2 sh[kCPT];
 #pragma unroll
-      for (int q = 0; q < 2 * kIG; ++q) acc[q] = 0.f;
-#pragma unroll
-      for (int ii = 0; ii < kIG; ++ii) {
-        int i = i0 + ii;
-        if (i > j) break;
-        const float2* v = bt.V_hi + vb + (size_t)i * bt.N;
-#pragma unroll
-        for (int q = 0; q < kCPT; ++q) {
-          int c = c0 + q * kArnT;
-          if (c < N) {
-            float2 a = v[c];
-            float sx = s[q].re.hi, sy = s[q].im.hi;
-            acc[2 * ii] += a.x * sx + a.y * sy;
-            acc[2 * ii + 1] += a.x * sy - a.y * sx;
-          }
-        }
-      }
-      block_reduce_add<2 * kIG>(acc, red);
-      if (threadIdx.x == 0) {
-        for (int ii = 0; ii < kIG && i0 + ii <= j; ++ii) {
-          double2* d = bt.dot + (size_t)b * 2 * (bt.maxit + 1) + (bt.maxit + 1) + (i0 + ii);
-          atomicAdd(&d->x, (double)acc[2 * ii]);
-          atomicAdd(&d->y, (double)acc[2 * ii + 1]);
-        }
-      }
-    }
+    for (int q = 0; q < kCPT; ++q) sh[q] = make_float2(s[q].re.hi, s[q].im.hi);
+    column_dots(bt.V_hi + vb, bt.N, N, c0, sh, j, part, bt.dot + (size_t)b * 2 * (bt.maxit + 1) + (bt.maxit + 1));
   } else {
     float acc[1] = {0.f};
 #pragma unroll
@@ -698,7 +725,7 @@ __device__ __forceinline__ df df_fma2(df acc, df a, df b, df c, df d) {   // acc
 // cells in df32, the block and the grid in double (a few additions per block)
 __global__ void __launch_bounds__(kArnT) k_dots_df(Batch bt, FineExact fe) {
   const int j = *bt.jdev;
-  __shared__ double red[32 * 2 * kIG];
+  __shared__ double2 part[kWarps][kMaxCol];
   const int b = blockIdx.y;
   if (!bt.active[b]) return;
   const int N = fe.N;
@@ -712,7 +739,7 @@ __global__ void __launch_bounds__(kArnT) k_dots_df(Batch bt, FineExact fe) {
                  : cdf{{0.f, 0.f}, {0.f, 0.f}};
   }
   const size_t vb = (size_t)b * (bt.maxit + 1) * bt.N;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i0 = 0; i0 <= j; i0 += kIG) {
     double acc[2 * kIG];
 #pragma unroll
@@ -735,21 +762,24 @@ __global__ void __launch_bounds__(kArnT) k_dots_df(Batch bt, FineExact fe) {
       acc[2 * ii] = (double)re.hi + (double)re.lo;
       acc[2 * ii + 1] = (double)im.hi + (double)im.lo;
     }
-#pragma unroll
-    for (int q = 0; q < 2 * kIG; ++q)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-    if (lane == 0)
-#pragma unroll
-      for (int q = 0; q < 2 * kIG; ++q) red[warp * 2 * kIG + q] = acc[q];
-    __syncthreads();
-    if (threadIdx.x < 2 * kIG && i0 + (int)threadIdx.x / 2 <= j) {
-      double t = 0.0;
-      for (int w = 0; w < nw; ++w) t += red[w * 2 * kIG + threadIdx.x];
-      double* d = (double*)(bt.dot + (size_t)b * 2 * (bt.maxit + 1) + i0 + threadIdx.x / 2);
-      atomicAdd(d + (threadIdx.x & 1), t);
+    const double r = warp_sum8(acc, lane);
+    const int k = lane >> 2;
+    if ((lane & 3) == 0 && i0 + (k >> 1) <= j) {
+      double* slot = reinterpret_cast<double*>(&part[warp][i0 + (k >> 1)]);
+      slot[k & 1] = r;
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  double2* dst = bt.dot + (size_t)b * 2 * (bt.maxit + 1);
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    double re = 0.0, im = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      re += part[w][i].x;
+      im += part[w][i].y;
+    }
+    atomicAdd(&dst[i].x, re);
+    atomicAdd(&dst[i].y, im);
   }
   if (threadIdx.x == 0) {
     const int n = min(kArnT * kCPT, N - (int)(blockIdx.x * kArnT * kCPT));
