@@ -39,7 +39,7 @@ extern "C" {
 /* boundary condition codes, one per face: x-, x+, y-, y+, z-, z+ (Sec. 2.1, Eq. timedomain) */
 #define LT_BC_DIRICHLET 0         /* phi = 0 (ghost half a cell outside the face) */
 #define LT_BC_NEUMANN   1         /* grad phi . n = 0 */
-#define LT_BC_WATERTABLE 2        /* linearised water table; not supported in this version (INVALID_ARG) */
+#define LT_BC_WATERTABLE 2        /* linearised water table: no flux, storage S_y x face area (Sec. 2.1) */
 
 /* preconditioner-shift policies (Sec. 3, last paragraph; Sec. 4.1) */
 #define LT_TAU_SINGLE   0         /* one shift: the node with the smallest real part */
@@ -155,10 +155,14 @@ int lt_set_stream(lt_ctx* ctx, void* stream);
  * M phi' + K phi = q(t) b restated on a cell-centred finite-volume grid):
  *   kappa, Ss : [nz][ny][nx] float64, every entry > 0 and finite, HOST pointers
  *   dx, dy, dz: cell sizes > 0
- *   bc        : 6 face codes (x-, x+, y-, y+, z-, z+), LT_BC_*
- *   Sy        : specific yield per top-face cell for water-table faces; must be NULL here
+ *   bc        : 6 face codes (x-, x+, y-, y+, z-, z+), LT_BC_*; at least one Dirichlet face
+ *   Sy        : specific yield [ncell] float64 HOST, finite and >= 0, read for the cells on
+ *               water-table faces (required when a face is LT_BC_WATERTABLE, else may be NULL)
  * Face transmissibility between cells a, b: (area/dist) * 2 kappa_a kappa_b / (kappa_a + kappa_b);
- * a Dirichlet face adds 2 kappa_c area / dist to the diagonal; M = diag(Ss_c * dx dy dz).
+ * a Dirichlet face adds 2 kappa_c area / dist to the diagonal; a water-table face carries no flux
+ * and adds Sy_c * (face area) to the cell's storage (the boundary term (S_y d phi/dt, psi) of the
+ * weak form of Sec. 2.1); M = diag(Ss_c * dx dy dz + water-table storage).  The adjoint's
+ * d/d log Ss_c differentiates the Ss_c * dx dy dz part only.
  * Builds the multigrid hierarchy.  Each dimension must be 1 or >= 2, and repeated halving of the
  * even dimensions must reach at most 1024 cells.
  */
@@ -267,6 +271,46 @@ int lt_adjoint_vjp(lt_ctx* ctx, int nt, const double* times, const double* g, do
  */
 int lt_adjoint_batch(int n, lt_ctx* const* ctxs, const int* nt, const double* const* times, double* const* J,
                      const double* const* g, double* const* grad, double* const* h, lt_stats* stats);
+
+/*
+ * Crank-Nicolson time stepping of the same semi-discrete problem (the time-stepping method the
+ * paper compares the Laplace-transform approach against, Sec. 1 and Sec. 5.3), from phi_0 (as set
+ * by lt_set_initial_state, else 0) with the sources' rates (lt_set_sources / lt_set_source_rates):
+ *   (M + dt/2 K) phi^{n+1} = (M - dt/2 K) phi^n + dt/2 (q(t_n) + q(t_{n+1})) e_s,
+ * `steps` uniform steps between consecutive output times (and from 0 to the first), the first
+ * step replaced by four backward-Euler quarter steps (Rannacher start, which damps the stiff
+ * modes the step source excites).  Each step solves (K + (2/dt) M) phi^{n+1} = ... for all sources
+ * together by FP64-residual iterative refinement around the float32 multigrid V-cycles
+ * (inner_rounds rounds of inner_cycles V-cycles) to the relative residual opts.tol.
+ *   times : HOST float64 [nt], strictly increasing, > 0;  steps in [2, 1e6]
+ *   h     : float64 [ns][nr][nt], HOST pointer if h_on_device == 0, else DEVICE
+ *   stats : n_shift_solves = steps x sources, max_true_residual = the largest step residual
+ * Returns LT_ERR_NOT_CONVERGED (h written) if some step's solve stopped above tol.  The time
+ * discretisation error is O(dt^2): two calls with steps and 2 steps allow Richardson extrapolation.
+ */
+int lt_crank_nicolson(lt_ctx* ctx, int nt, const double* times, int steps, double* h, int h_on_device,
+                      lt_stats* stats);
+
+/*
+ * One iteration of the quasi-linear geostatistical inversion (Sec. 5.1, Algorithm 2) for
+ * s = log kappa on the context's 2D grid, at the current coefficients s_k = log kappa (set by
+ * lt_setup_grid), with the prior s ~ N(X beta, Q): X = the column of ones (one drift coefficient),
+ * Q_ij = sigma2 exp(-|x_i - x_j| / ell) between cell centres (metres), and data y = h(s) + eps,
+ * eps ~ N(0, diag(R)):
+ *   J = d h / d s at s_k (the adjoint Jacobian, Sec. 5.2),
+ *   [J Q J^T + R, J X; (J X)^T, 0] [xi; beta] = [y - h(s_k) + J s_k; 0],
+ *   s_{k+1} = X beta + Q J^T xi,
+ * with Q J^T formed by FFT on the circulant embedding of the covariance (exact, no truncation),
+ * J Q J^T by an FP64 GEMM and the system through a Cholesky factorisation of J Q J^T + R.
+ *   y, R   : HOST float64 [ns][nr][nt] (measurements, noise variances > 0)
+ *   s_next : HOST float64 [ncell];  beta : HOST float64 [1]
+ *   xi, h  : HOST float64 [ns][nr][nt] or NULL (the multipliers; h(s_k))
+ * The caller iterates (lt_setup_grid with kappa = exp(s_next), then this call again).
+ * Needs nz = 1 and nx, ny <= 1024.  Returns LT_ERR_NOT_CONVERGED (results written) if a shifted
+ * solve of the Jacobian missed tol, LT_ERR_INVALID_ARG if J Q J^T + R is not positive definite.
+ */
+int lt_geostat_step(lt_ctx* ctx, int nt, const double* times, const double* y, const double* R, double sigma2,
+                    double ell, double* s_next, double* beta, double* xi, double* h, lt_stats* stats);
 
 /*
  * lt_forward without device allocation.  The paper has no counterpart: this

@@ -460,11 +460,18 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
   if (!(dx > 0 && dy > 0 && dz > 0) || !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dz))
     return fail(ctx, LT_ERR_INVALID_ARG, "cell sizes must be positive and finite");
   if (!kappa || !Ss || !bc) return fail(ctx, LT_ERR_INVALID_ARG, "kappa, Ss and bc are required");
-  if (Sy) return fail(ctx, LT_ERR_INVALID_ARG, "water-table faces (Sy) are not supported in this version");
-  for (int d = 0; d < 6; ++d)
-    if (bc[d] != LT_BC_DIRICHLET && bc[d] != LT_BC_NEUMANN)
-      return fail(ctx, LT_ERR_INVALID_ARG, "bc[%d]=%d: only Dirichlet (0) and Neumann (1) are supported", d, bc[d]);
+  bool any_wt = false;
+  for (int d = 0; d < 6; ++d) {
+    if (bc[d] != LT_BC_DIRICHLET && bc[d] != LT_BC_NEUMANN && bc[d] != LT_BC_WATERTABLE)
+      return fail(ctx, LT_ERR_INVALID_ARG, "bc[%d]=%d: must be Dirichlet (0), Neumann (1) or water table (2)", d, bc[d]);
+    any_wt |= bc[d] == LT_BC_WATERTABLE;
+  }
+  if (any_wt && !Sy) return fail(ctx, LT_ERR_INVALID_ARG, "a water-table face needs the specific yield Sy");
   const int64_t N = (int64_t)nx * ny * nz;
+  if (any_wt)
+    for (int64_t c = 0; c < N; ++c)
+      if (!(Sy[c] >= 0.0) || !std::isfinite(Sy[c]))
+        return fail(ctx, LT_ERR_INVALID_ARG, "Sy[%lld]=%g must be finite and >= 0", (long long)c, Sy[c]);
   for (int64_t c = 0; c < N; ++c) {
     if (!(kappa[c] > 0.0) || !std::isfinite(kappa[c]))
       return fail(ctx, LT_ERR_INVALID_ARG, "kappa[%lld]=%g must be positive and finite", (long long)c, kappa[c]);
@@ -527,7 +534,19 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
         if (j == ny - 1 && bc[3] == 0) bf.b[3][q] = 2.0 * kc * ay;
         if (k == 0 && bc[4] == 0) bf.b[4][q] = 2.0 * kc * az;
         if (k == nz - 1 && bc[5] == 0) bf.b[5][q] = 2.0 * kc * az;
-        L0.m[q] = Ss[q] * vol;
+        // storage: Ss V, plus S_y times the face area on water-table faces (Sec. 2.1, the boundary
+        // term (S_y d phi / dt, psi) of the weak form; no flux through those faces)
+        double m = Ss[q] * vol;
+        if (any_wt) {
+          const double sy = Sy[q];
+          if (i == 0 && bc[0] == LT_BC_WATERTABLE) m += sy * dy * dz;
+          if (i == nx - 1 && bc[1] == LT_BC_WATERTABLE) m += sy * dy * dz;
+          if (j == 0 && bc[2] == LT_BC_WATERTABLE) m += sy * dx * dz;
+          if (j == ny - 1 && bc[3] == LT_BC_WATERTABLE) m += sy * dx * dz;
+          if (k == 0 && bc[4] == LT_BC_WATERTABLE) m += sy * dx * dy;
+          if (k == nz - 1 && bc[5] == LT_BC_WATERTABLE) m += sy * dx * dy;
+        }
+        L0.m[q] = m;
       }
   level_diag(L0, bf);
   ctx->hl.clear();
@@ -596,9 +615,11 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
   if ((rc = upload_df(ctx, ctx->grid_allocs, &fe.D_hi, &fe.D_lo, ctx->hl[0].D))) return rc;
   if ((rc = upload_df(ctx, ctx->grid_allocs, &fe.m_hi, &fe.m_lo, L0.m))) return rc;
   {
-    std::vector<double> Bd(N, 0.0);
-    for (int64_t c = 0; c < N; ++c)
+    std::vector<double> Bd(N, 0.0), mss(N);
+    for (int64_t c = 0; c < N; ++c) {
       for (int d = 0; d < 6; ++d) Bd[c] += bfs[0].b[d][c];
+      mss[c] = Ss[c] * vol;      // dM / dlog Ss_c: the water-table storage S_y A does not depend on Ss
+    }
     auto up = [&](double** dst, const std::vector<double>& v) -> int {
       int r = dalloc(ctx, ctx->grid_allocs, dst, v.size());
       if (r) return r;
@@ -606,7 +627,7 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
       return LT_OK;
     };
     if ((rc = up(&ctx->g_Te, L0.Te)) || (rc = up(&ctx->g_Tn, L0.Tn)) || (rc = up(&ctx->g_Tu, L0.Tu)) ||
-        (rc = up(&ctx->g_kap, ctx->kappa)) || (rc = up(&ctx->g_Bd, Bd)) || (rc = up(&ctx->g_m, L0.m)))
+        (rc = up(&ctx->g_kap, ctx->kappa)) || (rc = up(&ctx->g_Bd, Bd)) || (rc = up(&ctx->g_m, mss)))
       return rc;
   }
   CK(cudaMalloc(&mg.d_levels, sizeof(lt::Level) * lt::kMaxLevels));
@@ -1819,6 +1840,273 @@ extern "C" int lt_precond_apply(lt_ctx* ctx, int nimg, const double* tau, const 
   CK(cudaStreamSynchronize(s));
   if (flag) return fail(ctx, LT_ERR_TIMEOUT, "a bulk tensor copy did not complete within its bounded wait");
   return LT_OK;
+}
+
+// ------------------------------------------------------------------ Crank-Nicolson (comparison method)
+// rate of source s at time t: sum_j a_j exp(-lambda_j t), or the constant Q_s
+static double qtime(const lt_ctx* ctx, int s, double t) {
+  if (ctx->rate_a.empty()) return ctx->Q[s];
+  double v = 0.0;
+  for (size_t j = 0; j < ctx->rate_a[s].size(); ++j) v += ctx->rate_a[s][j] * std::exp(-ctx->rate_l[s][j] * t);
+  return v;
+}
+
+extern "C" int lt_crank_nicolson(lt_ctx* ctx, int nt, const double* times, int steps, double* h, int h_on_device,
+                                 lt_stats* st) {
+  if (!ctx) return LT_ERR_INVALID_ARG;
+  int rc = check_times(ctx, nt, times);
+  if (rc) return rc;
+  for (int t = 1; t < nt; ++t)
+    if (!(times[t] > times[t - 1])) return fail(ctx, LT_ERR_INVALID_ARG, "times must increase strictly");
+  if (steps < 2 || steps > 1000000) return fail(ctx, LT_ERR_INVALID_ARG, "steps=%d must be in [2, 1e6]", steps);
+  if (ctx->src.empty() || ctx->rec.empty()) return fail(ctx, LT_ERR_STATE, "sources and receivers must be set");
+  if (!h) return fail(ctx, LT_ERR_INVALID_ARG, "h is null");
+  if (ctx->arena_base) return fail(ctx, LT_ERR_STATE, "not available inside lt_forward_noalloc");
+  CK(cudaSetDevice(ctx->device));
+  stats_reset(st, true);
+  const lt_opts& o = ctx->opts;
+  const int ns = (int)ctx->src.size(), nr = (int)ctx->rec.size();
+  const int64_t N = ctx->N;
+  const int R = o.inner_rounds, cycles = o.inner_cycles;
+  cudaStream_t s = ctx->stream;
+  CK(cudaEventRecord(ctx->ev0, s));
+  // schedule: interval i covers (t_{i-1}, t_i] with `steps` uniform steps; the first interval opens
+  // with four backward-Euler quarter steps in place of its first step (Rannacher start)
+  struct Seg { double tau, theta; int count, slot; };
+  std::vector<Seg> segs;
+  std::vector<double> srcw;
+  double tprev = 0.0;
+  for (int i = 0; i < nt; ++i) {
+    const double dt = (times[i] - tprev) / steps;
+    double tc = tprev;
+    if (i == 0) {
+      segs.push_back({4.0 / dt, 0.0, 4, 0});
+      for (int q = 0; q < 4; ++q) {
+        tc += dt / 4;
+        for (int b = 0; b < ns; ++b) srcw.push_back(qtime(ctx, b, tc));
+      }
+    }
+    const int ncn = i == 0 ? steps - 1 : steps;
+    segs.push_back({2.0 / dt, 1.0, ncn, i + 1});
+    for (int q = 0; q < ncn; ++q, tc += dt)
+      for (int b = 0; b < ns; ++b) srcw.push_back(qtime(ctx, b, tc) + qtime(ctx, b, tc + dt));
+    tprev = times[i];
+  }
+  const int nslots = nt + 1;
+  // workspace (this call's own: the Krylov workspace of the context is left untouched)
+  std::vector<void*> tmp;
+  lt::MGHost mg = ctx->mg;
+  mg.tma_cache = nullptr;
+  lt::Batch bt{};
+  lt::CnArgs a{};
+  const HostLevel& Lc = ctx->hl.back();
+  const size_t nc2 = ctx->mg.coarse_direct ? (size_t)Lc.N * Lc.N : 0;
+  double *dD = nullptr, *dm = nullptr, *dsrcw = nullptr, *d_h = nullptr;
+  int64_t *dcell = nullptr, *drc = nullptr;
+  int* dstep = nullptr;
+#define AL(p, n) if ((rc = dalloc(ctx, tmp, &p, (size_t)(n)))) { free_list(tmp); return rc; }
+  AL(dD, N); AL(dm, N); AL(a.phi, (size_t)ns * N); AL(a.x, (size_t)ns * N); AL(a.f, (size_t)ns * N);
+  AL(dcell, ns); AL(dsrcw, srcw.size()); AL(a.fnorm2, ns); AL(a.maxres2, 1); AL(dstep, 1); AL(drc, nr);
+  AL(bt.active, ns); AL(bt.rnorm2, (size_t)ns * (R + 1)); AL(bt.itol2, ns); AL(bt.tau_cur, ns); AL(bt.tau_slot, ns);
+  AL(bt.work, lt::kWorkSlots);
+  if (nc2) AL(bt.coarse_inv, nslots * nc2);
+  for (int l = 0; l < mg.nlev; ++l) {
+    AL(mg.h_levels[l].u, (size_t)ns * mg.h_levels[l].N);
+    AL(mg.h_levels[l].f, (size_t)ns * mg.h_levels[l].N);
+  }
+  lt::Level* dl = nullptr;
+  AL(dl, lt::kMaxLevels);
+  if (!h_on_device) AL(d_h, (size_t)ns * nr * nt);
+#undef AL
+  CK(cudaMemcpyAsync(dl, mg.h_levels, sizeof(lt::Level) * mg.nlev, cudaMemcpyHostToDevice, s));
+  mg.d_levels = dl;
+  mg.npre = o.mg_pre; mg.npost = o.mg_post; mg.tile = o.mg_tile; mg.tma = o.mg_tma;
+  CK(cudaMemcpyAsync(dD, ctx->hl[0].D.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dm, ctx->hl[0].m.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dcell, ctx->src.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(drc, ctx->rec.data(), nr * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dsrcw, srcw.data(), srcw.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  for (int b = 0; b < ns; ++b) {
+    if (ctx->phi0.empty()) CK(cudaMemsetAsync(a.phi + (size_t)b * N, 0, N * sizeof(double), s));
+    else CK(cudaMemcpyAsync(a.phi + (size_t)b * N, ctx->phi0.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaMemsetAsync(a.fnorm2, 0, ns * sizeof(double), s));
+  CK(cudaMemsetAsync(a.maxres2, 0, sizeof(double), s));
+  CK(cudaMemsetAsync(dstep, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(bt.work, 0, lt::kWorkSlots * sizeof(unsigned long long), s));
+  if (nc2) {
+    std::vector<float2> inv32(nslots * nc2);
+    for (const Seg& g : segs) {
+      std::vector<cplx> inv;
+      if (!dense_inverse(Lc, cplx(g.tau, 0.0), inv)) { free_list(tmp); return fail(ctx, LT_ERR_INVALID_ARG, "singular coarse operator"); }
+      for (size_t q = 0; q < nc2; ++q) inv32[g.slot * nc2 + q] = make_float2((float)inv[q].real(), (float)inv[q].imag());
+    }
+    CK(cudaMemcpyAsync(bt.coarse_inv, inv32.data(), inv32.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+  }
+  bt.nb = ns; bt.rounds = R; bt.N = N; bt.coarse_direct = ctx->mg.coarse_direct;
+  bt.tma_polls = (unsigned)o.tma_wait_polls;
+  a.nb = ns; a.N = N; a.nx = ctx->nx; a.ny = ctx->ny; a.nz = ctx->nz;
+  a.Te = ctx->g_Te; a.Tn = ctx->g_Tn; a.Tu = ctx->g_Tu; a.D = dD; a.m = dm;
+  a.cell = dcell; a.srcw = dsrcw; a.step = dstep; a.tol = o.tol;
+  double* out = h_on_device ? h : d_h;
+  int nl = 0;
+  cudaStream_t cap = nullptr;
+  CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&e1, cudaEventDisableTiming));
+  CK(cudaEventRecord(e0, s));
+  CK(cudaStreamWaitEvent(cap, e0, 0));
+  int t_out = 0, total = 0;
+  for (size_t gi = 0; gi < segs.size() && rc == LT_OK; ++gi) {
+    const Seg& g = segs[gi];
+    std::vector<double2> tc(ns, make_double2(g.tau, 0.0));
+    std::vector<int> sl(ns, g.slot);
+    CK(cudaMemcpyAsync(bt.tau_cur, tc.data(), ns * sizeof(double2), cudaMemcpyHostToDevice, cap));
+    CK(cudaMemcpyAsync(bt.tau_slot, sl.data(), ns * sizeof(int), cudaMemcpyHostToDevice, cap));
+    CK(cudaStreamSynchronize(cap));     // host tables go out of scope
+    a.tau = g.tau; a.theta = g.theta;
+    // one step captured, replayed g.count times (the step index lives on the device)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int per = 0;
+    CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    int lr = lt::launch_cn_step(mg, bt, a, cycles, cap, &per);
+    cudaError_t ec = cudaStreamEndCapture(cap, &graph);
+    if (lr || ec != cudaSuccess) { rc = fail(ctx, LT_ERR_CUDA, "capture of a time step failed"); break; }
+    ec = cudaGraphInstantiate(&gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ec != cudaSuccess) { rc = fail(ctx, LT_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ec)); break; }
+    for (int q = 0; q < g.count; ++q) CK(cudaGraphLaunch(gexec, cap));
+    cudaGraphExecDestroy(gexec);
+    nl += per * g.count;
+    total += g.count;
+    // an output time ends every CN segment
+    if (g.theta != 0.0) {
+      lt::launch_cn_measure(a, drc, nr, nt, t_out++, out, cap);
+      ++nl;
+    }
+  }
+  CK(cudaEventRecord(e1, cap));
+  CK(cudaStreamWaitEvent(s, e1, 0));
+  CK(cudaEventRecord(ctx->ev1, s));
+  double maxres2 = 0.0;
+  unsigned long long flag = 0;
+  if (rc == LT_OK) {
+    if (!h_on_device) CK(cudaMemcpyAsync(h, d_h, (size_t)ns * nr * nt * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&maxres2, a.maxres2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&flag, bt.work + lt::kTimeoutSlot, sizeof(flag), cudaMemcpyDeviceToHost, s));
+  }
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(cap);
+  lt::tma_cache_free(mg);
+  free_list(tmp);
+  if (rc) return rc;
+  if (flag) return fail(ctx, LT_ERR_TIMEOUT, "a bulk tensor copy did not complete within its bounded wait");
+  const double maxres = std::sqrt(maxres2);
+  if (st) {
+    cudaEventElapsedTime(&st->ms_total, ctx->ev0, ctx->ev1);
+    st->kernel_launches = nl;
+    st->n_bases = ns;
+    st->n_shift_solves = total * ns;
+    st->n_converged = maxres <= o.tol ? total * ns : 0;
+    st->max_true_residual = maxres;
+  }
+  if (!(maxres <= o.tol)) return fail(ctx, LT_ERR_NOT_CONVERGED, "a time step's solve stopped at %.3g > tol", maxres);
+  return LT_OK;
+}
+
+// ------------------------------------------------------------------ geostatistical inversion (Algorithm 2)
+extern "C" int lt_geostat_step(lt_ctx* ctx, int nt, const double* times, const double* y, const double* R,
+                               double sigma2, double ell, double* s_next, double* beta, double* xi, double* h,
+                               lt_stats* st) {
+  if (!ctx) return LT_ERR_INVALID_ARG;
+  int rc = check_times(ctx, nt, times);
+  if (rc) return rc;
+  if (ctx->nz != 1) return fail(ctx, LT_ERR_INVALID_ARG, "the FFT covariance product is implemented for 2D grids");
+  if (!y || !R || !s_next || !beta) return fail(ctx, LT_ERR_INVALID_ARG, "y, R, s_next and beta are required");
+  if (!(sigma2 > 0.0) || !(ell > 0.0)) return fail(ctx, LT_ERR_INVALID_ARG, "sigma2 and ell must be positive");
+  if (ctx->src.empty() || ctx->rec.empty()) return fail(ctx, LT_ERR_STATE, "sources and receivers must be set");
+  const int ns = (int)ctx->src.size(), nr = (int)ctx->rec.size();
+  const int ny = ns * nr * nt;
+  for (int i = 0; i < ny; ++i)
+    if (!(R[i] > 0.0) || !std::isfinite(y[i])) return fail(ctx, LT_ERR_INVALID_ARG, "R[%d] must be > 0, y finite", i);
+  const int nx = ctx->nx, nyg = ctx->ny;
+  const int64_t N = ctx->N;
+  int P0 = 1, P1 = 1;
+  while (P0 < 2 * nx) P0 <<= 1;
+  while (P1 < 2 * nyg) P1 <<= 1;
+  if (P0 > 2048 || P1 > 2048) return fail(ctx, LT_ERR_INVALID_ARG, "grid too large for the FFT product (side <= 1024)");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  // J (both halves; the log-kappa half is used) and h at s_k
+  std::vector<void*> tmp;
+  double *dJ = nullptr, *dh = nullptr;
+  if ((rc = dalloc(ctx, tmp, &dJ, (size_t)ny * 2 * N)) || (rc = dalloc(ctx, tmp, &dh, ny))) { free_list(tmp); return rc; }
+  rc = adjoint_impl(ctx, nt, times, dJ, nullptr, nullptr, dh, 1, 0, st);
+  if (rc && rc != LT_ERR_NOT_CONVERGED) { free_list(tmp); return rc; }
+  const int solve_rc = rc;
+  const size_t ldj = 2 * (size_t)N;
+  // covariance spectrum: sigma2 exp(-r / ell) on the P1 x P0 torus (cell-centre distances in metres)
+  const size_t nimg = (size_t)P0 * P1;
+  const int chunk = (int)std::max<size_t>(1, std::min<size_t>(ny, ((size_t)1 << 28) / (nimg * sizeof(double2))));
+  double2 *img = nullptr, *tmpi = nullptr;
+  double *lam = nullptr, *G = nullptr, *A = nullptr, *rhs = nullptr, *z = nullptr, *dbeta = nullptr, *dxi = nullptr;
+  double *ds = nullptr, *dsn = nullptr, *dy = nullptr, *dR = nullptr;
+  int* flag = nullptr;
+  if ((rc = dalloc(ctx, tmp, &img, (size_t)chunk * nimg)) || (rc = dalloc(ctx, tmp, &tmpi, (size_t)chunk * nimg)) ||
+      (rc = dalloc(ctx, tmp, &lam, nimg)) || (rc = dalloc(ctx, tmp, &G, (size_t)ny * N)) ||
+      (rc = dalloc(ctx, tmp, &A, (size_t)ny * ny)) || (rc = dalloc(ctx, tmp, &rhs, 2 * (size_t)ny)) ||
+      (rc = dalloc(ctx, tmp, &z, 2 * (size_t)ny)) || (rc = dalloc(ctx, tmp, &dbeta, 1)) ||
+      (rc = dalloc(ctx, tmp, &dxi, ny)) || (rc = dalloc(ctx, tmp, &ds, N)) || (rc = dalloc(ctx, tmp, &dsn, N)) ||
+      (rc = dalloc(ctx, tmp, &dy, ny)) || (rc = dalloc(ctx, tmp, &dR, ny)) || (rc = dalloc(ctx, tmp, &flag, 1))) {
+    free_list(tmp);
+    return rc;
+  }
+  {
+    std::vector<double2> c(nimg);
+    for (int j = 0; j < P1; ++j)
+      for (int i = 0; i < P0; ++i) {
+        const double ddx = ctx->dx * std::min(i, P0 - i), ddy = ctx->dy * std::min(j, P1 - j);
+        c[(size_t)j * P0 + i] = make_double2(sigma2 * std::exp(-std::sqrt(ddx * ddx + ddy * ddy) / ell), 0.0);
+      }
+    std::vector<double> sk(N);
+    for (int64_t q = 0; q < N; ++q) sk[q] = std::log(ctx->kappa[q]);
+    CK(cudaMemcpyAsync(img, c.data(), nimg * sizeof(double2), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ds, sk.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dy, y, ny * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dR, R, ny * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    if (lt::geostat_prepare(P0, P1) || lt::geostat_spectrum(img, tmpi, P0, P1, lam, s)) {
+      free_list(tmp);
+      return fail(ctx, LT_ERR_CUDA, "covariance spectrum failed");
+    }
+    CK(cudaStreamSynchronize(s));     // host tables go out of scope
+  }
+  // Q J^T by FFT, chunk images at a time
+  for (int r0 = 0; r0 < ny; r0 += chunk) {
+    const int nrows = std::min(chunk, ny - r0);
+    if (lt::geostat_qjt(dJ, ldj, r0, nrows, nx, nyg, P0, P1, lam, img, tmpi, G, s)) {
+      free_list(tmp);
+      return fail(ctx, LT_ERR_CUDA, "Q J^T launch failed");
+    }
+  }
+  if (lt::geostat_solve(dJ, ldj, G, ny, (int)N, dR, ds, dy, dh, A, rhs, z, dbeta, dxi, dsn, flag, s)) {
+    free_list(tmp);
+    return fail(ctx, LT_ERR_CUDA, "saddle-point solve launch failed");
+  }
+  int hflag = 0;
+  CK(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(s_next, dsn, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(beta, dbeta, sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (xi) CK(cudaMemcpyAsync(xi, dxi, ny * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (h) CK(cudaMemcpyAsync(h, dh, ny * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  free_list(tmp);
+  if (hflag) return fail(ctx, LT_ERR_INVALID_ARG, "J Q J^T + R is not positive definite");
+  return solve_rc;
 }
 
 // ------------------------------------------------------------------ learned preconditioner: data

@@ -83,6 +83,32 @@ struct SensLaunch {
   int mode;
 };
 int launch_sens2(const SensLaunch& L, cudaStream_t st);
+
+// -------- cn.cu: Crank-Nicolson time stepping (the paper's comparison method)
+struct CnArgs {
+  int nb;                                   // sources (one trajectory each)
+  int64_t N;
+  int nx, ny, nz;
+  const double *Te, *Tn, *Tu, *D, *m;       // FP64 fine operator; m includes water-table storage
+  double *phi, *x, *f;                      // [nb][N]: state, iterate of the step's solve, right-hand side
+  const int64_t* cell;                      // [nb] source cell
+  const double* srcw;                       // [steps][nb] source term of each step (q(t) + q(t + dt), or q(t + h))
+  double* fnorm2;                           // [nb] ||f||^2 of the current step
+  double* maxres2;                          // [1] largest relative residual^2 of any step and source
+  int* step;                                // device step counter
+  double tau, theta, tol;                   // (K + tau M) x = tau M phi - theta K phi + srcw e_cell
+};
+int launch_cn_step(const MGHost& mg, const Batch& bt, const CnArgs& a, int cycles, cudaStream_t st, int* nl);
+void launch_cn_measure(const CnArgs& a, const int64_t* rcells, int nr, int nt, int t, double* h, cudaStream_t st);
+
+// -------- geostat.cu: one iteration of the quasi-linear geostatistical inversion (Algorithm 2)
+int geostat_prepare(int P0, int P1);
+int geostat_spectrum(double2* cimg, double2* tmp, int P0, int P1, double* lam, cudaStream_t st);
+int geostat_qjt(const double* J, size_t ldj, int row0, int nrows, int nx, int ny, int P0, int P1, const double* lam,
+                double2* img, double2* tmp, double* G, cudaStream_t st);
+int geostat_solve(const double* J, size_t ldj, const double* G, int ny, int N, const double* R, const double* s,
+                  const double* y, const double* h, double* A, double* rhs, double* z, double* beta, double* xi,
+                  double* s_next, int* flag, cudaStream_t st);
 void launch_xk(const Batch& bt, float2* X_hi, float2* X_lo, cudaStream_t st, Prof* pf);
 void launch_true_res(const Batch& bt, const FineExact& fe, const int* sh_basis, const float2* X_hi,
                      const float2* X_lo, double* res2, cudaStream_t st, Prof* pf);

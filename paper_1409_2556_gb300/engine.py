@@ -76,7 +76,8 @@ class Engine:
         self._check(self.lib.lt_set_stream(self.h, C.c_void_p(handle or 0)), "lt_set_stream")
 
     # -------------------------------------------------------------- problem
-    def setup_grid(self, kappa, Ss, dx: float, dy: float, dz: float, bc: Sequence[int] = (0, 0, 0, 0, 1, 1)):
+    def setup_grid(self, kappa, Ss, dx: float, dy: float, dz: float, bc: Sequence[int] = (0, 0, 0, 0, 1, 1),
+                   Sy=None):
         k = _f64(kappa)
         s = _f64(Ss)
         if k.ndim == 2:
@@ -88,8 +89,11 @@ class Engine:
         b = np.ascontiguousarray(np.asarray(bc, dtype=np.int32))
         if b.size != 6:
             raise ValueError("bc needs 6 face codes")
+        sy = None if Sy is None else _f64(Sy).ravel()
+        if sy is not None and sy.size != k.size:
+            raise ValueError("Sy needs one value per cell")
         self._check(self.lib.lt_setup_grid(self.h, nx, ny, nz, float(dx), float(dy), float(dz), _ptr(k), _ptr(s),
-                                           _ptr(b), None), "lt_setup_grid")
+                                           _ptr(b), _ptr(sy) if sy is not None else None), "lt_setup_grid")
         self.shape = (nz, ny, nx)
         self.ncell = nx * ny * nz
 
@@ -138,7 +142,7 @@ class Engine:
 
     def load_problem(self, prob, **opts):
         """Configure from a workloads.Problem (grid, wells, Nz, tol, groups)."""
-        self.setup_grid(prob.kappa, prob.Ss, prob.dx, prob.dy, prob.dz, prob.bc)
+        self.setup_grid(prob.kappa, prob.Ss, prob.dx, prob.dy, prob.dz, prob.bc, getattr(prob, "Sy", None))
         self.set_sources(prob.src_cells, prob.Q)
         self.set_receivers(prob.rec_cells)
         if getattr(prob, "rate_terms", None) is not None:
@@ -180,6 +184,24 @@ class Engine:
         self.last_stats = st.as_dict()
         self._check(rc, "lt_forward_noalloc", (L.LT_ERR_NOT_CONVERGED,) if allow_unconverged else ())
         return out
+
+    def crank_nicolson(self, times, steps: int, out=None, allow_unconverged: bool = False):
+        """h[ns][nr][nt] by Crank-Nicolson time stepping on the GPU (lt_crank_nicolson)."""
+        t = _f64(times)
+        st = L.LtStats()
+        allow = (L.LT_ERR_NOT_CONVERGED,) if allow_unconverged else ()
+        if out is None:
+            h = np.zeros((self.ns, self.nr, t.size))
+            rc = self.lib.lt_crank_nicolson(self.h, t.size, _ptr(t), int(steps), _ptr(h), 0, C.byref(st))
+            res = h
+        else:
+            _check_dev(out, (self.ns, self.nr, t.size))
+            rc = self.lib.lt_crank_nicolson(self.h, t.size, _ptr(t), int(steps), C.c_void_p(out.data_ptr()), 1,
+                                            C.byref(st))
+            res = out
+        self.last_stats = st.as_dict()
+        self._check(rc, "lt_crank_nicolson", allow)
+        return res
 
     def forward_fields(self, times, out=None, allow_unconverged: bool = False):
         t = _f64(times)
