@@ -387,6 +387,70 @@ def batch_adjoint(dev, aqs, budget_gb: float = 150.0):
             "timing": "host wall clock around each batched call, device synchronised"}
 
 
+def cn_comparison(dev, h_laplace, ms_laplace):
+    """The paper's timing comparison (Sec. 5.3) on the config-2 workload: Crank-Nicolson on the GPU
+    (lt_crank_nicolson) at 150 and 300 steps per output interval, Richardson-extrapolated, against
+    the heads of the Laplace-transform step timed above."""
+    import numpy as np
+    import torch
+    from paper_1409_2556_gb300 import Engine
+    prob = workload(0)
+    eng = Engine(dev, stream=torch.cuda.Stream(device=dev))
+    eng.load_problem(prob, tol=1e-10, inner_rounds=8, inner_cycles=4)
+    out = {}
+    hs = {}
+    for steps in (150, 300):
+        eng.crank_nicolson(prob.times, steps, allow_unconverged=True)      # warm (module load, graphs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hs[steps] = eng.crank_nicolson(prob.times, steps, allow_unconverged=True)
+        torch.cuda.synchronize()
+        out[steps] = time.perf_counter() - t0
+        st = eng.last_stats
+    eng.close()
+    rel = lambda a: float(np.linalg.norm(a - h_laplace) / np.linalg.norm(h_laplace))
+    rich = (4.0 * hs[300] - hs[150]) / 3.0
+    secs = out[150] + out[300]
+    return {"value": secs, "unit": "s", "workload": WORKLOAD_NAME,
+            "method": "Crank-Nicolson, Rannacher start, 150 and 300 steps per interval, Richardson",
+            "rel_diff_vs_laplace": {"150": rel(hs[150]), "300": rel(hs[300]), "richardson": rel(rich)},
+            "seconds": {"150": out[150], "300": out[300]}, "laplace_ms_per_step": ms_laplace,
+            "laplace_speedup": secs / (ms_laplace / 1000.0), "max_step_residual_300": st["max_true_residual"],
+            "timing": "host wall clock, device synchronised"}
+
+
+def gn_timing(dev):
+    """Wall time of one iteration of the geostatistical inversion (Algorithm 2, lt_geostat_step) on
+    the config-2 aquifer: 9 x 25 x 12 = 2700 measurements of a seeded truth plus noise, from the
+    prior mean (J: 2700 x 65536, Q J^T by FFT, FP64 GEMM and Cholesky)."""
+    import numpy as np
+    import torch
+    from paper_1409_2556_gb300 import Engine, inversion
+    truth = workload(0)
+    eng = Engine(dev, stream=torch.cuda.Stream(device=dev))
+    eng.load_problem(truth, tol=1e-10, inner_relax=1e-4)
+    h_true = eng.forward(truth.times)
+    rng = np.random.default_rng(11)
+    R = np.full(h_true.size, (1e-3 * np.abs(h_true).max()) ** 2)
+    y = h_true.ravel() + np.sqrt(R) * rng.standard_normal(h_true.size)
+    s0 = np.full(truth.ncell, np.log(1e-4))
+    eng.setup_grid(np.exp(s0).reshape(truth.kappa.shape), truth.Ss, truth.dx, truth.dy, truth.dz, truth.bc)
+    eng.set_sources(truth.src_cells, truth.Q)
+    eng.set_receivers(truth.rec_cells)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s1, beta, xi, h0 = inversion.geostat_step(eng, truth.times, y, R, 1.5, 20.0 * truth.dx, allow_unconverged=True)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    eng.close()
+    s_true = np.log(truth.kappa.ravel())
+    corr = float(np.corrcoef(s1, s_true)[0, 1])
+    return {"value": dt, "unit": "s per iteration", "measurements": int(h_true.size), "unknowns": int(truth.ncell),
+            "workload": WORKLOAD_NAME + ", prior exp-cov variance 1.5, length 20 cells",
+            "misfit_prior_mean": float(np.sum((y - h0) ** 2 / R)), "corr_first_iterate_vs_truth": corr,
+            "timing": "host wall clock around lt_geostat_step (Jacobian included), device synchronised"}
+
+
 LEARNED_WORKLOAD = ("train: 8 seeded 64x64 aquifers (log-kappa variance 1.5), 20480 (residual, multigrid solve) "
                     "pairs; test: unseen 512x512 aquifer, variance 2.0, 9 sources, 25 receivers, 8 times, Nz=32")
 
@@ -480,7 +544,7 @@ def main():
                     help="profiling only: run warmup + the timed steps, print nothing else")
     ap.add_argument("--sources", type=int, default=0,
                     help="profiling only: keep the first K wells (smaller device footprint)")
-    ap.add_argument("--only", default="", choices=["", "jacobian", "batch"],
+    ap.add_argument("--only", default="", choices=["", "jacobian", "batch", "gn"],
                     help="profiling only: run one extra leg (config-3 Jacobian or the config-5 batch) and print it")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -506,7 +570,8 @@ def main():
     torch.cuda.set_device(dev)
     if args.only:
         stream = torch.cuda.Stream(device=dev)
-        res = jacobian_rows(dev, stream) if args.only == "jacobian" else batch_throughput(dev)
+        res = (jacobian_rows(dev, stream) if args.only == "jacobian" else
+               gn_timing(dev) if args.only == "gn" else batch_throughput(dev))
         print(json.dumps({"only": args.only, **res}), flush=True)
         return
     prob = workload(rank)
@@ -640,6 +705,8 @@ def main():
         achieved = (work * bpu / 1e9) / (timed_ms / 1e3) if timed_ms > 0 else None
         roof = dict(common, kernel=KERNEL_NAMES["fused_up"], bound="hbm", achieved=achieved, peak=peak_bw,
                     unit="GB/s", frac=(achieved / peak_bw) if achieved else None, traffic=None, bytes_per_unit=bpu)
+    cnc = None if args.no_jacobian else cn_comparison(dev, h.cpu().numpy(), ms_step)
+    gn = None if args.no_jacobian else gn_timing(dev)
     jac = None if args.no_jacobian else jacobian_rows(dev, stream)
     bat = None if args.no_batch else batch_throughput(dev)
     lrn = None if args.no_learned else learned_gain(dev)
@@ -687,6 +754,7 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (Krylov bases ~GBs per step)"},
             "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(), "jacobian": jac, "batch": bat, "learned": lrn,
+            "crank_nicolson": cnc, "gauss_newton": gn,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": launches}
     print(json.dumps(line), flush=True)

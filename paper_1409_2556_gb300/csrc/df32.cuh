@@ -106,6 +106,27 @@ __device__ __forceinline__ cdf cdf_mul_r(cdf a, df r) { return {df_mul(a.re, r),
 __device__ __forceinline__ cdf cdf_mul(cdf a, cdf b) {
   return {df_sub(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
 }
+// acc + a x + b y (a, b df; x, y float) with one renormalisation: the two products by TwoProduct,
+// their high parts summed into acc.hi by TwoSum, every rounding error and the lo-word products
+// gathered in the low word
+__device__ __forceinline__ df df_fma2f(df acc, df a, float x, df b, float y) {
+  float p1, e1, p2, e2, s1, t1, s2, t2;
+  two_prod(a.hi, x, p1, e1);
+  two_prod(b.hi, y, p2, e2);
+  two_sum(acc.hi, p1, s1, t1);
+  two_sum(s1, p2, s2, t2);
+  float lo = __fadd_rn(acc.lo, __fadd_rn(t1, t2));
+  lo = __fadd_rn(lo, __fadd_rn(e1, e2));
+  lo = __fmaf_rn(a.lo, x, lo);
+  lo = __fmaf_rn(b.lo, y, lo);
+  df r;
+  fast_two_sum(s2, lo, r.hi, r.lo);
+  return r;
+}
+// s - v (cr + i ci) for a complex float coefficient, one renormalisation per component
+__device__ __forceinline__ cdf cdf_sub_mul_cf(cdf s, cdf v, float cr, float ci) {
+  return {df_fma2f(s.re, v.re, -cr, v.im, ci), df_fma2f(s.im, v.re, -ci, v.im, -cr)};
+}
 // a * c with c a complex float (exact float components)
 __device__ __forceinline__ cdf cdf_mul_cf(cdf a, float cr, float ci) {
   return {df_sub(df_mul_f(a.re, cr), df_mul_f(a.im, ci)), df_add(df_mul_f(a.re, ci), df_mul_f(a.im, cr))};

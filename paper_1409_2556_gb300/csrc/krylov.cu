@@ -281,7 +281,7 @@ __device__ __forceinline__ void column_dots(const float2* V, size_t N, int Nc, i
 }
 
 // pass 1: dot[0][i] = V_hi[i]^H s_hi, s = M u_j (float32 estimate)
-__global__ void __launch_bounds__(kArnT) k_dots1(Batch bt, FineExact fe, int) {
+__global__ void __launch_bounds__(kArnT, 6) k_dots1(Batch bt, FineExact fe, int) {
   const int j = *bt.jdev;   // outer iteration (device counter, so one captured graph serves every j)
   __shared__ float2 part[kWarps][kMaxCol];
   int b = blockIdx.y;
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(kArnT) k_dots1(Batch bt, FineExact fe, int) {
 // mode 0 (pass 2): s' = M u_j - V c1 (df32, exact); dot[1][i] = V_hi[i]^H s'_hi; S <- s'
 // mode 1 (pass 3): s'' = S - V c2; snorm2 += ||s''||^2; S <- s''
 // mode 2 (the one-pass form): s' = M u_j - V c1 with c1 from the df32 dots; snorm2 += ||s'||^2; S <- s'
-__global__ void __launch_bounds__(kArnT) k_update(Batch bt, FineExact fe, int, int mode) {
+__global__ void __launch_bounds__(kArnT, 6) k_update(Batch bt, FineExact fe, int, int mode) {
   const bool from_u = mode != 1, do_dots = mode == 0;
   const int second = mode == 1;
   const int j = *bt.jdev;   // outer iteration (device counter, so one captured graph serves every j)
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(kArnT) k_update(Batch bt, FineExact fe, int, i
       if (c < N) {
         float2 h = vh[c], l = vl ? vl[c] : make_float2(0.f, 0.f);
         cdf v = {{h.x, l.x}, {h.y, l.y}};
-        s[q] = cdf_sub(s[q], cdf_mul_cf(v, ci.x, ci.y));
+        s[q] = cdf_sub_mul_cf(s[q], v, ci.x, ci.y);
         if (mode == 2) {   // - V_hi c_lo: the rest of the coefficient (V_lo c_lo is below 1e-14 |c|)
           s[q].re = df_add_f(s[q].re, -(h.x * cli.x - h.y * cli.y));
           s[q].im = df_add_f(s[q].im, -(h.x * cli.y + h.y * cli.x));
