@@ -87,6 +87,14 @@ typedef struct {
                            2 = classical Gram-Schmidt twice, coefficients from float32 dots (default);
                            1 = one classical pass whose coefficients come from df32 dots (V read twice
                            instead of four times per column) */
+  int    block;         /* 0: one Krylov basis per (source, window) (default);
+                           1: block flexible GMRES-Sh: the sources of a window share one block Krylov space
+                           (the block variant of Algorithm 1 that Sec. 6 names as future work).  Each
+                           source still gets its own preconditioner solve per iteration; the Arnoldi process
+                           and each shift's least squares treat the p sources as p right-hand sides, and each
+                           (shift, source) stops on its own residual.  lt_forward and lt_forward_fields only,
+                           with 1 <= p <= 16 sources in distinct cells, LT_KRYLOV_GMRES, LT_STOP_SHIFT,
+                           LT_PREC_FP64 and no initial state; other entry points return LT_ERR_INVALID_ARG */
 } lt_opts;
 
 /* arithmetic of the outer Krylov method (lt_opts.precision) */

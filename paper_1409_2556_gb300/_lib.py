@@ -44,7 +44,8 @@ class LtOpts(C.Structure):
                 ("true_residual", C.c_int), ("check_every", C.c_int), ("timing_class", C.c_int),
                 ("inner_relax", C.c_double), ("graphs", C.c_int), ("mg_tile", C.c_int), ("precond", C.c_int),
                 ("mg_tma", C.c_int), ("mg_cluster", C.c_int), ("precision", C.c_int), ("krylov", C.c_int),
-                ("stop_rule", C.c_int), ("tma_wait_polls", C.c_int), ("gram_schmidt", C.c_int)]
+                ("stop_rule", C.c_int), ("tma_wait_polls", C.c_int), ("gram_schmidt", C.c_int),
+                ("block", C.c_int)]
 
 
 class LtStats(C.Structure):

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblt.so")
-SOURCES = ["lt_api.cu", "mg.cu", "krylov.cu", "inner.cu", "adjoint.cu", "unet.cu", "cn.cu", "geostat.cu"]
+SOURCES = ["lt_api.cu", "mg.cu", "krylov.cu", "inner.cu", "adjoint.cu", "unet.cu", "cn.cu", "geostat.cu", "block.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,695 @@
+// block.cu -- block flexible GMRES for shifted systems: Algorithm 1 (Sec. 3) with the point sources
+// of one time group taken as one block of right-hand sides (the block Krylov variant that Sec. 6
+// leaves to future work).
+//
+// The p sources of group g keep their own bases b_q = q * G + g, so their preconditioner solves
+// are the ordinary ones; the Arnoldi process and the least squares are shared by the block:
+//   s_q = M u_j^{(q)} is orthogonalised against every member's columns v_i^{(q')}, i <= j, by
+//   classical Gram-Schmidt twice (float32 dots, df32 updates; V is read once for all p members);
+//   the p vectors are orthonormalised together by CholQR2: Gram matrix from the hi planes,
+//   Cholesky in double, V <- S W with W = R^{-1} rounded to float32 and applied in df32, twice;
+//   the subdiagonal block H_{j+1,j} = (W_1 W_2)^{-1} is exactly the inverse of what was applied,
+//   so M U_j = V_{j+1} Hbar_j holds to df32 accuracy whatever the rounding of W;
+//   every shift solves min || E_1 - Hbar(z_k; T_j) Y || for its p right-hand sides at once by
+//   Givens rotations, p per column (the lower bandwidth of the block Hessenberg matrix is p);
+//   right-hand side q of shift k stops when its residual, the norm of rows (j+1)p..(j+2)p-1 of
+//   column q of the rotated E_1, falls to tol/2.
+// Column c = i * p + q' of the block is column i of member q'.  The point right-hand sides e_cell
+// of distinct cells are orthonormal, so V_1 = B and beta = I.
+#include <cstdio>
+#include "df32.cuh"
+#include "exact.cuh"
+#include "lt_internal.h"
+#include "lt_kernels.h"
+
+namespace lt {
+
+constexpr int kBT = 256;        // threads per CTA of the vector kernels
+constexpr int kBAcc = 2048;     // float2 accumulators / coefficients staged in shared memory
+
+__device__ __forceinline__ size_t vcol_off(const Batch& bt, int g, int col) {
+  const int p = bt.bp, i = col / p, q = col - i * p;
+  return ((size_t)(q * bt.ngroups + g) * (bt.maxit + 1) + i) * bt.N;
+}
+__device__ __forceinline__ size_t ucol_off(const Batch& bt, int g, int col) {
+  const int p = bt.bp, i = col / p, q = col - i * p;
+  return ((size_t)(q * bt.ngroups + g) * bt.maxit + i) * bt.N;
+}
+
+// Column dots D[col][q] += x_col^H s_q for col < ncol, q < p, from the hi planes: s holds the
+// thread's CPT cells (cell0 + c * kBT) of every member; xcol(col) points at column col.  Per
+// column, each warp reduces its 2p partial sums by shuffles and adds them into float shared
+// accumulators; each chunk of columns ends with one double atomicAdd per (col, q) and CTA.
+template <int PMAX, int CPT, class XCol>
+__device__ void block_dots(XCol xcol, int ncol, int p, int N, int cell0, const float2 (&s)[PMAX][CPT], double2* D,
+                           float2* acc) {
+  constexpr int CH = kBAcc / PMAX;
+  const int lane = threadIdx.x & 31;
+  for (int cb = 0; cb < ncol; cb += CH) {
+    const int ce = min(cb + CH, ncol);
+    for (int i = threadIdx.x; i < (ce - cb) * p; i += blockDim.x) acc[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int col = cb; col < ce; ++col) {
+      const float2* x = xcol(col);
+      float re[PMAX], im[PMAX];
+#pragma unroll
+      for (int q = 0; q < PMAX; ++q) re[q] = im[q] = 0.f;
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) {
+        const int cell = cell0 + c * kBT;
+        if (cell < N) {
+          const float2 a = x[cell];
+#pragma unroll
+          for (int q = 0; q < PMAX; ++q) {
+            re[q] = fmaf(a.x, s[q][c].x, fmaf(a.y, s[q][c].y, re[q]));
+            im[q] = fmaf(a.x, s[q][c].y, fmaf(-a.y, s[q][c].x, im[q]));
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < PMAX; ++q) {
+        if (q < p) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            re[q] += __shfl_xor_sync(0xffffffffu, re[q], o);
+            im[q] += __shfl_xor_sync(0xffffffffu, im[q], o);
+          }
+          if (lane == 0) {
+            atomicAdd(&acc[(col - cb) * p + q].x, re[q]);
+            atomicAdd(&acc[(col - cb) * p + q].y, im[q]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < (ce - cb) * p; i += blockDim.x) {
+      atomicAdd(&D[(size_t)cb * p + i].x, (double)acc[i].x);
+      atomicAdd(&D[(size_t)cb * p + i].y, (double)acc[i].y);
+    }
+    __syncthreads();
+  }
+}
+
+// per-iteration reset of the group's accumulators (before the Gram-Schmidt dots)
+__global__ void k_bzero(Batch bt) {
+  const int g = blockIdx.x;
+  if (!bt.active[g]) return;
+  const int j = *bt.jdev, p = bt.bp;
+  const size_t n = (size_t)(j + 1) * p * p;
+  double2* d = bt.bdot + (size_t)g * 2 * bt.bld * p;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+    d[i] = make_double2(0.0, 0.0);
+    d[(size_t)bt.bld * p + i] = make_double2(0.0, 0.0);
+  }
+  double2* gm = bt.bgram + (size_t)g * 2 * p * p;
+  for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) gm[i] = make_double2(0.0, 0.0);
+  if (threadIdx.x == 0) {
+    bt.gany[g] = 0;
+    bt.grmax[g] = 0ull;
+  }
+}
+
+// first Gram-Schmidt pass: bdot[g][0][col][q] = v_col^H (M u_j^{(q)})
+template <int PMAX, int CPT>
+__global__ void __launch_bounds__(kBT) k_bdots(Batch bt, FineExact fe) {
+  __shared__ float2 acc[kBAcc];
+  const int g = blockIdx.y;
+  if (!bt.active[g]) return;
+  const int j = *bt.jdev, p = bt.bp, N = fe.N, G = bt.ngroups;
+  const int cell0 = blockIdx.x * kBT * CPT + threadIdx.x;
+  float2 s[PMAX][CPT];
+#pragma unroll
+  for (int q = 0; q < PMAX; ++q)
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int cell = cell0 + c * kBT;
+      s[q][c] = make_float2(0.f, 0.f);
+      if (q < p && cell < N) {
+        const float2 u = bt.U_hi[((size_t)(q * G + g) * bt.maxit + j) * bt.N + cell];
+        const float m = fe.m_hi[cell];
+        s[q][c] = make_float2(m * u.x, m * u.y);
+      }
+    }
+  const float2* V = bt.V_hi;
+  auto xcol = [&](int col) { return V + vcol_off(bt, g, col); };
+  block_dots<PMAX, CPT>(xcol, (j + 1) * p, p, N, cell0, s, bt.bdot + (size_t)g * 2 * bt.bld * p, acc);
+}
+
+// mode 0: s_q = M u_j^{(q)} - sum_col v_col c1[col][q] (df32), S_q <- s_q, and the second pass's
+// dots bdot[g][1] = V^H s; mode 1: S_q <- S_q - sum_col v_col c2[col][q]
+template <int PMAX, int CPT>
+__global__ void __launch_bounds__(kBT) k_bupdate(Batch bt, FineExact fe, int mode) {
+  __shared__ float2 cf[kBAcc];
+  __shared__ float2 acc[kBAcc];
+  constexpr int CH = kBAcc / PMAX;
+  const int g = blockIdx.y;
+  if (!bt.active[g]) return;
+  const int j = *bt.jdev, p = bt.bp, N = fe.N, G = bt.ngroups;
+  const int ncol = (j + 1) * p;
+  const int cell0 = blockIdx.x * kBT * CPT + threadIdx.x;
+  cdf s[PMAX][CPT];
+#pragma unroll
+  for (int q = 0; q < PMAX; ++q)
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int cell = cell0 + c * kBT;
+      s[q][c] = {{0.f, 0.f}, {0.f, 0.f}};
+      if (q < p && cell < N) {
+        const size_t b = (size_t)(q * G + g);
+        s[q][c] = mode == 0 ? cdf_mul_r(load_cdf(bt.U_hi, bt.U_lo, (b * bt.maxit + j) * bt.N + cell),
+                                        ldf(fe.m_hi, fe.m_lo, cell))
+                            : load_cdf(bt.S_hi, bt.S_lo, b * bt.N + cell);
+      }
+    }
+  const double2* D = bt.bdot + ((size_t)g * 2 + mode) * bt.bld * p;
+  for (int cb = 0; cb < ncol; cb += CH) {
+    const int ce = min(cb + CH, ncol);
+    __syncthreads();
+    for (int i = threadIdx.x; i < (ce - cb) * p; i += blockDim.x) {
+      const double2 d = D[(size_t)cb * p + i];
+      cf[i] = make_float2((float)d.x, (float)d.y);
+    }
+    __syncthreads();
+    for (int col = cb; col < ce; ++col) {
+      const size_t off = vcol_off(bt, g, col);
+      const float2* vh = bt.V_hi + off;
+      const float2* vl = lo_at(bt.V_lo, off);
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) {
+        const int cell = cell0 + c * kBT;
+        if (cell < N) {
+          const cdf v = load_cdf(vh, vl, cell);
+#pragma unroll
+          for (int q = 0; q < PMAX; ++q)
+            if (q < p) {
+              const float2 k = cf[(col - cb) * p + q];
+              s[q][c] = cdf_sub_mul_cf(s[q][c], v, k.x, k.y);
+            }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < PMAX; ++q)
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int cell = cell0 + c * kBT;
+      if (q < p && cell < N) store_cdf(bt.S_hi, bt.S_lo, (size_t)(q * G + g) * bt.N + cell, s[q][c]);
+    }
+  if (mode == 0) {
+    float2 sh[PMAX][CPT];
+#pragma unroll
+    for (int q = 0; q < PMAX; ++q)
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) sh[q][c] = make_float2(s[q][c].re.hi, s[q][c].im.hi);
+    const float2* V = bt.V_hi;
+    auto xcol = [&](int col) { return V + vcol_off(bt, g, col); };
+    block_dots<PMAX, CPT>(xcol, ncol, p, N, cell0, sh, bt.bdot + ((size_t)g * 2 + 1) * bt.bld * p, acc);
+  }
+  if (threadIdx.x == 0) {
+    const int n = min(kBT * CPT, N - (int)(blockIdx.x * kBT * CPT));
+    atomicAdd(&bt.work[KC_ORTHO], (unsigned long long)n * (unsigned long long)ncol);
+  }
+}
+
+// Gram matrix of the block's new vectors, from the hi planes: pass 0 of S (after Gram-Schmidt),
+// pass 1 of V_{j+1} (after the first CholQR step).  bgram[g][pass][a][q] = x_a^H x_q.
+template <int PMAX, int CPT>
+__global__ void __launch_bounds__(kBT) k_bgram(Batch bt, int pass) {
+  __shared__ float2 acc[kBAcc];
+  const int g = blockIdx.y;
+  if (!bt.active[g]) return;
+  const int j = *bt.jdev, p = bt.bp, N = (int)bt.N, G = bt.ngroups;
+  const int cell0 = blockIdx.x * kBT * CPT + threadIdx.x;
+  auto xcol = [&](int a) {
+    const size_t b = (size_t)(a * G + g);
+    return pass == 0 ? bt.S_hi + b * bt.N : bt.V_hi + (b * (bt.maxit + 1) + j + 1) * bt.N;
+  };
+  float2 s[PMAX][CPT];
+#pragma unroll
+  for (int q = 0; q < PMAX; ++q) {
+    const float2* x = q < p ? xcol(q) : nullptr;
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int cell = cell0 + c * kBT;
+      s[q][c] = (q < p && cell < N) ? x[cell] : make_float2(0.f, 0.f);
+    }
+  }
+  block_dots<PMAX, CPT>(xcol, p, p, N, cell0, s, bt.bgram + ((size_t)g * 2 + pass) * p * p, acc);
+}
+
+__device__ __forceinline__ double2 bz_mul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 bz_cmul(double2 a, double2 b) {   // conj(a) * b
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ double2 bz_div(double2 a, double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// inverse of an upper-triangular p x p matrix (row-major, complex double): X = A^{-1}
+__device__ void upper_inverse(const double2* A, double2* X, int p) {
+  for (int q = 0; q < p; ++q) {
+    for (int l = 0; l < p; ++l) X[l * p + q] = make_double2(0.0, 0.0);
+    X[q * p + q] = bz_div(make_double2(1.0, 0.0), A[q * p + q]);
+    for (int l = q - 1; l >= 0; --l) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int k = l + 1; k <= q; ++k) {
+        const double2 t = bz_mul(A[l * p + k], X[k * p + q]);
+        acc.x += t.x; acc.y += t.y;
+      }
+      X[l * p + q] = bz_div(make_double2(-acc.x, -acc.y), A[l * p + l]);
+    }
+  }
+}
+
+// CholQR step of pass `pass`: Gram = R^H R (Cholesky, double), W = R^{-1} rounded to float32 into
+// bw[g][pass].  A pivot below 1e-26 of its column's squared norm (numerical rank loss of the block)
+// is raised to that floor, so W stays finite; the Arnoldi relation still holds exactly because H
+// takes the inverse of the W that was applied.  Pass 1 also writes block column j of H: rows
+// i p + q' (i <= j) the Gram-Schmidt coefficients the updates subtracted, rows (j+1)p + l the
+// subdiagonal block (W_1 W_2)^{-1}.
+__global__ void k_bchol(Batch bt, int pass) {
+  __shared__ double2 Gm[256], Rm[256], Wd[256], T[256];
+  const int g = blockIdx.x;
+  if (!bt.active[g]) return;
+  const int j = *bt.jdev, p = bt.bp;
+  const double2* gram = bt.bgram + ((size_t)g * 2 + pass) * p * p;
+  float2* W = bt.bw + ((size_t)g * 2 + pass) * p * p;
+  for (int i = threadIdx.x; i < p * p; i += blockDim.x) Gm[i] = gram[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < p; ++q) {
+      for (int l = 0; l < q; ++l) {
+        double2 acc = Gm[l * p + q];
+        for (int k = 0; k < l; ++k) {
+          const double2 t = bz_cmul(Rm[k * p + l], Rm[k * p + q]);
+          acc.x -= t.x; acc.y -= t.y;
+        }
+        Rm[l * p + q] = bz_div(acc, Rm[l * p + l]);
+      }
+      double d = Gm[q * p + q].x;
+      for (int k = 0; k < q; ++k) d -= Rm[k * p + q].x * Rm[k * p + q].x + Rm[k * p + q].y * Rm[k * p + q].y;
+      const double floor_d = fmax(1e-26 * Gm[q * p + q].x, 1e-280);
+      if (!(d > floor_d)) d = floor_d;
+      Rm[q * p + q] = make_double2(sqrt(d), 0.0);
+      for (int l = q + 1; l < p; ++l) Rm[l * p + q] = make_double2(0.0, 0.0);
+    }
+    upper_inverse(Rm, Wd, p);
+    // W as applied: float32 entries
+    for (int i = 0; i < p * p; ++i) Wd[i] = make_double2((double)(float)Wd[i].x, (double)(float)Wd[i].y);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < p * p; i += blockDim.x) W[i] = make_float2((float)Wd[i].x, (float)Wd[i].y);
+  if (pass == 0) return;
+  if (threadIdx.x == 0) {
+    // T = W_1 W_2 (both upper triangular, float entries), then Hsub = T^{-1} into Rm
+    const float2* W1 = bt.bw + (size_t)g * 2 * p * p;
+    for (int l = 0; l < p; ++l)
+      for (int q = 0; q < p; ++q) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int k = l; k <= q; ++k) {
+          const double2 t = bz_mul(make_double2(W1[l * p + k].x, W1[l * p + k].y), Wd[k * p + q]);
+          acc.x += t.x; acc.y += t.y;
+        }
+        T[l * p + q] = acc;
+      }
+    upper_inverse(T, Rm, p);
+  }
+  __syncthreads();
+  const int rows = (j + 2) * p, nr = (j + 1) * p;
+  const double2* D1 = bt.bdot + (size_t)g * 2 * bt.bld * p;
+  const double2* D2 = D1 + (size_t)bt.bld * p;
+  for (int idx = threadIdx.x; idx < p * rows; idx += blockDim.x) {
+    const int q = idx / rows, r = idx - q * rows;
+    const int c = j * p + q;
+    double2 h;
+    if (r < nr) {
+      const double2 a = D1[(size_t)r * p + q], b = D2[(size_t)r * p + q];
+      h = make_double2((double)(float)a.x + (double)(float)b.x, (double)(float)a.y + (double)(float)b.y);
+    } else {
+      const int l = r - nr;
+      h = l <= q ? Rm[l * p + q] : make_double2(0.0, 0.0);
+    }
+    bt.bH[((size_t)g * bt.bld + c) * bt.hld + r] = h;
+  }
+}
+
+// V_{j+1}^{(q)} = sum_{l <= q} x_l W[l][q] in df32 (float32 coefficients): pass 0 reads x = S,
+// pass 1 reads x = V_{j+1} (in place)
+template <int PMAX, int CPT>
+__global__ void __launch_bounds__(kBT) k_btransform(Batch bt, int pass) {
+  __shared__ float2 W[PMAX * PMAX];
+  const int g = blockIdx.y;
+  if (!bt.active[g]) return;
+  const int j = *bt.jdev, p = bt.bp, N = (int)bt.N, G = bt.ngroups;
+  const float2* Wg = bt.bw + ((size_t)g * 2 + pass) * p * p;
+  for (int i = threadIdx.x; i < p * p; i += blockDim.x) W[i] = Wg[i];
+  __syncthreads();
+  const int cell0 = blockIdx.x * kBT * CPT + threadIdx.x;
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) {
+    const int cell = cell0 + c * kBT;
+    if (cell >= N) continue;
+    cdf x[PMAX];
+#pragma unroll
+    for (int l = 0; l < PMAX; ++l) {
+      x[l] = {{0.f, 0.f}, {0.f, 0.f}};
+      if (l < p) {
+        const size_t b = (size_t)(l * G + g);
+        const size_t off = pass == 0 ? b * bt.N : (b * (bt.maxit + 1) + j + 1) * bt.N;
+        x[l] = pass == 0 ? load_cdf(bt.S_hi, bt.S_lo, off + cell) : load_cdf(bt.V_hi, bt.V_lo, off + cell);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < PMAX; ++q) {
+      if (q >= p) continue;
+      cdf acc = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+      for (int l = 0; l < PMAX; ++l)
+        if (l <= q) {
+          const float2 w = W[l * p + q];
+          acc.re = df_fma2f(acc.re, x[l].re, w.x, x[l].im, -w.y);
+          acc.im = df_fma2f(acc.im, x[l].re, w.y, x[l].im, w.x);
+        }
+      store_cdf(bt.V_hi, bt.V_lo, ((size_t)(q * G + g) * (bt.maxit + 1) + j + 1) * bt.N + cell, acc);
+    }
+  }
+}
+
+// Givens rotation zeroing b against a (a <- rho e^{i arg a}), the convention of the
+// per-shift least squares: x_r' = c x_r + s x_r2, x_r2' = -conj(s) x_r + c x_r2
+__device__ __forceinline__ void bgivens(double2 a, double2 b, double& c, double2& s, double2& r) {
+  const double na = hypot(a.x, a.y), nb = hypot(b.x, b.y), rho = hypot(na, nb);
+  if (rho == 0.0) {
+    c = 1.0; s = make_double2(0.0, 0.0); r = make_double2(0.0, 0.0);
+  } else if (na == 0.0) {
+    c = 0.0; s = make_double2(b.x / nb, -b.y / nb); r = make_double2(nb, 0.0);
+  } else {
+    c = na / rho;
+    const double2 ph = make_double2(a.x / na, a.y / na);
+    s = bz_mul(ph, make_double2(b.x / rho, -b.y / rho));
+    r = make_double2(ph.x * rho, ph.y * rho);
+  }
+}
+__device__ __forceinline__ void brot(double2* x, int r1, int r2, double c, double2 s) {
+  const double2 a = x[r1], b = x[r2];
+  const double2 sb = bz_mul(s, b), sa = bz_cmul(s, a);
+  x[r1] = make_double2(c * a.x + sb.x, c * a.y + sb.y);
+  x[r2] = make_double2(c * b.x - sa.x, c * b.y - sa.y);
+}
+// the same on a row-major [row][p] right-hand-side block, column q
+__device__ __forceinline__ void brot_g(double2* G, int p, int q, int r1, int r2, double c, double2 s) {
+  const double2 a = G[(size_t)r1 * p + q], b = G[(size_t)r2 * p + q];
+  const double2 sb = bz_mul(s, b), sa = bz_cmul(s, a);
+  G[(size_t)r1 * p + q] = make_double2(c * a.x + sb.x, c * a.y + sb.y);
+  G[(size_t)r2 * p + q] = make_double2(c * b.x - sa.x, c * b.y - sa.y);
+}
+
+// group of the member-0 shift bs (member-0 bases are 0..G-1, their shifts contiguous)
+__device__ __forceinline__ int bshift_group(const Batch& bt, int bs) {
+  int g = 0;
+  while (g + 1 < bt.ngroups && bt.shift_off[g + 1] <= bs) ++g;
+  return g;
+}
+
+// Block least squares of one shift z (one warp): the new block column j of
+// Hbar(z; T_j) = [I; 0] + Hbar_j (z - tau_j) gets every earlier rotation (lane q < p: column
+// jp + q), then its own p rotations per column, in column order; lanes 16 + q carry column q of the
+// rotated right-hand side E_1 (beta = I).  The rotated matrix R (upper triangular) and the
+// rotated right-hand side are kept per shift for the back-substitution.
+__global__ void __launch_bounds__(32) k_block_ls(Batch bt) {
+  __shared__ double rc_s[16];
+  __shared__ double2 rs_s[16];
+  const int bs = blockIdx.x;
+  const int g = bshift_group(bt, bs);
+  if (!bt.active[g]) return;
+  const int j = *bt.jdev, p = bt.bp, G = bt.ngroups, hld = bt.hld;
+  const int i_sh = bs - bt.shift_off[g];
+  const int lane = threadIdx.x;
+  // all right-hand sides of this shift already converged: nothing left to do here
+  int open = 0;
+  for (int q = 0; q < p; ++q) open |= bt.conv_it[bt.shift_off[q * G + g] + i_sh] == 0;
+  if (!open) return;
+  const double2 z = bt.zsh[bs], tau = bt.tau_cur[g];
+  const double2 dz = make_double2(z.x - tau.x, z.y - tau.y);
+  double2* R = bt.bR + (size_t)bs * bt.bld * hld;
+  double* rcs = bt.brc + (size_t)bs * bt.bld * p;
+  double2* rss = bt.brs + (size_t)bs * bt.bld * p;
+  double2* Gr = bt.bG + (size_t)bs * hld * p;
+  const double2* H = bt.bH + (size_t)g * bt.bld * hld;
+  const int c0 = j * p;
+  if (lane < p) {
+    const int c = c0 + lane;
+    double2* Rc = R + (size_t)c * hld;
+    const double2* Hc = H + (size_t)c * hld;
+    for (int r = 0; r <= c + p; ++r) {
+      double2 v = bz_mul(dz, Hc[r]);
+      if (r == c) v.x += 1.0;
+      Rc[r] = v;
+    }
+    for (int cc = 0; cc < c0; ++cc)
+      for (int k = 0; k < p; ++k) brot(Rc, cc, cc + 1 + k, rcs[(size_t)cc * p + k], rss[(size_t)cc * p + k]);
+  } else if (lane >= 16 && lane - 16 < p) {
+    const int q = lane - 16;
+    if (j == 0)
+      for (int r = 0; r < p; ++r) Gr[(size_t)r * p + q] = make_double2(r == q ? 1.0 : 0.0, 0.0);
+    for (int r = (j + 1) * p; r < (j + 2) * p; ++r) Gr[(size_t)r * p + q] = make_double2(0.0, 0.0);
+  }
+  __syncwarp();
+  for (int qq = 0; qq < p; ++qq) {
+    const int c = c0 + qq;
+    if (lane == qq) {
+      double2* Rc = R + (size_t)c * hld;
+      for (int k = 0; k < p; ++k) {
+        double cs;
+        double2 sn, r;
+        bgivens(Rc[c], Rc[c + 1 + k], cs, sn, r);
+        Rc[c] = r;
+        Rc[c + 1 + k] = make_double2(0.0, 0.0);
+        rcs[(size_t)c * p + k] = cs;
+        rss[(size_t)c * p + k] = sn;
+        rc_s[k] = cs;
+        rs_s[k] = sn;
+      }
+    }
+    __syncwarp();
+    if (lane < p && lane > qq) {
+      double2* Rl = R + (size_t)(c0 + lane) * hld;
+      for (int k = 0; k < p; ++k) brot(Rl, c, c + 1 + k, rc_s[k], rs_s[k]);
+    } else if (lane >= 16 && lane - 16 < p) {
+      for (int k = 0; k < p; ++k) brot_g(Gr, p, lane - 16, c, c + 1 + k, rc_s[k], rs_s[k]);
+    }
+    __syncwarp();
+  }
+  if (lane >= 16 && lane - 16 < p) {
+    const int q = lane - 16;
+    double r2 = 0.0;
+    for (int r = (j + 1) * p; r < (j + 2) * p; ++r) {
+      const double2 v = Gr[(size_t)r * p + q];
+      r2 += v.x * v.x + v.y * v.y;
+    }
+    const double res = sqrt(r2);
+    const int sh = bt.shift_off[q * G + g] + i_sh;
+    if (bt.conv_it[sh] == 0) {
+      bt.pres[sh] = res;
+      if (res <= 0.5 * bt.tol) {
+        bt.conv_it[sh] = j + 1;
+      } else {
+        atomicOr(&bt.gany[g], 1);
+        atomicMax(&bt.grmax[g], (unsigned long long)__double_as_longlong(res));
+      }
+    }
+  }
+}
+
+// iteration counters, active flags and the largest open residual of every member basis
+__global__ void k_block_flags(Batch bt) {
+  const int j = *bt.jdev;
+  for (int b = threadIdx.x; b < bt.nb; b += blockDim.x) {
+    if (!bt.active[b]) continue;
+    const int g = b % bt.ngroups;
+    bt.nit[b] = j + 1;
+    bt.active[b] = (bt.gany[g] && j + 1 < bt.maxit) ? 1 : 0;
+    bt.rmax[b] = __longlong_as_double((long long)bt.grmax[g]);
+  }
+}
+
+// y = R^{-1} g for every (shift, right-hand side): n = (iterations at convergence, else done) * p
+// columns of the shift's rotated block system.  sh is the global shift of member q of group g.
+__global__ void k_bbacksolve(Batch bt, const int* sh_basis) {
+  const int sh = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sh >= bt.nsh) return;
+  const int b = sh_basis[sh], G = bt.ngroups, p = bt.bp, hld = bt.hld;
+  const int g = b % G, q = b / G;
+  const int bs = bt.shift_off[g] + (sh - bt.shift_off[b]);
+  const int m = bt.conv_it[sh] > 0 ? bt.conv_it[sh] : bt.nit[b];
+  const int n = m * p;
+  const double2* R = bt.bR + (size_t)bs * bt.bld * hld;
+  const double2* Gr = bt.bG + (size_t)bs * hld * p;
+  double2* y = bt.bY + (size_t)sh * bt.bld;
+  for (int i = n; i < bt.bld; ++i) y[i] = make_double2(0.0, 0.0);
+  for (int i = n - 1; i >= 0; --i) {
+    double2 acc = Gr[(size_t)i * p + q];
+    for (int l = i + 1; l < n; ++l) {
+      const double2 t = bz_mul(R[(size_t)l * hld + i], y[l]);
+      acc.x -= t.x; acc.y -= t.y;
+    }
+    const double2 d = R[(size_t)i * hld + i];
+    y[i] = (d.x != 0.0 || d.y != 0.0) ? bz_div(acc, d) : make_double2(0.0, 0.0);
+  }
+}
+
+constexpr int kBXS = 16;    // shifts per pass of the solution kernel
+constexpr int kBXC = 128;   // coefficient columns staged per pass
+
+__device__ __forceinline__ cdf bcdf_fma(cdf acc, cdf u, cdf y) {   // acc + u * y
+  const df nyi = df_neg(y.im);
+  return {df_add(acc.re, df_add(df_mul(u.re, y.re), df_mul(u.im, nyi))),
+          df_add(acc.im, df_add(df_mul(u.re, y.im), df_mul(u.im, y.re)))};
+}
+
+// X[sh] = sum_c U_c y_sh[c] over the block's columns (every member's U), df32
+__global__ void __launch_bounds__(kBT) k_bxk(Batch bt, float2* X_hi, float2* X_lo) {
+  __shared__ cdf ys[kBXS][kBXC];
+  const int b = blockIdx.y;
+  const int g = b % bt.ngroups;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = bt.nit[b] * bt.bp;
+  const int s0 = bt.shift_off[b], s1 = bt.shift_off[b + 1];
+  for (int sa = s0; sa < s1; sa += kBXS) {
+    cdf acc[kBXS];
+#pragma unroll
+    for (int q = 0; q < kBXS; ++q) acc[q] = {{0.f, 0.f}, {0.f, 0.f}};
+    for (int cb = 0; cb < n; cb += kBXC) {
+      const int ce = min(cb + kBXC, n);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < kBXS * kBXC; idx += blockDim.x) {
+        const int q = idx / kBXC, i = idx % kBXC;
+        const int sh = sa + q;
+        const double2 y = (sh < s1 && cb + i < ce) ? bt.bY[(size_t)sh * bt.bld + cb + i] : make_double2(0.0, 0.0);
+        ys[q][i] = {df_from_double(y.x), df_from_double(y.y)};
+      }
+      __syncthreads();
+      if (c < bt.N)
+        for (int col = cb; col < ce; ++col) {
+          const size_t off = ucol_off(bt, g, col);
+          const cdf u = load_cdf(bt.U_hi + off, lo_at(bt.U_lo, off), c);
+#pragma unroll
+          for (int q = 0; q < kBXS; ++q) acc[q] = bcdf_fma(acc[q], u, ys[q][col - cb]);
+        }
+    }
+    if (c < bt.N)
+#pragma unroll
+      for (int q = 0; q < kBXS; ++q)
+        if (sa + q < s1) store_cdf(X_hi, X_lo, (size_t)(sa + q) * bt.N + c, acc[q]);
+  }
+}
+
+// quadrature coefficients over the block's columns: C[item][c] = sum_k w_k y_{sh0+k}[c]
+__global__ void k_bquad_coef(Batch bt, const QuadItem* items, int nitems, const double2* wq, double2* C) {
+  const int q = blockIdx.x;
+  if (q >= nitems) return;
+  const QuadItem it = items[q];
+  for (int i = threadIdx.x; i < bt.bld; i += blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = 0; k < it.nk; ++k) {
+      const double2 t = bz_mul(wq[it.sh0 + k], bt.bY[(size_t)(it.sh0 + k) * bt.bld + i]);
+      acc.x += t.x; acc.y += t.y;
+    }
+    C[(size_t)q * bt.bld + i] = acc;
+  }
+}
+
+__device__ __forceinline__ double bquad_dot(const Batch& bt, const QuadItem& it, const double2* C, int q, int64_t cell) {
+  const int g = it.basis % bt.ngroups;
+  const int n = bt.nit[it.basis] * bt.bp;
+  double acc = 0.0;
+  for (int col = 0; col < n; ++col) {
+    const size_t ui = ucol_off(bt, g, col) + cell;
+    const float2 hi = bt.U_hi[ui], lo = bt.U_lo ? bt.U_lo[ui] : make_float2(0.f, 0.f);
+    const double2 cf = C[(size_t)q * bt.bld + col];
+    acc += ((double)hi.x + (double)lo.x) * cf.x - ((double)hi.y + (double)lo.y) * cf.y;
+  }
+  return acc;
+}
+
+// h[s][r][t] = 2 Re (U_block[rcell] . C_{s,t})
+__global__ void k_bmeasure(Batch bt, const QuadItem* items, const double2* C, int ns, int nr, int nt,
+                           const int64_t* rcells, double* h) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ns * nr * nt) return;
+  const int t = idx % nt, r = (idx / nt) % nr, s = idx / (nt * nr);
+  const int q = s * nt + t;
+  h[idx] = 2.0 * bquad_dot(bt, items[q], C, q, rcells[r]);
+}
+
+// phi[q][c] for the items q = s * nt + t
+__global__ void k_bfields(Batch bt, const QuadItem* items, const double2* C, double* phi) {
+  const int q = blockIdx.y;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= bt.N) return;
+  phi[(size_t)q * bt.N + c] = 2.0 * bquad_dot(bt, items[q], C, q, c);
+}
+
+// ------------------------------------------------------------------ host launchers
+template <int PMAX, int CPT>
+static void block_arnoldi_t(const Batch& bt, const FineExact& fe, cudaStream_t st, Prof* pf) {
+  const dim3 grid((unsigned)((fe.N + kBT * CPT - 1) / (kBT * CPT)), bt.ngroups);
+  k_bzero<<<bt.ngroups, 256, 0, st>>>(bt);
+  prof_begin(pf, KC_DOTS, st);
+  k_bdots<PMAX, CPT><<<grid, kBT, 0, st>>>(bt, fe);
+  prof_end(pf, KC_DOTS, st);
+  for (int mode = 0; mode < 2; ++mode) {
+    prof_begin(pf, KC_ORTHO, st);
+    k_bupdate<PMAX, CPT><<<grid, kBT, 0, st>>>(bt, fe, mode);
+    prof_end(pf, KC_ORTHO, st);
+  }
+  prof_begin(pf, KC_NORMALIZE, st);
+  for (int pass = 0; pass < 2; ++pass) {
+    k_bgram<PMAX, CPT><<<grid, kBT, 0, st>>>(bt, pass);
+    k_bchol<<<bt.ngroups, 128, 0, st>>>(bt, pass);
+    k_btransform<PMAX, CPT><<<grid, kBT, 0, st>>>(bt, pass);
+  }
+  prof_end(pf, KC_NORMALIZE, st);
+}
+
+int launch_block_iteration(const Batch& bt, const FineExact& fe, cudaStream_t st, int* nlaunch, Prof* pf) {
+  if (bt.bp <= 4) block_arnoldi_t<4, 4>(bt, fe, st, pf);
+  else if (bt.bp <= 8) block_arnoldi_t<8, 2>(bt, fe, st, pf);
+  else if (bt.bp <= 16) block_arnoldi_t<16, 1>(bt, fe, st, pf);
+  else return 1;
+    prof_begin(pf, KC_SHIFT_LS, st);
+  k_block_ls<<<bt.nbs, 32, 0, st>>>(bt);
+  prof_end(pf, KC_SHIFT_LS, st);
+  k_block_flags<<<1, 256, 0, st>>>(bt);
+  *nlaunch += 12;
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+void launch_block_backsolve(const Batch& bt, const int* sh_basis, cudaStream_t st) {
+  k_bbacksolve<<<(bt.nsh + 127) / 128, 128, 0, st>>>(bt, sh_basis);
+}
+
+void launch_block_xk(const Batch& bt, float2* X_hi, float2* X_lo, cudaStream_t st, Prof* pf) {
+  const dim3 g((unsigned)((bt.N + kBT - 1) / kBT), bt.nb);
+  prof_begin(pf, KC_XK, st);
+  k_bxk<<<g, kBT, 0, st>>>(bt, X_hi, X_lo);
+  prof_end(pf, KC_XK, st);
+}
+
+void launch_block_quad(const Batch& bt, const QuadItem* items, int nitems, const double2* wq, double2* C,
+                       int ns, int nr, int nt, const int64_t* rcells, double* out, int fields, cudaStream_t st) {
+  k_bquad_coef<<<nitems, 128, 0, st>>>(bt, items, nitems, wq, C);
+  if (fields) {
+    const dim3 g((unsigned)((bt.N + 255) / 256), ns * nt);
+    k_bfields<<<g, 256, 0, st>>>(bt, items, C, out);
+  } else {
+    const int n = ns * nr * nt;
+    k_bmeasure<<<(n + 127) / 128, 128, 0, st>>>(bt, items, C, ns, nr, nt, rcells, out);
+  }
+}
+
+}  // namespace lt

@@ -65,6 +65,9 @@ struct Workspace {
   float2* X_lo = nullptr;
   size_t x_elems = 0;
   float4* l0q = nullptr;          // [nb][N] finest-level scratch of the cluster-resident solve
+  // block flexible GMRES arrays (Batch::bdot .. grmax), sized for (p, groups, maxit, block shifts, shifts)
+  std::vector<void*> block_allocs;
+  int bk_p = 0, bk_G = 0, bk_M = 0, bk_nbs = 0, bk_nsh = 0;
 };
 
 struct lt_ctx {
@@ -200,6 +203,7 @@ int lt_default_options(lt_opts* o) {
   o->stop_rule = LT_STOP_SHIFT;
   o->tma_wait_polls = 1 << 26;
   o->gram_schmidt = 2;
+  o->block = 0;
   return LT_OK;
 }
 
@@ -244,6 +248,7 @@ int lt_set_stream(lt_ctx* ctx, void* stream) {
 
 static void free_ws(lt_ctx* ctx) {
   free_list(ctx->ws.allocs);
+  free_list(ctx->ws.block_allocs);
   ctx->ws = Workspace();
 }
 
@@ -308,6 +313,9 @@ int lt_set_options(lt_ctx* ctx, const lt_opts* o) {
   if (o->tma_wait_polls < 0) return fail(ctx, LT_ERR_INVALID_ARG, "tma_wait_polls=%d must be >= 0", o->tma_wait_polls);
   if (o->gram_schmidt != 1 && o->gram_schmidt != 2)
     return fail(ctx, LT_ERR_INVALID_ARG, "gram_schmidt=%d must be 1 or 2", o->gram_schmidt);
+  if (o->block != 0 && o->block != 1) return fail(ctx, LT_ERR_INVALID_ARG, "block=%d must be 0 or 1", o->block);
+  if (o->block && (o->krylov != LT_KRYLOV_GMRES || o->stop_rule != LT_STOP_SHIFT || o->precision != LT_PREC_FP64))
+    return fail(ctx, LT_ERR_INVALID_ARG, "block = 1 needs LT_KRYLOV_GMRES, LT_STOP_SHIFT and LT_PREC_FP64");
   ctx->opts = *o;
   ctx->mg.npre = o->mg_pre;
   ctx->mg.npost = o->mg_post;
@@ -754,6 +762,7 @@ struct Plan {
   int dense_b0 = -1;
   double beta0 = 0.0;
   std::vector<double> wabs;             // [nsh] |w_k qhat(z_k)| (quadrature stopping rule)
+  bool block = false;                   // block flexible GMRES over the sources of each group
 };
 
 // rhs: one point right-hand side per entry; the first n_src of them are sources (weights of the
@@ -942,6 +951,43 @@ static int ensure_ws(lt_ctx* ctx, const Plan& P) {
   return LT_OK;
 }
 
+// Arrays of the block flexible GMRES (block = 1): the bases q * G + g of group g form one block of
+// p = nb / G right-hand sides; the member-0 shifts [shift_off[0], shift_off[G]) index the block shifts.
+static int ensure_block_ws(lt_ctx* ctx, const Plan& P) {
+  Workspace& ws = ctx->ws;
+  lt::Batch& bt = ws.bt;
+  const int p = P.nb / P.G, G = P.G, M = ctx->opts.maxit, nbs = P.shift_off[G], nsh = P.nsh;
+  const size_t bld = (size_t)M * p, hld = (size_t)(M + 1) * p;
+  if (!(ws.bk_p == p && ws.bk_G == G && ws.bk_M == M && ws.bk_nbs == nbs && ws.bk_nsh == nsh)) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    free_list(ws.block_allocs);
+    ws.bk_p = ws.bk_G = ws.bk_M = ws.bk_nbs = ws.bk_nsh = 0;
+    auto& A = ws.block_allocs;
+    int rc = 0;
+#define AL(ptr, n) if ((rc = dalloc(ctx, A, &ptr, (size_t)(n)))) return rc
+    AL(bt.bdot, (size_t)G * 2 * bld * p);
+    AL(bt.bgram, (size_t)G * 2 * p * p);
+    AL(bt.bw, (size_t)G * 2 * p * p);
+    AL(bt.bH, (size_t)G * bld * hld);
+    AL(bt.bR, (size_t)nbs * bld * hld);
+    AL(bt.brc, (size_t)nbs * bld * p);
+    AL(bt.brs, (size_t)nbs * bld * p);
+    AL(bt.bG, (size_t)nbs * hld * p);
+    AL(bt.bY, (size_t)nsh * bld);
+    AL(bt.gany, G);
+    AL(bt.grmax, G);
+#undef AL
+    ws.bk_p = p; ws.bk_G = G; ws.bk_M = M; ws.bk_nbs = nbs; ws.bk_nsh = nsh;
+  }
+  bt.block = 1;
+  bt.bp = p;
+  bt.ngroups = G;
+  bt.bld = (int)bld;
+  bt.hld = (int)hld;
+  bt.nbs = nbs;
+  return LT_OK;
+}
+
 // State of the batched flexible shifted Krylov solves of one context between
 // the stages below (begin: tables, workspace, graph capture; launch: enqueue
 // outer iterations; poll: read the active flags; end: back-substitution, x_k,
@@ -991,7 +1037,8 @@ static int launch_iteration_cluster(lt_ctx* ctx, cudaStream_t q, int jj, int* nl
   lt::Batch& bt = ctx->ws.bt;
   const int nb = bt.nb;
   // (not inside lt_forward_noalloc, which creates no streams or events)
-  const int parts = (nb > ctx->inner.max_clusters && nb >= 2 && ctx->arena_base == nullptr) ? 2 : 1;
+  // (nor in block mode, whose Arnoldi process couples the bases of a group)
+  const int parts = (!bt.block && nb > ctx->inner.max_clusters && nb >= 2 && ctx->arena_base == nullptr) ? 2 : 1;
   if (parts == 2) {
     if (!ctx->side_stream) CK(cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking));
     if (!ctx->ev_fork) CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
@@ -1013,6 +1060,11 @@ static int launch_iteration_cluster(lt_ctx* ctx, cudaStream_t q, int jj, int* nl
                                  o.inner_cycles, qs, pf))
       return LT_ERR_CUDA;
     lt::launch_inner_record(v, qs);
+    if (bt.block) {
+      if (lt::launch_block_iteration(v, ctx->fe, qs, nlq, pf)) return LT_ERR_CUDA;
+      *nlq += 2;
+      continue;
+    }
     lt::launch_arnoldi(v, ctx->fe, jj, qs, nlq, pf);
     lt::launch_shift_ls_only(v, jj, qs);
     *nlq += 4;
@@ -1049,6 +1101,12 @@ static int launch_iteration(lt_ctx* ctx, cudaStream_t q, int jj, int* nlq, lt::P
   lt::launch_exact_residual(bt, ctx->fe, L0, jj, o.inner_rounds, 1, q, pf);
   lt::launch_inner_record(bt, q);
   *nlq += 2;
+  if (bt.block) {
+    if (lt::launch_block_iteration(bt, ctx->fe, q, nlq, pf)) return LT_ERR_CUDA;
+    lt::launch_next_iter(bt, q);
+    ++*nlq;
+    return LT_OK;
+  }
   lt::launch_arnoldi(bt, ctx->fe, jj, q, nlq, pf);
   lt::launch_shift_ls(bt, jj, q);
   *nlq += 2;
@@ -1082,8 +1140,15 @@ static int learned_tables(lt_ctx* ctx) {
 
 static int solve_begin(lt_ctx* ctx, const Plan& P, SolveState& S, int* nl) {
   const lt_opts& o = ctx->opts;
+  if (o.block && !P.block)
+    return fail(ctx, LT_ERR_INVALID_ARG, "block = 1 applies to lt_forward and lt_forward_fields only");
   int rc = ensure_ws(ctx, P);
   if (rc) return rc;
+  if (P.block) {
+    if ((rc = ensure_block_ws(ctx, P))) return rc;
+  } else {
+    ctx->ws.bt.block = 0;
+  }
   lt::Batch& bt = ctx->ws.bt;
   bt.nb = P.nb;
   bt.nsh = P.nsh;
@@ -1269,7 +1334,8 @@ static int solve_end(lt_ctx* ctx, const Plan& P, SolveState& S, std::vector<doub
   std::vector<void*> tmp;
   if ((rc = dalloc(ctx, tmp, &d_shb, P.nsh))) return rc;
   CK(cudaMemcpyAsync(d_shb, P.sh_basis.data(), P.nsh * sizeof(int), cudaMemcpyHostToDevice, s));
-  lt::launch_backsolve_map(bt, d_shb, s);
+  if (bt.block) lt::launch_block_backsolve(bt, d_shb, s);
+  else lt::launch_backsolve_map(bt, d_shb, s);
   ++*nl;
   true_res.assign(P.nsh, -1.0);
   if (o.true_residual || need_x) {
@@ -1282,7 +1348,8 @@ static int solve_end(lt_ctx* ctx, const Plan& P, SolveState& S, std::vector<doub
       if (o.precision == LT_PREC_FP64 && (rc = dalloc(ctx, ws.allocs, &ws.X_lo, need))) { free_list(tmp); return rc; }
       ws.x_elems = need;
     }
-    lt::launch_xk(bt, ws.X_hi, ws.X_lo, s, pf);
+    if (bt.block) lt::launch_block_xk(bt, ws.X_hi, ws.X_lo, s, pf);
+    else lt::launch_xk(bt, ws.X_hi, ws.X_lo, s, pf);
     ++*nl;
     if (o.true_residual) {
       double* d_res2 = nullptr;
@@ -1389,6 +1456,16 @@ static int forward_impl(lt_ctx* ctx, int nt, const double* times, double* out, i
   stats_reset(st, ctx->opts.true_residual);
   Plan P;
   make_plan(ctx, nt, times, ctx->src, P, (int)ctx->src.size(), !ctx->phi0.empty());
+  if (ctx->opts.block) {
+    if (ctx->arena_base) return fail(ctx, LT_ERR_INVALID_ARG, "lt_forward_noalloc does not support block = 1");
+    if (ctx->src.size() > 16) return fail(ctx, LT_ERR_INVALID_ARG, "block = 1 takes at most 16 sources");
+    if (!ctx->phi0.empty()) return fail(ctx, LT_ERR_INVALID_ARG, "block = 1 does not take an initial state");
+    for (size_t a = 0; a < ctx->src.size(); ++a)
+      for (size_t b = 0; b < a; ++b)
+        if (ctx->src[a] == ctx->src[b])
+          return fail(ctx, LT_ERR_INVALID_ARG, "block = 1 needs sources in distinct cells (%zu and %zu share one)", b, a);
+    P.block = true;
+  }
   int nl = 0;
   CK(cudaEventRecord(ctx->ev0, ctx->stream));
   std::vector<double> tres;
@@ -1436,7 +1513,8 @@ static int forward_finish(lt_ctx* ctx, const Plan& P, const std::vector<double>&
   double* d_out = nullptr;
   const size_t out_n = fields ? (size_t)ns * nt * ctx->N : (size_t)ns * nr * nt;
   if ((rc = dalloc(ctx, tmp, &d_items, items.size())) || (rc = dalloc(ctx, tmp, &d_wq, wq.size())) ||
-      (rc = dalloc(ctx, tmp, &d_C, items.size() * ctx->opts.maxit)) || (rc = dalloc(ctx, tmp, &d_rc, std::max(nr, 1)))) {
+      (rc = dalloc(ctx, tmp, &d_C, items.size() * (P.block ? (size_t)ctx->ws.bt.bld : (size_t)ctx->opts.maxit))) ||
+      (rc = dalloc(ctx, tmp, &d_rc, std::max(nr, 1)))) {
     free_list(tmp);
     return rc;
   }
@@ -1445,9 +1523,13 @@ static int forward_finish(lt_ctx* ctx, const Plan& P, const std::vector<double>&
   CK(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(lt::QuadItem), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(d_wq, wq.data(), wq.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
   if (nr) CK(cudaMemcpyAsync(d_rc, ctx->rec.data(), nr * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-  lt::launch_quad_coef(ctx->ws.bt, d_items, (int)items.size(), d_wq, d_C, s);
-  if (fields) lt::launch_fields(ctx->ws.bt, d_items, d_C, ns * nt, d_out, s, nt, dense_q0);
-  else lt::launch_measure(ctx->ws.bt, d_items, d_C, ns, nr, nt, d_rc, d_out, s, dense_q0);
+  if (P.block) {
+    lt::launch_block_quad(ctx->ws.bt, d_items, (int)items.size(), d_wq, d_C, ns, nr, nt, d_rc, d_out, fields, s);
+  } else {
+    lt::launch_quad_coef(ctx->ws.bt, d_items, (int)items.size(), d_wq, d_C, s);
+    if (fields) lt::launch_fields(ctx->ws.bt, d_items, d_C, ns * nt, d_out, s, nt, dense_q0);
+    else lt::launch_measure(ctx->ws.bt, d_items, d_C, ns, nr, nt, d_rc, d_out, s, dense_q0);
+  }
   nl += 2;
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev1, s));
@@ -2230,6 +2312,7 @@ extern "C" int lt_forward_noalloc(lt_ctx* ctx, int nt, const double* times, doub
   if (ctx->src.empty() || ctx->rec.empty()) return fail(ctx, LT_ERR_STATE, "sources and receivers must be set");
   if (!h) return fail(ctx, LT_ERR_INVALID_ARG, "h (device pointer) is null");
   if (ctx->opts.precond != 0) return fail(ctx, LT_ERR_INVALID_ARG, "lt_forward_noalloc supports only precond = 0");
+  if (ctx->opts.block) return fail(ctx, LT_ERR_INVALID_ARG, "lt_forward_noalloc does not support block = 1");
   if (ctx->device < 0 || ctx->device >= 256) return fail(ctx, LT_ERR_INVALID_ARG, "device ordinal out of range");
   CK(cudaSetDevice(ctx->device));
   void* base = nullptr;

@@ -86,6 +86,24 @@ struct Batch {
   // (M phi_0 / ||M phi_0||), df32 real
   const float* rhs_hi;
   const float* rhs_lo;
+  // block flexible GMRES (block = 1): the bases q * ngroups + g, q < bp, of group g form one block
+  int block;
+  int bp;                          // right-hand sides per block
+  int ngroups;                     // groups (blocks)
+  int bld;                         // block columns maxit * bp
+  int hld;                         // block rows (maxit + 1) * bp
+  int nbs;                         // shifts per block, summed over blocks (= the member-0 shifts)
+  double2* bdot;                   // [ngroups][2][bld][bp] Gram-Schmidt coefficients of both passes
+  double2* bgram;                  // [ngroups][2][bp][bp] Gram matrices of the two CholQR passes
+  float2* bw;                      // [ngroups][2][bp][bp] W = R^{-1} of the two passes, as applied
+  double2* bH;                     // [ngroups][bld][hld] block Hessenberg, column-major
+  double2* bR;                     // [nbs][bld][hld] rotated Hbar(z; T), column-major
+  double* brc;                     // [nbs][bld][bp] rotation cosines (p per column)
+  double2* brs;                    // [nbs][bld][bp] rotation sines
+  double2* bG;                     // [nbs][hld][bp] rotated right-hand sides E_1
+  double2* bY;                     // [nsh][bld] coefficients of each (shift, right-hand side)
+  int* gany;                       // [ngroups] some (shift, rhs) of the block still open
+  unsigned long long* grmax;       // [ngroups] largest open residual (bits of a non-negative double)
 };
 
 // kernel classes for the live per-kernel timing and work counters

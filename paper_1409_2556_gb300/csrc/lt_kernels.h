@@ -112,6 +112,12 @@ int geostat_solve(const double* J, size_t ldj, const double* G, int ny, int N, c
 void launch_xk(const Batch& bt, float2* X_hi, float2* X_lo, cudaStream_t st, Prof* pf);
 void launch_true_res(const Batch& bt, const FineExact& fe, const int* sh_basis, const float2* X_hi,
                      const float2* X_lo, double* res2, cudaStream_t st, Prof* pf);
+// block.cu: block flexible GMRES over the sources of each group (Batch::block)
+int launch_block_iteration(const Batch& bt, const FineExact& fe, cudaStream_t st, int* nlaunch, Prof* pf);
+void launch_block_backsolve(const Batch& bt, const int* sh_basis, cudaStream_t st);
+void launch_block_xk(const Batch& bt, float2* X_hi, float2* X_lo, cudaStream_t st, Prof* pf);
+void launch_block_quad(const Batch& bt, const QuadItem* items, int nitems, const double2* wq, double2* C,
+                       int ns, int nr, int nt, const int64_t* rcells, double* out, int fields, cudaStream_t st);
 
 }  // namespace lt
 
