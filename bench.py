@@ -501,6 +501,48 @@ def learned_gain(dev):
             "workload": LEARNED_WORKLOAD}
 
 
+def block_comparison(dev, steps: int = 3, warmup: int = 2):
+    """Config 2 with the sources of each time group as one block (block flexible GMRES-Sh) against
+    one basis per (source, group): step time on device-resident inputs, outer iterations,
+    preconditioner solves (sum over bases of their iterations) and the heads' relative difference."""
+    import numpy as np
+    import torch
+    from paper_1409_2556_gb300 import Engine
+    prob = workload(0)
+    stream = torch.cuda.Stream(device=dev)
+    ns, nr, nt = len(prob.src_cells), len(prob.rec_cells), len(prob.times)
+    out = {}
+    hs = {}
+    for blk in (0, 1):
+        eng = Engine(dev, stream=stream)
+        eng.load_problem(prob, **dict(SOLVE_OPTS, block=blk))
+        h = torch.zeros((ns, nr, nt), dtype=torch.float64, device=f"cuda:{dev}")
+        for _ in range(warmup):
+            eng.forward(prob.times, out=h)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        conv, solves, iters = 0, 0, 0
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(steps):
+                eng.forward(prob.times, out=h)
+                st = eng.last_stats
+                conv += st["n_converged"]
+                solves = st["outer_iters_sum"]
+                iters = st["outer_iters_max"]
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        hs[blk] = h.cpu().numpy()
+        out["block" if blk else "single"] = {"ms_per_step": ms, "value": conv / steps / (ms / 1e3), "unit": UNIT,
+                                             "outer_iters_max": iters, "preconditioner_solves": solves,
+                                             "max_true_residual": st["max_true_residual"]}
+        eng.close()
+    out["heads_rel_diff"] = float(np.linalg.norm(hs[1] - hs[0]) / np.linalg.norm(hs[0]))
+    out["workload"] = WORKLOAD_NAME
+    return out
+
+
 def run_reference(args, rank, world):
     """The oracle arm: O1 (contour + SuperLU per shifted system, FP64) on every host core, each step a
     bounded sample of the config-2 workload (2 shifted systems per core)."""
@@ -544,7 +586,7 @@ def main():
                     help="profiling only: run warmup + the timed steps, print nothing else")
     ap.add_argument("--sources", type=int, default=0,
                     help="profiling only: keep the first K wells (smaller device footprint)")
-    ap.add_argument("--only", default="", choices=["", "jacobian", "batch", "gn"],
+    ap.add_argument("--only", default="", choices=["", "jacobian", "batch", "gn", "block"],
                     help="profiling only: run one extra leg (config-3 Jacobian or the config-5 batch) and print it")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -571,7 +613,8 @@ def main():
     if args.only:
         stream = torch.cuda.Stream(device=dev)
         res = (jacobian_rows(dev, stream) if args.only == "jacobian" else
-               gn_timing(dev) if args.only == "gn" else batch_throughput(dev))
+               gn_timing(dev) if args.only == "gn" else
+               block_comparison(dev) if args.only == "block" else batch_throughput(dev))
         print(json.dumps({"only": args.only, **res}), flush=True)
         return
     prob = workload(rank)

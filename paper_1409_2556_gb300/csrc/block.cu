@@ -16,6 +16,7 @@
 //   column q of the rotated E_1, falls to tol/2.
 // Column c = i * p + q' of the block is column i of member q'.  The point right-hand sides e_cell
 // of distinct cells are orthonormal, so V_1 = B and beta = I.
+#include <algorithm>
 #include <cstdio>
 #include "df32.cuh"
 #include "exact.cuh"
@@ -36,48 +37,80 @@ __device__ __forceinline__ size_t ucol_off(const Batch& bt, int g, int col) {
   return ((size_t)(q * bt.ngroups + g) * bt.maxit + i) * bt.N;
 }
 
-// Column dots D[col][q] += x_col^H s_q for col < ncol, q < p, from the hi planes: s holds the
-// thread's CPT cells (cell0 + c * kBT) of every member; xcol(col) points at column col.  Per
-// column, each warp reduces its 2p partial sums by shuffles and adds them into float shared
-// accumulators; each chunk of columns ends with one double atomicAdd per (col, q) and CTA.
-template <int PMAX, int CPT, class XCol>
-__device__ void block_dots(XCol xcol, int ncol, int p, int N, int cell0, const float2 (&s)[PMAX][CPT], double2* D,
-                           float2* acc) {
+// Sum of NV = 2^k values over the warp, scattered: on return lane l holds the warp total of value
+// index l >> (5 - k) (halving exchanges while the values outnumber the lanes left, then plain
+// butterfly steps): NV - 1 shuffles instead of 5 NV.
+template <int NV>
+__device__ __forceinline__ float warp_reduce_scatter(float (&v)[NV], int lane) {
+  int o = 16;
+#pragma unroll
+  for (int h = NV / 2; h >= 1; h >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const float send = up ? v[i] : v[i + h];
+      const float keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+    o >>= 1;
+  }
+  float r = v[0];
+  for (; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  return r;
+}
+template <int NV>
+struct Log2 { static constexpr int v = 1 + Log2<NV / 2>::v; };
+template <>
+struct Log2<1> { static constexpr int v = 0; };
+
+// Tiles of kBT * CPT cells; a CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+template <int CPT>
+__device__ __forceinline__ int n_tiles(int N) { return (N + kBT * CPT - 1) / (kBT * CPT); }
+
+// Column dots D[col][q] += x_col^H s_q for col < ncol, q < p, from the hi planes, over the CTA's
+// tiles: load(cell0, s) gives the members' values at the thread's CPT cells (cell0 + c * kBT) of a
+// tile; xcol(col) points at column col.  Per column each warp reduce-scatters its 2 PMAX partial
+// sums and adds them into float shared accumulators; a chunk of columns ends with one double
+// atomicAdd per (col, q) and CTA.
+template <int PMAX, int CPT, class Load, class XCol>
+__device__ void block_dots(Load load, XCol xcol, int ncol, int p, int N, double2* D, float2* acc) {
   constexpr int CH = kBAcc / PMAX;
+  constexpr int NV = 2 * PMAX;
+  constexpr int SH = 5 - Log2<NV>::v;
   const int lane = threadIdx.x & 31;
+  const int idx = lane >> SH;
+  const bool owner = (lane & ((1 << SH) - 1)) == 0;
+  const int q_own = idx < PMAX ? idx : idx - PMAX;
+  const int nt = n_tiles<CPT>(N);
   for (int cb = 0; cb < ncol; cb += CH) {
     const int ce = min(cb + CH, ncol);
     for (int i = threadIdx.x; i < (ce - cb) * p; i += blockDim.x) acc[i] = make_float2(0.f, 0.f);
     __syncthreads();
-    for (int col = cb; col < ce; ++col) {
-      const float2* x = xcol(col);
-      float re[PMAX], im[PMAX];
+    for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+      const int cell0 = tile * kBT * CPT + threadIdx.x;
+      float2 s[PMAX][CPT];
+      load(cell0, s);
+      for (int col = cb; col < ce; ++col) {
+        const float2* x = xcol(col);
+        float v[NV];
 #pragma unroll
-      for (int q = 0; q < PMAX; ++q) re[q] = im[q] = 0.f;
+        for (int q = 0; q < NV; ++q) v[q] = 0.f;
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) {
-        const int cell = cell0 + c * kBT;
-        if (cell < N) {
-          const float2 a = x[cell];
+        for (int c = 0; c < CPT; ++c) {
+          const int cell = cell0 + c * kBT;
+          if (cell < N) {
+            const float2 a = x[cell];
 #pragma unroll
-          for (int q = 0; q < PMAX; ++q) {
-            re[q] = fmaf(a.x, s[q][c].x, fmaf(a.y, s[q][c].y, re[q]));
-            im[q] = fmaf(a.x, s[q][c].y, fmaf(-a.y, s[q][c].x, im[q]));
+            for (int q = 0; q < PMAX; ++q) {
+              v[q] = fmaf(a.x, s[q][c].x, fmaf(a.y, s[q][c].y, v[q]));
+              v[PMAX + q] = fmaf(a.x, s[q][c].y, fmaf(-a.y, s[q][c].x, v[PMAX + q]));
+            }
           }
         }
-      }
-#pragma unroll
-      for (int q = 0; q < PMAX; ++q) {
-        if (q < p) {
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            re[q] += __shfl_xor_sync(0xffffffffu, re[q], o);
-            im[q] += __shfl_xor_sync(0xffffffffu, im[q], o);
-          }
-          if (lane == 0) {
-            atomicAdd(&acc[(col - cb) * p + q].x, re[q]);
-            atomicAdd(&acc[(col - cb) * p + q].y, im[q]);
-          }
+        const float r = warp_reduce_scatter<NV>(v, lane);
+        if (owner && q_own < p) {
+          float* dst = idx < PMAX ? &acc[(col - cb) * p + q_own].x : &acc[(col - cb) * p + q_own].y;
+          atomicAdd(dst, r);
         }
       }
     }
@@ -116,27 +149,34 @@ __global__ void __launch_bounds__(kBT) k_bdots(Batch bt, FineExact fe) {
   const int g = blockIdx.y;
   if (!bt.active[g]) return;
   const int j = *bt.jdev, p = bt.bp, N = fe.N, G = bt.ngroups;
-  const int cell0 = blockIdx.x * kBT * CPT + threadIdx.x;
-  float2 s[PMAX][CPT];
+  auto load = [&](int cell0, float2 (&s)[PMAX][CPT]) {
 #pragma unroll
-  for (int q = 0; q < PMAX; ++q)
+    for (int q = 0; q < PMAX; ++q)
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-      const int cell = cell0 + c * kBT;
-      s[q][c] = make_float2(0.f, 0.f);
-      if (q < p && cell < N) {
-        const float2 u = bt.U_hi[((size_t)(q * G + g) * bt.maxit + j) * bt.N + cell];
-        const float m = fe.m_hi[cell];
-        s[q][c] = make_float2(m * u.x, m * u.y);
+      for (int c = 0; c < CPT; ++c) {
+        const int cell = cell0 + c * kBT;
+        s[q][c] = make_float2(0.f, 0.f);
+        if (q < p && cell < N) {
+          const float2 u = bt.U_hi[((size_t)(q * G + g) * bt.maxit + j) * bt.N + cell];
+          const float m = fe.m_hi[cell];
+          s[q][c] = make_float2(m * u.x, m * u.y);
+        }
       }
-    }
+  };
   const float2* V = bt.V_hi;
   auto xcol = [&](int col) { return V + vcol_off(bt, g, col); };
-  block_dots<PMAX, CPT>(xcol, (j + 1) * p, p, N, cell0, s, bt.bdot + (size_t)g * 2 * bt.bld * p, acc);
+  block_dots<PMAX, CPT>(load, xcol, (j + 1) * p, p, N, bt.bdot + (size_t)g * 2 * bt.bld * p, acc);
 }
 
-// mode 0: s_q = M u_j^{(q)} - sum_col v_col c1[col][q] (df32), S_q <- s_q, and the second pass's
-// dots bdot[g][1] = V^H s; mode 1: S_q <- S_q - sum_col v_col c2[col][q]
+// Gram-Schmidt updates of the block over the CTA's tiles.
+// mode 0: s_q = M u_j^{(q)} - sum_col v_col c1[col][q] in df32 (the first pass cancels most of
+//   M u_j, so every product enters exactly), S_q <- s_q, then the second pass's dots
+//   bdot[g][1] = V^H S;
+// mode 1: S_q <- S_q - sum_col v_col c2[col][q].  The second-pass coefficients are of the order of
+//   the first pass's float32 dot error (about 2^-24 ||M u_j||), so their products are formed in
+//   float32 from the hi planes and folded into the df32 S every 8 columns: the Arnoldi relation
+//   keeps an error near 2^-24 * 2^-24 * 8 * sqrt(columns / 8) of ||M u_j|| (about 1e-13), while
+//   the pass costs a seventh of the df32 one.
 template <int PMAX, int CPT>
 __global__ void __launch_bounds__(kBT) k_bupdate(Batch bt, FineExact fe, int mode) {
   __shared__ float2 cf[kBAcc];
@@ -146,70 +186,112 @@ __global__ void __launch_bounds__(kBT) k_bupdate(Batch bt, FineExact fe, int mod
   if (!bt.active[g]) return;
   const int j = *bt.jdev, p = bt.bp, N = fe.N, G = bt.ngroups;
   const int ncol = (j + 1) * p;
-  const int cell0 = blockIdx.x * kBT * CPT + threadIdx.x;
-  cdf s[PMAX][CPT];
-#pragma unroll
-  for (int q = 0; q < PMAX; ++q)
-#pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-      const int cell = cell0 + c * kBT;
-      s[q][c] = {{0.f, 0.f}, {0.f, 0.f}};
-      if (q < p && cell < N) {
-        const size_t b = (size_t)(q * G + g);
-        s[q][c] = mode == 0 ? cdf_mul_r(load_cdf(bt.U_hi, bt.U_lo, (b * bt.maxit + j) * bt.N + cell),
-                                        ldf(fe.m_hi, fe.m_lo, cell))
-                            : load_cdf(bt.S_hi, bt.S_lo, b * bt.N + cell);
-      }
-    }
+  const int nt = n_tiles<CPT>(N);
   const double2* D = bt.bdot + ((size_t)g * 2 + mode) * bt.bld * p;
-  for (int cb = 0; cb < ncol; cb += CH) {
-    const int ce = min(cb + CH, ncol);
-    __syncthreads();
-    for (int i = threadIdx.x; i < (ce - cb) * p; i += blockDim.x) {
-      const double2 d = D[(size_t)cb * p + i];
-      cf[i] = make_float2((float)d.x, (float)d.y);
-    }
-    __syncthreads();
-    for (int col = cb; col < ce; ++col) {
-      const size_t off = vcol_off(bt, g, col);
-      const float2* vh = bt.V_hi + off;
-      const float2* vl = lo_at(bt.V_lo, off);
+  unsigned long long cells = 0;
+  for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    const int cell0 = tile * kBT * CPT + threadIdx.x;
+    cdf s[PMAX][CPT];
+#pragma unroll
+    for (int q = 0; q < PMAX; ++q)
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
         const int cell = cell0 + c * kBT;
-        if (cell < N) {
-          const cdf v = load_cdf(vh, vl, cell);
+        s[q][c] = {{0.f, 0.f}, {0.f, 0.f}};
+        if (q < p && cell < N) {
+          const size_t b = (size_t)(q * G + g);
+          s[q][c] = mode == 0 ? cdf_mul_r(load_cdf(bt.U_hi, bt.U_lo, (b * bt.maxit + j) * bt.N + cell),
+                                          ldf(fe.m_hi, fe.m_lo, cell))
+                              : load_cdf(bt.S_hi, bt.S_lo, b * bt.N + cell);
+        }
+      }
+    for (int cb = 0; cb < ncol; cb += CH) {
+      const int ce = min(cb + CH, ncol);
+      __syncthreads();
+      for (int i = threadIdx.x; i < (ce - cb) * p; i += blockDim.x) {
+        const double2 d = D[(size_t)cb * p + i];
+        cf[i] = make_float2((float)d.x, (float)d.y);
+      }
+      __syncthreads();
+      if (mode == 0) {
+        for (int col = cb; col < ce; ++col) {
+          const size_t off = vcol_off(bt, g, col);
+          const float2* vh = bt.V_hi + off;
+          const float2* vl = lo_at(bt.V_lo, off);
+#pragma unroll
+          for (int c = 0; c < CPT; ++c) {
+            const int cell = cell0 + c * kBT;
+            if (cell < N) {
+              const cdf v = load_cdf(vh, vl, cell);
+#pragma unroll
+              for (int q = 0; q < PMAX; ++q)
+                if (q < p) {
+                  const float2 k = cf[(col - cb) * p + q];
+                  s[q][c] = cdf_sub_mul_cf(s[q][c], v, k.x, k.y);
+                }
+            }
+          }
+        }
+      } else {
+        for (int c8 = cb; c8 < ce; c8 += 8) {
+          const int c8e = min(c8 + 8, ce);
+          float2 t[PMAX][CPT];
 #pragma unroll
           for (int q = 0; q < PMAX; ++q)
-            if (q < p) {
-              const float2 k = cf[(col - cb) * p + q];
-              s[q][c] = cdf_sub_mul_cf(s[q][c], v, k.x, k.y);
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) t[q][c] = make_float2(0.f, 0.f);
+          for (int col = c8; col < c8e; ++col) {
+            const float2* vh = bt.V_hi + vcol_off(bt, g, col);
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+              const int cell = cell0 + c * kBT;
+              if (cell < N) {
+                const float2 v = vh[cell];
+#pragma unroll
+                for (int q = 0; q < PMAX; ++q)
+                  if (q < p) {
+                    const float2 k = cf[(col - cb) * p + q];
+                    t[q][c].x = fmaf(v.x, k.x, fmaf(-v.y, k.y, t[q][c].x));
+                    t[q][c].y = fmaf(v.x, k.y, fmaf(v.y, k.x, t[q][c].y));
+                  }
+              }
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < PMAX; ++q)
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+              s[q][c].re = df_add_f(s[q][c].re, -t[q][c].x);
+              s[q][c].im = df_add_f(s[q][c].im, -t[q][c].y);
             }
         }
       }
     }
-  }
-#pragma unroll
-  for (int q = 0; q < PMAX; ++q)
-#pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-      const int cell = cell0 + c * kBT;
-      if (q < p && cell < N) store_cdf(bt.S_hi, bt.S_lo, (size_t)(q * G + g) * bt.N + cell, s[q][c]);
-    }
-  if (mode == 0) {
-    float2 sh[PMAX][CPT];
 #pragma unroll
     for (int q = 0; q < PMAX; ++q)
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) sh[q][c] = make_float2(s[q][c].re.hi, s[q][c].im.hi);
+      for (int c = 0; c < CPT; ++c) {
+        const int cell = cell0 + c * kBT;
+        if (q < p && cell < N) store_cdf(bt.S_hi, bt.S_lo, (size_t)(q * G + g) * bt.N + cell, s[q][c]);
+      }
+    cells += (unsigned long long)min(kBT * CPT, N - tile * kBT * CPT);
+  }
+  if (mode == 0) {
+    // the thread reads back the S cells it wrote itself
+    auto load = [&](int cell0, float2 (&sh)[PMAX][CPT]) {
+#pragma unroll
+      for (int q = 0; q < PMAX; ++q)
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          const int cell = cell0 + c * kBT;
+          sh[q][c] = (q < p && cell < N) ? bt.S_hi[(size_t)(q * G + g) * bt.N + cell] : make_float2(0.f, 0.f);
+        }
+    };
     const float2* V = bt.V_hi;
     auto xcol = [&](int col) { return V + vcol_off(bt, g, col); };
-    block_dots<PMAX, CPT>(xcol, ncol, p, N, cell0, sh, bt.bdot + ((size_t)g * 2 + 1) * bt.bld * p, acc);
+    block_dots<PMAX, CPT>(load, xcol, ncol, p, N, bt.bdot + ((size_t)g * 2 + 1) * bt.bld * p, acc);
   }
-  if (threadIdx.x == 0) {
-    const int n = min(kBT * CPT, N - (int)(blockIdx.x * kBT * CPT));
-    atomicAdd(&bt.work[KC_ORTHO], (unsigned long long)n * (unsigned long long)ncol);
-  }
+  if (threadIdx.x == 0) atomicAdd(&bt.work[KC_ORTHO], cells * (unsigned long long)ncol * p);
 }
 
 // Gram matrix of the block's new vectors, from the hi planes: pass 0 of S (after Gram-Schmidt),
@@ -220,23 +302,24 @@ __global__ void __launch_bounds__(kBT) k_bgram(Batch bt, int pass) {
   const int g = blockIdx.y;
   if (!bt.active[g]) return;
   const int j = *bt.jdev, p = bt.bp, N = (int)bt.N, G = bt.ngroups;
-  const int cell0 = blockIdx.x * kBT * CPT + threadIdx.x;
   auto xcol = [&](int a) {
     const size_t b = (size_t)(a * G + g);
     return pass == 0 ? bt.S_hi + b * bt.N : bt.V_hi + (b * (bt.maxit + 1) + j + 1) * bt.N;
   };
-  float2 s[PMAX][CPT];
+  auto load = [&](int cell0, float2 (&s)[PMAX][CPT]) {
 #pragma unroll
-  for (int q = 0; q < PMAX; ++q) {
-    const float2* x = q < p ? xcol(q) : nullptr;
+    for (int q = 0; q < PMAX; ++q) {
+      const float2* x = xcol(q < p ? q : 0);
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-      const int cell = cell0 + c * kBT;
-      s[q][c] = (q < p && cell < N) ? x[cell] : make_float2(0.f, 0.f);
+      for (int c = 0; c < CPT; ++c) {
+        const int cell = cell0 + c * kBT;
+        s[q][c] = (q < p && cell < N) ? x[cell] : make_float2(0.f, 0.f);
+      }
     }
-  }
-  block_dots<PMAX, CPT>(xcol, p, p, N, cell0, s, bt.bgram + ((size_t)g * 2 + pass) * p * p, acc);
+  };
+  block_dots<PMAX, CPT>(load, xcol, p, p, N, bt.bgram + ((size_t)g * 2 + pass) * p * p, acc);
 }
+
 
 __device__ __forceinline__ double2 bz_mul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -420,9 +503,14 @@ __device__ __forceinline__ int bshift_group(const Batch& bt, int bs) {
 // jp + q), then its own p rotations per column, in column order; lanes 16 + q carry column q of the
 // rotated right-hand side E_1 (beta = I).  The rotated matrix R (upper triangular) and the
 // rotated right-hand side are kept per shift for the back-substitution.
+// The rotations of an earlier column cc act on rows cc..cc+p only, so a lane walks its column down
+// with a window of p+1 rows in registers: row cc leaves the window final, row cc+p+1 enters it
+// from H; the earlier rotations come through shared memory, kBLsChunk columns at a time.
+constexpr int kBLsChunk = 32;
+template <int PMAX>
 __global__ void __launch_bounds__(32) k_block_ls(Batch bt) {
-  __shared__ double rc_s[16];
-  __shared__ double2 rs_s[16];
+  __shared__ double rc_s[kBLsChunk * PMAX];
+  __shared__ double2 rs_s[kBLsChunk * PMAX];
   const int bs = blockIdx.x;
   const int g = bshift_group(bt, bs);
   if (!bt.active[g]) return;
@@ -441,17 +529,59 @@ __global__ void __launch_bounds__(32) k_block_ls(Batch bt) {
   double2* Gr = bt.bG + (size_t)bs * hld * p;
   const double2* H = bt.bH + (size_t)g * bt.bld * hld;
   const int c0 = j * p;
-  if (lane < p) {
-    const int c = c0 + lane;
-    double2* Rc = R + (size_t)c * hld;
-    const double2* Hc = H + (size_t)c * hld;
-    for (int r = 0; r <= c + p; ++r) {
-      double2 v = bz_mul(dz, Hc[r]);
+  const bool col_lane = lane < p;
+  const int c = c0 + (col_lane ? lane : 0);
+  double2* Rc = R + (size_t)c * hld;
+  const double2* Hc = H + (size_t)c * hld;
+  // row r of column c of Hbar(z; T_j); rows below c + p are zero (and never written in H)
+  auto hz = [&](int r) {
+    double2 v = make_double2(0.0, 0.0);
+    if (r <= c + p) {
+      v = bz_mul(dz, Hc[r]);
       if (r == c) v.x += 1.0;
-      Rc[r] = v;
     }
-    for (int cc = 0; cc < c0; ++cc)
-      for (int k = 0; k < p; ++k) brot(Rc, cc, cc + 1 + k, rcs[(size_t)cc * p + k], rss[(size_t)cc * p + k]);
+    return v;
+  };
+  double2 win[PMAX + 1];
+#pragma unroll
+  for (int r = 0; r <= PMAX; ++r) win[r] = (col_lane && r <= p) ? hz(r) : make_double2(0.0, 0.0);
+  for (int cb = 0; cb < c0; cb += kBLsChunk) {
+    const int ce = min(cb + kBLsChunk, c0);
+    __syncwarp();
+    for (int i = lane; i < (ce - cb) * p; i += 32) {
+      rc_s[i] = rcs[(size_t)cb * p + i];
+      rs_s[i] = rss[(size_t)cb * p + i];
+    }
+    __syncwarp();
+    if (col_lane) {
+      for (int cc = cb; cc < ce; ++cc) {
+        const double* rcp = rc_s + (cc - cb) * p;
+        const double2* rsp = rs_s + (cc - cb) * p;
+        const double2 nv = hz(cc + p + 1);
+#pragma unroll
+        for (int k = 0; k < PMAX; ++k)
+          if (k < p) {
+            const double cs = rcp[k];
+            const double2 sn = rsp[k];
+            const double2 a = win[0], b = win[1 + k];
+            const double2 sb = bz_mul(sn, b), sa = bz_cmul(sn, a);
+            win[0] = make_double2(cs * a.x + sb.x, cs * a.y + sb.y);
+            win[1 + k] = make_double2(cs * b.x - sa.x, cs * b.y - sa.y);
+          }
+        Rc[cc] = win[0];
+#pragma unroll
+        for (int r = 0; r < PMAX; ++r) win[r] = win[r + 1];
+#pragma unroll
+        for (int r = 0; r <= PMAX; ++r)
+          if (r == p) win[r] = nv;
+      }
+    }
+  }
+  if (col_lane) {
+#pragma unroll
+    for (int r = 0; r <= PMAX; ++r)
+      if (r <= p) Rc[c0 + r] = win[r];
+    for (int r = c0 + p + 1; r <= c + p; ++r) Rc[r] = hz(r);
   } else if (lane >= 16 && lane - 16 < p) {
     const int q = lane - 16;
     if (j == 0)
@@ -460,27 +590,25 @@ __global__ void __launch_bounds__(32) k_block_ls(Batch bt) {
   }
   __syncwarp();
   for (int qq = 0; qq < p; ++qq) {
-    const int c = c0 + qq;
+    const int cn = c0 + qq;
     if (lane == qq) {
-      double2* Rc = R + (size_t)c * hld;
       for (int k = 0; k < p; ++k) {
         double cs;
         double2 sn, r;
-        bgivens(Rc[c], Rc[c + 1 + k], cs, sn, r);
-        Rc[c] = r;
-        Rc[c + 1 + k] = make_double2(0.0, 0.0);
-        rcs[(size_t)c * p + k] = cs;
-        rss[(size_t)c * p + k] = sn;
+        bgivens(Rc[cn], Rc[cn + 1 + k], cs, sn, r);
+        Rc[cn] = r;
+        Rc[cn + 1 + k] = make_double2(0.0, 0.0);
+        rcs[(size_t)cn * p + k] = cs;
+        rss[(size_t)cn * p + k] = sn;
         rc_s[k] = cs;
         rs_s[k] = sn;
       }
     }
     __syncwarp();
-    if (lane < p && lane > qq) {
-      double2* Rl = R + (size_t)(c0 + lane) * hld;
-      for (int k = 0; k < p; ++k) brot(Rl, c, c + 1 + k, rc_s[k], rs_s[k]);
+    if (col_lane && lane > qq) {
+      for (int k = 0; k < p; ++k) brot(Rc, cn, cn + 1 + k, rc_s[k], rs_s[k]);
     } else if (lane >= 16 && lane - 16 < p) {
-      for (int k = 0; k < p; ++k) brot_g(Gr, p, lane - 16, c, c + 1 + k, rc_s[k], rs_s[k]);
+      for (int k = 0; k < p; ++k) brot_g(Gr, p, lane - 16, cn, cn + 1 + k, rc_s[k], rs_s[k]);
     }
     __syncwarp();
   }
@@ -545,21 +673,25 @@ __global__ void k_bbacksolve(Batch bt, const int* sh_basis) {
 constexpr int kBXS = 16;    // shifts per pass of the solution kernel
 constexpr int kBXC = 128;   // coefficient columns staged per pass
 
-__device__ __forceinline__ cdf bcdf_fma(cdf acc, cdf u, cdf y) {   // acc + u * y
-  const df nyi = df_neg(y.im);
-  return {df_add(acc.re, df_add(df_mul(u.re, y.re), df_mul(u.im, nyi))),
-          df_add(acc.im, df_add(df_mul(u.re, y.im), df_mul(u.im, y.re)))};
-}
-
-// X[sh] = sum_c U_c y_sh[c] over the block's columns (every member's U), df32
+// X[sh] = sum_c U_c y_sh[c] over the block's columns (every member's U), df32.  A chunk of kBXS
+// shifts runs over the columns of its latest-converging shift only (the coefficients beyond a
+// shift's own convergence are zero).
 __global__ void __launch_bounds__(kBT) k_bxk(Batch bt, float2* X_hi, float2* X_lo) {
   __shared__ cdf ys[kBXS][kBXC];
+  __shared__ int s_n;
   const int b = blockIdx.y;
   const int g = b % bt.ngroups;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = bt.nit[b] * bt.bp;
   const int s0 = bt.shift_off[b], s1 = bt.shift_off[b + 1];
   for (int sa = s0; sa < s1; sa += kBXS) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int m = 0;
+      for (int sh = sa; sh < min(sa + kBXS, s1); ++sh) m = max(m, bt.conv_it[sh] > 0 ? bt.conv_it[sh] : bt.nit[b]);
+      s_n = m * bt.bp;
+    }
+    __syncthreads();
+    const int n = s_n;
     cdf acc[kBXS];
 #pragma unroll
     for (int q = 0; q < kBXS; ++q) acc[q] = {{0.f, 0.f}, {0.f, 0.f}};
@@ -578,7 +710,7 @@ __global__ void __launch_bounds__(kBT) k_bxk(Batch bt, float2* X_hi, float2* X_l
           const size_t off = ucol_off(bt, g, col);
           const cdf u = load_cdf(bt.U_hi + off, lo_at(bt.U_lo, off), c);
 #pragma unroll
-          for (int q = 0; q < kBXS; ++q) acc[q] = bcdf_fma(acc[q], u, ys[q][col - cb]);
+          for (int q = 0; q < kBXS; ++q) acc[q] = cdf_fma(acc[q], u, ys[q][col - cb]);
         }
     }
     if (c < bt.N)
@@ -635,35 +767,59 @@ __global__ void k_bfields(Batch bt, const QuadItem* items, const double2* C, dou
 }
 
 // ------------------------------------------------------------------ host launchers
-template <int PMAX, int CPT>
+static int device_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+  }
+  return sms;
+}
+
+// CTAs per group for the tile-looping kernels: about four CTAs per SM over all groups, every CTA
+// with the same number of tiles
+static unsigned tile_grid(int64_t N, int cpt, int groups) {
+  const int64_t nt = (N + kBT * cpt - 1) / (kBT * cpt);
+  const int64_t target = std::max<int64_t>(1, 4 * device_sms() / std::max(groups, 1));
+  const int64_t per = (nt + target - 1) / target;
+  return (unsigned)((nt + per - 1) / per);
+}
+
+// PMAX: register layout for up to PMAX right-hand sides; CPTD, CPTU: cells per thread of the dot
+// kernels and of the update kernels
+template <int PMAX, int CPTD, int CPTU>
 static void block_arnoldi_t(const Batch& bt, const FineExact& fe, cudaStream_t st, Prof* pf) {
-  const dim3 grid((unsigned)((fe.N + kBT * CPT - 1) / (kBT * CPT)), bt.ngroups);
-  k_bzero<<<bt.ngroups, 256, 0, st>>>(bt);
+  const int G = bt.ngroups;
+  const dim3 gd(tile_grid(fe.N, CPTD, G), G), gu(tile_grid(fe.N, CPTU, G), G);
+  const dim3 gt((unsigned)((fe.N + kBT * CPTU - 1) / (kBT * CPTU)), G);
+  k_bzero<<<G, 256, 0, st>>>(bt);
   prof_begin(pf, KC_DOTS, st);
-  k_bdots<PMAX, CPT><<<grid, kBT, 0, st>>>(bt, fe);
+  k_bdots<PMAX, CPTD><<<gd, kBT, 0, st>>>(bt, fe);
   prof_end(pf, KC_DOTS, st);
   for (int mode = 0; mode < 2; ++mode) {
     prof_begin(pf, KC_ORTHO, st);
-    k_bupdate<PMAX, CPT><<<grid, kBT, 0, st>>>(bt, fe, mode);
+    k_bupdate<PMAX, CPTU><<<gu, kBT, 0, st>>>(bt, fe, mode);
     prof_end(pf, KC_ORTHO, st);
   }
   prof_begin(pf, KC_NORMALIZE, st);
   for (int pass = 0; pass < 2; ++pass) {
-    k_bgram<PMAX, CPT><<<grid, kBT, 0, st>>>(bt, pass);
-    k_bchol<<<bt.ngroups, 128, 0, st>>>(bt, pass);
-    k_btransform<PMAX, CPT><<<grid, kBT, 0, st>>>(bt, pass);
+    k_bgram<PMAX, CPTD><<<gd, kBT, 0, st>>>(bt, pass);
+    k_bchol<<<G, 128, 0, st>>>(bt, pass);
+    k_btransform<PMAX, CPTU><<<gt, kBT, 0, st>>>(bt, pass);
   }
   prof_end(pf, KC_NORMALIZE, st);
+  prof_begin(pf, KC_SHIFT_LS, st);
+  k_block_ls<PMAX><<<bt.nbs, 32, 0, st>>>(bt);
+  prof_end(pf, KC_SHIFT_LS, st);
 }
 
 int launch_block_iteration(const Batch& bt, const FineExact& fe, cudaStream_t st, int* nlaunch, Prof* pf) {
-  if (bt.bp <= 4) block_arnoldi_t<4, 4>(bt, fe, st, pf);
-  else if (bt.bp <= 8) block_arnoldi_t<8, 2>(bt, fe, st, pf);
-  else if (bt.bp <= 16) block_arnoldi_t<16, 1>(bt, fe, st, pf);
+  if (bt.bp <= 4) block_arnoldi_t<4, 4, 4>(bt, fe, st, pf);
+  else if (bt.bp <= 8) block_arnoldi_t<8, 4, 2>(bt, fe, st, pf);
+  else if (bt.bp <= 16) block_arnoldi_t<16, 2, 1>(bt, fe, st, pf);
   else return 1;
-    prof_begin(pf, KC_SHIFT_LS, st);
-  k_block_ls<<<bt.nbs, 32, 0, st>>>(bt);
-  prof_end(pf, KC_SHIFT_LS, st);
   k_block_flags<<<1, 256, 0, st>>>(bt);
   *nlaunch += 12;
   return cudaGetLastError() == cudaSuccess ? 0 : 1;

@@ -132,4 +132,28 @@ __device__ __forceinline__ cdf cdf_mul_cf(cdf a, float cr, float ci) {
   return {df_sub(df_mul_f(a.re, cr), df_mul_f(a.im, ci)), df_add(df_mul_f(a.re, ci), df_mul_f(a.im, cr))};
 }
 
+// acc + u * y for df32 complex values, with one renormalisation per component: the two hi x hi
+// products enter the running sum through TwoSum, their rounding errors and the hi x lo cross terms
+// go to the low word.
+__device__ __forceinline__ df df_fma2(df acc, df a, df b, df c, df d) {   // acc + a*b - c*d
+  float p1, e1, p2, e2, s1, t1, s2, t2;
+  two_prod(a.hi, b.hi, p1, e1);
+  two_prod(c.hi, d.hi, p2, e2);
+  two_sum(acc.hi, p1, s1, t1);
+  two_sum(s1, -p2, s2, t2);
+  float lo = __fadd_rn(acc.lo, __fadd_rn(t1, t2));
+  lo = __fadd_rn(lo, __fsub_rn(e1, e2));
+  lo = __fmaf_rn(a.hi, b.lo, lo);
+  lo = __fmaf_rn(a.lo, b.hi, lo);
+  lo = __fmaf_rn(-c.hi, d.lo, lo);
+  lo = __fmaf_rn(-c.lo, d.hi, lo);
+  df r;
+  fast_two_sum(s2, lo, r.hi, r.lo);
+  return r;
+}
+// acc + u y for df32 complex u and y
+__device__ __forceinline__ cdf cdf_fma(cdf acc, cdf u, cdf y) {
+  return {df_fma2(acc.re, u.re, y.re, u.im, y.im), df_fma2(acc.im, u.re, y.im, df_neg(u.im), y.re)};
+}
+
 }  // namespace lt

@@ -310,7 +310,11 @@ __global__ void __launch_bounds__(kArnT, 6) k_dots1(Batch bt, FineExact fe, int)
 }
 
 // mode 0 (pass 2): s' = M u_j - V c1 (df32, exact); dot[1][i] = V_hi[i]^H s'_hi; S <- s'
-// mode 1 (pass 3): s'' = S - V c2; snorm2 += ||s''||^2; S <- s''
+// mode 1 (pass 3): s'' = S - V c2; snorm2 += ||s''||^2; S <- s''.  The second-pass coefficients are
+//   of the order of the first pass's float32 dot error (about 2^-24 ||M u_j||), so their products
+//   are formed in float32 from the hi plane and folded into the df32 s every 8 columns: the
+//   Arnoldi relation keeps an error near 2^-48 * 8 * sqrt(columns / 8) of ||M u_j|| (about 1e-13),
+//   and the pass reads only the hi plane of V (k_update_second)
 // mode 2 (the one-pass form): s' = M u_j - V c1 with c1 from the df32 dots; snorm2 += ||s'||^2; S <- s'
 __global__ void __launch_bounds__(kArnT, 6) k_update(Batch bt, FineExact fe, int, int mode) {
   const bool from_u = mode != 1, do_dots = mode == 0;
@@ -392,6 +396,66 @@ __global__ void __launch_bounds__(kArnT, 6) k_update(Batch bt, FineExact fe, int
   }
 }
 
+// pass 3 of CGS2 (mode 1 above): s'' = S - V c2 with float32 products folded every 8 columns
+__global__ void __launch_bounds__(kArnT, 6) k_update_second(Batch bt, FineExact fe) {
+  const int j = *bt.jdev;
+  __shared__ float red[32];
+  __shared__ float2 cf[kMaxCol];
+  const int b = blockIdx.y;
+  if (!bt.active[b]) return;
+  const int N = fe.N;
+  const double2* dsrc = bt.dot + (size_t)b * 2 * (bt.maxit + 1) + (bt.maxit + 1);
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) cf[i] = make_float2((float)dsrc[i].x, (float)dsrc[i].y);
+  __syncthreads();
+  const int c0 = blockIdx.x * kArnT * kCPT + threadIdx.x;
+  const size_t sb = (size_t)b * bt.N, vb = (size_t)b * (bt.maxit + 1) * bt.N;
+  cdf s[kCPT];
+#pragma unroll
+  for (int q = 0; q < kCPT; ++q) {
+    const int c = c0 + q * kArnT;
+    s[q] = c < N ? load_cdf(bt.S_hi, bt.S_lo, sb + c) : cdf{{0.f, 0.f}, {0.f, 0.f}};
+  }
+  for (int i0 = 0; i0 <= j; i0 += 8) {
+    const int ie = min(i0 + 8, j + 1);
+    float2 t[kCPT];
+#pragma unroll
+    for (int q = 0; q < kCPT; ++q) t[q] = make_float2(0.f, 0.f);
+    for (int i = i0; i < ie; ++i) {
+      const float2 ci = cf[i];
+      const float2* vh = bt.V_hi + vb + (size_t)i * bt.N;
+#pragma unroll
+      for (int q = 0; q < kCPT; ++q) {
+        const int c = c0 + q * kArnT;
+        if (c < N) {
+          const float2 h = vh[c];
+          t[q].x = fmaf(h.x, ci.x, fmaf(-h.y, ci.y, t[q].x));
+          t[q].y = fmaf(h.x, ci.y, fmaf(h.y, ci.x, t[q].y));
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kCPT; ++q) {
+      s[q].re = df_add_f(s[q].re, -t[q].x);
+      s[q].im = df_add_f(s[q].im, -t[q].y);
+    }
+  }
+  float acc[1] = {0.f};
+#pragma unroll
+  for (int q = 0; q < kCPT; ++q) {
+    const int c = c0 + q * kArnT;
+    if (c < N) {
+      store_cdf(bt.S_hi, bt.S_lo, sb + c, s[q]);
+      acc[0] += s[q].re.hi * s[q].re.hi + s[q].im.hi * s[q].im.hi;
+    }
+  }
+  block_reduce_add<1>(acc, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(&bt.snorm2[b], (double)acc[0]);
+    const int n = min(kArnT * kCPT, N - (int)(blockIdx.x * kArnT * kCPT));
+    atomicAdd(&bt.work[KC_ORTHO], (unsigned long long)n * (unsigned long long)(j + 1));
+  }
+}
+
 // v_{j+1} = s'' / h, h = float(||s''||); H column j
 __global__ void k_normalize(Batch bt, int) {
   const int j = *bt.jdev;   // outer iteration (device counter, so one captured graph serves every j)
@@ -450,11 +514,12 @@ void launch_arnoldi(const Batch& bt, const FineExact& fe, int j, cudaStream_t st
     prof_begin(pf, KC_DOTS, st);
     k_dots1<<<g, kArnT, 0, st>>>(bt, fe, j);
     prof_end(pf, KC_DOTS, st);
-    for (int mode = 0; mode < 2; ++mode) {
-      prof_begin(pf, KC_ORTHO, st);
-      k_update<<<g, kArnT, 0, st>>>(bt, fe, j, mode);
-      prof_end(pf, KC_ORTHO, st);
-    }
+    prof_begin(pf, KC_ORTHO, st);
+    k_update<<<g, kArnT, 0, st>>>(bt, fe, j, 0);
+    prof_end(pf, KC_ORTHO, st);
+    prof_begin(pf, KC_ORTHO, st);
+    k_update_second<<<g, kArnT, 0, st>>>(bt, fe);
+    prof_end(pf, KC_ORTHO, st);
   }
   dim3 gn((fe.N + 255) / 256, bt.nb);
   k_normalize<<<gn, 256, 0, st>>>(bt, j);
@@ -702,25 +767,6 @@ void launch_fields(const Batch& bt, const QuadItem* items, const double2* C, int
 // ------------------------------------------------------------ true residual (judge)
 constexpr int kXS = 16;   // shifts per pass (U is read once per pass)
 
-// acc + u * y for df32 complex values, with one renormalisation per component: the two hi x hi
-// products enter the running sum through TwoSum, their rounding errors and the hi x lo cross terms
-// go to the low word.
-__device__ __forceinline__ df df_fma2(df acc, df a, df b, df c, df d) {   // acc + a*b - c*d
-  float p1, e1, p2, e2, s1, t1, s2, t2;
-  two_prod(a.hi, b.hi, p1, e1);
-  two_prod(c.hi, d.hi, p2, e2);
-  two_sum(acc.hi, p1, s1, t1);
-  two_sum(s1, -p2, s2, t2);
-  float lo = __fadd_rn(acc.lo, __fadd_rn(t1, t2));
-  lo = __fadd_rn(lo, __fsub_rn(e1, e2));
-  lo = __fmaf_rn(a.hi, b.lo, lo);
-  lo = __fmaf_rn(a.lo, b.hi, lo);
-  lo = __fmaf_rn(-c.hi, d.lo, lo);
-  lo = __fmaf_rn(-c.lo, d.hi, lo);
-  df r;
-  fast_two_sum(s2, lo, r.hi, r.lo);
-  return r;
-}
 // one-pass Gram-Schmidt: dot[0][i] = V_i^H (M u_j) with V and M u_j in df32; each thread sums its
 // cells in df32, the block and the grid in double (a few additions per block)
 __global__ void __launch_bounds__(kArnT) k_dots_df(Batch bt, FineExact fe) {
@@ -791,9 +837,6 @@ void launch_dots_df(const Batch& bt, const FineExact& fe, dim3 g, cudaStream_t s
   k_dots_df<<<g, kArnT, 0, st>>>(bt, fe);
 }
 
-__device__ __forceinline__ cdf cdf_fma(cdf acc, cdf u, cdf y) {
-  return {df_fma2(acc.re, u.re, y.re, u.im, y.im), df_fma2(acc.im, u.re, y.im, df_neg(u.im), y.re)};
-}
 
 // X[sh] = U_b y_sh for every shift of basis b (df32 accumulation); ys: [kXS][maxit] in shared memory
 __global__ void __launch_bounds__(256) k_xk(Batch bt, float2* X_hi, float2* X_lo) {
