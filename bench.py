@@ -790,7 +790,7 @@ def main():
             "vs_baseline": None, "dtype": "df32+f32", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "shifted_systems_per_step": ns * nt * prob.Nz // 2,
                        "solver_tol": SOLVE_OPTS["tol"], "residual_bar": RESIDUAL_BAR,
-                       "autotuned": {k: tuned[k] for k in ("mg_cluster", "mg_tile", "mg_pre", "mg_post",
+                       "autotuned": {k: tuned.get(k) for k in ("mg_cluster", "mg_tile", "mg_pre", "mg_post",
                                                              "inner_rounds", "inner_cycles", "inner_relax",
                                                              "mg_tma")},
                        "max_true_residual": tres, "outer_iters_max": max(iters),

@@ -7,8 +7,8 @@
 // (red-black Gauss-Seidel, sum restriction, bilinear prolongation, dense
 // inverse or sweeps at the coarsest level), u_j += d in df32, until
 // ||r||^2 <= itol2.  What changes is where the data lives:
-//   * the kCS CTAs of a cluster split every multigrid level above
-//     kCoarseCells cells into kCS strips of whole rows; each CTA keeps the
+//   * the cs CTAs of a cluster (8, or 16 with half-height strips) split every multigrid level above
+//     kCoarseCells cells into cs strips of whole rows; each CTA keeps the
 //     iterate and right-hand side of its strips in shared memory for the
 //     whole solve and reads the row just outside a strip from the
 //     neighbouring CTA's shared memory (distributed shared memory);
@@ -37,8 +37,7 @@ namespace cg = cooperative_groups;
 
 namespace lt {
 
-constexpr int kCS = 8;                        // CTAs per cluster (portable cluster size)
-constexpr int kIT = 512;                      // threads per CTA
+constexpr int kIT = 512;                      // most threads per CTA (the launch bound)
 constexpr size_t kInnerSmemMax = 220 * 1024;  // dynamic shared memory per CTA
 constexpr int kL0Batch = 1;                   // finest-level cells per thread whose loads are issued together
 
@@ -76,6 +75,7 @@ struct InnerArgs {
   const float4* p4;             // [N] finest level: (Te east, Te west, Tn north, Tn south), red-black order
   float4* q4;                   // [nb][N] finest level: (1 / (D + tau m), right-hand side) per basis, same order
   int nlev, ld;                 // levels [0, ld) in strips, [ld, nlev) in rank 0
+  int cs;                       // CTAs per cluster (row strips per strip level)
   int npre, npost, dmask, coarse_direct, rounds, cycles;
   LevOff off[kMaxLevels];
   int off_rhs;                  // byte offset of rank 0's coarsest right-hand side copy
@@ -179,18 +179,18 @@ __device__ __forceinline__ float2 nb_dot(float4 t, const float2* nb) {
 // one red (color 0) or black (color 1) half-sweep over the strip's cells of that colour
 __device__ __forceinline__ void l0_half_sweep(const L0V& S, FastDiv dhx, int color) {
   const int hx = S.nx >> 1, n = S.h * hx;
-  for (int q0 = threadIdx.x; q0 < n; q0 += kL0Batch * kIT) {
+  for (int q0 = threadIdx.x; q0 < n; q0 += kL0Batch * (int)blockDim.x) {
     L0Cell cq[kL0Batch];
 #pragma unroll
     for (int k = 0; k < kL0Batch; ++k) {
-      const int q = q0 + k * kIT;
+      const int q = q0 + k * (int)blockDim.x;
       if (q < n) {
         cq[k] = l0_load(S, color * (S.ny * hx) + S.y0 * hx + q);   // red-black order: contiguous in q
       }
     }
 #pragma unroll
     for (int k = 0; k < kL0Batch; ++k) {
-      const int q = q0 + k * kIT;
+      const int q = q0 + k * (int)blockDim.x;
       if (q < n) {
         const int ly = fdiv(q, dhx);
         float2 nb[4];
@@ -220,7 +220,7 @@ __device__ __forceinline__ float l0_restrict(const L0V& S, float2* fc, int ncx, 
   const int nch = S.h >> 1, n = nch * ncx;
   const int nchild = red_only ? 2 : 4;
   float rr = 0.f;
-  for (int q = threadIdx.x; q < n; q += kIT) {
+  for (int q = threadIdx.x; q < n; q += (int)blockDim.x) {
     const int lJ = fdiv(q, dncx), I = q - lJ * ncx;
     float2 acc = make_float2(0.f, 0.f);
     for (int ch = 0; ch < nchild; ++ch) {
@@ -254,7 +254,7 @@ __device__ __forceinline__ void rbv_cell(const RBV& S, int c, int ly, int k, flo
 
 __device__ __forceinline__ void rbv_half_sweep(const RBV& S, FastDiv dhx, int color) {
   const int n = S.plane;
-  for (int q = threadIdx.x; q < n; q += kIT) {
+  for (int q = threadIdx.x; q < n; q += (int)blockDim.x) {
     const int ly = fdiv(q, dhx), k = q - ly * S.hx;
     float4 t;
     float2 nb[4];
@@ -271,7 +271,7 @@ __device__ __forceinline__ void rbv_restrict(const RBV& S, float2* fc, int ncx, 
                                              int fc_planec, bool red_only) {
   const int nch = S.h >> 1, n = nch * ncx;
   const int nchild = red_only ? 2 : 4;
-  for (int q = threadIdx.x; q < n; q += kIT) {
+  for (int q = threadIdx.x; q < n; q += (int)blockDim.x) {
     const int lJ = fdiv(q, dncx), I = q - lJ * ncx;
     float2 acc = make_float2(0.f, 0.f);
     for (int ch = 0; ch < nchild; ++ch) {
@@ -308,7 +308,7 @@ __device__ __forceinline__ void sv_gather(const SV& S, int x, int y, int ly, int
 // cell of the colour
 __device__ __forceinline__ void sv_half_sweep_even(const SV& S, FastDiv dhx, int color) {
   const int hx = S.nx >> 1, n = S.h * hx;
-  for (int q = threadIdx.x; q < n; q += kIT) {
+  for (int q = threadIdx.x; q < n; q += (int)blockDim.x) {
     const int ly = fdiv(q, dhx), y = S.y0 + ly, x = 2 * (q - ly * hx) + ((color + y) & 1);
     const int li = ly * S.nx + x;
     float4 t;
@@ -324,7 +324,7 @@ __device__ __forceinline__ void sv_half_sweep_even(const SV& S, FastDiv dhx, int
 // red-black half-sweep of a whole coarse level (any shape) held by this CTA
 __device__ __forceinline__ void sv_half_sweep_full(const SV& S, FastDiv dnx, int color) {
   const int n = S.h * S.nx;
-  for (int q = threadIdx.x; q < n; q += kIT) {
+  for (int q = threadIdx.x; q < n; q += (int)blockDim.x) {
     const int ly = fdiv(q, dnx), x = q - ly * S.nx;
     if (((x + S.y0 + ly) & 1) != color) continue;
     const int y = S.y0 + ly, li = q;
@@ -344,7 +344,7 @@ __device__ __forceinline__ void sv_half_sweep_full(const SV& S, FastDiv dnx, int
 __device__ __forceinline__ void sv_restrict(const SV& S, int rx, int ry, float2* fc, float2* uc, int ncx,
                                             FastDiv dncx, int row0, bool red_only) {
   const int nch = S.h / ry, n = nch * ncx;
-  for (int q = threadIdx.x; q < n; q += kIT) {
+  for (int q = threadIdx.x; q < n; q += (int)blockDim.x) {
     const int lJ = fdiv(q, dncx), I = q - lJ * ncx;
     float2 acc = make_float2(0.f, 0.f);
     for (int dj = 0; dj < ry; ++dj)
@@ -384,7 +384,7 @@ __device__ __forceinline__ void strip_prolong(float2* u, int nx, FastDiv dhx, in
   const int ncx = nx >> 1, n = (h >> 1) * ncx;
   const float sxl = (dmask & 1) ? -1.f : 1.f, sxh = (dmask & 2) ? -1.f : 1.f;
   const float syl = (dmask & 4) ? -1.f : 1.f, syh = (dmask & 8) ? -1.f : 1.f;
-  for (int q = threadIdx.x; q < n; q += kIT) {
+  for (int q = threadIdx.x; q < n; q += (int)blockDim.x) {
     const int lJ = fdiv(q, dhx), I = q - lJ * ncx, J = (y0 >> 1) + lJ;
     float2 c[3][3];
 #pragma unroll
@@ -427,7 +427,7 @@ __device__ __forceinline__ void block_sum(float v, float* red, double* dst) {
   if (lane == 0) red[warp] = v;
   __syncthreads();
   if (warp == 0) {
-    v = lane < kIT / 32 ? red[lane] : 0.f;
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) *dst = (double)v;
@@ -435,15 +435,15 @@ __device__ __forceinline__ void block_sum(float v, float* red, double* dst) {
 }
 
 // sum of v over the cluster's threads; identical on every CTA (ranks added in order)
-__device__ __forceinline__ double cluster_sum(cg::cluster_group& cl, float v, float* red, double* part, int slot,
-                                              double* bcast) {
+__device__ __forceinline__ double cluster_sum(cg::cluster_group& cl, int cs, float v, float* red, double* part,
+                                              int slot, double* bcast) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if (lane == 0) red[warp] = v;
   __syncthreads();
   if (warp == 0) {
-    v = lane < kIT / 32 ? red[lane] : 0.f;
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) part[slot] = (double)v;
@@ -451,14 +451,14 @@ __device__ __forceinline__ double cluster_sum(cg::cluster_group& cl, float v, fl
   cl.sync();
   if (threadIdx.x == 0) {
     double s = 0.0;
-    for (int q = 0; q < kCS; ++q) s += *cl.map_shared_rank(&part[slot], q);
+    for (int q = 0; q < cs; ++q) s += *cl.map_shared_rank(&part[slot], q);
     *bcast = s;
   }
   __syncthreads();
   return *bcast;
 }
 
-__global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cluster(const __grid_constant__ InnerArgs a) {
+__global__ void __launch_bounds__(kIT, 1) k_inner_cluster(const __grid_constant__ InnerArgs a) {
   extern __shared__ float4 dsm4[];
   char* smb = reinterpret_cast<char*>(dsm4);
   __shared__ Level sL[kMaxLevels];
@@ -469,7 +469,9 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
   __shared__ int vstop;                 // 1: this V-cycle ends the round
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  const int b = blockIdx.x / kCS;
+  const int cs = a.cs;                  // CTAs per cluster (8 or 16)
+  const int nthr = (int)blockDim.x;     // threads per CTA
+  const int b = blockIdx.x / cs;
   const Batch& bt = a.bt;
   if (!bt.active[b]) return;            // the same answer on every CTA of the cluster
   const int tid = threadIdx.x;
@@ -488,14 +490,14 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
     const Level& L = sL[l];
     const LevOff& o = a.off[l];
     RBV S;
-    S.nx = L.nx; S.ny = L.ny; S.h = L.ny / kCS; S.y0 = rank * S.h; S.hx = L.nx >> 1; S.plane = S.h * S.hx;
+    S.nx = L.nx; S.ny = L.ny; S.h = L.ny / cs; S.y0 = rank * S.h; S.hx = L.nx >> 1; S.plane = S.h * S.hx;
     S.u = reinterpret_cast<float2*>(smb + o.u);
     S.f = reinterpret_cast<float2*>(smb + o.f);
     S.te = reinterpret_cast<float*>(smb + o.te);
     S.ts = reinterpret_cast<float*>(smb + o.tn);
     S.di = reinterpret_cast<float2*>(smb + o.di);
     S.u_dn = rank > 0 ? cl.map_shared_rank(S.u, rank - 1) : nullptr;
-    S.u_up = rank + 1 < kCS ? cl.map_shared_rank(S.u, rank + 1) : nullptr;
+    S.u_up = rank + 1 < cs ? cl.map_shared_rank(S.u, rank + 1) : nullptr;
     return S;
   };
   auto sview = [&](int l) {
@@ -522,10 +524,10 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
       V.loc = cl.map_shared_rank(uc, 0);
       V.dn = nullptr; V.up = nullptr;
     } else {
-      V.full = 0; V.hc = Lc.ny / kCS; V.yc0 = rank * V.hc; V.hxc = Lc.nx >> 1; V.planec = V.hc * V.hxc;
+      V.full = 0; V.hc = Lc.ny / cs; V.yc0 = rank * V.hc; V.hxc = Lc.nx >> 1; V.planec = V.hc * V.hxc;
       V.loc = uc;
       V.dn = rank > 0 ? cl.map_shared_rank(uc, rank - 1) : nullptr;
-      V.up = rank + 1 < kCS ? cl.map_shared_rank(uc, rank + 1) : nullptr;
+      V.up = rank + 1 < cs ? cl.map_shared_rank(uc, rank + 1) : nullptr;
     }
     return V;
   };
@@ -536,7 +538,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
     const Level& L = sL[l];
     const RBV S = rbview(l);
     const int tplane = (S.h + 1) * S.hx;
-    for (int q = tid; q < S.h * S.nx; q += kIT) {
+    for (int q = tid; q < S.h * S.nx; q += nthr) {
       const int ly = q / S.nx, x = q - ly * S.nx, c = (S.y0 + ly) * S.nx + x;
       const int rbi = ((x + ly) & 1) * S.plane + ly * S.hx + (x >> 1);
       S.te[rbi] = L.Te[c];
@@ -544,7 +546,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
       S.di[rbi] = cinv(make_float2(L.D[c] + tau.x * mm, tau.y * mm));
       S.u[rbi] = make_float2(0.f, 0.f);
     }
-    for (int q = tid; q < (S.h + 1) * S.nx; q += kIT) {   // south faces of local rows 0 .. h
+    for (int q = tid; q < (S.h + 1) * S.nx; q += nthr) {   // south faces of local rows 0 .. h
       const int r = q / S.nx, x = q - r * S.nx, y = S.y0 + r;
       S.ts[((x + r) & 1) * tplane + r * S.hx + (x >> 1)] = (y >= 1 && y - 1 < S.ny) ? L.Tn[(y - 1) * S.nx + x] : 0.f;
     }
@@ -554,28 +556,28 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
       const Level& L = sL[l];
       const SV S = sview(l);
       const int n = S.h * S.nx;
-      for (int q = tid; q < n; q += kIT) {
+      for (int q = tid; q < n; q += nthr) {
         S.te[q] = L.Te[q];
         S.tn[S.nx + q] = L.Tn[q];
         const float mm = L.m[q];
         S.di[q] = cinv(make_float2(L.D[q] + tau.x * mm, tau.y * mm));
         S.u[q] = make_float2(0.f, 0.f);
       }
-      for (int x = tid; x < S.nx; x += kIT) S.tn[x] = 0.f;
+      for (int x = tid; x < S.nx; x += nthr) S.tn[x] = 0.f;
     }
   L0V S0;
   float4* q0 = a.q4 + (size_t)b * bt.N;
   {
     const Level& L = sL[0];
-    S0.nx = L.nx; S0.ny = L.ny; S0.h = L.ny / kCS; S0.y0 = rank * S0.h;
+    S0.nx = L.nx; S0.ny = L.ny; S0.h = L.ny / cs; S0.y0 = rank * S0.h;
     S0.hx = L.nx >> 1; S0.plane = S0.h * S0.hx;
     S0.P = a.p4;
     S0.Q = q0;
     S0.u = reinterpret_cast<float2*>(smb + a.off[0].u);
     S0.u_dn = rank > 0 ? cl.map_shared_rank(S0.u, rank - 1) : nullptr;
-    S0.u_up = rank + 1 < kCS ? cl.map_shared_rank(S0.u, rank + 1) : nullptr;
+    S0.u_up = rank + 1 < cs ? cl.map_shared_rank(S0.u, rank + 1) : nullptr;
     // inverse diagonal of this basis's shift on this CTA's rows (right-hand sides follow every round)
-    for (int q = tid; q < S0.h * S0.nx; q += kIT) {
+    for (int q = tid; q < S0.h * S0.nx; q += nthr) {
       const int c = S0.y0 * S0.nx + q;
       const float mm = L.m[c];
       const float2 di = cinv(make_float2(L.D[c] + tau.x * mm, tau.y * mm));
@@ -594,11 +596,11 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
     // df32 residual of the current u_j on this CTA's rows; it is the next round's right-hand side
     // (two cells per pass, both evaluated before either is stored, so their loads overlap)
     float acc = 0.f;
-    for (int q0i = tid; q0i < n0; q0i += 2 * kIT) {
+    for (int q0i = tid; q0i < n0; q0i += 2 * nthr) {
       cdf rr[2];
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        const int q = q0i + k * kIT;
+        const int q = q0i + k * nthr;
         if (q < n0) {
           const int c = c0 + q;
           rr[k] = load_cdf(bt.V_hi, bt.V_lo, vb + c);
@@ -607,7 +609,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
       }
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        const int q = q0i + k * kIT;
+        const int q = q0i + k * nthr;
         if (q < n0) {
           if (r < R) {
             const int ly = fdiv(q, a.dnx[0]), x = q - ly * S0.nx;
@@ -619,7 +621,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
         }
       }
     }
-    const double rn2 = cluster_sum(cl, acc, red, part, slot, &bcast);
+    const double rn2 = cluster_sum(cl, cs, acc, red, part, slot, &bcast);
     slot ^= 1;
     const bool done = (r == R) || (rn2 <= itol2);
     if (rank == 0 && tid == 0) {
@@ -629,7 +631,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
     }
     if (done) {
       if (r == 0)   // v_j itself is below the tolerance: u_j = 0
-        for (int q = tid; q < n0; q += kIT) {
+        for (int q = tid; q < n0; q += nthr) {
           bt.U_hi[ub + c0 + q] = make_float2(0.f, 0.f);
           if (bt.U_lo) bt.U_lo[ub + c0 + q] = make_float2(0.f, 0.f);
         }
@@ -650,7 +652,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
             l0_half_sweep(S0, a.dhx[0], h & 1);
             cl.sync();
           }
-          const int fhx = last ? 0 : sL[1].nx >> 1, fplane = last ? 0 : (sL[1].ny / kCS) * fhx;
+          const int fhx = last ? 0 : sL[1].nx >> 1, fplane = last ? 0 : (sL[1].ny / cs) * fhx;
           const float rr = l0_restrict(S0, fc, ncx, a.dnx[1], S0.y0 / 2, fhx, fplane, a.npre > 0);
           block_sum(rr, red, &vpart[cy & 1]);
         } else {
@@ -659,7 +661,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
             rbv_half_sweep(S, a.dhx[l], h & 1);
             cl.sync();
           }
-          const int fhx = last ? 0 : sL[l + 1].nx >> 1, fplane = last ? 0 : (sL[l + 1].ny / kCS) * fhx;
+          const int fhx = last ? 0 : sL[l + 1].nx >> 1, fplane = last ? 0 : (sL[l + 1].ny / cs) * fhx;
           rbv_restrict(S, fc, ncx, a.dnx[l + 1], S.y0 / 2, fhx, fplane, a.npre > 0);
         }
         __syncthreads();   // the next level's sweeps read right-hand sides written by other threads
@@ -667,7 +669,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
       cl.sync();   // rank 0 holds the whole restricted residual of level ld
       if (tid == 0) {
         double s2 = 0.0;
-        for (int q = 0; q < kCS; ++q) s2 += *cl.map_shared_rank(&vpart[cy & 1], q);
+        for (int q = 0; q < cs; ++q) s2 += *cl.map_shared_rank(&vpart[cy & 1], q);
         vstop = s2 <= goal2;
         n_cyc += (unsigned long long)bt.N;
       }
@@ -695,11 +697,11 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
         const float2* fr = cl.map_shared_rank(reinterpret_cast<float2*>(smb + a.off[lc].f), 0);
         float2* ur = cl.map_shared_rank(reinterpret_cast<float2*>(smb + a.off[lc].u), 0);
         float2* rhs = reinterpret_cast<float2*>(smb + a.off_rhs);
-        for (int i = tid; i < N; i += kIT) rhs[i] = fr[i];
+        for (int i = tid; i < N; i += nthr) rhs[i] = fr[i];
         __syncthreads();
         const float2* A = bt.coarse_inv + (size_t)bt.tau_slot[b] * N * N;
         const int warp = tid >> 5, lane = tid & 31;
-        for (int row = rank * (kIT / 32) + warp; row < N; row += kCS * (kIT / 32)) {
+        for (int row = rank * (nthr / 32) + warp; row < N; row += cs * (nthr / 32)) {
           const float2* Ar = A + (size_t)row * N;
           float sx = 0.f, sy = 0.f;
           for (int c = lane; c < N; c += 32) {
@@ -734,7 +736,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
             V.loc = uc; V.dn = nullptr; V.up = nullptr;
             strip_prolong(S.u, S.nx, a.dhx[l], S.h, 0, V, a.dmask, false);
           } else {
-            for (int c = tid; c < sL[l].N; c += kIT) prolong_cell(sL[l], sL[l + 1], S.u, uc, c, a.dmask);
+            for (int c = tid; c < sL[l].N; c += nthr) prolong_cell(sL[l], sL[l + 1], S.u, uc, c, a.dmask);
           }
           __syncthreads();
           for (int h = 0; h < 2 * a.npost; ++h) {
@@ -756,10 +758,10 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
         // every rank has read the coarse iterate: clear it for the next cycle
         if (l + 1 < a.ld) {
           const RBV C = rbview(l + 1);
-          for (int q = tid; q < C.h * C.nx; q += kIT) C.u[q] = make_float2(0.f, 0.f);
+          for (int q = tid; q < C.h * C.nx; q += nthr) C.u[q] = make_float2(0.f, 0.f);
         } else if (rank == 0) {
           const SV C = sview(l + 1);
-          for (int q = tid; q < C.h * C.nx; q += kIT) C.u[q] = make_float2(0.f, 0.f);
+          for (int q = tid; q < C.h * C.nx; q += nthr) C.u[q] = make_float2(0.f, 0.f);
         }
         for (int h = 0; h < 2 * a.npost; ++h) {
           if (l == 0) l0_half_sweep(S0, a.dhx[0], (h + 1) & 1);
@@ -770,7 +772,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
       if (vstop) break;   // the same on every CTA: all read the same partial sums in the same order
     }
     // u_j += d (df32) on this CTA's rows; the next residual reads the neighbours' rows
-    for (int q = tid; q < n0; q += kIT) {
+    for (int q = tid; q < n0; q += nthr) {
       const size_t ui = ub + c0 + q;
       const int ly = fdiv(q, a.dnx[0]), x = q - ly * S0.nx;
       const float2 d = S0.u[((x + ly) & 1) * S0.plane + ly * S0.hx + (x >> 1)];
@@ -795,9 +797,23 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kIT, 1) k_inner_cl
 
 static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-int inner_cluster_plan(const MGHost& mg, InnerPlan& p) {
+int inner_cluster_plan(const MGHost& mg, InnerPlan& p, int cs, int threads) {
   p.ok = 0;
-  const int ld = mg.lc;
+  p.cs = cs;
+  p.threads = threads;
+  // levels [ld, nlev) live whole in rank 0 (their arrays are reserved in every CTA): those of at most
+  // kCoarseCells cells; with 16-CTA clusters the levels of more than 256 cells among them are split
+  // into strips too where they split evenly (so that two CTAs of half the shared memory fit on an SM)
+  auto splits = [&](int l) {
+    if (l + 1 >= mg.nlev) return false;
+    const Level& L = mg.h_levels[l];
+    const Level& Lc = mg.h_levels[l + 1];
+    return L.rx == 2 && L.ry == 2 && L.rz == 1 && L.nx % 2 == 0 && L.ny % (2 * cs) == 0 && Lc.nx * 2 == L.nx &&
+           Lc.ny * 2 == L.ny;
+  };
+  int ld = mg.lc;
+  if (cs > 8)
+    while (ld < mg.nlev && mg.h_levels[ld].N > 256 && splits(ld)) ++ld;
   if (ld < 1 || ld >= mg.nlev) return 0;
   for (int l = 0; l < mg.nlev; ++l)
     if (mg.h_levels[l].nz != 1) return 0;
@@ -805,14 +821,14 @@ int inner_cluster_plan(const MGHost& mg, InnerPlan& p) {
     const Level& L = mg.h_levels[l];
     const Level& Lc = mg.h_levels[l + 1];
     if (L.rx != 2 || L.ry != 2 || L.rz != 1) return 0;
-    if (L.nx % 2 != 0 || L.ny % (2 * kCS) != 0) return 0;
+    if (L.nx % 2 != 0 || L.ny % (2 * cs) != 0) return 0;
     if (Lc.nx * 2 != L.nx || Lc.ny * 2 != L.ny) return 0;
   }
   size_t cur = 0;
   auto take = [&](size_t bytes) { const size_t o = cur; cur = align16(cur + bytes); return (int)o; };
   for (int l = 0; l < mg.nlev; ++l) {
     const Level& L = mg.h_levels[l];
-    const size_t h = l < ld ? (size_t)L.ny / kCS : (size_t)L.ny;
+    const size_t h = l < ld ? (size_t)L.ny / cs : (size_t)L.ny;
     const size_t n = h * L.nx;
     p.off_u[l] = take(n * sizeof(float2));
     if (l == 0) {
@@ -834,14 +850,18 @@ int inner_cluster_plan(const MGHost& mg, InnerPlan& p) {
     cudaGetLastError();
     return 0;
   }
-  // the cluster must fit on the device (kCS SMs with this much shared memory each)
+  if (cs > 8 && cudaFuncSetAttribute(k_inner_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  // the cluster must fit on the device (cs CTAs with this much shared memory each)
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kCS);
-  cfg.blockDim = dim3(kIT);
+  cfg.gridDim = dim3(cs);
+  cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = p.smem;
   cudaLaunchAttribute attr;
   attr.id = cudaLaunchAttributeClusterDimension;
-  attr.val.clusterDim.x = kCS; attr.val.clusterDim.y = 1; attr.val.clusterDim.z = 1;
+  attr.val.clusterDim.x = cs; attr.val.clusterDim.y = 1; attr.val.clusterDim.z = 1;
   cfg.attrs = &attr;
   cfg.numAttrs = 1;
   int nclusters = 0;
@@ -879,10 +899,21 @@ int launch_inner_cluster(const MGHost& mg, const InnerPlan& p, const Batch& bt, 
     a.dnx[l] = make_fastdiv((uint32_t)nx);
     a.dhx[l] = make_fastdiv((uint32_t)(nx / 2 > 0 ? nx / 2 : 1));
   }
+  a.cs = p.cs;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(bt.nb * p.cs));
+  cfg.blockDim = dim3((unsigned)p.threads);
+  cfg.dynamicSmemBytes = p.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = p.cs; attr.val.clusterDim.y = 1; attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
   prof_begin(pf, KC_INNER, st);
-  k_inner_cluster<<<bt.nb * kCS, kIT, p.smem, st>>>(a);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_inner_cluster, a);
   prof_end(pf, KC_INNER, st);
-  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+  return (e == cudaSuccess && cudaGetLastError() == cudaSuccess) ? 0 : -3;
 }
 
 }  // namespace lt

@@ -85,6 +85,7 @@ struct lt_ctx {
   std::vector<HostLevel> hl;
   lt::MGHost mg{};
   lt::InnerPlan inner{};          // cluster-resident preconditioner solve on this grid (inner.ok = 0: not possible)
+  lt::InnerPlan inner16{};        // the same with 16-CTA clusters of 256 threads, half-height strips (mg_cluster = 2)
   std::vector<void*> grid_allocs;
   lt::FineExact fe{};
   // float64 fine-level geometry for the sensitivity assembly
@@ -296,8 +297,8 @@ int lt_set_options(lt_ctx* ctx, const lt_opts* o) {
   if (o->precond != 0 && o->precond != 1) return fail(ctx, LT_ERR_INVALID_ARG, "precond=%d must be 0 or 1", o->precond);
   if (o->mg_tma != 0 && o->mg_tma != 1) return fail(ctx, LT_ERR_INVALID_ARG, "mg_tma=%d must be 0 or 1", o->mg_tma);
   if (o->graphs != 0 && o->graphs != 1) return fail(ctx, LT_ERR_INVALID_ARG, "graphs=%d must be 0 or 1", o->graphs);
-  if (o->mg_cluster != 0 && o->mg_cluster != 1)
-    return fail(ctx, LT_ERR_INVALID_ARG, "mg_cluster=%d must be 0 or 1", o->mg_cluster);
+  if (o->mg_cluster < 0 || o->mg_cluster > 2)
+    return fail(ctx, LT_ERR_INVALID_ARG, "mg_cluster=%d must be 0, 1 or 2", o->mg_cluster);
   if (!(o->inner_relax >= 0.0 && o->inner_relax < 1.0))
     return fail(ctx, LT_ERR_INVALID_ARG, "inner_relax=%g must be in [0,1)", o->inner_relax);
   if (o->timing_class < -1 || o->timing_class >= LT_KC_COUNT)
@@ -641,7 +642,8 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
   CK(cudaMalloc(&mg.d_levels, sizeof(lt::Level) * lt::kMaxLevels));
   if (ctx->ws.nb > 0)   // kept workspace: the device level table must point at the new coefficients
     CK(cudaMemcpy(mg.d_levels, mg.h_levels, sizeof(lt::Level) * nlev, cudaMemcpyHostToDevice));
-  if (lt::inner_cluster_plan(mg, ctx->inner)) {
+  lt::inner_cluster_plan(mg, ctx->inner16, 16, 256);
+  if (lt::inner_cluster_plan(mg, ctx->inner) || ctx->inner16.ok) {
     // the four faces of every finest-level cell in one 16-byte record (zero across domain edges),
     // in red-black order: colour (x + y) & 1 first, then row by row, x / 2 within the row
     const HostLevel& h0 = ctx->hl[0];
@@ -655,6 +657,7 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
     if ((rc = dalloc(ctx, ctx->grid_allocs, &d4, (size_t)N))) return rc;
     CK(cudaMemcpy(d4, p4.data(), N * sizeof(float4), cudaMemcpyHostToDevice));
     ctx->inner.p4 = d4;
+    ctx->inner16.p4 = d4;
   }
   ctx->have_grid = true;
   ctx->src.clear(); ctx->Q.clear(); ctx->rec.clear();
@@ -936,7 +939,7 @@ static int ensure_ws(lt_ctx* ctx, const Plan& P) {
     bt.wabs = w; bt.rhs_hi = rh; bt.rhs_lo = rl;
   }
   if (nc2) AL(bt.coarse_inv, (size_t)2 * P.G * nc2);
-  if (ctx->inner.ok) AL(ws.l0q, (size_t)nb * N);
+  if (ctx->inner.ok || ctx->inner16.ok) AL(ws.l0q, (size_t)nb * N);
   // multigrid vectors
   for (int l = 0; l < ctx->mg.nlev; ++l) {
     lt::Level& L = ctx->mg.h_levels[l];
@@ -1004,7 +1007,8 @@ struct SolveState {
 
 // the whole preconditioner solve of each basis runs in one thread-block cluster
 static bool uses_cluster_solve(const lt_ctx* ctx) {
-  return ctx->opts.mg_cluster == 1 && ctx->opts.precond == 0 && ctx->inner.ok;
+  return ctx->opts.precond == 0 && ((ctx->opts.mg_cluster == 1 && ctx->inner.ok) ||
+                                    (ctx->opts.mg_cluster == 2 && ctx->inner16.ok));
 }
 
 // The bases [b0, b0 + n) of a batch as a batch of their own: per-basis arrays
@@ -1038,7 +1042,8 @@ static int launch_iteration_cluster(lt_ctx* ctx, cudaStream_t q, int jj, int* nl
   const int nb = bt.nb;
   // (not inside lt_forward_noalloc, which creates no streams or events)
   // (nor in block mode, whose Arnoldi process couples the bases of a group)
-  const int parts = (!bt.block && nb > ctx->inner.max_clusters && nb >= 2 && ctx->arena_base == nullptr) ? 2 : 1;
+  const lt::InnerPlan& ip = o.mg_cluster == 2 ? ctx->inner16 : ctx->inner;
+  const int parts = (!bt.block && nb > ip.max_clusters && nb >= 2 && ctx->arena_base == nullptr) ? 2 : 1;
   if (parts == 2) {
     if (!ctx->side_stream) CK(cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking));
     if (!ctx->ev_fork) CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
@@ -1056,7 +1061,7 @@ static int launch_iteration_cluster(lt_ctx* ctx, cudaStream_t q, int jj, int* nl
     cudaStream_t qs = (part == 0 || timing) ? q : ctx->side_stream;
     const lt::Batch v = parts == 1 ? bt : sub_batch(bt, b0, n);
     lt::launch_prep_iter(v, jj, qs);
-    if (lt::launch_inner_cluster(ctx->mg, ctx->inner, v, ctx->fe, ctx->ws.l0q + (size_t)b0 * ctx->N,
+    if (lt::launch_inner_cluster(ctx->mg, ip, v, ctx->fe, ctx->ws.l0q + (size_t)b0 * ctx->N,
                                  o.inner_cycles, qs, pf))
       return LT_ERR_CUDA;
     lt::launch_inner_record(v, qs);
@@ -2296,7 +2301,7 @@ static size_t noalloc_need(const lt_ctx* ctx, const Plan& P) {
   add(nsh * M, 16); add(nsh * (M + 1), 16); add(nsh, 4); add(nsh, 8);
   add(nsh * M, 16); add(lt::kWorkSlots, 8); add(nb, 8); add(nb, 8); add(1, 4);
   if (ctx->mg.coarse_direct) add(2 * G * (size_t)ctx->hl.back().N * ctx->hl.back().N, 8);
-  if (ctx->inner.ok) add(nb * N, 16);
+  if (ctx->inner.ok || ctx->inner16.ok) add(nb * N, 16);
   for (int l = 0; l < ctx->mg.nlev; ++l) { add(nb * ctx->mg.h_levels[l].N, 8); add(nb * ctx->mg.h_levels[l].N, 8); }
   add(nsh, 4);
   if (o.true_residual) { add(nsh * N, 8); if (df) add(nsh * N, 8); add(nsh, 8); }

@@ -21,6 +21,8 @@ struct MGHost {
 // -------- inner.cu: the whole preconditioner solve of a basis in one thread-block cluster
 struct InnerPlan {
   int ok = 0;                      // 1 if the grid and the device allow the cluster-resident solve
+  int cs = 8;                      // CTAs per cluster = row strips per strip level (8, or 16 non-portable)
+  int threads = 512;               // threads per CTA
   int ld = 0;                      // levels split into per-CTA row strips: [0, ld); [ld, nlev) in rank 0
   int max_clusters = 0;            // clusters the device can hold at once
   int off_u[kMaxLevels] = {}, off_f[kMaxLevels] = {};               // byte offsets in shared memory
@@ -28,8 +30,9 @@ struct InnerPlan {
   size_t smem = 0;                 // dynamic shared memory per CTA
   const float4* p4 = nullptr;      // [N] finest-level faces (Te east, Te west, Tn north, Tn south), set by the host
 };
-// fills p (p.ok = 0 when the levels do not split into 8 even row strips or do not fit); returns p.ok
-int inner_cluster_plan(const MGHost& mg, InnerPlan& p);
+// fills p for clusters of cs CTAs of `threads` threads (p.ok = 0 when the levels do not split into cs
+// even row strips, do not fit in shared memory, or the device cannot hold such a cluster); returns p.ok
+int inner_cluster_plan(const MGHost& mg, InnerPlan& p, int cs = 8, int threads = 512);
 // rounds x cycles V-cycles of every active basis, one cluster per basis (bt.rounds rounds)
 // q4: [nb][N] float4 scratch of the finest level (inverse diagonal, right-hand side)
 int launch_inner_cluster(const MGHost& mg, const InnerPlan& p, const Batch& bt, const FineExact& fe, float4* q4,

@@ -224,6 +224,30 @@ def test_cluster_resident_solve_matches_batched_launches(Engine, shape, pre, rel
     assert _rel(h1, ref) < TOL_H
 
 
+@pytest.mark.parametrize("shape", [(64, 64), (256, 128), (128, 128)])
+def test_sixteen_cta_clusters_match_eight(Engine, shape):
+    """mg_cluster = 2: 16-CTA clusters of 256 threads with half-height strips (two CTAs of
+    different bases per SM) give the 8-CTA solve: same outer iterations to within one, heads
+    within the bar of the direct oracle."""
+    from paper_1409_2556_gb300._lib import KC
+    nx, ny = shape
+    p = W.random_problem(nx, ny, 1, variance=1.5, seed=nx + 2 * ny, ns=2, nr=3, nt=3, Nz=16, tol=1e-11, groups=2)
+    outs = []
+    for cl in (1, 2):
+        eng = Engine(0)
+        eng.load_problem(p, mg_cluster=cl, mg_pre=1, mg_post=2)
+        outs.append((eng.forward(p.times), eng.last_stats))
+        eng.close()
+    (h1, s1), (h2, s2) = outs
+    assert s1["work"][KC["inner"]] > 0 and s2["work"][KC["inner"]] > 0   # both ran the cluster kernel
+    assert abs(s1["outer_iters_max"] - s2["outer_iters_max"]) <= 1
+    assert s2["n_converged"] == s2["n_shift_solves"]
+    assert s2["max_true_residual"] <= 1e-11
+    ref = direct.forward(p)
+    assert _rel(h1, ref) < TOL_H
+    assert _rel(h2, ref) < TOL_H
+
+
 def test_cluster_solve_falls_back_on_grids_that_do_not_split(Engine):
     """40 rows do not split into 8 strips of even height: the batched launches run instead."""
     from paper_1409_2556_gb300._lib import KC
