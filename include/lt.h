@@ -73,8 +73,10 @@ typedef struct {
                            (2D, rows divisible into 8 strips per level, levels fit in shared memory; default);
                            2: the same in 16-CTA clusters (non-portable size) of 256 threads with half-height
                            strips, so that two CTAs of different bases share an SM (rows divisible into 16
-                           strips per level); 0: batched multigrid launches.  A grid the chosen form does not
-                           fit runs the batched launches */
+                           strips per level); 3: 8-CTA clusters of 256 threads with the finest level's iterate
+                           in global memory (L2) instead of shared memory, so that two CTAs of different bases
+                           share an SM; 0: batched multigrid launches.  A grid the chosen form does not fit
+                           runs the batched launches */
   int    precision;     /* LT_PREC_FP64 (default) or LT_PREC_FP32 (reduced precision, tolerances down to 2e-6) */
   int    krylov;        /* LT_KRYLOV_GMRES (default): minimal-residual coefficients per shift (FGMRES-Sh);
                            LT_KRYLOV_FOM: Petrov-Galerkin coefficients H_j(z_k; T_j) y = beta e_1 (FFOM-Sh),

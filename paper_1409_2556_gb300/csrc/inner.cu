@@ -76,6 +76,7 @@ struct InnerArgs {
   float4* q4;                   // [nb][N] finest level: (1 / (D + tau m), right-hand side) per basis, same order
   int nlev, ld;                 // levels [0, ld) in strips, [ld, nlev) in rank 0
   int cs;                       // CTAs per cluster (row strips per strip level)
+  float2* u0g;                  // [nb][N] finest-level iterates in strip blocks, or null (shared memory)
   int npre, npost, dmask, coarse_direct, rounds, cycles;
   LevOff off[kMaxLevels];
   int off_rhs;                  // byte offset of rank 0's coarsest right-hand side copy
@@ -93,9 +94,11 @@ struct InnerArgs {
 // The finest level's rows [y0, y0 + h) of this CTA.
 struct L0V {
   int nx, ny, h, y0, hx, plane;  // hx = nx / 2, plane = h hx (cells of one colour in the strip)
+  int gl;                        // 1: the iterates are strip blocks of a global array (rows of the neighbour
+                                 //    ranks are read past L1, from L2), 0: shared memory
   const float4* __restrict__ P;  // faces (red-black order over the whole level)
   const float4* Q;               // inverse diagonal and right-hand side (same order; rewritten every round)
-  float2* u;                     // [2][h][hx], shared memory
+  float2* u;                     // [2][h][hx], shared memory or global
   const float2* u_dn;            // iterate of rank - 1 (its last row lies just below y0), or null
   const float2* u_up;            // iterate of rank + 1 (its first row lies just above y0 + h - 1), or null
 };
@@ -168,7 +171,18 @@ __device__ __forceinline__ void rb_gather(const float2* u, const float2* u_dn, c
   nb[3] = y > 0 ? (ly > 0 ? u[row - hx + k] : u_dn[ob + (h - 1) * hx + k]) : z;
 }
 __device__ __forceinline__ void l0_gather(const L0V& S, int c, int ly, int k, float2* nb) {
-  rb_gather(S.u, S.u_dn, S.u_up, S.nx, S.ny, S.h, S.y0, S.hx, S.plane, c, ly, k, nb);
+  if (!S.gl) {
+    rb_gather(S.u, S.u_dn, S.u_up, S.nx, S.ny, S.h, S.y0, S.hx, S.plane, c, ly, k, nb);
+    return;
+  }
+  // global strip blocks: a neighbour rank's rows were written by another SM, so they come from L2
+  const float2 z = make_float2(0.f, 0.f);
+  const int p = (c + ly) & 1, x = 2 * k + p, y = S.y0 + ly;
+  const int ob = (c ^ 1) * S.plane, row = ob + ly * S.hx;
+  nb[0] = x + 1 < S.nx ? S.u[row + k + p] : z;
+  nb[1] = x > 0 ? S.u[row + k - 1 + p] : z;
+  nb[2] = y + 1 < S.ny ? (ly + 1 < S.h ? S.u[row + S.hx + k] : __ldcg(&S.u_up[ob + k])) : z;
+  nb[3] = y > 0 ? (ly > 0 ? S.u[row - S.hx + k] : __ldcg(&S.u_dn[ob + (S.h - 1) * S.hx + k])) : z;
 }
 
 __device__ __forceinline__ float2 nb_dot(float4 t, const float2* nb) {
@@ -573,9 +587,17 @@ __global__ void __launch_bounds__(kIT, 1) k_inner_cluster(const __grid_constant_
     S0.hx = L.nx >> 1; S0.plane = S0.h * S0.hx;
     S0.P = a.p4;
     S0.Q = q0;
-    S0.u = reinterpret_cast<float2*>(smb + a.off[0].u);
-    S0.u_dn = rank > 0 ? cl.map_shared_rank(S0.u, rank - 1) : nullptr;
-    S0.u_up = rank + 1 < cs ? cl.map_shared_rank(S0.u, rank + 1) : nullptr;
+    S0.gl = a.u0g != nullptr;
+    if (S0.gl) {
+      // this rank's block of the basis's array; the neighbour ranks' blocks lie just before and after
+      S0.u = a.u0g + (size_t)b * bt.N + (size_t)rank * S0.h * S0.nx;
+      S0.u_dn = rank > 0 ? S0.u - S0.h * S0.nx : nullptr;
+      S0.u_up = rank + 1 < cs ? S0.u + S0.h * S0.nx : nullptr;
+    } else {
+      S0.u = reinterpret_cast<float2*>(smb + a.off[0].u);
+      S0.u_dn = rank > 0 ? cl.map_shared_rank(S0.u, rank - 1) : nullptr;
+      S0.u_up = rank + 1 < cs ? cl.map_shared_rank(S0.u, rank + 1) : nullptr;
+    }
     // inverse diagonal of this basis's shift on this CTA's rows (right-hand sides follow every round)
     for (int q = tid; q < S0.h * S0.nx; q += nthr) {
       const int c = S0.y0 * S0.nx + q;
@@ -797,13 +819,15 @@ __global__ void __launch_bounds__(kIT, 1) k_inner_cluster(const __grid_constant_
 
 static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-int inner_cluster_plan(const MGHost& mg, InnerPlan& p, int cs, int threads) {
+int inner_cluster_plan(const MGHost& mg, InnerPlan& p, int cs, int threads, int u0_global) {
   p.ok = 0;
   p.cs = cs;
   p.threads = threads;
+  p.u0_global = u0_global;
   // levels [ld, nlev) live whole in rank 0 (their arrays are reserved in every CTA): those of at most
-  // kCoarseCells cells; with 16-CTA clusters the levels of more than 256 cells among them are split
-  // into strips too where they split evenly (so that two CTAs of half the shared memory fit on an SM)
+  // kCoarseCells cells; in the two-CTAs-per-SM forms (16-CTA clusters, or the finest iterate in global
+  // memory) the levels of more than 256 cells among them are split into strips too where they split
+  // evenly
   auto splits = [&](int l) {
     if (l + 1 >= mg.nlev) return false;
     const Level& L = mg.h_levels[l];
@@ -812,7 +836,7 @@ int inner_cluster_plan(const MGHost& mg, InnerPlan& p, int cs, int threads) {
            Lc.ny * 2 == L.ny;
   };
   int ld = mg.lc;
-  if (cs > 8)
+  if (cs > 8 || u0_global)
     while (ld < mg.nlev && mg.h_levels[ld].N > 256 && splits(ld)) ++ld;
   if (ld < 1 || ld >= mg.nlev) return 0;
   for (int l = 0; l < mg.nlev; ++l)
@@ -830,7 +854,7 @@ int inner_cluster_plan(const MGHost& mg, InnerPlan& p, int cs, int threads) {
     const Level& L = mg.h_levels[l];
     const size_t h = l < ld ? (size_t)L.ny / cs : (size_t)L.ny;
     const size_t n = h * L.nx;
-    p.off_u[l] = take(n * sizeof(float2));
+    p.off_u[l] = take(l == 0 && u0_global ? 0 : n * sizeof(float2));
     if (l == 0) {
       p.off_f[l] = p.off_te[l] = p.off_tn[l] = p.off_di[l] = 0;
       continue;
@@ -876,7 +900,7 @@ int inner_cluster_plan(const MGHost& mg, InnerPlan& p, int cs, int threads) {
 }
 
 int launch_inner_cluster(const MGHost& mg, const InnerPlan& p, const Batch& bt, const FineExact& fe, float4* q4,
-                         int cycles, cudaStream_t st, Prof* pf) {
+                         float2* u0, int cycles, cudaStream_t st, Prof* pf) {
   InnerArgs a;
   a.bt = bt;
   a.fe = fe;
@@ -900,6 +924,7 @@ int launch_inner_cluster(const MGHost& mg, const InnerPlan& p, const Batch& bt, 
     a.dhx[l] = make_fastdiv((uint32_t)(nx / 2 > 0 ? nx / 2 : 1));
   }
   a.cs = p.cs;
+  a.u0g = p.u0_global ? u0 : nullptr;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(bt.nb * p.cs));
   cfg.blockDim = dim3((unsigned)p.threads);

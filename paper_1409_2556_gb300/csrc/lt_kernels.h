@@ -23,6 +23,7 @@ struct InnerPlan {
   int ok = 0;                      // 1 if the grid and the device allow the cluster-resident solve
   int cs = 8;                      // CTAs per cluster = row strips per strip level (8, or 16 non-portable)
   int threads = 512;               // threads per CTA
+  int u0_global = 0;               // 1: finest-level iterates in a global [nb][N] array, not shared memory
   int ld = 0;                      // levels split into per-CTA row strips: [0, ld); [ld, nlev) in rank 0
   int max_clusters = 0;            // clusters the device can hold at once
   int off_u[kMaxLevels] = {}, off_f[kMaxLevels] = {};               // byte offsets in shared memory
@@ -32,11 +33,12 @@ struct InnerPlan {
 };
 // fills p for clusters of cs CTAs of `threads` threads (p.ok = 0 when the levels do not split into cs
 // even row strips, do not fit in shared memory, or the device cannot hold such a cluster); returns p.ok
-int inner_cluster_plan(const MGHost& mg, InnerPlan& p, int cs = 8, int threads = 512);
+int inner_cluster_plan(const MGHost& mg, InnerPlan& p, int cs = 8, int threads = 512, int u0_global = 0);
 // rounds x cycles V-cycles of every active basis, one cluster per basis (bt.rounds rounds)
-// q4: [nb][N] float4 scratch of the finest level (inverse diagonal, right-hand side)
+// q4: [nb][N] float4 scratch of the finest level (inverse diagonal, right-hand side); u0: [nb][N] float2
+// scratch of the finest-level iterates when p.u0_global (else unused)
 int launch_inner_cluster(const MGHost& mg, const InnerPlan& p, const Batch& bt, const FineExact& fe, float4* q4,
-                         int cycles, cudaStream_t st, Prof* pf);
+                         float2* u0, int cycles, cudaStream_t st, Prof* pf);
 
 // one V-cycle on every active basis of the batch whose refinement round `round` is not done
 int launch_vcycle(const MGHost& mg, const Batch& bt, int round, cudaStream_t st, int* nlaunch, Prof* pf);
