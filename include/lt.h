@@ -75,8 +75,9 @@ typedef struct {
                            strips, so that two CTAs of different bases share an SM (rows divisible into 16
                            strips per level); 3: 8-CTA clusters of 256 threads with the finest level's iterate
                            in global memory (L2) instead of shared memory, so that two CTAs of different bases
-                           share an SM; 0: batched multigrid launches.  A grid the chosen form does not fit
-                           runs the batched launches */
+                           share an SM; 4: 4-CTA clusters of 512 threads, finest-level iterate in global
+                           memory (half the SMs per basis); 0: batched multigrid launches.  A grid the chosen
+                           form does not fit runs the batched launches */
   int    precision;     /* LT_PREC_FP64 (default) or LT_PREC_FP32 (reduced precision, tolerances down to 2e-6) */
   int    krylov;        /* LT_KRYLOV_GMRES (default): minimal-residual coefficients per shift (FGMRES-Sh);
                            LT_KRYLOV_FOM: Petrov-Galerkin coefficients H_j(z_k; T_j) y = beta e_1 (FFOM-Sh),

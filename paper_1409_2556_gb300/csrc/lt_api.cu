@@ -86,8 +86,10 @@ struct lt_ctx {
   std::vector<HostLevel> hl;
   lt::MGHost mg{};
   lt::InnerPlan inner{};          // cluster-resident preconditioner solve on this grid (inner.ok = 0: not possible)
-  lt::InnerPlan inner16{};        // the same with 16-CTA clusters of 256 threads, half-height strips (mg_cluster = 2)
-  lt::InnerPlan innerg{};         // 8-CTA clusters of 256 threads, finest iterate in global memory (mg_cluster = 3)
+  // other shapes of the same solve, by lt_opts.mg_cluster: [2] 16-CTA clusters of 256 threads with half-height
+  // strips; [3] 8-CTA clusters of 256 threads and [4] 4-CTA clusters of 512 threads, both with the finest
+  // level's iterate in global memory ([1] is `inner`)
+  lt::InnerPlan inner_alt[5]{};
   std::vector<void*> grid_allocs;
   lt::FineExact fe{};
   // float64 fine-level geometry for the sensitivity assembly
@@ -150,6 +152,19 @@ static int fail(lt_ctx* ctx, int code, const char* fmt, ...) {
   } while (0)
 
 static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// the cluster-resident solve selected by lt_opts.mg_cluster (its ok flag says whether the grid allows it;
+// mg_cluster = 0 selects none)
+static const lt::InnerPlan& cluster_plan(const lt_ctx* ctx) {
+  static const lt::InnerPlan none{};
+  const int m = ctx->opts.mg_cluster;
+  return m == 1 ? ctx->inner : (m >= 2 && m <= 4) ? ctx->inner_alt[m] : none;
+}
+static bool any_cluster_plan(const lt_ctx* ctx) {
+  for (const lt::InnerPlan& q : ctx->inner_alt)
+    if (q.ok) return true;
+  return false;
+}
 
 template <typename T>
 static int dalloc(lt_ctx* ctx, std::vector<void*>& list, T** p, size_t n) {
@@ -299,8 +314,8 @@ int lt_set_options(lt_ctx* ctx, const lt_opts* o) {
   if (o->precond != 0 && o->precond != 1) return fail(ctx, LT_ERR_INVALID_ARG, "precond=%d must be 0 or 1", o->precond);
   if (o->mg_tma != 0 && o->mg_tma != 1) return fail(ctx, LT_ERR_INVALID_ARG, "mg_tma=%d must be 0 or 1", o->mg_tma);
   if (o->graphs != 0 && o->graphs != 1) return fail(ctx, LT_ERR_INVALID_ARG, "graphs=%d must be 0 or 1", o->graphs);
-  if (o->mg_cluster < 0 || o->mg_cluster > 3)
-    return fail(ctx, LT_ERR_INVALID_ARG, "mg_cluster=%d must be 0, 1, 2 or 3", o->mg_cluster);
+  if (o->mg_cluster < 0 || o->mg_cluster > 4)
+    return fail(ctx, LT_ERR_INVALID_ARG, "mg_cluster=%d must be 0 .. 4", o->mg_cluster);
   if (!(o->inner_relax >= 0.0 && o->inner_relax < 1.0))
     return fail(ctx, LT_ERR_INVALID_ARG, "inner_relax=%g must be in [0,1)", o->inner_relax);
   if (o->timing_class < -1 || o->timing_class >= LT_KC_COUNT)
@@ -644,9 +659,10 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
   CK(cudaMalloc(&mg.d_levels, sizeof(lt::Level) * lt::kMaxLevels));
   if (ctx->ws.nb > 0)   // kept workspace: the device level table must point at the new coefficients
     CK(cudaMemcpy(mg.d_levels, mg.h_levels, sizeof(lt::Level) * nlev, cudaMemcpyHostToDevice));
-  lt::inner_cluster_plan(mg, ctx->inner16, 16, 256);
-  lt::inner_cluster_plan(mg, ctx->innerg, 8, 256, 1);
-  if (lt::inner_cluster_plan(mg, ctx->inner) || ctx->inner16.ok || ctx->innerg.ok) {
+  lt::inner_cluster_plan(mg, ctx->inner_alt[2], 16, 256);
+  lt::inner_cluster_plan(mg, ctx->inner_alt[3], 8, 256, 1);
+  lt::inner_cluster_plan(mg, ctx->inner_alt[4], 4, 512, 1);
+  if (lt::inner_cluster_plan(mg, ctx->inner) || any_cluster_plan(ctx)) {
     // the four faces of every finest-level cell in one 16-byte record (zero across domain edges),
     // in red-black order: colour (x + y) & 1 first, then row by row, x / 2 within the row
     const HostLevel& h0 = ctx->hl[0];
@@ -660,8 +676,7 @@ extern "C" int lt_setup_grid(lt_ctx* ctx, int nx, int ny, int nz, double dx, dou
     if ((rc = dalloc(ctx, ctx->grid_allocs, &d4, (size_t)N))) return rc;
     CK(cudaMemcpy(d4, p4.data(), N * sizeof(float4), cudaMemcpyHostToDevice));
     ctx->inner.p4 = d4;
-    ctx->inner16.p4 = d4;
-    ctx->innerg.p4 = d4;
+    for (lt::InnerPlan& q : ctx->inner_alt) q.p4 = d4;
   }
   ctx->have_grid = true;
   ctx->src.clear(); ctx->Q.clear(); ctx->rec.clear();
@@ -905,7 +920,7 @@ static int ensure_ws(lt_ctx* ctx, const Plan& P) {
   const int nc2 = ctx->mg.coarse_direct ? nc * nc : 0;
   if (ws.nb >= P.nb && ws.maxit == o.maxit && ws.nsh >= P.nsh && ws.rounds == o.inner_rounds && ws.N == ctx->N &&
       ws.ngroups >= P.G && ws.nc2 >= nc2 && ws.prec == o.precision &&
-      (ws.l0u != nullptr) == (o.mg_cluster == 3 && ctx->innerg.ok))
+      (ws.l0u != nullptr) == cluster_plan(ctx).u0_global)
     return LT_OK;
   CK(cudaStreamSynchronize(ctx->stream));
   free_ws(ctx);
@@ -944,8 +959,8 @@ static int ensure_ws(lt_ctx* ctx, const Plan& P) {
     bt.wabs = w; bt.rhs_hi = rh; bt.rhs_lo = rl;
   }
   if (nc2) AL(bt.coarse_inv, (size_t)2 * P.G * nc2);
-  if (ctx->inner.ok || ctx->inner16.ok || ctx->innerg.ok) AL(ws.l0q, (size_t)nb * N);
-  if (o.mg_cluster == 3 && ctx->innerg.ok) AL(ws.l0u, (size_t)nb * N);
+  if (ctx->inner.ok || any_cluster_plan(ctx)) AL(ws.l0q, (size_t)nb * N);
+  if (cluster_plan(ctx).u0_global) AL(ws.l0u, (size_t)nb * N);
   // multigrid vectors
   for (int l = 0; l < ctx->mg.nlev; ++l) {
     lt::Level& L = ctx->mg.h_levels[l];
@@ -1013,9 +1028,7 @@ struct SolveState {
 
 // the whole preconditioner solve of each basis runs in one thread-block cluster
 static bool uses_cluster_solve(const lt_ctx* ctx) {
-  return ctx->opts.precond == 0 && ((ctx->opts.mg_cluster == 1 && ctx->inner.ok) ||
-                                    (ctx->opts.mg_cluster == 2 && ctx->inner16.ok) ||
-                                    (ctx->opts.mg_cluster == 3 && ctx->innerg.ok));
+  return ctx->opts.precond == 0 && ctx->opts.mg_cluster >= 1 && cluster_plan(ctx).ok;
 }
 
 // The bases [b0, b0 + n) of a batch as a batch of their own: per-basis arrays
@@ -1049,7 +1062,7 @@ static int launch_iteration_cluster(lt_ctx* ctx, cudaStream_t q, int jj, int* nl
   const int nb = bt.nb;
   // (not inside lt_forward_noalloc, which creates no streams or events)
   // (nor in block mode, whose Arnoldi process couples the bases of a group)
-  const lt::InnerPlan& ip = o.mg_cluster == 2 ? ctx->inner16 : o.mg_cluster == 3 ? ctx->innerg : ctx->inner;
+  const lt::InnerPlan& ip = cluster_plan(ctx);
   if (ip.u0_global && !ctx->ws.l0u) return fail(ctx, LT_ERR_STATE, "finest-level iterate array missing");
   const int parts = (!bt.block && nb > ip.max_clusters && nb >= 2 && ctx->arena_base == nullptr) ? 2 : 1;
   if (parts == 2) {
@@ -2310,8 +2323,8 @@ static size_t noalloc_need(const lt_ctx* ctx, const Plan& P) {
   add(nsh * M, 16); add(nsh * (M + 1), 16); add(nsh, 4); add(nsh, 8);
   add(nsh * M, 16); add(lt::kWorkSlots, 8); add(nb, 8); add(nb, 8); add(1, 4);
   if (ctx->mg.coarse_direct) add(2 * G * (size_t)ctx->hl.back().N * ctx->hl.back().N, 8);
-  if (ctx->inner.ok || ctx->inner16.ok || ctx->innerg.ok) add(nb * N, 16);
-  if (o.mg_cluster == 3 && ctx->innerg.ok) add(nb * N, 8);
+  if (ctx->inner.ok || any_cluster_plan(ctx)) add(nb * N, 16);
+  if (cluster_plan(ctx).u0_global) add(nb * N, 8);
   for (int l = 0; l < ctx->mg.nlev; ++l) { add(nb * ctx->mg.h_levels[l].N, 8); add(nb * ctx->mg.h_levels[l].N, 8); }
   add(nsh, 4);
   if (o.true_residual) { add(nsh * N, 8); if (df) add(nsh * N, 8); add(nsh, 8); }

@@ -224,13 +224,13 @@ def test_cluster_resident_solve_matches_batched_launches(Engine, shape, pre, rel
     assert _rel(h1, ref) < TOL_H
 
 
-@pytest.mark.parametrize("form", [2, 3])
+@pytest.mark.parametrize("form", [2, 3, 4])
 @pytest.mark.parametrize("shape", [(64, 64), (256, 128), (128, 128)])
 def test_cluster_forms_match_eight_cta_clusters(Engine, shape, form):
-    """mg_cluster = 2 (16-CTA clusters of 256 threads, half-height strips) and 3 (8-CTA clusters of
-    256 threads, finest-level iterate in global memory): two CTAs of different bases per SM.  Both
-    give the 8-CTA solve: same outer iterations to within one, heads within the bar of the direct
-    oracle."""
+    """mg_cluster = 2 (16-CTA clusters of 256 threads, half-height strips), 3 (8-CTA clusters of 256
+    threads) and 4 (4-CTA clusters of 512 threads), the last two with the finest-level iterate in
+    global memory.  Each gives the 8-CTA solve: same outer iterations to within one, heads within the
+    bar of the direct oracle."""
     from paper_1409_2556_gb300._lib import KC
     nx, ny = shape
     p = W.random_problem(nx, ny, 1, variance=1.5, seed=nx + 2 * ny, ns=2, nr=3, nt=3, Nz=16, tol=1e-11, groups=2)
