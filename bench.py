@@ -753,6 +753,7 @@ def main():
     jac = None if args.no_jacobian else jacobian_rows(dev, stream)
     bat = None if args.no_batch else batch_throughput(dev)
     lrn = None if args.no_learned else learned_gain(dev)
+    blk = None if args.no_batch else block_comparison(dev)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -797,7 +798,7 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (Krylov bases ~GBs per step)"},
             "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(), "jacobian": jac, "batch": bat, "learned": lrn,
-            "crank_nicolson": cnc, "gauss_newton": gn,
+            "crank_nicolson": cnc, "gauss_newton": gn, "block": blk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": launches}
     print(json.dumps(line), flush=True)

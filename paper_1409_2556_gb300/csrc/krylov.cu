@@ -838,17 +838,26 @@ void launch_dots_df(const Batch& bt, const FineExact& fe, dim3 g, cudaStream_t s
 }
 
 
-// X[sh] = U_b y_sh for every shift of basis b (df32 accumulation); ys: [kXS][maxit] in shared memory
+// X[sh] = U_b y_sh for every shift of basis b (df32 accumulation); ys: [kXS][maxit] in shared memory.
+// A chunk of kXS shifts runs over the columns of its latest-converging shift only (the coefficients
+// of a shift beyond its own convergence are zero).
 __global__ void __launch_bounds__(256) k_xk(Batch bt, float2* X_hi, float2* X_lo) {
   extern __shared__ cdf ys[];
+  __shared__ int s_m;
   int b = blockIdx.y;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int M = bt.maxit;
-  int m = bt.nit[b];
   int s0 = bt.shift_off[b], s1 = bt.shift_off[b + 1];
   size_t ub = (size_t)b * M * bt.N;
   for (int sa = s0; sa < s1; sa += kXS) {
     __syncthreads();
+    if (threadIdx.x == 0) {
+      int mm = 0;
+      for (int sh = sa; sh < min(sa + kXS, s1); ++sh) mm = max(mm, bt.conv_it[sh] > 0 ? bt.conv_it[sh] : bt.nit[b]);
+      s_m = min(mm, bt.nit[b]);
+    }
+    __syncthreads();
+    const int m = s_m;
     for (int idx = threadIdx.x; idx < kXS * m; idx += blockDim.x) {
       int q = idx / m, i = idx % m;
       int sh = sa + q;
