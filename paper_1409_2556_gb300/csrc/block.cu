@@ -75,11 +75,11 @@ __device__ __forceinline__ int n_tiles(int N) { return (N + kBT * CPT - 1) / (kB
 template <int PMAX, int CPT, class Load, class XCol>
 __device__ void block_dots(Load load, XCol xcol, int ncol, int p, int N, double2* D, float2* acc) {
   constexpr int CH = kBAcc / PMAX;
-  constexpr int NV = 2 * PMAX;
+  constexpr int NV = 2 * PMAX <= 8 ? 8 : 2 * PMAX <= 16 ? 16 : 32;   // values reduced, padded to a power of two
   constexpr int SH = 5 - Log2<NV>::v;
   const int lane = threadIdx.x & 31;
   const int idx = lane >> SH;
-  const bool owner = (lane & ((1 << SH) - 1)) == 0;
+  const bool owner = (lane & ((1 << SH) - 1)) == 0 && idx < 2 * PMAX;
   const int q_own = idx < PMAX ? idx : idx - PMAX;
   const int nt = n_tiles<CPT>(N);
   for (int cb = 0; cb < ncol; cb += CH) {
@@ -332,80 +332,98 @@ __device__ __forceinline__ double2 bz_div(double2 a, double2 b) {
   return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
 
-// inverse of an upper-triangular p x p matrix (row-major, complex double): X = A^{-1}
-__device__ void upper_inverse(const double2* A, double2* X, int p) {
-  for (int q = 0; q < p; ++q) {
-    for (int l = 0; l < p; ++l) X[l * p + q] = make_double2(0.0, 0.0);
-    X[q * p + q] = bz_div(make_double2(1.0, 0.0), A[q * p + q]);
-    for (int l = q - 1; l >= 0; --l) {
-      double2 acc = make_double2(0.0, 0.0);
-      for (int k = l + 1; k <= q; ++k) {
-        const double2 t = bz_mul(A[l * p + k], X[k * p + q]);
-        acc.x += t.x; acc.y += t.y;
-      }
-      X[l * p + q] = bz_div(make_double2(-acc.x, -acc.y), A[l * p + l]);
+// inverse of an upper-triangular p x p matrix (row-major, complex double): X = A^{-1}, thread q < p
+// solving for column q (call from every thread; a barrier follows in the caller)
+__device__ void upper_inverse_cols(const double2* A, double2* X, int p) {
+  const int q = threadIdx.x;
+  if (q >= p) return;
+  for (int l = 0; l < p; ++l) X[l * p + q] = make_double2(0.0, 0.0);
+  X[q * p + q] = bz_div(make_double2(1.0, 0.0), A[q * p + q]);
+  for (int l = q - 1; l >= 0; --l) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = l + 1; k <= q; ++k) {
+      const double2 t = bz_mul(A[l * p + k], X[k * p + q]);
+      acc.x += t.x; acc.y += t.y;
     }
+    X[l * p + q] = bz_div(make_double2(-acc.x, -acc.y), A[l * p + l]);
   }
 }
 
-// CholQR step of pass `pass`: Gram = R^H R (Cholesky, double), W = R^{-1} rounded to float32 into
-// bw[g][pass].  A pivot below 1e-26 of its column's squared norm (numerical rank loss of the block)
-// is raised to that floor, so W stays finite; the Arnoldi relation still holds exactly because H
-// takes the inverse of the W that was applied.  Pass 1 also writes block column j of H: rows
-// i p + q' (i <= j) the Gram-Schmidt coefficients the updates subtracted, rows (j+1)p + l the
-// subdiagonal block (W_1 W_2)^{-1}.
-__global__ void k_bchol(Batch bt, int pass) {
+// CholQR step of pass `pass`: Gram = R^H R (right-looking Cholesky in double, the row and trailing
+// updates of each step spread over the CTA), W = R^{-1} rounded to float32 into bw[g][pass].  A
+// pivot below 1e-26 of its column's squared norm (numerical rank loss of the block) is raised to
+// that floor, so W stays finite; the Arnoldi relation still holds exactly because H takes the
+// inverse of the W that was applied.  Pass 1 also writes block column j of H: rows i p + q' (i <= j)
+// the Gram-Schmidt coefficients the updates subtracted, rows (j+1)p + l the subdiagonal block
+// (W_1 W_2)^{-1}.
+__global__ void __launch_bounds__(256) k_bchol(Batch bt, int pass) {
   __shared__ double2 Gm[256], Rm[256], Wd[256], T[256];
+  __shared__ double diag0[16];
   const int g = blockIdx.x;
   if (!bt.active[g]) return;
-  const int j = *bt.jdev, p = bt.bp;
+  const int j = *bt.jdev, p = bt.bp, tid = threadIdx.x, nt = blockDim.x;
   const double2* gram = bt.bgram + ((size_t)g * 2 + pass) * p * p;
   float2* W = bt.bw + ((size_t)g * 2 + pass) * p * p;
-  for (int i = threadIdx.x; i < p * p; i += blockDim.x) Gm[i] = gram[i];
+  for (int i = tid; i < p * p; i += nt) {
+    Gm[i] = gram[i];
+    Rm[i] = make_double2(0.0, 0.0);
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < p; ++q) {
-      for (int l = 0; l < q; ++l) {
-        double2 acc = Gm[l * p + q];
-        for (int k = 0; k < l; ++k) {
-          const double2 t = bz_cmul(Rm[k * p + l], Rm[k * p + q]);
-          acc.x -= t.x; acc.y -= t.y;
-        }
-        Rm[l * p + q] = bz_div(acc, Rm[l * p + l]);
-      }
+  if (tid < p) diag0[tid] = Gm[tid * p + tid].x;
+  __syncthreads();
+  for (int q = 0; q < p; ++q) {
+    if (tid == 0) {
       double d = Gm[q * p + q].x;
-      for (int k = 0; k < q; ++k) d -= Rm[k * p + q].x * Rm[k * p + q].x + Rm[k * p + q].y * Rm[k * p + q].y;
-      const double floor_d = fmax(1e-26 * Gm[q * p + q].x, 1e-280);
+      const double floor_d = fmax(1e-26 * diag0[q], 1e-280);
       if (!(d > floor_d)) d = floor_d;
       Rm[q * p + q] = make_double2(sqrt(d), 0.0);
-      for (int l = q + 1; l < p; ++l) Rm[l * p + q] = make_double2(0.0, 0.0);
     }
-    upper_inverse(Rm, Wd, p);
-    // W as applied: float32 entries
-    for (int i = 0; i < p * p; ++i) Wd[i] = make_double2((double)(float)Wd[i].x, (double)(float)Wd[i].y);
+    __syncthreads();
+    const double rq = Rm[q * p + q].x;
+    for (int c = q + 1 + tid; c < p; c += nt) {
+      const double2 a = Gm[q * p + c];
+      Rm[q * p + c] = make_double2(a.x / rq, a.y / rq);
+    }
+    __syncthreads();
+    const int w = p - q - 1;
+    for (int idx = tid; idx < w * w; idx += nt) {
+      const int a = q + 1 + idx / w, c = q + 1 + idx % w;
+      if (a <= c) {
+        const double2 t = bz_cmul(Rm[q * p + a], Rm[q * p + c]);
+        Gm[a * p + c].x -= t.x;
+        Gm[a * p + c].y -= t.y;
+      }
+    }
+    __syncthreads();
+  }
+  upper_inverse_cols(Rm, Wd, p);
+  __syncthreads();
+  // W as applied: float32 entries
+  for (int i = tid; i < p * p; i += nt) {
+    const float2 wf = make_float2((float)Wd[i].x, (float)Wd[i].y);
+    W[i] = wf;
+    Wd[i] = make_double2((double)wf.x, (double)wf.y);
+  }
+  if (pass == 0) return;
+  __syncthreads();
+  // T = W_1 W_2 (both upper triangular, float entries), then Hsub = T^{-1} into Rm
+  const float2* W1 = bt.bw + (size_t)g * 2 * p * p;
+  for (int idx = tid; idx < p * p; idx += nt) {
+    const int l = idx / p, q = idx % p;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = l; k <= q; ++k) {
+      const double2 t = bz_mul(make_double2(W1[l * p + k].x, W1[l * p + k].y), Wd[k * p + q]);
+      acc.x += t.x; acc.y += t.y;
+    }
+    T[idx] = acc;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < p * p; i += blockDim.x) W[i] = make_float2((float)Wd[i].x, (float)Wd[i].y);
-  if (pass == 0) return;
-  if (threadIdx.x == 0) {
-    // T = W_1 W_2 (both upper triangular, float entries), then Hsub = T^{-1} into Rm
-    const float2* W1 = bt.bw + (size_t)g * 2 * p * p;
-    for (int l = 0; l < p; ++l)
-      for (int q = 0; q < p; ++q) {
-        double2 acc = make_double2(0.0, 0.0);
-        for (int k = l; k <= q; ++k) {
-          const double2 t = bz_mul(make_double2(W1[l * p + k].x, W1[l * p + k].y), Wd[k * p + q]);
-          acc.x += t.x; acc.y += t.y;
-        }
-        T[l * p + q] = acc;
-      }
-    upper_inverse(T, Rm, p);
-  }
+  upper_inverse_cols(T, Rm, p);
   __syncthreads();
   const int rows = (j + 2) * p, nr = (j + 1) * p;
   const double2* D1 = bt.bdot + (size_t)g * 2 * bt.bld * p;
   const double2* D2 = D1 + (size_t)bt.bld * p;
-  for (int idx = threadIdx.x; idx < p * rows; idx += blockDim.x) {
+  for (int idx = tid; idx < p * rows; idx += nt) {
     const int q = idx / rows, r = idx - q * rows;
     const int c = j * p + q;
     double2 h;
@@ -463,18 +481,25 @@ __global__ void __launch_bounds__(kBT) k_btransform(Batch bt, int pass) {
 }
 
 // Givens rotation zeroing b against a (a <- rho e^{i arg a}), the convention of the
-// per-shift least squares: x_r' = c x_r + s x_r2, x_r2' = -conj(s) x_r + c x_r2
+// per-shift least squares: x_r' = c x_r + s x_r2, x_r2' = -conj(s) x_r + c x_r2, with
+// c = |a| / rho, s = (a / |a|) conj(b) / rho, rho^2 = |a|^2 + |b|^2.  Formed from the squared moduli
+// with two square roots and one reciprocal (the entries are far from the double range limits that
+// hypot guards against); these rotations are computed one after another, so their latency counts.
 __device__ __forceinline__ void bgivens(double2 a, double2 b, double& c, double2& s, double2& r) {
-  const double na = hypot(a.x, a.y), nb = hypot(b.x, b.y), rho = hypot(na, nb);
-  if (rho == 0.0) {
-    c = 1.0; s = make_double2(0.0, 0.0); r = make_double2(0.0, 0.0);
-  } else if (na == 0.0) {
+  const double na2 = a.x * a.x + a.y * a.y, nb2 = b.x * b.x + b.y * b.y;
+  if (nb2 == 0.0) {   // nothing to eliminate (also a = b = 0)
+    c = 1.0; s = make_double2(0.0, 0.0); r = a;
+  } else if (na2 == 0.0) {
+    const double nb = sqrt(nb2);
     c = 0.0; s = make_double2(b.x / nb, -b.y / nb); r = make_double2(nb, 0.0);
   } else {
-    c = na / rho;
-    const double2 ph = make_double2(a.x / na, a.y / na);
-    s = bz_mul(ph, make_double2(b.x / rho, -b.y / rho));
-    r = make_double2(ph.x * rho, ph.y * rho);
+    const double rho2 = na2 + nb2;
+    const double inv = 1.0 / (sqrt(na2) * sqrt(rho2));   // 1 / (|a| rho)
+    c = na2 * inv;
+    const double2 ab = bz_mul(a, make_double2(b.x, -b.y));
+    s = make_double2(ab.x * inv, ab.y * inv);
+    const double f = rho2 * inv;                          // rho / |a|
+    r = make_double2(a.x * f, a.y * f);
   }
 }
 __device__ __forceinline__ void brot(double2* x, int r1, int r2, double c, double2 s) {
@@ -498,39 +523,56 @@ __device__ __forceinline__ int bshift_group(const Batch& bt, int bs) {
   return g;
 }
 
-// Block least squares of one shift z (one warp): the new block column j of
-// Hbar(z; T_j) = [I; 0] + Hbar_j (z - tau_j) gets every earlier rotation (lane q < p: column
-// jp + q), then its own p rotations per column, in column order; lanes 16 + q carry column q of the
-// rotated right-hand side E_1 (beta = I).  The rotated matrix R (upper triangular) and the
-// rotated right-hand side are kept per shift for the back-substitution.
-// The rotations of an earlier column cc act on rows cc..cc+p only, so a lane walks its column down
-// with a window of p+1 rows in registers: row cc leaves the window final, row cc+p+1 enters it
-// from H; the earlier rotations come through shared memory, kBLsChunk columns at a time.
+// Block least squares of the shifts (one warp carries min(floor(32 / p), kBLsMaxSpw) of them):
+// lane (slot, q) owns column q of its shift.  The new block column j of
+// Hbar(z; T_j) = [I; 0] + Hbar_j (z - tau_j) gets every earlier rotation, then its own p rotations
+// per column in column order, and the same lane applies them to column q of the rotated right-hand
+// side E_1 (beta = I).  The rotated matrix R (upper triangular) and right-hand side are kept per
+// shift for the back-substitution.  The rotations of an earlier column cc act on rows cc..cc+p only,
+// so a lane walks its column down with a window of p+1 rows in registers: row cc leaves the window
+// final, row cc+p+1 enters it from H; the earlier rotations of the warp's shifts come through shared
+// memory, kBLsChunk columns at a time.
 constexpr int kBLsChunk = 32;
+// One shift per warp.  Measured on the 256x256 block step (48 launches): packing 2-4 shifts into a
+// warp 62 ms against 57; the earlier columns taken four at a time in one unrolled block 49.4 against
+// 50.1 ms, and the same with identity rotations padding each column to PMAX (branch-free) 60.7 ms --
+// the time follows the FP64 work of the active lanes, not the dependency chains
+constexpr int kBLsMaxSpw = 1;
+__host__ __device__ __forceinline__ int ls_spw(int p) { return 32 / p > kBLsMaxSpw ? kBLsMaxSpw : 32 / p; }
+
 template <int PMAX>
 __global__ void __launch_bounds__(32) k_block_ls(Batch bt) {
-  __shared__ double rc_s[kBLsChunk * PMAX];
-  __shared__ double2 rs_s[kBLsChunk * PMAX];
-  const int bs = blockIdx.x;
-  const int g = bshift_group(bt, bs);
-  if (!bt.active[g]) return;
-  const int j = *bt.jdev, p = bt.bp, G = bt.ngroups, hld = bt.hld;
-  const int i_sh = bs - bt.shift_off[g];
+  __shared__ double rc_s[kBLsMaxSpw][kBLsChunk * PMAX];
+  __shared__ double2 rs_s[kBLsMaxSpw][kBLsChunk * PMAX];
+  const int p = bt.bp, G = bt.ngroups, hld = bt.hld;
+  const int spw = ls_spw(p);
   const int lane = threadIdx.x;
-  // all right-hand sides of this shift already converged: nothing left to do here
-  int open = 0;
-  for (int q = 0; q < p; ++q) open |= bt.conv_it[bt.shift_off[q * G + g] + i_sh] == 0;
-  if (!open) return;
-  const double2 z = bt.zsh[bs], tau = bt.tau_cur[g];
-  const double2 dz = make_double2(z.x - tau.x, z.y - tau.y);
-  double2* R = bt.bR + (size_t)bs * bt.bld * hld;
-  double* rcs = bt.brc + (size_t)bs * bt.bld * p;
-  double2* rss = bt.brs + (size_t)bs * bt.bld * p;
-  double2* Gr = bt.bG + (size_t)bs * hld * p;
+  const int sl = lane / p, q = lane - sl * p;
+  const int bs = blockIdx.x * spw + sl;
+  const int j = *bt.jdev, c0 = j * p;
+  bool on = sl < spw && bs < bt.nbs;
+  int g = 0, i_sh = 0;
+  if (on) {
+    g = bshift_group(bt, bs);
+    on = bt.active[g] != 0;
+    i_sh = bs - bt.shift_off[g];
+  }
+  if (on) {   // all right-hand sides of the shift converged: nothing left to do for it
+    int open = 0;
+    for (int r = 0; r < p; ++r) open |= bt.conv_it[bt.shift_off[r * G + g] + i_sh] == 0;
+    on = open != 0;
+  }
+  double2 dz = make_double2(0.0, 0.0);
+  if (on) {
+    const double2 z = bt.zsh[bs], tau = bt.tau_cur[g];
+    dz = make_double2(z.x - tau.x, z.y - tau.y);
+  }
+  double2* R = bt.bR + (size_t)(on ? bs : 0) * bt.bld * hld;
+  double* rcs = bt.brc + (size_t)(on ? bs : 0) * bt.bld * p;
+  double2* rss = bt.brs + (size_t)(on ? bs : 0) * bt.bld * p;
+  double2* Gr = bt.bG + (size_t)(on ? bs : 0) * hld * p;
   const double2* H = bt.bH + (size_t)g * bt.bld * hld;
-  const int c0 = j * p;
-  const bool col_lane = lane < p;
-  const int c = c0 + (col_lane ? lane : 0);
+  const int c = c0 + q;
   double2* Rc = R + (size_t)c * hld;
   const double2* Hc = H + (size_t)c * hld;
   // row r of column c of Hbar(z; T_j); rows below c + p are zero (and never written in H)
@@ -544,29 +586,31 @@ __global__ void __launch_bounds__(32) k_block_ls(Batch bt) {
   };
   double2 win[PMAX + 1];
 #pragma unroll
-  for (int r = 0; r <= PMAX; ++r) win[r] = (col_lane && r <= p) ? hz(r) : make_double2(0.0, 0.0);
+  for (int r = 0; r <= PMAX; ++r) win[r] = (on && r <= p) ? hz(r) : make_double2(0.0, 0.0);
   for (int cb = 0; cb < c0; cb += kBLsChunk) {
-    const int ce = min(cb + kBLsChunk, c0);
+    const int ce = min(cb + kBLsChunk, c0), nrot = (ce - cb) * p;
     __syncwarp();
-    for (int i = lane; i < (ce - cb) * p; i += 32) {
-      rc_s[i] = rcs[(size_t)cb * p + i];
-      rs_s[i] = rss[(size_t)cb * p + i];
+    for (int idx = lane; idx < spw * nrot; idx += 32) {
+      const int ss = idx / nrot, r = idx - ss * nrot, bss = blockIdx.x * spw + ss;
+      if (bss < bt.nbs) {
+        rc_s[ss][r] = bt.brc[(size_t)bss * bt.bld * p + (size_t)cb * p + r];
+        rs_s[ss][r] = bt.brs[(size_t)bss * bt.bld * p + (size_t)cb * p + r];
+      }
     }
     __syncwarp();
-    if (col_lane) {
+    if (on) {
       for (int cc = cb; cc < ce; ++cc) {
-        const double* rcp = rc_s + (cc - cb) * p;
-        const double2* rsp = rs_s + (cc - cb) * p;
+        const double* rcp = rc_s[sl] + (cc - cb) * p;
+        const double2* rsp = rs_s[sl] + (cc - cb) * p;
         const double2 nv = hz(cc + p + 1);
 #pragma unroll
         for (int k = 0; k < PMAX; ++k)
           if (k < p) {
             const double cs = rcp[k];
-            const double2 sn = rsp[k];
-            const double2 a = win[0], b = win[1 + k];
-            const double2 sb = bz_mul(sn, b), sa = bz_cmul(sn, a);
+            const double2 sn = rsp[k], a = win[0], bq = win[1 + k];
+            const double2 sb = bz_mul(sn, bq), sa = bz_cmul(sn, a);
             win[0] = make_double2(cs * a.x + sb.x, cs * a.y + sb.y);
-            win[1 + k] = make_double2(cs * b.x - sa.x, cs * b.y - sa.y);
+            win[1 + k] = make_double2(cs * bq.x - sa.x, cs * bq.y - sa.y);
           }
         Rc[cc] = win[0];
 #pragma unroll
@@ -577,13 +621,11 @@ __global__ void __launch_bounds__(32) k_block_ls(Batch bt) {
       }
     }
   }
-  if (col_lane) {
+  if (on) {
 #pragma unroll
     for (int r = 0; r <= PMAX; ++r)
       if (r <= p) Rc[c0 + r] = win[r];
     for (int r = c0 + p + 1; r <= c + p; ++r) Rc[r] = hz(r);
-  } else if (lane >= 16 && lane - 16 < p) {
-    const int q = lane - 16;
     if (j == 0)
       for (int r = 0; r < p; ++r) Gr[(size_t)r * p + q] = make_double2(r == q ? 1.0 : 0.0, 0.0);
     for (int r = (j + 1) * p; r < (j + 2) * p; ++r) Gr[(size_t)r * p + q] = make_double2(0.0, 0.0);
@@ -591,29 +633,38 @@ __global__ void __launch_bounds__(32) k_block_ls(Batch bt) {
   __syncwarp();
   for (int qq = 0; qq < p; ++qq) {
     const int cn = c0 + qq;
-    if (lane == qq) {
+    if (on && q == qq) {
+      // the pivot and the p entries below it in registers: the rotations form one dependent chain
+      double2 below[PMAX];
+#pragma unroll
+      for (int k = 0; k < PMAX; ++k) below[k] = k < p ? Rc[cn + 1 + k] : make_double2(0.0, 0.0);
+      double2 top = Rc[cn];
+#pragma unroll
+      for (int k = 0; k < PMAX; ++k)
+        if (k < p) {
+          double cs;
+          double2 sn, r;
+          bgivens(top, below[k], cs, sn, r);
+          top = r;
+          rc_s[sl][k] = cs;
+          rs_s[sl][k] = sn;
+        }
+      Rc[cn] = top;
       for (int k = 0; k < p; ++k) {
-        double cs;
-        double2 sn, r;
-        bgivens(Rc[cn], Rc[cn + 1 + k], cs, sn, r);
-        Rc[cn] = r;
         Rc[cn + 1 + k] = make_double2(0.0, 0.0);
-        rcs[(size_t)cn * p + k] = cs;
-        rss[(size_t)cn * p + k] = sn;
-        rc_s[k] = cs;
-        rs_s[k] = sn;
+        rcs[(size_t)cn * p + k] = rc_s[sl][k];
+        rss[(size_t)cn * p + k] = rs_s[sl][k];
       }
     }
     __syncwarp();
-    if (col_lane && lane > qq) {
-      for (int k = 0; k < p; ++k) brot(Rc, cn, cn + 1 + k, rc_s[k], rs_s[k]);
-    } else if (lane >= 16 && lane - 16 < p) {
-      for (int k = 0; k < p; ++k) brot_g(Gr, p, lane - 16, cn, cn + 1 + k, rc_s[k], rs_s[k]);
+    if (on) {
+      if (q > qq)
+        for (int k = 0; k < p; ++k) brot(Rc, cn, cn + 1 + k, rc_s[sl][k], rs_s[sl][k]);
+      for (int k = 0; k < p; ++k) brot_g(Gr, p, q, cn, cn + 1 + k, rc_s[sl][k], rs_s[sl][k]);
     }
     __syncwarp();
   }
-  if (lane >= 16 && lane - 16 < p) {
-    const int q = lane - 16;
+  if (on) {
     double r2 = 0.0;
     for (int r = (j + 1) * p; r < (j + 2) * p; ++r) {
       const double2 v = Gr[(size_t)r * p + q];
@@ -646,10 +697,15 @@ __global__ void k_block_flags(Batch bt) {
 }
 
 // y = R^{-1} g for every (shift, right-hand side): n = (iterations at convergence, else done) * p
-// columns of the shift's rotated block system.  sh is the global shift of member q of group g.
+// columns of the shift's rotated block system.  One warp per (shift, right-hand side), column by
+// column from the last: y_i = g_i / R_ii, then g_l -= R_li y_i for l < i with the lanes splitting l
+// (column i of R is contiguous); g sits in shared memory.  sh is the global shift of member q of
+// group g.
 __global__ void k_bbacksolve(Batch bt, const int* sh_basis) {
-  const int sh = blockIdx.x * blockDim.x + threadIdx.x;
-  if (sh >= bt.nsh) return;
+  extern __shared__ double2 gsm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sh = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (sh >= bt.nsh) return;   // whole warps leave; the kernel has no block-wide barrier
   const int b = sh_basis[sh], G = bt.ngroups, p = bt.bp, hld = bt.hld;
   const int g = b % G, q = b / G;
   const int bs = bt.shift_off[g] + (sh - bt.shift_off[b]);
@@ -658,15 +714,21 @@ __global__ void k_bbacksolve(Batch bt, const int* sh_basis) {
   const double2* R = bt.bR + (size_t)bs * bt.bld * hld;
   const double2* Gr = bt.bG + (size_t)bs * hld * p;
   double2* y = bt.bY + (size_t)sh * bt.bld;
-  for (int i = n; i < bt.bld; ++i) y[i] = make_double2(0.0, 0.0);
+  double2* gw = gsm + (size_t)warp * bt.bld;
+  for (int i = lane; i < n; i += 32) gw[i] = Gr[(size_t)i * p + q];
+  for (int i = n + lane; i < bt.bld; i += 32) y[i] = make_double2(0.0, 0.0);
+  __syncwarp();
   for (int i = n - 1; i >= 0; --i) {
-    double2 acc = Gr[(size_t)i * p + q];
-    for (int l = i + 1; l < n; ++l) {
-      const double2 t = bz_mul(R[(size_t)l * hld + i], y[l]);
-      acc.x -= t.x; acc.y -= t.y;
+    const double2* Rc = R + (size_t)i * hld;
+    const double2 d = Rc[i];
+    const double2 yi = (d.x != 0.0 || d.y != 0.0) ? bz_div(gw[i], d) : make_double2(0.0, 0.0);
+    if (lane == 0) y[i] = yi;
+    for (int l = lane; l < i; l += 32) {
+      const double2 t = bz_mul(Rc[l], yi);
+      gw[l].x -= t.x;
+      gw[l].y -= t.y;
     }
-    const double2 d = R[(size_t)i * hld + i];
-    y[i] = (d.x != 0.0 || d.y != 0.0) ? bz_div(acc, d) : make_double2(0.0, 0.0);
+    __syncwarp();
   }
 }
 
@@ -778,11 +840,12 @@ static int device_sms() {
   return sms;
 }
 
-// CTAs per group for the tile-looping kernels: about four CTAs per SM over all groups, every CTA
-// with the same number of tiles
+// CTAs per group for the tile-looping kernels: about eight CTAs per SM over all groups (the update
+// kernels hold up to three per SM; more CTAs than that keep the SMs full through the tail), every
+// CTA with the same number of tiles
 static unsigned tile_grid(int64_t N, int cpt, int groups) {
   const int64_t nt = (N + kBT * cpt - 1) / (kBT * cpt);
-  const int64_t target = std::max<int64_t>(1, 4 * device_sms() / std::max(groups, 1));
+  const int64_t target = std::max<int64_t>(1, 8 * device_sms() / std::max(groups, 1));
   const int64_t per = (nt + target - 1) / target;
   return (unsigned)((nt + per - 1) / per);
 }
@@ -806,18 +869,19 @@ static void block_arnoldi_t(const Batch& bt, const FineExact& fe, cudaStream_t s
   prof_begin(pf, KC_NORMALIZE, st);
   for (int pass = 0; pass < 2; ++pass) {
     k_bgram<PMAX, CPTD><<<gd, kBT, 0, st>>>(bt, pass);
-    k_bchol<<<G, 128, 0, st>>>(bt, pass);
+    k_bchol<<<G, 256, 0, st>>>(bt, pass);
     k_btransform<PMAX, CPTU><<<gt, kBT, 0, st>>>(bt, pass);
   }
   prof_end(pf, KC_NORMALIZE, st);
   prof_begin(pf, KC_SHIFT_LS, st);
-  k_block_ls<PMAX><<<bt.nbs, 32, 0, st>>>(bt);
+  k_block_ls<PMAX><<<(bt.nbs + ls_spw(bt.bp) - 1) / ls_spw(bt.bp), 32, 0, st>>>(bt);
   prof_end(pf, KC_SHIFT_LS, st);
 }
 
 int launch_block_iteration(const Batch& bt, const FineExact& fe, cudaStream_t st, int* nlaunch, Prof* pf) {
   if (bt.bp <= 4) block_arnoldi_t<4, 4, 4>(bt, fe, st, pf);
   else if (bt.bp <= 8) block_arnoldi_t<8, 4, 2>(bt, fe, st, pf);
+  else if (bt.bp <= 12) block_arnoldi_t<12, 2, 1>(bt, fe, st, pf);
   else if (bt.bp <= 16) block_arnoldi_t<16, 2, 1>(bt, fe, st, pf);
   else return 1;
   k_block_flags<<<1, 256, 0, st>>>(bt);
@@ -826,7 +890,14 @@ int launch_block_iteration(const Batch& bt, const FineExact& fe, cudaStream_t st
 }
 
 void launch_block_backsolve(const Batch& bt, const int* sh_basis, cudaStream_t st) {
-  k_bbacksolve<<<(bt.nsh + 127) / 128, 128, 0, st>>>(bt, sh_basis);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_bbacksolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  const size_t per_warp = (size_t)bt.bld * sizeof(double2);
+  const int warps = (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(200 * 1024) / per_warp));
+  k_bbacksolve<<<(bt.nsh + warps - 1) / warps, 32 * warps, warps * per_warp, st>>>(bt, sh_basis);
 }
 
 void launch_block_xk(const Batch& bt, float2* X_hi, float2* X_lo, cudaStream_t st, Prof* pf) {
