@@ -229,16 +229,39 @@ __device__ __forceinline__ int coarse_slot(int I, int lJ, int ncx, int rowoff, i
 // the black half-sweep every black cell satisfies its equation, so its residual is zero up to rounding
 // and only the two red children are evaluated; red_only = false evaluates all four.  The children of
 // coarse cell I all sit at position k = I of their colour and row (strips start on even rows).
+// Which fine cells the restriction evaluates (the others have a zero residual, or all four when
+// nothing is known): kRestrictAll; kRestrictRed after a sweep ending with a black half-sweep;
+// kRestrictBlack after one ending with a red half-sweep; kRestrictZeroU when the iterate is zero,
+// so the residual is the right-hand side itself (no neighbours read).
+constexpr int kRestrictAll = 0, kRestrictRed = 1, kRestrictBlack = 2, kRestrictZeroU = 3;
+
 __device__ __forceinline__ float l0_restrict(const L0V& S, float2* fc, int ncx, FastDiv dncx, int rowoff, int fc_hx,
-                                             int fc_planec, bool red_only) {
+                                             int fc_planec, int mode) {
   const int nch = S.h >> 1, n = nch * ncx;
-  const int nchild = red_only ? 2 : 4;
   float rr = 0.f;
+  if (mode == kRestrictZeroU) {
+    for (int q = threadIdx.x; q < n; q += (int)blockDim.x) {
+      const int lJ = fdiv(q, dncx), I = q - lJ * ncx;
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int ch = 0; ch < 4; ++ch) {
+        const int c = ch >> 1, ly = 2 * lJ + (ch & 1);
+        const float4 qq = S.Q[c * (S.ny * S.hx) + (S.y0 + ly) * S.hx + I];
+        acc.x += qq.z;
+        acc.y += qq.w;
+        rr += qq.z * qq.z + qq.w * qq.w;
+      }
+      fc[coarse_slot(I, lJ, ncx, rowoff, fc_hx, fc_planec)] = acc;
+    }
+    return rr;
+  }
+  const int nchild = mode == kRestrictAll ? 4 : 2;
+  const int c1 = mode == kRestrictBlack ? 1 : 0;   // colour of the two children when only two are evaluated
   for (int q = threadIdx.x; q < n; q += (int)blockDim.x) {
     const int lJ = fdiv(q, dncx), I = q - lJ * ncx;
     float2 acc = make_float2(0.f, 0.f);
     for (int ch = 0; ch < nchild; ++ch) {
-      const int c = ch >> 1, ly = 2 * lJ + (ch & 1);
+      const int c = nchild == 4 ? ch >> 1 : c1, ly = 2 * lJ + (ch & 1);
       const L0Cell cq = l0_load(S, c * (S.ny * S.hx) + (S.y0 + ly) * S.hx + I);
       float2 nb[4];
       l0_gather(S, c, ly, I, nb);
@@ -282,14 +305,29 @@ __device__ __forceinline__ void rbv_half_sweep(const RBV& S, FastDiv dhx, int co
 }
 
 __device__ __forceinline__ void rbv_restrict(const RBV& S, float2* fc, int ncx, FastDiv dncx, int rowoff, int fc_hx,
-                                             int fc_planec, bool red_only) {
+                                             int fc_planec, int mode) {
   const int nch = S.h >> 1, n = nch * ncx;
-  const int nchild = red_only ? 2 : 4;
+  if (mode == kRestrictZeroU) {
+    for (int q = threadIdx.x; q < n; q += (int)blockDim.x) {
+      const int lJ = fdiv(q, dncx), I = q - lJ * ncx;
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int ch = 0; ch < 4; ++ch) {
+        const float2 fv = S.f[(ch >> 1) * S.plane + (2 * lJ + (ch & 1)) * S.hx + I];
+        acc.x += fv.x;
+        acc.y += fv.y;
+      }
+      fc[coarse_slot(I, lJ, ncx, rowoff, fc_hx, fc_planec)] = acc;
+    }
+    return;
+  }
+  const int nchild = mode == kRestrictAll ? 4 : 2;
+  const int c1 = mode == kRestrictBlack ? 1 : 0;
   for (int q = threadIdx.x; q < n; q += (int)blockDim.x) {
     const int lJ = fdiv(q, dncx), I = q - lJ * ncx;
     float2 acc = make_float2(0.f, 0.f);
     for (int ch = 0; ch < nchild; ++ch) {
-      const int c = ch >> 1, ly = 2 * lJ + (ch & 1);
+      const int c = nchild == 4 ? ch >> 1 : c1, ly = 2 * lJ + (ch & 1);
       float4 t;
       float2 nb[4];
       rbv_cell(S, c, ly, I, t, nb);
@@ -675,7 +713,12 @@ __global__ void __launch_bounds__(kIT, 1) k_inner_cluster(const __grid_constant_
             cl.sync();
           }
           const int fhx = last ? 0 : sL[1].nx >> 1, fplane = last ? 0 : (sL[1].ny / cs) * fhx;
-          const float rr = l0_restrict(S0, fc, ncx, a.dnx[1], S0.y0 / 2, fhx, fplane, a.npre > 0);
+          // after pre-smoothing (ending black) only the red children carry a residual; without it, the
+          // first cycle of a round starts from u = 0 and every later one follows post-smoothing that
+          // ended with a red half-sweep
+          const int mode = a.npre > 0 ? kRestrictRed : cy == 0 ? kRestrictZeroU
+                         : a.npost > 0 ? kRestrictBlack : kRestrictAll;
+          const float rr = l0_restrict(S0, fc, ncx, a.dnx[1], S0.y0 / 2, fhx, fplane, mode);
           block_sum(rr, red, &vpart[cy & 1]);
         } else {
           const RBV S = rbview(l);
@@ -684,7 +727,8 @@ __global__ void __launch_bounds__(kIT, 1) k_inner_cluster(const __grid_constant_
             cl.sync();
           }
           const int fhx = last ? 0 : sL[l + 1].nx >> 1, fplane = last ? 0 : (sL[l + 1].ny / cs) * fhx;
-          rbv_restrict(S, fc, ncx, a.dnx[l + 1], S.y0 / 2, fhx, fplane, a.npre > 0);
+          // the coarser strip levels start every cycle from u = 0 (cleared after the last prolongation)
+          rbv_restrict(S, fc, ncx, a.dnx[l + 1], S.y0 / 2, fhx, fplane, a.npre > 0 ? kRestrictRed : kRestrictZeroU);
         }
         __syncthreads();   // the next level's sweeps read right-hand sides written by other threads
       }

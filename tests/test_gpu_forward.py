@@ -250,6 +250,27 @@ def test_cluster_forms_match_eight_cta_clusters(Engine, shape, form):
     assert _rel(h2, ref) < TOL_H
 
 
+@pytest.mark.parametrize("shape,post", [((128, 96), 2), ((256, 128), 3)])
+def test_post_smoothing_only_cycles(Engine, shape, post):
+    """V(0, post) cycles: the cluster-resident solve restricts the right-hand side alone at the first
+    cycle of a round (zero iterate) and only the black children afterwards (post-smoothing ends with
+    a red half-sweep); heads against the direct oracle on both solve paths."""
+    from paper_1409_2556_gb300._lib import KC
+    nx, ny = shape
+    p = W.random_problem(nx, ny, 1, variance=1.5, seed=3 * nx + ny, ns=2, nr=3, nt=3, Nz=16, tol=1e-11, groups=2)
+    ref = direct.forward(p)
+    for cl in (1, 0):
+        eng = Engine(0)
+        eng.load_problem(p, mg_cluster=cl, mg_pre=0, mg_post=post, inner_relax=1e-2)
+        h = eng.forward(p.times)
+        st = eng.last_stats
+        eng.close()
+        assert (st["work"][KC["inner"]] > 0) == (cl == 1)
+        assert st["n_converged"] == st["n_shift_solves"]
+        assert st["max_true_residual"] <= 1e-11
+        assert _rel(h, ref) < TOL_H
+
+
 def test_cluster_solve_falls_back_on_grids_that_do_not_split(Engine):
     """40 rows do not split into 8 strips of even height: the batched launches run instead."""
     from paper_1409_2556_gb300._lib import KC
