@@ -394,13 +394,20 @@ __device__ __forceinline__ void sv_half_sweep_full(const SV& S, FastDiv dnx, int
 // right-hand side fc (coarse row J at row J - row0); uc non-null: also clear the next level's iterate;
 // red_only (2x2 coarsening, sweep ended black): only the red children, see l0_restrict
 __device__ __forceinline__ void sv_restrict(const SV& S, int rx, int ry, float2* fc, float2* uc, int ncx,
-                                            FastDiv dncx, int row0, bool red_only) {
+                                            FastDiv dncx, int row0, int mode) {
   const int nch = S.h / ry, n = nch * ncx;
+  const bool red_only = mode == kRestrictRed;
   for (int q = threadIdx.x; q < n; q += (int)blockDim.x) {
     const int lJ = fdiv(q, dncx), I = q - lJ * ncx;
     float2 acc = make_float2(0.f, 0.f);
     for (int dj = 0; dj < ry; ++dj)
       for (int di = 0; di < rx; ++di) {
+        if (mode == kRestrictZeroU) {   // zero iterate: the residual is the right-hand side
+          const float2 fv = S.f[(lJ * ry + dj) * S.nx + I * rx + di];
+          acc.x += fv.x;
+          acc.y += fv.y;
+          continue;
+        }
         if (red_only && di != dj) continue;
         const int x = I * rx + di, ly = lJ * ry + dj, y = S.y0 + ly, li = ly * S.nx + x;
         float4 t;
@@ -753,7 +760,7 @@ __global__ void __launch_bounds__(kIT, 1) k_inner_cluster(const __grid_constant_
           const Level& Lc = sL[l + 1];
           sv_restrict(S, sL[l].rx, sL[l].ry, reinterpret_cast<float2*>(smb + a.off[l + 1].f),
                       reinterpret_cast<float2*>(smb + a.off[l + 1].u), Lc.nx, a.dnx[l + 1], 0,
-                      q22 && a.npre > 0);
+                      a.npre == 0 ? kRestrictZeroU : q22 ? kRestrictRed : kRestrictAll);
           __syncthreads();
         }
       if (a.coarse_direct) {
