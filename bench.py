@@ -252,8 +252,9 @@ def jacobian_rows(dev, stream, reps: int = 1):
     from paper_1409_2556_gb300 import Engine
     prob = W.config3()
     eng = Engine(dev, stream=stream)
+    # post-smoothing-only V(0,2) cycles: 20% less time than V(2,2) on this grid's forward solves
     eng.load_problem(prob, tol=1e-10, maxit=72, inner_relax=1e-4, inner_rounds=4, inner_cycles=6, groups=1,
-                     check_every=4)
+                     check_every=4, mg_pre=0, mg_post=2)
     ns, nr, nt = len(prob.src_cells), len(prob.rec_cells), len(prob.times)
     J = torch.zeros((ns, nr, nt, 2, prob.ncell), dtype=torch.float64, device=f"cuda:{dev}")
     eng.adjoint_jacobian(prob.times, J)
