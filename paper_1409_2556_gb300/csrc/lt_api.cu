@@ -1120,8 +1120,11 @@ static int launch_iteration(lt_ctx* ctx, cudaStream_t q, int jj, int* nlq, lt::P
       learned_guess(ctx->net, bt, L0, r, ctx->d_lk, ctx->d_mD, ctx->d_xin, ctx->d_gn2, q);
       *nlq += 24;
     }
+    // the round's correction starts at zero (unless the learned guess seeded it), and each later
+    // cycle follows the previous one's post-smoothing
     for (int cy = 0; cy < o.inner_cycles; ++cy)
-      if (lt::launch_vcycle(ctx->mg, bt, r, q, nlq, pf)) return LT_ERR_CUDA;
+      if (lt::launch_vcycle(ctx->mg, bt, r, q, nlq, pf, cy > 0 ? 0 : (o.precond == 1 && r == 0) ? -1 : 1))
+        return LT_ERR_CUDA;
     lt::launch_update_u(bt, L0, jj, r, q);
     ++*nlq;
   }

@@ -41,7 +41,10 @@ int launch_inner_cluster(const MGHost& mg, const InnerPlan& p, const Batch& bt, 
                          float2* u0, int cycles, cudaStream_t st, Prof* pf);
 
 // one V-cycle on every active basis of the batch whose refinement round `round` is not done
-int launch_vcycle(const MGHost& mg, const Batch& bt, int round, cudaStream_t st, int* nlaunch, Prof* pf);
+// u0_state: 1 if the finest level's iterate is zero on entry, 0 if it follows a previous cycle's
+// post-smoothing (which ends with the red half-sweep), -1 if unknown
+int launch_vcycle(const MGHost& mg, const Batch& bt, int round, cudaStream_t st, int* nlaunch, Prof* pf,
+                  int u0_state = -1);
 void tma_cache_free(MGHost& mg);
 
 // -------- krylov.cu

@@ -57,13 +57,40 @@ __global__ void k_rbgs(Level L, Batch bt, int round, int color) {
   rbgs_cell(L, L.u + (size_t)b * L.N, L.f + (size_t)b * L.N, c, tau32(bt, b));
 }
 
-__global__ void k_restrict(Level Lf, Level Lc, Batch bt, int round) {
+// Restriction of the residual to coarse cell C, evaluating only the fine cells that can carry one:
+// kMgRestrictAll, kMgRestrictBlack (after a sweep ending with the red half-sweep the red cells
+// satisfy their equations) or kMgRestrictZeroU (zero iterate: the residual is the right-hand side).
+constexpr int kMgRestrictAll = 0, kMgRestrictBlack = 2, kMgRestrictZeroU = 3;
+__global__ void k_restrict(Level Lf, Level Lc, Batch bt, int round, int mode) {
   int b = blockIdx.y;
   if (mg_skip(bt, b, round)) return;
   int C = blockIdx.x * blockDim.x + threadIdx.x;
   if (C >= Lc.N) return;
-  restrict_cell(Lf, Lc, Lf.u + (size_t)b * Lf.N, Lf.f + (size_t)b * Lf.N, Lc.f + (size_t)b * Lc.N,
-                Lc.u + (size_t)b * Lc.N, C, tau32(bt, b));
+  const float2* uf = Lf.u + (size_t)b * Lf.N;
+  const float2* ff = Lf.f + (size_t)b * Lf.N;
+  if (mode == kMgRestrictAll) {
+    restrict_cell(Lf, Lc, uf, ff, Lc.f + (size_t)b * Lc.N, Lc.u + (size_t)b * Lc.N, C, tau32(bt, b));
+    return;
+  }
+  const float2 tau = tau32(bt, b);
+  const int I = C % Lc.nx, J = (C / Lc.nx) % Lc.ny, K = C / (Lc.nx * Lc.ny);
+  float2 acc = make_float2(0.f, 0.f);
+  for (int dk = 0; dk < Lf.rz; ++dk)
+    for (int dj = 0; dj < Lf.ry; ++dj)
+      for (int di = 0; di < Lf.rx; ++di) {
+        const int i = I * Lf.rx + di, j = J * Lf.ry + dj, k = K * Lf.rz + dk;
+        const int c = (k * Lf.ny + j) * Lf.nx + i;
+        float2 r;
+        if (mode == kMgRestrictZeroU) {
+          r = ff[c];
+        } else {
+          if (((i + j + k) & 1) == 0) continue;   // red: zero residual after the red half-sweep
+          r = resid_cell(Lf, uf, ff, c, tau);
+        }
+        acc.x += r.x; acc.y += r.y;
+      }
+  Lc.f[(size_t)b * Lc.N + C] = acc;
+  Lc.u[(size_t)b * Lc.N + C] = make_float2(0.f, 0.f);
 }
 
 __global__ void k_prolong(Level Lf, Level Lc, Batch bt, int round, int dmask) {
@@ -650,7 +677,8 @@ static bool launch_up_tma(const MGHost& mg, int l, int tile, const Level& L, con
 }
 
 // ---------------------------------------------------------------- host launcher
-int launch_vcycle(const MGHost& mg, const Batch& bt, int round, cudaStream_t st, int* nlaunch, Prof* pf) {
+int launch_vcycle(const MGHost& mg, const Batch& bt, int round, cudaStream_t st, int* nlaunch, Prof* pf,
+                  int u0_state) {
   const int nb = bt.nb;
   const int T = 256;
   static bool attr_done = false;
@@ -684,8 +712,17 @@ int launch_vcycle(const MGHost& mg, const Batch& bt, int round, cudaStream_t st,
         ++*nlaunch;
       }
     dim3 gc((Lc.N + T - 1) / T, nb);
+    // without pre-smoothing the coarser levels enter with the zero iterate the restriction above
+    // left them; the finest level as the caller says (u0_state)
+    int mode = kMgRestrictAll;
+    if (mg.npre == 0) {
+      if (l > 0 || u0_state == 1) mode = kMgRestrictZeroU;
+      // (exact only after the plain half-sweeps: the fused tiles' asynchronous halo leaves small red
+      // residuals at tile edges)
+      else if (u0_state == 0 && mg.npost > 0 && !fused_ok(L)) mode = kMgRestrictBlack;
+    }
     prof_begin(pf, KC_RESTRICT, st);
-    k_restrict<<<gc, T, 0, st>>>(L, Lc, bt, round); ++*nlaunch;
+    k_restrict<<<gc, T, 0, st>>>(L, Lc, bt, round, mode); ++*nlaunch;
     prof_end(pf, KC_RESTRICT, st);
   }
   int thr = mg.h_levels[mg.lc].N >= 1024 ? 1024 : ((mg.h_levels[mg.lc].N + 31) / 32) * 32;

@@ -64,11 +64,15 @@ def test_heterogeneous_2d_ragged(Engine, shape, groups):
     assert st["max_true_residual"] <= 1e-11
 
 
-def test_3d_neumann_top_bottom(Engine):
+@pytest.mark.parametrize("sweeps", [(2, 2), (0, 2)])
+def test_3d_neumann_top_bottom(Engine, sweeps):
+    """3D levels on the batched launches; V(0, 2) also exercises the restriction of the right-hand
+    side alone (zero iterates) and of the black children after post-smoothing."""
     p = W.random_problem(16, 12, 8, variance=1.0, seed=5, ns=2, nr=3, nt=3, Nz=16, tol=1e-12,
                          ss_variance=0.25)
-    h, st = _solve(Engine, p)
+    h, st = _solve(Engine, p, mg_pre=sweeps[0], mg_post=sweeps[1])
     assert _rel(h, direct.forward(p)) < TOL_H
+    assert st["n_converged"] == st["n_shift_solves"]
 
 
 @pytest.mark.parametrize("policy,gs", [(0, 2), (1, 2), (1, 1)])
