@@ -63,7 +63,7 @@ KERNEL_NAMES = {"fused_up": "k_up2d (prolongation + correction + red-black post-
 # timed) / (2 x 151.5e6 units) = 3.11 B; the 2-source case has 6 bases per launch, config 2 has 13-14
 # (the per-basis records dominate, so the per-unit figure carries over).  Set to None when the
 # kernel changes until it is captured again.
-INNER_TRAFFIC_PER_UNIT = 3.11
+INNER_TRAFFIC_PER_UNIT = 2.60
 
 
 def vcycle_bytes_per_unit(R: int) -> float:
