@@ -794,7 +794,7 @@ def main():
                        "solver_tol": SOLVE_OPTS["tol"], "residual_bar": RESIDUAL_BAR,
                        "autotuned": {k: tuned.get(k) for k in ("mg_cluster", "mg_tile", "mg_pre", "mg_post",
                                                              "inner_rounds", "inner_cycles", "inner_relax",
-                                                             "mg_tma")},
+                                                             "inner_tol", "mg_tma")},
                        "max_true_residual": tres, "outer_iters_max": max(iters),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (Krylov bases ~GBs per step)"},

@@ -3,7 +3,7 @@
 Times short forward solves of the actual problem for a small grid of
 candidate settings -- cluster-resident or batched preconditioner solves,
 fused-smoother tile shape and TMA staging (batched only), pre/post smoothing
-sweeps, V-cycles per refinement round, refinement rounds, relaxation -- and
+sweeps, V-cycles per refinement round, refinement rounds, relaxation, base inner tolerance -- and
 keeps the fastest candidate whose every shifted system reaches the tolerance
 (true residual).
 Results are cached per problem shape in memory (and optionally in a JSON
@@ -28,7 +28,10 @@ DEFAULT_GRID = {
     # ((0, 2), (0, 3)) with relaxation 1e-2 measured 2% faster than V(1, 2)
     "sweeps": [(0, 2), (0, 3), (1, 2), (2, 2)],
     "inner": [(4, 6), (5, 4), (8, 6)],
-    "inner_relax": [1e-3, 1e-2],
+    "inner_relax": [1e-2],
+    # base inner tolerance as a multiple of the outer tolerance (0.01 is the library default); a
+    # candidate only counts if every shifted system still reaches the outer tolerance (true residual)
+    "inner_tol_factor": [0.01, 0.1],
     "mg_tma": [1],
 }
 
@@ -56,18 +59,21 @@ def autotune(engine, prob, base_opts: dict, grid: Optional[dict] = None, reps: i
     engine.load_problem(prob, **base_opts)
     best, best_ms = None, float("inf")
     relax = grid.get("inner_relax", [base_opts.get("inner_relax", 0.0)])
+    tol = base_opts.get("tol", prob.tol)
+    itols = [f * tol for f in grid["inner_tol_factor"]] if "inner_tol_factor" in grid else \
+        [base_opts.get("inner_tol", 0.0)]
     clusters = grid.get("mg_cluster", [base_opts.get("mg_cluster", 1)])
     cluster_possible = True
     for cl in clusters:
         # tile shape and TMA staging only matter to the batched launches
         tiles = grid["mg_tile"] if cl == 0 else [base_opts.get("mg_tile", 2)]
         tmas = grid.get("mg_tma", [base_opts.get("mg_tma", 1)]) if cl == 0 else [base_opts.get("mg_tma", 1)]
-        for tile, (pre, post), (rounds, cycles), rx, tma in itertools.product(tiles, grid["sweeps"],
-                                                                             grid["inner"], relax, tmas):
+        for tile, (pre, post), (rounds, cycles), rx, itol, tma in itertools.product(
+                tiles, grid["sweeps"], grid["inner"], relax, itols, tmas):
             if cl == 1 and not cluster_possible:
                 break
             cand = dict(base_opts, mg_cluster=cl, mg_tile=tile, mg_pre=pre, mg_post=post, inner_rounds=rounds,
-                        inner_cycles=cycles, inner_relax=rx, mg_tma=tma)
+                        inner_cycles=cycles, inner_relax=rx, inner_tol=itol, mg_tma=tma)
             engine.set_options(**{k: v for k, v in cand.items() if k not in ("Nz", "tol", "groups")})
             ok = True
             for _ in range(reps + 1):                      # first run warms the graph and workspace
@@ -80,7 +86,7 @@ def autotune(engine, prob, base_opts: dict, grid: Optional[dict] = None, reps: i
                 continue
             if verbose:
                 print(f"autotune cluster={cl} tile={tile} tma={tma} sweeps={pre},{post} inner={rounds}x{cycles} "
-                      f"relax={rx}: {ms:.1f} ms ok={ok}")
+                      f"relax={rx} inner_tol={itol:g}: {ms:.1f} ms ok={ok}")
             if ok and ms < best_ms:
                 best, best_ms = cand, ms
     if best is None:

@@ -76,3 +76,19 @@ def test_result_cached_per_problem_shape():
     n = len(eng.calls)
     AT.autotune(eng, _prob(), {"tol": 1e-10}, grid=GRID)
     assert len(eng.calls) == n           # second call: no solves
+
+
+def test_inner_tolerance_candidates_scale_with_tol():
+    """inner_tol_factor candidates are multiples of the outer tolerance; the looser one wins only
+    while every shifted system still converges."""
+    AT._CACHE.clear()
+    grid = dict(GRID, inner_relax=[1e-2], inner_tol_factor=[0.01, 0.1])
+    cost = lambda o: 100.0 - (10.0 if o["inner_tol"] > 5e-12 else 0.0) - (1.0 if o["mg_pre"] == 1 else 0.0)
+    eng = FakeEngine(cost, lambda o: True)
+    best = AT.autotune(eng, _prob(), {"tol": 1e-10, "Nz": 16, "groups": 1}, grid=grid)
+    assert sorted({round(o["inner_tol"], 15) for o in eng.calls}) == [1e-12, 1e-11]
+    assert abs(best["inner_tol"] - 1e-11) < 1e-20
+    AT._CACHE.clear()
+    eng = FakeEngine(cost, lambda o: o["inner_tol"] < 5e-12)    # the looser tolerance misses some systems
+    best = AT.autotune(eng, _prob(), {"tol": 1e-10, "Nz": 16, "groups": 1}, grid=grid)
+    assert abs(best["inner_tol"] - 1e-12) < 1e-20
