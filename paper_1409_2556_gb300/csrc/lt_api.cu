@@ -69,7 +69,11 @@ struct Workspace {
   // block flexible GMRES arrays (Batch::bdot .. grmax), sized for (p, groups, maxit, block shifts, shifts)
   std::vector<void*> block_allocs;
   int bk_p = 0, bk_G = 0, bk_M = 0, bk_nbs = 0, bk_nsh = 0;
+  // small per-call buffers of the forward path, kept between calls (slot = kScr*)
+  void* scr[8] = {};
+  size_t scr_bytes[8] = {};
 };
+enum { kScrShb = 0, kScrRes2, kScrItems, kScrWq, kScrC, kScrRc, kScrOut };
 
 struct lt_ctx {
   int device = 0;
@@ -187,6 +191,31 @@ static int dalloc(lt_ctx* ctx, std::vector<void*>& list, T** p, size_t n) {
   return LT_OK;
 }
 
+// A per-call device buffer of the forward path, kept in the workspace between calls (grown when a
+// call needs more; cudaMalloc / cudaFree synchronise the device, which the steady state avoids).  In
+// lt_forward_noalloc it is carved from the static region like every other buffer.
+template <typename T>
+static int scratch(lt_ctx* ctx, int slot, T** p, size_t n) {
+  if (ctx->arena_base) {
+    std::vector<void*> none;
+    return dalloc(ctx, none, p, n);
+  }
+  Workspace& ws = ctx->ws;
+  const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+  if (ws.scr_bytes[slot] < bytes) {
+    if (ws.scr[slot]) cudaFree(ws.scr[slot]);
+    ws.scr[slot] = nullptr;
+    ws.scr_bytes[slot] = 0;
+    const cudaError_t e = cudaMalloc(&ws.scr[slot], bytes);
+    if (e != cudaSuccess)
+      return fail(ctx, e == cudaErrorMemoryAllocation ? LT_ERR_OOM : LT_ERR_CUDA, "cudaMalloc of %zu bytes: %s", bytes,
+                  cudaGetErrorString(e));
+    ws.scr_bytes[slot] = bytes;
+  }
+  *p = reinterpret_cast<T*>(ws.scr[slot]);
+  return LT_OK;
+}
+
 static void free_list(std::vector<void*>& list) {
   for (void* p : list) cudaFree(p);
   list.clear();
@@ -267,6 +296,8 @@ int lt_set_stream(lt_ctx* ctx, void* stream) {
 static void free_ws(lt_ctx* ctx) {
   free_list(ctx->ws.allocs);
   free_list(ctx->ws.block_allocs);
+  for (void*& q : ctx->ws.scr)
+    if (q) cudaFree(q);
   ctx->ws = Workspace();
 }
 
@@ -1362,7 +1393,7 @@ static int solve_end(lt_ctx* ctx, const Plan& P, SolveState& S, std::vector<doub
   // y per shift
   int* d_shb = nullptr;
   std::vector<void*> tmp;
-  if ((rc = dalloc(ctx, tmp, &d_shb, P.nsh))) return rc;
+  if ((rc = scratch(ctx, kScrShb, &d_shb, P.nsh))) return rc;
   CK(cudaMemcpyAsync(d_shb, P.sh_basis.data(), P.nsh * sizeof(int), cudaMemcpyHostToDevice, s));
   if (bt.block) lt::launch_block_backsolve(bt, d_shb, s);
   else lt::launch_backsolve_map(bt, d_shb, s);
@@ -1383,7 +1414,7 @@ static int solve_end(lt_ctx* ctx, const Plan& P, SolveState& S, std::vector<doub
     ++*nl;
     if (o.true_residual) {
       double* d_res2 = nullptr;
-      if ((rc = dalloc(ctx, tmp, &d_res2, P.nsh))) { free_list(tmp); return rc; }
+      if ((rc = scratch(ctx, kScrRes2, &d_res2, P.nsh))) { free_list(tmp); return rc; }
       CK(cudaMemsetAsync(d_res2, 0, P.nsh * sizeof(double), s));
       lt::launch_true_res(bt, ctx->fe, d_shb, ws.X_hi, ws.X_lo, d_res2, s, pf);
       ++*nl;
@@ -1542,14 +1573,14 @@ static int forward_finish(lt_ctx* ctx, const Plan& P, const std::vector<double>&
   int64_t* d_rc;
   double* d_out = nullptr;
   const size_t out_n = fields ? (size_t)ns * nt * ctx->N : (size_t)ns * nr * nt;
-  if ((rc = dalloc(ctx, tmp, &d_items, items.size())) || (rc = dalloc(ctx, tmp, &d_wq, wq.size())) ||
-      (rc = dalloc(ctx, tmp, &d_C, items.size() * (P.block ? (size_t)ctx->ws.bt.bld : (size_t)ctx->opts.maxit))) ||
-      (rc = dalloc(ctx, tmp, &d_rc, std::max(nr, 1)))) {
+  if ((rc = scratch(ctx, kScrItems, &d_items, items.size())) || (rc = scratch(ctx, kScrWq, &d_wq, wq.size())) ||
+      (rc = scratch(ctx, kScrC, &d_C, items.size() * (P.block ? (size_t)ctx->ws.bt.bld : (size_t)ctx->opts.maxit))) ||
+      (rc = scratch(ctx, kScrRc, &d_rc, std::max(nr, 1)))) {
     free_list(tmp);
     return rc;
   }
   if (on_device) d_out = out;
-  else if ((rc = dalloc(ctx, tmp, &d_out, out_n))) { free_list(tmp); return rc; }
+  else if ((rc = scratch(ctx, kScrOut, &d_out, out_n))) { free_list(tmp); return rc; }
   CK(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(lt::QuadItem), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(d_wq, wq.data(), wq.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
   if (nr) CK(cudaMemcpyAsync(d_rc, ctx->rec.data(), nr * sizeof(int64_t), cudaMemcpyHostToDevice, s));
