@@ -115,6 +115,7 @@ struct lt_ctx {
   size_t arena_cap = 0, arena_off = 0;
   // non-blocking stream on which the per-iteration CUDA graph is captured and replayed
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t cap_stream2 = nullptr;   // the second half's stream when the halves run decoupled
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   // second branch of an outer iteration whose bases are split in two (cluster-resident solves)
   cudaStream_t side_stream = nullptr;
@@ -314,6 +315,7 @@ void lt_destroy(lt_ctx* ctx) {
   if (ctx->ev_a) cudaEventDestroy(ctx->ev_a);
   if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->cap_stream2) cudaStreamDestroy(ctx->cap_stream2);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
@@ -982,7 +984,7 @@ static int ensure_ws(lt_ctx* ctx, const Plan& P) {
   AL(bt.work, lt::kWorkSlots);
   AL(bt.itol2, nb);
   AL(bt.rmax, nb);
-  AL(bt.jdev, 1);
+  AL(bt.jdev, 2);
   {
     double* w = nullptr;
     float *rh = nullptr, *rl = nullptr;
@@ -1055,6 +1057,13 @@ struct SolveState {
   cudaStream_t q = nullptr;
   lt::Prof* pf = nullptr;
   std::vector<int> act;
+  // decoupled halves (nbr = 2): bases [bb0[p], bb0[p] + bbn[p]) with their own iteration counter,
+  // graph and stream, so that one half's solves run while the other half orthogonalises
+  int nbr = 0;
+  cudaGraphExec_t bgx[2] = {nullptr, nullptr};
+  cudaStream_t bq[2] = {nullptr, nullptr};
+  int bj[2] = {0, 0}, bb0[2] = {0, 0}, bbn[2] = {0, 0}, bper[2] = {0, 0};
+  bool bdone[2] = {false, false};
 };
 
 // the whole preconditioner solve of each basis runs in one thread-block cluster
@@ -1065,8 +1074,9 @@ static bool uses_cluster_solve(const lt_ctx* ctx) {
 // The bases [b0, b0 + n) of a batch as a batch of their own: per-basis arrays
 // offset by b0; shift indices (shift_off) stay global, so per-shift arrays
 // are shared; the outer-iteration counter is shared too.
-static lt::Batch sub_batch(const lt::Batch& bt, int b0, int n) {
+static lt::Batch sub_batch(const lt::Batch& bt, int b0, int n, int jslot = 0) {
   lt::Batch v = bt;
+  v.jdev = bt.jdev + jslot;
   const size_t N = (size_t)bt.N, M = (size_t)bt.maxit;
   v.nb = n;
   v.itol2 += b0; v.rmax += b0;
@@ -1136,6 +1146,23 @@ static int launch_iteration_cluster(lt_ctx* ctx, cudaStream_t q, int jj, int* nl
   return LT_OK;
 }
 
+// One outer iteration of the bases [b0, b0 + n) on the cluster-resident path with iteration counter
+// slot jslot: each half of a decoupled solve replays a graph of this on its own stream
+static int launch_half_iteration(lt_ctx* ctx, cudaStream_t q, int b0, int n, int jslot, int* nlq) {
+  const lt_opts& o = ctx->opts;
+  const lt::Batch v = sub_batch(ctx->ws.bt, b0, n, jslot);
+  lt::launch_prep_iter(v, 0, q);
+  if (lt::launch_inner_cluster(ctx->mg, cluster_plan(ctx), v, ctx->fe, ctx->ws.l0q + (size_t)b0 * ctx->N,
+                               ctx->ws.l0u ? ctx->ws.l0u + (size_t)b0 * ctx->N : nullptr, o.inner_cycles, q,
+                               nullptr))
+    return LT_ERR_CUDA;
+  lt::launch_inner_record(v, q);
+  lt::launch_arnoldi(v, ctx->fe, 0, q, nlq, nullptr);
+  lt::launch_shift_ls(v, 0, q);   // the least squares, then this half's iteration counter
+  *nlq += 5;
+  return LT_OK;
+}
+
 // one outer iteration of every active basis (kernels read j from bt.jdev)
 static int launch_iteration(lt_ctx* ctx, cudaStream_t q, int jj, int* nlq, lt::Prof* pf) {
   const lt_opts& o = ctx->opts;
@@ -1199,7 +1226,7 @@ static int learned_tables(lt_ctx* ctx) {
   return LT_OK;
 }
 
-static int solve_begin(lt_ctx* ctx, const Plan& P, SolveState& S, int* nl) {
+static int solve_begin(lt_ctx* ctx, const Plan& P, SolveState& S, int* nl, bool decouple = false) {
   const lt_opts& o = ctx->opts;
   if (o.block && !P.block)
     return fail(ctx, LT_ERR_INVALID_ARG, "block = 1 applies to lt_forward and lt_forward_fields only");
@@ -1312,6 +1339,33 @@ static int solve_begin(lt_ctx* ctx, const Plan& P, SolveState& S, int* nl) {
     S.q = ctx->cap_stream;
     CK(cudaEventRecord(ctx->ev_a, s));
     CK(cudaStreamWaitEvent(S.q, ctx->ev_a, 0));
+    // Decoupled halves: with more bases than resident clusters, the two halves of the cluster-resident
+    // path each get their own iteration counter, graph and stream, and run without a join per outer
+    // iteration (one half's solves fill the clusters while the other half orthogonalises).
+    if (decouple && uses_cluster_solve(ctx) && !bt.block && P.nb >= 2 && P.nb > cluster_plan(ctx).max_clusters) {
+      if (!ctx->cap_stream2) CK(cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking));
+      CK(cudaStreamWaitEvent(ctx->cap_stream2, ctx->ev_a, 0));
+      const int half = (P.nb + 1) / 2;
+      S.nbr = 2;
+      S.bq[0] = ctx->cap_stream;
+      S.bq[1] = ctx->cap_stream2;
+      S.bb0[0] = 0; S.bbn[0] = half;
+      S.bb0[1] = half; S.bbn[1] = P.nb - half;
+      for (int h = 0; h < 2; ++h) {
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(S.bq[h], cudaStreamCaptureModeThreadLocal));
+        const int rc2 = launch_half_iteration(ctx, S.bq[h], S.bb0[h], S.bbn[h], h, &S.bper[h]);
+        const cudaError_t ec = cudaStreamEndCapture(S.bq[h], &graph);
+        if (rc2 || ec != cudaSuccess) {
+          if (graph) cudaGraphDestroy(graph);
+          return fail(ctx, LT_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ec));
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&S.bgx[h], graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) return fail(ctx, LT_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ei));
+      }
+      return LT_OK;
+    }
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(S.q, cudaStreamCaptureModeThreadLocal));
     int rc2 = launch_iteration(ctx, S.q, 0, &S.per_iter, nullptr);
@@ -1384,7 +1438,14 @@ static int solve_end(lt_ctx* ctx, const Plan& P, SolveState& S, std::vector<doub
   lt::Prof* pf = S.pf;
   int rc = LT_OK;
   const int cycles = S.cycles;
-  if (S.use_graph) {
+  if (S.nbr) {
+    for (int h = 0; h < S.nbr; ++h) {
+      CK(cudaEventRecord(ctx->ev_b, S.bq[h]));
+      CK(cudaStreamWaitEvent(s, ctx->ev_b, 0));
+      cudaGraphExecDestroy(S.bgx[h]);
+      S.bgx[h] = nullptr;
+    }
+  } else if (S.use_graph) {
     CK(cudaEventRecord(ctx->ev_b, S.q));
     CK(cudaStreamWaitEvent(s, ctx->ev_b, 0));
     cudaGraphExecDestroy(S.gexec);
@@ -1477,8 +1538,38 @@ static int solve_end(lt_ctx* ctx, const Plan& P, SolveState& S, std::vector<doub
 static int run_solves(lt_ctx* ctx, const Plan& P, std::vector<double>& true_res, lt_stats* st, int* nl,
                       bool need_x = false) {
   SolveState S;
-  int rc = solve_begin(ctx, P, S, nl);
+  int rc = solve_begin(ctx, P, S, nl, true);
   if (rc) return rc;
+  if (S.nbr) {
+    // decoupled halves: fill both queues, then refill each half as soon as its own queue drains
+    // (only that half's stream is waited on, so the other one keeps running)
+    const lt_opts& o = ctx->opts;
+    auto enqueue = [&](int h) -> int {
+      for (int k = 0; k < o.check_every && S.bj[h] < o.maxit; ++k) {
+        if (cudaGraphLaunch(S.bgx[h], S.bq[h]) != cudaSuccess) return fail(ctx, LT_ERR_CUDA, "graph launch failed");
+        *nl += S.bper[h];
+        if (h == 0) S.cycles += o.inner_rounds * o.inner_cycles;   // (per outer iteration, as joined)
+        ++S.bj[h];
+      }
+      return LT_OK;
+    };
+    for (int h = 0; h < S.nbr; ++h)
+      if ((rc = enqueue(h))) return rc;
+    while (!(S.bdone[0] && S.bdone[1])) {
+      for (int h = 0; h < S.nbr; ++h) {
+        if (S.bdone[h]) continue;
+        CK(cudaMemcpyAsync(S.act.data() + S.bb0[h], ctx->ws.bt.active + S.bb0[h], S.bbn[h] * sizeof(int),
+                           cudaMemcpyDeviceToHost, S.bq[h]));
+        CK(cudaStreamSynchronize(S.bq[h]));
+        bool any = false;
+        for (int b = S.bb0[h]; b < S.bb0[h] + S.bbn[h]; ++b) any |= S.act[b] != 0;
+        if (!any || S.bj[h] >= o.maxit) S.bdone[h] = true;
+        else if ((rc = enqueue(h))) return rc;
+      }
+    }
+    S.j = std::max(S.bj[0], S.bj[1]);
+    S.done = true;
+  }
   while (!S.done) {
     if ((rc = solve_launch(ctx, S, ctx->opts.check_every, nl))) return rc;
     if ((rc = solve_poll(ctx, P, S))) return rc;
@@ -2355,7 +2446,7 @@ static size_t noalloc_need(const lt_ctx* ctx, const Plan& P) {
   add(nb, 8); add(nb, 4); add(nb, 4); add(nb, 8); add(nb, 8);
   add(nb + 1, 4); add(nsh, 16); add(nsh * M * M, 16); add(nsh * M, 8);
   add(nsh * M, 16); add(nsh * (M + 1), 16); add(nsh, 4); add(nsh, 8);
-  add(nsh * M, 16); add(lt::kWorkSlots, 8); add(nb, 8); add(nb, 8); add(1, 4);
+  add(nsh * M, 16); add(lt::kWorkSlots, 8); add(nb, 8); add(nb, 8); add(2, 4);
   if (ctx->mg.coarse_direct) add(2 * G * (size_t)ctx->hl.back().N * ctx->hl.back().N, 8);
   if (ctx->inner.ok || any_cluster_plan(ctx)) add(nb * N, 16);
   if (cluster_plan(ctx).u0_global) add(nb * N, 8);
