@@ -72,7 +72,7 @@ __global__ void k_init_shifts(Batch bt) {
     bt.conv_it[sh] = 0;
     bt.pres[sh] = 1.0;
   }
-  if (sh == 0) { bt.jdev[0] = 0; bt.jdev[1] = 0; }   // (slot 1: the second half's counter when the halves run decoupled)
+  if (sh < 8) bt.jdev[sh] = 0;   // (slots 1-7: the counters of the other parts when the bases run decoupled)
   if (sh < bt.nb) {
     bt.active[sh] = 1;
     bt.nit[sh] = 0;

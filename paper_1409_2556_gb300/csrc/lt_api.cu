@@ -115,7 +115,7 @@ struct lt_ctx {
   size_t arena_cap = 0, arena_off = 0;
   // non-blocking stream on which the per-iteration CUDA graph is captured and replayed
   cudaStream_t cap_stream = nullptr;
-  cudaStream_t cap_stream2 = nullptr;   // the second half's stream when the halves run decoupled
+  cudaStream_t part_stream[7] = {};     // the streams of parts 1-7 when the bases run decoupled
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   // second branch of an outer iteration whose bases are split in two (cluster-resident solves)
   cudaStream_t side_stream = nullptr;
@@ -315,7 +315,8 @@ void lt_destroy(lt_ctx* ctx) {
   if (ctx->ev_a) cudaEventDestroy(ctx->ev_a);
   if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
-  if (ctx->cap_stream2) cudaStreamDestroy(ctx->cap_stream2);
+  for (cudaStream_t& q : ctx->part_stream)
+    if (q) cudaStreamDestroy(q);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
@@ -984,7 +985,7 @@ static int ensure_ws(lt_ctx* ctx, const Plan& P) {
   AL(bt.work, lt::kWorkSlots);
   AL(bt.itol2, nb);
   AL(bt.rmax, nb);
-  AL(bt.jdev, 2);
+  AL(bt.jdev, 8);
   {
     double* w = nullptr;
     float *rh = nullptr, *rl = nullptr;
@@ -1057,13 +1058,13 @@ struct SolveState {
   cudaStream_t q = nullptr;
   lt::Prof* pf = nullptr;
   std::vector<int> act;
-  // decoupled halves (nbr = 2): bases [bb0[p], bb0[p] + bbn[p]) with their own iteration counter,
-  // graph and stream, so that one half's solves run while the other half orthogonalises
+  // decoupled parts (nbr > 0): bases [bb0[p], bb0[p] + bbn[p]) with their own iteration counter,
+  // graph and stream, so that one part's solves run while another part orthogonalises
   int nbr = 0;
-  cudaGraphExec_t bgx[2] = {nullptr, nullptr};
-  cudaStream_t bq[2] = {nullptr, nullptr};
-  int bj[2] = {0, 0}, bb0[2] = {0, 0}, bbn[2] = {0, 0}, bper[2] = {0, 0};
-  bool bdone[2] = {false, false};
+  cudaGraphExec_t bgx[8] = {};
+  cudaStream_t bq[8] = {};
+  int bj[8] = {}, bb0[8] = {}, bbn[8] = {}, bper[8] = {};
+  bool bdone[8] = {};
 };
 
 // the whole preconditioner solve of each basis runs in one thread-block cluster
@@ -1145,6 +1146,9 @@ static int launch_iteration_cluster(lt_ctx* ctx, cudaStream_t q, int jj, int* nl
   *nlq += 1;
   return LT_OK;
 }
+
+// parts of a decoupled cluster-resident solve (each its own counter slot, graph and stream; up to 8)
+constexpr int kDecoupledParts = 4;
 
 // One outer iteration of the bases [b0, b0 + n) on the cluster-resident path with iteration counter
 // slot jslot: each half of a decoupled solve replays a graph of this on its own stream
@@ -1342,16 +1346,21 @@ static int solve_begin(lt_ctx* ctx, const Plan& P, SolveState& S, int* nl, bool 
     // Decoupled halves: with more bases than resident clusters, the two halves of the cluster-resident
     // path each get their own iteration counter, graph and stream, and run without a join per outer
     // iteration (one half's solves fill the clusters while the other half orthogonalises).
-    if (decouple && uses_cluster_solve(ctx) && !bt.block && P.nb >= 2 && P.nb > cluster_plan(ctx).max_clusters) {
-      if (!ctx->cap_stream2) CK(cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking));
-      CK(cudaStreamWaitEvent(ctx->cap_stream2, ctx->ev_a, 0));
-      const int half = (P.nb + 1) / 2;
-      S.nbr = 2;
-      S.bq[0] = ctx->cap_stream;
-      S.bq[1] = ctx->cap_stream2;
-      S.bb0[0] = 0; S.bbn[0] = half;
-      S.bb0[1] = half; S.bbn[1] = P.nb - half;
-      for (int h = 0; h < 2; ++h) {
+    if (decouple && uses_cluster_solve(ctx) && !bt.block && P.nb >= kDecoupledParts &&
+        P.nb > cluster_plan(ctx).max_clusters) {
+      S.nbr = kDecoupledParts;
+      for (int h = 0; h < S.nbr; ++h) {
+        if (h == 0) {
+          S.bq[h] = ctx->cap_stream;
+        } else {
+          if (!ctx->part_stream[h - 1]) CK(cudaStreamCreateWithFlags(&ctx->part_stream[h - 1], cudaStreamNonBlocking));
+          S.bq[h] = ctx->part_stream[h - 1];
+          CK(cudaStreamWaitEvent(S.bq[h], ctx->ev_a, 0));
+        }
+        S.bb0[h] = (int)((int64_t)P.nb * h / S.nbr);
+        S.bbn[h] = (int)((int64_t)P.nb * (h + 1) / S.nbr) - S.bb0[h];
+      }
+      for (int h = 0; h < S.nbr; ++h) {
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(S.bq[h], cudaStreamCaptureModeThreadLocal));
         const int rc2 = launch_half_iteration(ctx, S.bq[h], S.bb0[h], S.bbn[h], h, &S.bper[h]);
@@ -1555,7 +1564,12 @@ static int run_solves(lt_ctx* ctx, const Plan& P, std::vector<double>& true_res,
     };
     for (int h = 0; h < S.nbr; ++h)
       if ((rc = enqueue(h))) return rc;
-    while (!(S.bdone[0] && S.bdone[1])) {
+    auto all_done = [&]() {
+      for (int h = 0; h < S.nbr; ++h)
+        if (!S.bdone[h]) return false;
+      return true;
+    };
+    while (!all_done()) {
       for (int h = 0; h < S.nbr; ++h) {
         if (S.bdone[h]) continue;
         CK(cudaMemcpyAsync(S.act.data() + S.bb0[h], ctx->ws.bt.active + S.bb0[h], S.bbn[h] * sizeof(int),
@@ -1567,7 +1581,7 @@ static int run_solves(lt_ctx* ctx, const Plan& P, std::vector<double>& true_res,
         else if ((rc = enqueue(h))) return rc;
       }
     }
-    S.j = std::max(S.bj[0], S.bj[1]);
+    for (int h = 0; h < S.nbr; ++h) S.j = std::max(S.j, S.bj[h]);
     S.done = true;
   }
   while (!S.done) {
@@ -2446,7 +2460,7 @@ static size_t noalloc_need(const lt_ctx* ctx, const Plan& P) {
   add(nb, 8); add(nb, 4); add(nb, 4); add(nb, 8); add(nb, 8);
   add(nb + 1, 4); add(nsh, 16); add(nsh * M * M, 16); add(nsh * M, 8);
   add(nsh * M, 16); add(nsh * (M + 1), 16); add(nsh, 4); add(nsh, 8);
-  add(nsh * M, 16); add(lt::kWorkSlots, 8); add(nb, 8); add(nb, 8); add(2, 4);
+  add(nsh * M, 16); add(lt::kWorkSlots, 8); add(nb, 8); add(nb, 8); add(8, 4);
   if (ctx->mg.coarse_direct) add(2 * G * (size_t)ctx->hl.back().N * ctx->hl.back().N, 8);
   if (ctx->inner.ok || any_cluster_plan(ctx)) add(nb * N, 16);
   if (cluster_plan(ctx).u0_global) add(nb * N, 8);

@@ -75,8 +75,8 @@ struct Batch {
   float2* coarse_inv;              // [ngroups*2][nc*nc] dense inverses of the coarsest operator
   int coarse_direct;               // 1 if coarse_inv is valid
   unsigned long long* work;        // [kWorkSlots] cells processed per kernel class (live roofline), flags
-  int* jdev;                       // current outer iteration (shared by all bases of the batch; [2]: a second
-                                   // counter for the second half when the halves run decoupled)
+  int* jdev;                       // current outer iteration (shared by all bases of the batch; [8]: one counter
+                                   // per part when the parts of the batch run decoupled)
   unsigned tma_polls;              // mbarrier polls of a TMA tile load before it counts as timed out
   int krylov;                      // 0: GMRES-Sh coefficients, 1: FOM-Sh (Algorithm 1)
   int stop_rule;                   // 0: per shift; 1: per output time, quadrature-weighted residual
