@@ -653,9 +653,9 @@ void launch_shift_ls_only(const Batch& bt, int j, cudaStream_t st) { k_shift_ls<
 void launch_next_iter(const Batch& bt, cudaStream_t st) { k_next_iter<<<1, 32, 0, st>>>(bt); }
 
 // y_k = R^{-1} g over the shift's converged (or final) column count
-__global__ void k_backsolve(Batch bt, const int* sh_basis) {
-  int sh = blockIdx.x * blockDim.x + threadIdx.x;
-  if (sh >= bt.nsh) return;
+__global__ void k_backsolve(Batch bt, const int* sh_basis, int s0, int s1) {
+  int sh = s0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (sh >= s1) return;
   const int M = bt.maxit;
   int m = bt.conv_it[sh] > 0 ? bt.conv_it[sh] : bt.nit[sh_basis[sh]];
   const double2* R = bt.R + (size_t)sh * M * M;
@@ -682,8 +682,10 @@ __global__ void k_backsolve(Batch bt, const int* sh_basis) {
   }
 }
 
-void launch_backsolve_map(const Batch& bt, const int* sh_basis, cudaStream_t st) {
-  k_backsolve<<<(bt.nsh + 127) / 128, 128, 0, st>>>(bt, sh_basis);
+void launch_backsolve_map(const Batch& bt, const int* sh_basis, cudaStream_t st, int s0, int s1) {
+  if (s1 < 0) s1 = bt.nsh;
+  if (s1 <= s0) return;
+  k_backsolve<<<(s1 - s0 + 127) / 128, 128, 0, st>>>(bt, sh_basis, s0, s1);
 }
 
 // ------------------------------------------------------------ quadrature (Eq. half)
@@ -895,9 +897,9 @@ void launch_xk(const Batch& bt, float2* X_hi, float2* X_lo, cudaStream_t st, Pro
 }
 
 __global__ void k_true_res(Batch bt, FineExact fe, const int* sh_basis, const float2* X_hi, const float2* X_lo,
-                           double* res2) {
+                           double* res2, int s0) {
   __shared__ float red[32];
-  int sh = blockIdx.y;
+  int sh = s0 + blockIdx.y;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   float acc[1] = {0.f};
   if (c < fe.N) {
@@ -917,10 +919,12 @@ __global__ void k_true_res(Batch bt, FineExact fe, const int* sh_basis, const fl
 }
 
 void launch_true_res(const Batch& bt, const FineExact& fe, const int* sh_basis, const float2* X_hi,
-                     const float2* X_lo, double* res2, cudaStream_t st, Prof* pf) {
-  dim3 g2((unsigned)((bt.N + 255) / 256), bt.nsh);
+                     const float2* X_lo, double* res2, cudaStream_t st, Prof* pf, int s0, int s1) {
+  if (s1 < 0) s1 = bt.nsh;
+  if (s1 <= s0) return;
+  dim3 g2((unsigned)((bt.N + 255) / 256), s1 - s0);
   prof_begin(pf, KC_TRUE_RES, st);
-  k_true_res<<<g2, 256, 0, st>>>(bt, fe, sh_basis, X_hi, X_lo, res2);
+  k_true_res<<<g2, 256, 0, st>>>(bt, fe, sh_basis, X_hi, X_lo, res2, s0);
   prof_end(pf, KC_TRUE_RES, st);
 }
 

@@ -24,10 +24,6 @@
 
 using cplx = std::complex<double>;
 
-namespace lt {
-void launch_backsolve_map(const Batch& bt, const int* sh_basis, cudaStream_t st);
-}
-
 // ------------------------------------------------------------------ contour (Sec. 2.2)
 // z(theta) = (Nz/t) (sigma + mu theta cot(alpha theta) + i nu theta), the
 // modified Talbot contour with the parameters of Trefethen, Weideman and
@@ -116,6 +112,7 @@ struct lt_ctx {
   // non-blocking stream on which the per-iteration CUDA graph is captured and replayed
   cudaStream_t cap_stream = nullptr;
   cudaStream_t part_stream[7] = {};     // the streams of parts 1-7 when the bases run decoupled
+  cudaEvent_t ev_tail = nullptr;        // end-of-solve buffers ready (decoupled parts queue their own tails)
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   // second branch of an outer iteration whose bases are split in two (cluster-resident solves)
   cudaStream_t side_stream = nullptr;
@@ -315,6 +312,7 @@ void lt_destroy(lt_ctx* ctx) {
   if (ctx->ev_a) cudaEventDestroy(ctx->ev_a);
   if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->ev_tail) cudaEventDestroy(ctx->ev_tail);
   for (cudaStream_t& q : ctx->part_stream)
     if (q) cudaStreamDestroy(q);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
@@ -1065,6 +1063,10 @@ struct SolveState {
   cudaStream_t bq[8] = {};
   int bj[8] = {}, bb0[8] = {}, bbn[8] = {}, bper[8] = {};
   bool bdone[8] = {};
+  // the end-of-solve work (y_k, x_k, true residuals) already queued part by part, as each finished
+  bool tail_done = false, tail_x = false;
+  int* d_shb = nullptr;      // [nsh] basis of each shift
+  double* d_res2 = nullptr;  // [nsh] squared true residuals
 };
 
 // the whole preconditioner solve of each basis runs in one thread-block cluster
@@ -1460,15 +1462,19 @@ static int solve_end(lt_ctx* ctx, const Plan& P, SolveState& S, std::vector<doub
     cudaGraphExecDestroy(S.gexec);
     S.gexec = nullptr;
   }
+  std::vector<void*> tmp;
+  true_res.assign(P.nsh, -1.0);
+  if (S.tail_done) {   // queued by the parts as they finished: only the true residuals to read back
+    if (o.true_residual)
+      CK(cudaMemcpyAsync(true_res.data(), S.d_res2, P.nsh * sizeof(double), cudaMemcpyDeviceToHost, s));
+  } else {
   // y per shift
   int* d_shb = nullptr;
-  std::vector<void*> tmp;
   if ((rc = scratch(ctx, kScrShb, &d_shb, P.nsh))) return rc;
   CK(cudaMemcpyAsync(d_shb, P.sh_basis.data(), P.nsh * sizeof(int), cudaMemcpyHostToDevice, s));
   if (bt.block) lt::launch_block_backsolve(bt, d_shb, s);
   else lt::launch_backsolve_map(bt, d_shb, s);
   ++*nl;
-  true_res.assign(P.nsh, -1.0);
   if (o.true_residual || need_x) {
     Workspace& ws = ctx->ws;
     size_t need = (size_t)P.nsh * ctx->N;
@@ -1490,6 +1496,7 @@ static int solve_end(lt_ctx* ctx, const Plan& P, SolveState& S, std::vector<doub
       ++*nl;
       CK(cudaMemcpyAsync(true_res.data(), d_res2, P.nsh * sizeof(double), cudaMemcpyDeviceToHost, s));
     }
+  }
   }
   // stats
   std::vector<int> nit(P.nb), conv(P.nsh);
@@ -1544,15 +1551,67 @@ static int solve_end(lt_ctx* ctx, const Plan& P, SolveState& S, std::vector<doub
   return LT_OK;
 }
 
+// The buffers of the end-of-solve work, set up on the context stream before the decoupled parts
+// finish (each part then queues its own y_k, x_k and true residuals on its stream)
+static int prepare_tail(lt_ctx* ctx, const Plan& P, SolveState& S, bool need_x) {
+  const lt_opts& o = ctx->opts;
+  Workspace& ws = ctx->ws;
+  cudaStream_t s = ctx->stream;
+  int rc = LT_OK;
+  if ((rc = scratch(ctx, kScrShb, &S.d_shb, P.nsh))) return rc;
+  CK(cudaMemcpyAsync(S.d_shb, P.sh_basis.data(), P.nsh * sizeof(int), cudaMemcpyHostToDevice, s));
+  S.tail_x = o.true_residual || need_x;
+  if (S.tail_x) {
+    const size_t need = (size_t)P.nsh * ctx->N;
+    if (ws.x_elems < need) {
+      if ((rc = dalloc(ctx, ws.allocs, &ws.X_hi, need))) return rc;
+      ws.X_lo = nullptr;
+      if (o.precision == LT_PREC_FP64 && (rc = dalloc(ctx, ws.allocs, &ws.X_lo, need))) return rc;
+      ws.x_elems = need;
+    }
+  }
+  if (o.true_residual) {
+    if ((rc = scratch(ctx, kScrRes2, &S.d_res2, P.nsh))) return rc;
+    CK(cudaMemsetAsync(S.d_res2, 0, P.nsh * sizeof(double), s));
+  }
+  if (!ctx->ev_tail) CK(cudaEventCreateWithFlags(&ctx->ev_tail, cudaEventDisableTiming));
+  CK(cudaEventRecord(ctx->ev_tail, s));
+  return LT_OK;
+}
+
+// y_k, x_k and the true residuals of part h's shifts, on its stream, once the part has finished
+static int launch_part_tail(lt_ctx* ctx, const Plan& P, SolveState& S, int h, int* nl) {
+  const lt_opts& o = ctx->opts;
+  const lt::Batch& bt = ctx->ws.bt;
+  Workspace& ws = ctx->ws;
+  cudaStream_t q = S.bq[h];
+  const int s0 = P.shift_off[S.bb0[h]], s1 = P.shift_off[S.bb0[h] + S.bbn[h]];
+  CK(cudaStreamWaitEvent(q, ctx->ev_tail, 0));
+  lt::launch_backsolve_map(bt, S.d_shb, q, s0, s1);
+  ++*nl;
+  if (S.tail_x) {
+    lt::launch_xk(sub_batch(bt, S.bb0[h], S.bbn[h], h), ws.X_hi, ws.X_lo, q, nullptr);
+    ++*nl;
+  }
+  if (o.true_residual) {
+    lt::launch_true_res(bt, ctx->fe, S.d_shb, ws.X_hi, ws.X_lo, S.d_res2, q, nullptr, s0, s1);
+    ++*nl;
+  }
+  CK(cudaGetLastError());
+  return LT_OK;
+}
+
 static int run_solves(lt_ctx* ctx, const Plan& P, std::vector<double>& true_res, lt_stats* st, int* nl,
                       bool need_x = false) {
   SolveState S;
   int rc = solve_begin(ctx, P, S, nl, true);
   if (rc) return rc;
   if (S.nbr) {
-    // decoupled halves: fill both queues, then refill each half as soon as its own queue drains
-    // (only that half's stream is waited on, so the other one keeps running)
+    // decoupled parts: fill every part's queue, then refill each part as soon as its own queue drains
+    // (only that part's stream is waited on, so the others keep running); a finished part queues its
+    // own end-of-solve work at once, next to the parts still iterating
     const lt_opts& o = ctx->opts;
+    if ((rc = prepare_tail(ctx, P, S, need_x))) return rc;
     auto enqueue = [&](int h) -> int {
       for (int k = 0; k < o.check_every && S.bj[h] < o.maxit; ++k) {
         if (cudaGraphLaunch(S.bgx[h], S.bq[h]) != cudaSuccess) return fail(ctx, LT_ERR_CUDA, "graph launch failed");
@@ -1577,12 +1636,17 @@ static int run_solves(lt_ctx* ctx, const Plan& P, std::vector<double>& true_res,
         CK(cudaStreamSynchronize(S.bq[h]));
         bool any = false;
         for (int b = S.bb0[h]; b < S.bb0[h] + S.bbn[h]; ++b) any |= S.act[b] != 0;
-        if (!any || S.bj[h] >= o.maxit) S.bdone[h] = true;
-        else if ((rc = enqueue(h))) return rc;
+        if (!any || S.bj[h] >= o.maxit) {
+          S.bdone[h] = true;
+          if ((rc = launch_part_tail(ctx, P, S, h, nl))) return rc;
+        } else if ((rc = enqueue(h))) {
+          return rc;
+        }
       }
     }
     for (int h = 0; h < S.nbr; ++h) S.j = std::max(S.j, S.bj[h]);
     S.done = true;
+    S.tail_done = true;
   }
   while (!S.done) {
     if ((rc = solve_launch(ctx, S, ctx->opts.check_every, nl))) return rc;

@@ -58,7 +58,8 @@ void launch_shift_ls(const Batch& bt, int j, cudaStream_t st);   // least square
 void launch_shift_ls_only(const Batch& bt, int j, cudaStream_t st);
 void launch_next_iter(const Batch& bt, cudaStream_t st);
 void launch_init_batch(const Batch& bt, cudaStream_t st);
-void launch_backsolve_map(const Batch& bt, const int* sh_basis, cudaStream_t st);
+// y_k for the shifts [s0, s1) (s1 < 0: every shift)
+void launch_backsolve_map(const Batch& bt, const int* sh_basis, cudaStream_t st, int s0 = 0, int s1 = -1);
 
 // quadrature-fused measurement: C[q][i] = sum_{k in item q} wq[k] Y[k][i]; h = 2 Re U[rcell] . C
 struct QuadItem {            // one (source-or-receiver, time) pair
@@ -118,8 +119,9 @@ int geostat_solve(const double* J, size_t ldj, const double* G, int ny, int N, c
                   const double* y, const double* h, double* A, double* rhs, double* z, double* beta, double* xi,
                   double* s_next, int* flag, cudaStream_t st);
 void launch_xk(const Batch& bt, float2* X_hi, float2* X_lo, cudaStream_t st, Prof* pf);
+// squared true residuals of the shifts [s0, s1) into res2 (s1 < 0: every shift)
 void launch_true_res(const Batch& bt, const FineExact& fe, const int* sh_basis, const float2* X_hi,
-                     const float2* X_lo, double* res2, cudaStream_t st, Prof* pf);
+                     const float2* X_lo, double* res2, cudaStream_t st, Prof* pf, int s0 = 0, int s1 = -1);
 // block.cu: block flexible GMRES over the sources of each group (Batch::block)
 int launch_block_iteration(const Batch& bt, const FineExact& fe, cudaStream_t st, int* nlaunch, Prof* pf);
 void launch_block_backsolve(const Batch& bt, const int* sh_basis, cudaStream_t st);
