@@ -502,6 +502,36 @@ def learned_gain(dev):
             "workload": LEARNED_WORKLOAD}
 
 
+# the network's 3x3 convolutions (c_in, c_out, level: 2^-level of the image side), as in the library
+UNET_CONVS = [(16, 16, 0), (16, 16, 0), (16, 32, 1), (32, 32, 1), (32, 32, 2), (32, 32, 2), (32, 64, 3),
+              (64, 64, 3), (96, 32, 2), (32, 32, 2), (64, 32, 1), (32, 32, 1), (48, 16, 0), (16, 16, 0),
+              (16, 16, 0)]
+UNET_MAC_PER_PIXEL = sum(9 * ci * co / 4 ** lv for ci, co, lv in UNET_CONVS)   # 30,816 per full-size pixel
+
+
+def unet_forward_timing(dev, n: int = 27, side: int = 256, steps: int = 5, warmup: int = 3):
+    """The learned preconditioner's network (tcgen05 convolutions) on n images of side x side --
+    one image per basis of the 256x256 nine-well workload -- timed with CUDA events."""
+    import torch
+    from paper_1409_2556_gb300 import learned
+    net = learned.UNet(dev, seed=1)
+    x = torch.randn(n, side, side, 5, device=f"cuda:{dev}")
+    for _ in range(warmup):
+        net.forward(x)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        net.forward(x)
+    b.record()
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / steps
+    net.close()
+    flop = 2.0 * UNET_MAC_PER_PIXEL * n * side * side
+    return {"images": n, "side": side, "ms_per_forward": ms, "mac_per_pixel": UNET_MAC_PER_PIXEL,
+            "tflops": flop / (ms * 1e-3) / 1e12}
+
+
 def block_comparison(dev, steps: int = 3, warmup: int = 2):
     """Config 2 with the sources of each time group as one block (block flexible GMRES-Sh) against
     one basis per (source, group): step time on device-resident inputs, outer iterations,
@@ -587,7 +617,7 @@ def main():
                     help="profiling only: run warmup + the timed steps, print nothing else")
     ap.add_argument("--sources", type=int, default=0,
                     help="profiling only: keep the first K wells (smaller device footprint)")
-    ap.add_argument("--only", default="", choices=["", "jacobian", "batch", "gn", "block"],
+    ap.add_argument("--only", default="", choices=["", "jacobian", "batch", "gn", "block", "learned", "unet"],
                     help="profiling only: run one extra leg (config-3 Jacobian or the config-5 batch) and print it")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -615,7 +645,9 @@ def main():
         stream = torch.cuda.Stream(device=dev)
         res = (jacobian_rows(dev, stream) if args.only == "jacobian" else
                gn_timing(dev) if args.only == "gn" else
-               block_comparison(dev) if args.only == "block" else batch_throughput(dev))
+               block_comparison(dev) if args.only == "block" else
+               learned_gain(dev) if args.only == "learned" else
+               unet_forward_timing(dev) if args.only == "unet" else batch_throughput(dev))
         print(json.dumps({"only": args.only, **res}), flush=True)
         return
     prob = workload(rank)

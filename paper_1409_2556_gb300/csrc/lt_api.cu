@@ -1330,6 +1330,8 @@ static int solve_begin(lt_ctx* ctx, const Plan& P, SolveState& S, int* nl, bool 
       ctx->xin_cap = need;
     }
     if ((rc = learned_tables(ctx))) return rc;
+    // every basis starts the solve with the network's guess switched on (int 0x01010101)
+    CK(cudaMemsetAsync(ctx->d_gn2 + 4 * (size_t)P.nb, 0x01, (size_t)P.nb * sizeof(int), s));
   }
   S = SolveState();
   S.act.assign(P.nb, 1);

@@ -3,8 +3,9 @@
 // convergent iteration and the fallback).
 //
 // Activations are NHWC bfloat16, convolutions 3x3 (padding 1) run on the
-// tensor cores with mma.sync m16n8k16 bf16 -> f32 as implicit GEMMs
-// (M = pixels, N = output channels, K = 9 taps x input channels); the
+// 5th-generation tensor cores (tcgen05.mma, bf16 operands in shared memory,
+// FP32 accumulator in tensor memory) as implicit GEMMs
+// (M = 128 pixels, N = output channels, K = 9 taps x input channels); the
 // backward-data pass is the same kernel with spatially flipped, transposed
 // weights; the weight gradient is an FP32 reduction over pixels.
 // Parameters are FP32 masters with Adam; bf16 copies feed the kernels.
@@ -49,91 +50,233 @@ constexpr int kNumLayers = 15;
 constexpr int kInChannels = 5;     // re r, im r, log kappa (normalised), Re(tau) m/D, Im(tau) m/D
 constexpr int kOutChannels = 2;
 
-// ------------------------------------------------------------------ tensor-core 3x3 convolution
-__device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+// ------------------------------------------------------------------ tensor-core 3x3 convolution (tcgen05)
+// out[img][p][co] = act(bias[co] + sum_{tap,ci} in[img][p + off(tap)][ci] * W[tap][co][ci]) as an
+// implicit GEMM on the 5th-generation tensor cores: for each of the 9 taps,
+//   D (128 pixels x cout, FP32, tensor memory) += A_tap (128 pixels x cin, bf16) * B_tap^T (cout x cin, bf16)
+// with one tcgen05.mma (M = 128, N = cout, K = 16) per 16 input channels, issued by one thread.
+// Both operands sit in shared memory in the canonical K-major layout without swizzle: "core
+// matrices" of 8 rows x 16 bytes (8 bf16), 128 contiguous bytes each; a matrix descriptor gives
+// the byte step between core matrices along K (leading byte offset, LBO) and between groups of 8
+// rows (stride byte offset, SBO), so the 8-row groups need not be adjacent.
+// Epilogue: warp w reads tensor-memory lanes 32w..32w+31 with tcgen05.ld, adds the bias, applies
+// the ReLU and stores bf16 or FP32 rows of 8 channels.
+// Every mbarrier wait is bounded: a wait that runs out raises *flag, then waits (again bounded)
+// for the MMAs in flight before the block frees its tensor memory and returns.
+// in: [nimg][H][W][cin], W: [9][cout][cin]; cin, cout multiples of 16, cin <= 96, cout <= 96.
+constexpr int kTcPix = 128;                   // MMA M = tensor-memory lanes = threads per CTA
+constexpr unsigned kTcPolls = 1u << 22;       // mbarrier polls before a wait counts as timed out
+constexpr unsigned kTcDrain = 1u << 24;       // further polls for the MMAs in flight after a timeout
 
-__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t pack_bf2(float lo, float hi) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// out[img][p][co] = act(bias[co] + sum_{tap,ci} in[img][p + off(tap)][ci] * W[tap][co][ci])
-// in: [nimg][H][W][cin] (cin % 16 == 0), W: [9][cout][cin], cout % 8 == 0, cout <= 64.
-// One warp = 16 consecutive pixels x all output channels; 4 warps per CTA.
-template <int NT>   // number of 8-wide output-channel tiles (cout / 8)
-__global__ void __launch_bounds__(128) k_conv3x3(const bf16* __restrict__ in, const bf16* __restrict__ Wt,
-                                                 const float* __restrict__ bias, bf16* out_bf, float* out_f,
-                                                 int H, int Wd, int cin, int relu) {
+__device__ __forceinline__ bool tc_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
+
+// bounded wait for the phase of the given parity; all threads take it, none branches on the outcome
+__device__ __forceinline__ void tc_wait(uint32_t bar, uint32_t parity, unsigned long long* flag) {
+  for (unsigned it = 0; it < kTcPolls; ++it)
+    if (tc_try_wait(bar, parity)) return;
+  if (flag) atomicAdd(flag, 1ull);
+  for (unsigned it = 0; it < kTcDrain; ++it)
+    if (tc_try_wait(bar, parity)) return;
+}
+
+// shared-memory matrix descriptor: start address, LBO, SBO (all >> 4), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both K-major, N x M = n x 128
+__device__ __forceinline__ uint32_t tc_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcPix >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// A CTA computes an output tile of 16 image rows x 8 MB columns as MB "M-blocks" of 16 rows x 8
+// columns (128 pixels = the MMA's M; a group of 8 rows of the MMA is one image row of the block).
+// It stages the tile's halo -- 18 rows x (8 MB + 2) positions, zero outside the image -- once, one
+// 16-byte chunk of 8 channels per cp.async, as [cin/8 planes][18][8 MB + 2][8 channels]; the A
+// operand of tap (dy, dx) for M-block mb is then the same halo seen through a shifted descriptor:
+//   start = plane 0 + ((dy + 1)(8 MB + 2) + 8 mb + dx + 1) x 16 B, SBO = (8 MB + 2) x 16 B (the
+//   halo row), LBO = one plane (the next 8 channels)
+// so all 9 taps x cin / 16 MMAs of every M-block are issued back to back after one barrier.  The
+// weights of all taps are staged in the same way: B per tap [cin/8][cout/8][8][8], LBO = 16 cout,
+// SBO = 128.  M-block mb accumulates in tensor-memory columns [mb cout, (mb + 1) cout).
+__host__ __device__ constexpr int tc_mb(int cout) { return cout <= 32 ? 4 : cout <= 64 ? 2 : 1; }
+__host__ __device__ constexpr int tc_hc(int mb) { return 8 * mb + 2; }                 // halo positions per row
+__host__ __device__ constexpr size_t tc_plane(int mb) { return (size_t)18 * tc_hc(mb) * 16; }
+// shared memory: [0, 8) mbarrier, [16, 20) tensor-memory address, halo from 128, then B
+__host__ __device__ constexpr size_t tc_halo_bytes(int cin, int cout) { return (size_t)(cin / 8) * tc_plane(tc_mb(cout)); }
+__host__ __device__ constexpr size_t tc_smem_bytes(int cin, int cout) {
+  return 128 + tc_halo_bytes(cin, cout) + (size_t)9 * cout * cin * 2;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+__global__ void __launch_bounds__(kTcPix, 1) k_conv3x3_tc(const bf16* __restrict__ in, const bf16* __restrict__ Wt,
+                                                          const float* __restrict__ bias, bf16* out_bf, float* out_f,
+                                                          int H, int Wd, int cin, int cout, int relu, int tcols,
+                                                          const int* img_on, unsigned long long* flag) {
+  if (img_on && !img_on[blockIdx.y]) return;   // image not needed (uniform per CTA, before any allocation)
+  extern __shared__ __align__(1024) uint8_t tsm[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tsm);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tsm + 16);
+  const int MB = tc_mb(cout), HC = tc_hc(MB);
+  const uint32_t plane = (uint32_t)tc_plane(MB);
+  uint8_t* halo = tsm + 128;
+  uint8_t* Bs = halo + (size_t)(cin >> 3) * plane;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int img = blockIdx.y;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, tg = lane & 3;
-  const int HW = H * Wd;
-  const int p0 = (blockIdx.x * 4 + warp) * 16;
-  if (p0 >= HW) return;
-  const int cout = NT * 8;
-  const bf16* inb = in + (size_t)img * HW * cin;
-  float acc[NT][4];
+  const int tiles_x = (Wd + 8 * MB - 1) / (8 * MB);
+  const int ty0 = (blockIdx.x / tiles_x) * 16, tx0 = (blockIdx.x % tiles_x) * (8 * MB);
+  const int c8n = cin >> 3;
+  const bf16* inb = in + (size_t)img * H * Wd * cin;
+
+  if (warp == 0) {   // tensor memory for the FP32 accumulators: tcols >= MB cout columns x 128 lanes
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(tcols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // weights: 16-byte chunk q = (tap, co, c8) -> core matrix (c8, co / 8), row co % 8 of the tap's B
+  const int nb16 = 9 * cout * c8n;
+  for (int q = tid; q < nb16; q += kTcPix) {
+    const int c8 = q % c8n, co = (q / c8n) % cout, tap = q / (c8n * cout);
+    cp_async16(su32(Bs + (size_t)tap * cout * cin * 2 + ((size_t)c8 * (cout >> 3) + (co >> 3)) * 128 + (co & 7) * 16),
+               Wt + ((size_t)tap * cout + co) * cin + c8 * 8, 16u);
+  }
+  // halo: chunk q = (position, c8), consecutive threads read consecutive 16-byte chunks of a row
+  const int nh16 = 18 * HC * c8n;
+  for (int q = tid; q < nh16; q += kTcPix) {
+    const int c8 = q % c8n, pos = q / c8n;
+    const int yy = ty0 - 1 + pos / HC, xx = tx0 - 1 + pos % HC;
+    const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < Wd;
+    const bf16* src = inb + (ok ? ((size_t)yy * Wd + xx) * cin + c8 * 8 : 0);
+    cp_async16(su32(halo + (size_t)c8 * plane + (size_t)pos * 16), src, ok ? 16u : 0u);   // 0 bytes read: zeros
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy writes -> tensor-core reads
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  if (tid == 0) {
+    const uint32_t idesc = tc_idesc(cout);
+    const uint32_t h0 = su32(halo), b0 = su32(Bs), b_lbo = (uint32_t)cout * 16, sbo = (uint32_t)HC * 16;
+    for (int mb = 0; mb < MB; ++mb)
+      for (int tap = 0; tap < 9; ++tap) {
+        const uint32_t a_tap = h0 + (uint32_t)(((tap / 3) * HC + 8 * mb + tap % 3) * 16);
+        const uint32_t b_tap = b0 + (uint32_t)(tap * cout * cin * 2);
+        for (int kk = 0; kk < (cin >> 4); ++kk)
+          tc_mma(tmem + (uint32_t)(mb * cout), tc_sdesc(a_tap + kk * 2 * plane, plane, sbo),
+                 tc_sdesc(b_tap + kk * 2 * b_lbo, b_lbo, 128), idesc, (tap | kk) ? 1u : 0u);
+      }
+    tc_commit(su32(bar));
+  }
+  tc_wait(su32(bar), 0u, flag);
+  tc_fence_after();
+  // lane 32 warp + l of M-block mb = row g = (32 warp + l) / 8, column j = l % 8 of the block
+  const int r = warp * 32 + (tid & 31);
+  const int y = ty0 + (r >> 3);
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  for (int mb = 0; mb < MB; ++mb) {
+    const int x = tx0 + 8 * mb + (r & 7);
+    const bool st = y < H && x < Wd;
+    for (int c0 = 0; c0 < cout; c0 += 8) {
+      float v[8];
+      tc_ld8(trow + (uint32_t)(mb * cout + c0), v);
 #pragma unroll
-  for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-  const int pa = p0 + g, pb = p0 + g + 8;
-  const int ya = pa / Wd, xa = pa % Wd, yb = pb / Wd, xb = pb % Wd;
-  for (int tap = 0; tap < 9; ++tap) {
-    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-    const int yya = ya + dy, xxa = xa + dx, yyb = yb + dy, xxb = xb + dx;
-    const bool va = pa < HW && yya >= 0 && yya < H && xxa >= 0 && xxa < Wd;
-    const bool vb = pb < HW && yyb >= 0 && yyb < H && xxb >= 0 && xxb < Wd;
-    const bf16* ra = inb + (size_t)(yya * Wd + xxa) * cin;
-    const bf16* rb = inb + (size_t)(yyb * Wd + xxb) * cin;
-    const bf16* wt = Wt + (size_t)tap * cout * cin;
-    for (int c0 = 0; c0 < cin; c0 += 16) {
-      uint32_t a[4];
-      a[0] = va ? ld32(ra + c0 + tg * 2) : 0u;
-      a[1] = vb ? ld32(rb + c0 + tg * 2) : 0u;
-      a[2] = va ? ld32(ra + c0 + 8 + tg * 2) : 0u;
-      a[3] = vb ? ld32(rb + c0 + 8 + tg * 2) : 0u;
-#pragma unroll
-      for (int n = 0; n < NT; ++n) {
-        const bf16* wr = wt + (size_t)(n * 8 + g) * cin + c0;
-        uint32_t b[2] = {ld32(wr + tg * 2), ld32(wr + 8 + tg * 2)};
-        mma_bf16(acc[n], a, b);
+      for (int q = 0; q < 8; ++q) {
+        v[q] += bias ? bias[c0 + q] : 0.f;
+        if (relu) v[q] = fmaxf(v[q], 0.f);
+      }
+      if (st) {
+        const size_t o = (((size_t)img * H + y) * Wd + x) * cout + c0;
+        if (out_bf) {
+          uint4 w;
+          w.x = pack_bf2(v[0], v[1]); w.y = pack_bf2(v[2], v[3]); w.z = pack_bf2(v[4], v[5]); w.w = pack_bf2(v[6], v[7]);
+          *reinterpret_cast<uint4*>(out_bf + o) = w;
+        }
+        if (out_f) {
+          *reinterpret_cast<float4*>(out_f + o) = make_float4(v[0], v[1], v[2], v[3]);
+          *reinterpret_cast<float4*>(out_f + o + 4) = make_float4(v[4], v[5], v[6], v[7]);
+        }
       }
     }
   }
-#pragma unroll
-  for (int n = 0; n < NT; ++n) {
-    const int co = n * 8 + tg * 2;
-    float b0 = bias ? bias[co] : 0.f, b1 = bias ? bias[co + 1] : 0.f;
-    float v[4] = {acc[n][0] + b0, acc[n][1] + b1, acc[n][2] + b0, acc[n][3] + b1};
-    if (relu)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) v[q] = fmaxf(v[q], 0.f);
-    if (pa < HW) {
-      size_t o = ((size_t)img * HW + pa) * cout + co;
-      if (out_bf) { out_bf[o] = __float2bfloat16(v[0]); out_bf[o + 1] = __float2bfloat16(v[1]); }
-      if (out_f) { out_f[o] = v[0]; out_f[o + 1] = v[1]; }
-    }
-    if (pb < HW) {
-      size_t o = ((size_t)img * HW + pb) * cout + co;
-      if (out_bf) { out_bf[o] = __float2bfloat16(v[2]); out_bf[o + 1] = __float2bfloat16(v[3]); }
-      if (out_f) { out_f[o] = v[2]; out_f[o + 1] = v[3]; }
-    }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
   }
 }
 
+// tensor-memory columns of a CTA and the shared memory it requests: every CTA asks for more than
+// its share (cols / 512) of an SM's 228 KB, so the CTAs that fit on an SM together -- of this
+// launch or of concurrent ones -- never hold more than its 512 columns, and an allocation never waits
+static int tc_cols(int cout) {
+  const int n = tc_mb(cout) * cout;
+  return n <= 32 ? 32 : n <= 64 ? 64 : 128;
+}
+static size_t tc_launch_smem(int cin, int cout) {
+  const size_t need = tc_smem_bytes(cin, cout);
+  const size_t floor = (size_t)(228 * 1024) * (size_t)tc_cols(cout) / 512 + 1024;
+  return need > floor ? need : floor;
+}
+constexpr size_t kTcSmemMax = 200 * 1024;   // above every layer's request (largest: 96 -> 32, 173 KB)
+
 static void conv3x3(const bf16* in, const bf16* Wt, const float* bias, bf16* out_bf, float* out_f, int nimg, int H,
-                    int Wd, int cin, int cout, int relu, cudaStream_t st) {
-  dim3 g((H * Wd + 63) / 64, nimg);
-  switch (cout / 8) {
-    case 2: k_conv3x3<2><<<g, 128, 0, st>>>(in, Wt, bias, out_bf, out_f, H, Wd, cin, relu); break;
-    case 4: k_conv3x3<4><<<g, 128, 0, st>>>(in, Wt, bias, out_bf, out_f, H, Wd, cin, relu); break;
-    case 6: k_conv3x3<6><<<g, 128, 0, st>>>(in, Wt, bias, out_bf, out_f, H, Wd, cin, relu); break;
-    case 8: k_conv3x3<8><<<g, 128, 0, st>>>(in, Wt, bias, out_bf, out_f, H, Wd, cin, relu); break;
-    case 12: k_conv3x3<12><<<g, 128, 0, st>>>(in, Wt, bias, out_bf, out_f, H, Wd, cin, relu); break;
-    default: break;
+                    int Wd, int cin, int cout, int relu, const int* img_on, unsigned long long* flag,
+                    cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_conv3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
+    attr = true;
   }
+  const int mb = tc_mb(cout);
+  dim3 g((unsigned)(((H + 15) / 16) * ((Wd + 8 * mb - 1) / (8 * mb))), nimg);
+  k_conv3x3_tc<<<g, kTcPix, tc_launch_smem(cin, cout), st>>>(in, Wt, bias, out_bf, out_f, H, Wd, cin, cout, relu,
+                                                            tc_cols(cout), img_on, flag);
 }
 
 // dW[tap][co][ci] += sum_p gout[p][co] * in[p + off(tap)][ci]; db[co] += sum_p gout[p][co]   (FP32)
@@ -173,20 +316,25 @@ __global__ void k_flip_weights(const bf16* W, bf16* Wf, int cin, int cout) {
 }
 
 // ------------------------------------------------------------------ elementwise helpers (NHWC)
-__global__ void k_pool2(const bf16* in, bf16* out, int H, int Wd, int C, int nimg) {
-  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+// The forward elementwise kernels run on a grid (blocks, nimg) with image blockIdx.y and a
+// grid-stride loop over its elements, so an image the solver does not need costs a few CTAs.
+__global__ void k_pool2(const bf16* in, bf16* out, int H, int Wd, int C, const int* on) {
+  const int img = blockIdx.y;
+  if (on && !on[img]) return;
   const int h = H / 2, w = Wd / 2;
-  size_t n = (size_t)nimg * h * w * C;
-  if (idx >= n) return;
-  int c = idx % C;
-  size_t pix = idx / C;
-  int x = pix % w, y = (pix / w) % h, img = pix / ((size_t)w * h);
+  const size_t n = (size_t)h * w * C;
   const bf16* b = in + (size_t)img * H * Wd * C;
-  float s = __bfloat162float(b[((size_t)(2 * y) * Wd + 2 * x) * C + c]) +
-            __bfloat162float(b[((size_t)(2 * y) * Wd + 2 * x + 1) * C + c]) +
-            __bfloat162float(b[((size_t)(2 * y + 1) * Wd + 2 * x) * C + c]) +
-            __bfloat162float(b[((size_t)(2 * y + 1) * Wd + 2 * x + 1) * C + c]);
-  out[idx] = __float2bfloat16(0.25f * s);
+  bf16* o = out + (size_t)img * n;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int c = idx % C;
+    const size_t pix = idx / C;
+    const int x = pix % w, y = pix / w;
+    float s = __bfloat162float(b[((size_t)(2 * y) * Wd + 2 * x) * C + c]) +
+              __bfloat162float(b[((size_t)(2 * y) * Wd + 2 * x + 1) * C + c]) +
+              __bfloat162float(b[((size_t)(2 * y + 1) * Wd + 2 * x) * C + c]) +
+              __bfloat162float(b[((size_t)(2 * y + 1) * Wd + 2 * x + 1) * C + c]);
+    o[idx] = __float2bfloat16(0.25f * s);
+  }
 }
 
 // gin (fine, FP32 accumulate) += 0.25 * gout (coarse)
@@ -201,16 +349,20 @@ __global__ void k_pool2_bwd(const float* gout, float* gin, int H, int Wd, int C,
 }
 
 // out[:, :, :, 0:C1] = up2(a) (coarse a, nearest), out[..., C1:C1+C2] = b
-__global__ void k_up_cat(const bf16* a, const bf16* b, bf16* out, int H, int Wd, int C1, int C2, int nimg) {
-  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_up_cat(const bf16* a, const bf16* b, bf16* out, int H, int Wd, int C1, int C2, const int* on) {
+  const int img = blockIdx.y;
+  if (on && !on[img]) return;
   const int C = C1 + C2;
-  size_t n = (size_t)nimg * H * Wd * C;
-  if (idx >= n) return;
-  int c = idx % C;
-  size_t pix = idx / C;
-  int x = pix % Wd, y = (pix / Wd) % H, img = pix / ((size_t)Wd * H);
-  if (c < C1) out[idx] = a[(((size_t)img * (H / 2) + y / 2) * (Wd / 2) + x / 2) * C1 + c];
-  else out[idx] = b[pix * C2 + (c - C1)];
+  const size_t n = (size_t)H * Wd * C;
+  const bf16* ai = a + (size_t)img * (H / 2) * (Wd / 2) * C1;
+  const bf16* bi = b + (size_t)img * H * Wd * C2;
+  bf16* o = out + (size_t)img * n;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int c = idx % C;
+    const size_t pix = idx / C;
+    const int x = pix % Wd, y = pix / Wd;
+    o[idx] = c < C1 ? ai[((size_t)(y / 2) * (Wd / 2) + x / 2) * C1 + c] : bi[pix * C2 + (c - C1)];
+  }
 }
 
 // split gradient of the concat: ga (coarse, FP32 +=) gets the up-sampled part summed, gb (fine, FP32 +=)
@@ -242,12 +394,16 @@ __global__ void k_to_f32(const float* in_dummy, const bf16* in, float* out, size
 }
 
 // FP32 [nimg][HW][5] -> bf16 [nimg][HW][16] (zero padded)
-__global__ void k_pack_input(const float* in, bf16* x, size_t npix) {
-  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= npix * 16) return;
-  int c = idx % 16;
-  size_t p = idx / 16;
-  x[idx] = __float2bfloat16(c < kInChannels ? in[p * kInChannels + c] : 0.f);
+__global__ void k_pack_input(const float* in, bf16* x, size_t hw, const int* on) {
+  const int img = blockIdx.y;
+  if (on && !on[img]) return;
+  const float* ii = in + (size_t)img * hw * kInChannels;
+  bf16* o = x + (size_t)img * hw * 16;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < hw * 16; idx += (size_t)gridDim.x * blockDim.x) {
+    const int c = idx % 16;
+    const size_t p = idx / 16;
+    o[idx] = __float2bfloat16(c < kInChannels ? ii[p * kInChannels + c] : 0.f);
+  }
 }
 
 // loss = mean over pixels and the 2 used channels of (out - target)^2; grad (FP32, [npix][16]) = d loss / d out
@@ -313,6 +469,11 @@ struct lt_unet {
   float* outf = nullptr;
   float* gout = nullptr;
   double* dloss = nullptr;
+  // error flag of the bounded tensor-core waits: own counter, or the solver's while it runs the network
+  unsigned long long* dflag = nullptr;
+  unsigned long long* flag = nullptr;
+  // images the network runs on (nullptr: all); set by the solver for the bases that still use the guess
+  const int* img_on = nullptr;
 };
 
 static size_t unet_npix(int nimg, int H, int W, int lvl) { return (size_t)nimg * (H >> lvl) * (W >> lvl); }
@@ -327,6 +488,18 @@ static const int kSlotC[NSLOT] = {16, 16, 16, 16, 32, 32, 32, 32, 32, 32, 64, 64
 static int unet_fail(lt_unet* u, int code, const char* msg) {
   if (u) u->err = msg;
   return code;
+}
+
+// wait for the network's stream; a bounded tensor-core wait that ran out is reported as -5 (timeout)
+static int unet_sync(lt_unet* u, const char* what) {
+  if (cudaStreamSynchronize(u->stream) != cudaSuccess) return unet_fail(u, -3, what);
+  unsigned long long f = 0;
+  if (cudaMemcpy(&f, u->dflag, sizeof(f), cudaMemcpyDeviceToHost) != cudaSuccess) return unet_fail(u, -3, what);
+  if (f) {
+    cudaMemset(u->dflag, 0, sizeof(f));
+    return unet_fail(u, -5, "a bounded wait of the tensor-core convolution ran out");
+  }
+  return 0;
 }
 
 static int unet_ensure(lt_unet* u, int nimg, int H, int W) {
@@ -359,6 +532,11 @@ static const int kLOut[15] = {A1, S0, A3, S1, A5, S2, A7, BB, A9, D2, A11, D1, A
 static const int kLLvl[15] = {0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0, 0};
 
 static inline unsigned nblk(size_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+// grid of a per-image elementwise kernel: at most 512 grid-stride blocks per image (blockIdx.y = image)
+static dim3 per_img(size_t n_per_image, int nimg) {
+  const unsigned b = nblk(n_per_image);
+  return dim3(b < 512u ? b : 512u, (unsigned)nimg);
+}
 
 static void unet_forward_dev(lt_unet* u, int nimg, int H, int W) {
   cudaStream_t st = u->stream;
@@ -367,17 +545,20 @@ static void unet_forward_dev(lt_unet* u, int nimg, int H, int W) {
     int h = H >> kLLvl[l], w = W >> kLLvl[l];
     bf16* out = kLOut[l] >= 0 ? u->A[kLOut[l]] : nullptr;
     float* outf = kLOut[l] >= 0 ? nullptr : u->outf;
-    lt::conv3x3(u->A[kLIn[l]], u->wb + u->woff[l], u->w + u->boff[l], out, outf, nimg, h, w, c.cin, c.cout, c.relu, st);
+    lt::conv3x3(u->A[kLIn[l]], u->wb + u->woff[l], u->w + u->boff[l], out, outf, nimg, h, w, c.cin, c.cout, c.relu,
+                u->img_on, u->flag, st);
   };
   auto pool = [&](int src, int dst) {
     int lv = kSlotLvl[src];
     size_t n = unet_npix(nimg, H, W, lv + 1) * kSlotC[src];
-    lt::k_pool2<<<nblk(n), 256, 0, st>>>(u->A[src], u->A[dst], H >> lv, W >> lv, kSlotC[src], nimg);
+    lt::k_pool2<<<per_img(n / nimg, nimg), 256, 0, st>>>(u->A[src], u->A[dst], H >> lv, W >> lv, kSlotC[src],
+                                                        u->img_on);
   };
   auto upcat = [&](int a, int b, int dst) {
     int lv = kSlotLvl[dst];
     size_t n = unet_npix(nimg, H, W, lv) * kSlotC[dst];
-    lt::k_up_cat<<<nblk(n), 256, 0, st>>>(u->A[a], u->A[b], u->A[dst], H >> lv, W >> lv, kSlotC[a], kSlotC[b], nimg);
+    lt::k_up_cat<<<per_img(n / nimg, nimg), 256, 0, st>>>(u->A[a], u->A[b], u->A[dst], H >> lv, W >> lv, kSlotC[a],
+                                                         kSlotC[b], u->img_on);
   };
   conv(0); conv(1); pool(S0, P0);
   conv(2); conv(3); pool(S1, P1);
@@ -407,7 +588,8 @@ static void unet_backward_dev(lt_unet* u, int nimg, int H, int W) {
     lt::k_conv_wgrad<<<gw, 256, 0, st>>>(u->A[kLIn[l]], u->gbf, u->g + u->woff[l], u->g + u->boff[l], h, w, c.cin,
                                         c.cout, chunk);
     if (l > 0)   // backward data: conv with flipped, transposed weights, FP32 output
-      lt::conv3x3(u->gbf, u->wflip + u->woff[l], nullptr, nullptr, u->G[kLIn[l]], nimg, h, w, c.cout, c.cin, 0, st);
+      lt::conv3x3(u->gbf, u->wflip + u->woff[l], nullptr, nullptr, u->G[kLIn[l]], nimg, h, w, c.cout, c.cin, 0,
+                  nullptr, u->flag, st);
   };
   auto upcat_bwd = [&](int a, int b, int dst) {
     int lv = kSlotLvl[dst];
@@ -457,8 +639,7 @@ static int unet_prepare(lt_unet* u, int nimg, int H, int W, const float* in) {
   if (!in) return unet_fail(u, -1, "input is null");
   cudaSetDevice(u->device);
   if (unet_ensure(u, nimg, H, W)) return unet_fail(u, -2, "device allocation failed");
-  size_t npix = unet_npix(nimg, H, W, 0);
-  lt::k_pack_input<<<nblk(npix * 16), 256, 0, u->stream>>>(in, u->A[X0], npix);
+  lt::k_pack_input<<<per_img((size_t)H * W * 16, nimg), 256, 0, u->stream>>>(in, u->A[X0], (size_t)H * W, nullptr);
   return 0;
 }
 
@@ -474,7 +655,7 @@ static int unet_loss_grad(lt_unet* u, int nimg, int H, int W, const float* in, c
   unet_backward_dev(u, nimg, H, W);
   double l = 0.0;
   cudaMemcpyAsync(&l, u->dloss, sizeof(double), cudaMemcpyDeviceToHost, u->stream);
-  if (cudaStreamSynchronize(u->stream) != cudaSuccess) return unet_fail(u, -3, "CUDA error in the network step");
+  if ((rc = unet_sync(u, "CUDA error in the network step"))) return rc;
   if (loss) *loss = l * scale;
   return 0;
 }
@@ -516,11 +697,14 @@ int lt_unet_create(lt_unet** out, int device, unsigned long long seed) {
   bool ok = cudaMalloc(&u->w, off * 4) == cudaSuccess && cudaMalloc(&u->g, off * 4) == cudaSuccess &&
             cudaMalloc(&u->m, off * 4) == cudaSuccess && cudaMalloc(&u->v, off * 4) == cudaSuccess &&
             cudaMalloc(&u->wb, off * 2) == cudaSuccess && cudaMalloc(&u->wflip, off * 2) == cudaSuccess &&
-            cudaMalloc(&u->dloss, sizeof(double)) == cudaSuccess;
+            cudaMalloc(&u->dloss, sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&u->dflag, sizeof(unsigned long long)) == cudaSuccess;
   if (!ok) { delete u; return -2; }
   cudaMemcpy(u->w, w.data(), off * 4, cudaMemcpyHostToDevice);
   cudaMemset(u->m, 0, off * 4);
   cudaMemset(u->v, 0, off * 4);
+  cudaMemset(u->dflag, 0, sizeof(unsigned long long));
+  u->flag = u->dflag;
   unet_refresh_bf16(u);
   if (cudaStreamSynchronize(u->stream) != cudaSuccess) { delete u; return -3; }
   *out = u;
@@ -550,7 +734,7 @@ int lt_unet_forward(lt_unet* u, int nimg, int H, int W, const float* in, float* 
   unet_forward_dev(u, nimg, H, W);
   size_t npix = unet_npix(nimg, H, W, 0);
   k_take2<<<nblk(npix * 2), 256, 0, u->stream>>>(u->outf, out, npix);
-  return cudaStreamSynchronize(u->stream) == cudaSuccess ? 0 : unet_fail(u, -3, "CUDA error in forward");
+  return unet_sync(u, "CUDA error in forward");
 }
 
 int lt_unet_grad(lt_unet* u, int nimg, int H, int W, const float* in, const float* target, float* grad_host,
@@ -586,7 +770,8 @@ void lt_unet_destroy(lt_unet* u) {
   if (!u) return;
   cudaSetDevice(u->device);
   for (void* p : u->acts) cudaFree(p);
-  for (void* p : {(void*)u->w, (void*)u->g, (void*)u->m, (void*)u->v, (void*)u->wb, (void*)u->wflip, (void*)u->dloss})
+  for (void* p : {(void*)u->w, (void*)u->g, (void*)u->m, (void*)u->v, (void*)u->wb, (void*)u->wflip, (void*)u->dloss,
+                  (void*)u->dflag})
     if (p) cudaFree(p);
   cudaGetLastError();
   delete u;
@@ -602,11 +787,18 @@ __device__ __forceinline__ bool lg_skip(const Batch& bt, int b, int round) {
   return bt.rnorm2[b * (bt.rounds + 1) + round] <= bt.itol2[b];
 }
 
-// network input from the round's float32 residual f0 = L0.f
-__global__ void k_net_pack(Batch bt, Level L0, int round, const float* lk, const float* mD, float* x) {
+// Gate of the learned guess per basis (int on[nb], int run[nb] after the four accumulators of each
+// basis): on[b] starts at 1 for every solve and drops to 0 for good once the basis's guess is
+// rejected; the network runs this round on the bases with run[b] = on[b] and an open solve.
+__device__ __forceinline__ int* gate_on(float* gn, int nb) { return reinterpret_cast<int*>(gn + 4 * nb); }
+
+// network input from the round's float32 residual f0 = L0.f; run[b] for the network's kernels
+__global__ void k_net_pack(Batch bt, Level L0, int round, const float* lk, const float* mD, float* x, float* gn) {
   int b = blockIdx.y;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= L0.N) return;
+  const bool run = gate_on(gn, bt.nb)[b] && !lg_skip(bt, b, round);
+  if (c == 0) gate_on(gn, bt.nb)[bt.nb + b] = run ? 1 : 0;
+  if (c >= L0.N || !run) return;
   double rn = bt.rnorm2[b * (bt.rounds + 1) + round];
   float s = (float)sqrt(rn / (double)L0.N);
   float inv = s > 0.f ? 1.f / s : 0.f;
@@ -627,6 +819,10 @@ __global__ void k_net_unpack(Batch bt, Level L0, int round, const float* outf, f
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L0.N) return;
   if (c < 4) gn[b * 4 + c] = 0.f;
+  if (!gate_on(gn, bt.nb)[b]) {   // guess switched off: the V-cycles start from zero
+    L0.u[(size_t)b * L0.N + c] = make_float2(0.f, 0.f);
+    return;
+  }
   const float* o = outf + ((size_t)b * L0.N + c) * 16;
   float Dc = L0.D[c];
   L0.u[(size_t)b * L0.N + c] = make_float2(o[0] / Dc, o[1] / Dc);
@@ -669,8 +865,9 @@ __global__ void k_net_dots(Batch bt, Level L0, int round, float* gn) {
 
 // u0 = alpha w with the minimal-residual alpha = a / q; the residual is then
 // ||f||^2 - |a|^2 / q <= ||f||^2, and a guess that removes less than 5% of the
-// residual norm is dropped in favour of the zero guess (multigrid fallback)
-__global__ void k_net_scale(Batch bt, Level L0, int round, const float* gn) {
+// residual norm is dropped in favour of the zero guess (multigrid fallback); the
+// basis then solves without the network for the rest of the solve
+__global__ void k_net_scale(Batch bt, Level L0, int round, float* gn) {
   int b = blockIdx.y;
   if (lg_skip(bt, b, round)) return;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -682,7 +879,11 @@ __global__ void k_net_scale(Batch bt, Level L0, int round, const float* gn) {
   float2 w = L0.u[(size_t)b * L0.N + c];
   float2 a = keep ? make_float2(ar / q, ai / q) : make_float2(0.f, 0.f);
   L0.u[(size_t)b * L0.N + c] = make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
-  if (c == 0 && keep) atomicAdd(&bt.work[KC_OTHER], 1ull);   // guesses kept (statistics)
+  if (c == 0) {   // the only thread of this launch that touches the gate
+    int* on = gate_on(gn, bt.nb);
+    if (keep && on[b]) atomicAdd(&bt.work[KC_OTHER], 1ull);   // guesses kept (statistics)
+    if (!keep) on[b] = 0;
+  }
 }
 
 // ---- training pairs (residual r, multigrid solution e of (K + tau M) e = r) -> (input, target)
@@ -746,13 +947,18 @@ void learned_guess(lt_unet* u, const lt::Batch& bt, const lt::Level& L0, int rou
                    float* xin, float* gnorm2, cudaStream_t q) {
   const int nb = bt.nb;
   dim3 g((L0.N + 255) / 256, nb);
-  lt::k_net_pack<<<g, 256, 0, q>>>(bt, L0, round, lk, mD, xin);
+  lt::k_net_pack<<<g, 256, 0, q>>>(bt, L0, round, lk, mD, xin, gnorm2);
   cudaStream_t saved = u->stream;
+  unsigned long long* saved_flag = u->flag;
+  const int* run = reinterpret_cast<const int*>(gnorm2 + 4 * nb) + nb;
   u->stream = q;
-  size_t npix = (size_t)nb * L0.N;
-  lt::k_pack_input<<<nblk(npix * 16), 256, 0, q>>>(xin, u->A[X0], npix);
+  u->flag = bt.work + lt::kTimeoutSlot;   // a timed-out wait is reported with the solve's status
+  u->img_on = run;
+  lt::k_pack_input<<<per_img((size_t)L0.N * 16, nb), 256, 0, q>>>(xin, u->A[X0], (size_t)L0.N, run);
   unet_forward_dev(u, nb, L0.ny, L0.nx);
   u->stream = saved;
+  u->flag = saved_flag;
+  u->img_on = nullptr;
   lt::k_net_unpack<<<g, 256, 0, q>>>(bt, L0, round, u->outf, gnorm2);
   lt::k_net_dots<<<g, 256, 0, q>>>(bt, L0, round, gnorm2);
   lt::k_net_scale<<<g, 256, 0, q>>>(bt, L0, round, gnorm2);
