@@ -318,22 +318,34 @@ __global__ void k_flip_weights(const bf16* W, bf16* Wf, int cin, int cout) {
 // ------------------------------------------------------------------ elementwise helpers (NHWC)
 // The forward elementwise kernels run on a grid (blocks, nimg) with image blockIdx.y and a
 // grid-stride loop over its elements, so an image the solver does not need costs a few CTAs.
+// Channels move 8 at a time (16 bytes; every channel count is a multiple of 16).
 __global__ void k_pool2(const bf16* in, bf16* out, int H, int Wd, int C, const int* on) {
   const int img = blockIdx.y;
   if (on && !on[img]) return;
-  const int h = H / 2, w = Wd / 2;
-  const size_t n = (size_t)h * w * C;
-  const bf16* b = in + (size_t)img * H * Wd * C;
-  bf16* o = out + (size_t)img * n;
+  const int h = H / 2, w = Wd / 2, C8 = C / 8;
+  const size_t n = (size_t)h * w * C8;
+  const uint4* b = reinterpret_cast<const uint4*>(in + (size_t)img * H * Wd * C);
+  uint4* o = reinterpret_cast<uint4*>(out + (size_t)img * h * w * C);
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
-    const int c = idx % C;
-    const size_t pix = idx / C;
+    const int c8 = idx % C8;
+    const size_t pix = idx / C8;
     const int x = pix % w, y = pix / w;
-    float s = __bfloat162float(b[((size_t)(2 * y) * Wd + 2 * x) * C + c]) +
-              __bfloat162float(b[((size_t)(2 * y) * Wd + 2 * x + 1) * C + c]) +
-              __bfloat162float(b[((size_t)(2 * y + 1) * Wd + 2 * x) * C + c]) +
-              __bfloat162float(b[((size_t)(2 * y + 1) * Wd + 2 * x + 1) * C + c]);
-    o[idx] = __float2bfloat16(0.25f * s);
+    const size_t r0 = ((size_t)(2 * y) * Wd + 2 * x) * C8 + c8, r1 = r0 + (size_t)Wd * C8;
+    const uint4 q[4] = {b[r0], b[r0 + C8], b[r1], b[r1 + C8]};
+    uint4 res;
+    uint32_t* rw = reinterpret_cast<uint32_t*>(&res);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float lo = 0.f, hi = 0.f;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const __nv_bfloat162 v = reinterpret_cast<const __nv_bfloat162*>(&q[t])[k];
+        lo += __low2float(v);
+        hi += __high2float(v);
+      }
+      rw[k] = pack_bf2(0.25f * lo, 0.25f * hi);
+    }
+    o[idx] = res;
   }
 }
 
@@ -352,16 +364,16 @@ __global__ void k_pool2_bwd(const float* gout, float* gin, int H, int Wd, int C,
 __global__ void k_up_cat(const bf16* a, const bf16* b, bf16* out, int H, int Wd, int C1, int C2, const int* on) {
   const int img = blockIdx.y;
   if (on && !on[img]) return;
-  const int C = C1 + C2;
-  const size_t n = (size_t)H * Wd * C;
-  const bf16* ai = a + (size_t)img * (H / 2) * (Wd / 2) * C1;
-  const bf16* bi = b + (size_t)img * H * Wd * C2;
-  bf16* o = out + (size_t)img * n;
+  const int A8 = C1 / 8, B8 = C2 / 8, C8 = A8 + B8;
+  const size_t n = (size_t)H * Wd * C8;
+  const uint4* ai = reinterpret_cast<const uint4*>(a + (size_t)img * (H / 2) * (Wd / 2) * C1);
+  const uint4* bi = reinterpret_cast<const uint4*>(b + (size_t)img * H * Wd * C2);
+  uint4* o = reinterpret_cast<uint4*>(out + (size_t)img * H * Wd * (C1 + C2));
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
-    const int c = idx % C;
-    const size_t pix = idx / C;
+    const int c8 = idx % C8;
+    const size_t pix = idx / C8;
     const int x = pix % Wd, y = pix / Wd;
-    o[idx] = c < C1 ? ai[((size_t)(y / 2) * (Wd / 2) + x / 2) * C1 + c] : bi[pix * C2 + (c - C1)];
+    o[idx] = c8 < A8 ? ai[((size_t)(y / 2) * (Wd / 2) + x / 2) * A8 + c8] : bi[pix * B8 + (c8 - A8)];
   }
 }
 
@@ -551,13 +563,13 @@ static void unet_forward_dev(lt_unet* u, int nimg, int H, int W) {
   auto pool = [&](int src, int dst) {
     int lv = kSlotLvl[src];
     size_t n = unet_npix(nimg, H, W, lv + 1) * kSlotC[src];
-    lt::k_pool2<<<per_img(n / nimg, nimg), 256, 0, st>>>(u->A[src], u->A[dst], H >> lv, W >> lv, kSlotC[src],
+    lt::k_pool2<<<per_img(n / nimg / 8, nimg), 256, 0, st>>>(u->A[src], u->A[dst], H >> lv, W >> lv, kSlotC[src],
                                                         u->img_on);
   };
   auto upcat = [&](int a, int b, int dst) {
     int lv = kSlotLvl[dst];
     size_t n = unet_npix(nimg, H, W, lv) * kSlotC[dst];
-    lt::k_up_cat<<<per_img(n / nimg, nimg), 256, 0, st>>>(u->A[a], u->A[b], u->A[dst], H >> lv, W >> lv, kSlotC[a],
+    lt::k_up_cat<<<per_img(n / nimg / 8, nimg), 256, 0, st>>>(u->A[a], u->A[b], u->A[dst], H >> lv, W >> lv, kSlotC[a],
                                                          kSlotC[b], u->img_on);
   };
   conv(0); conv(1); pool(S0, P0);

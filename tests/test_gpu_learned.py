@@ -75,4 +75,7 @@ def test_training_lowers_loss_and_solver_stays_exact(mods):
         assert st["n_converged"] == st["n_shift_solves"]
     kept = res[1][1]["work"][14]
     print("learned guess kept in", kept, "rounds; ms without/with:", res[0][1]["ms_total"], res[1][1]["ms_total"])
+    # what the trained network gains: the solver keeps a guess only when it removes at least 5% of the
+    # residual norm of a preconditioner solve's first round, and on the unseen field it keeps some
+    assert kept >= 1
     net.close()
