@@ -283,7 +283,7 @@ BATCH_WORKLOAD = ("40 independent 2D aquifers, sides in {96,128,192,256,384}, lo
                   "4-16 sources, 16-64 receivers, 8 times, Nz=24, 2 groups (forward solves)")
 
 
-def batch_throughput(dev, wave: int = 10):
+def batch_throughput(dev, wave: int = 10, extra=None, adjoint_extra=None):
     """Shifted solves/s of the uneven 40-aquifer batch, solved with lt_forward_batch in waves of
     `wave` aquifers (each on its own stream), and the same aquifers solved one after another."""
     import torch
@@ -291,8 +291,10 @@ def batch_throughput(dev, wave: int = 10):
     from paper_1409_2556_gb300 import Engine
     from paper_1409_2556_gb300.batch import forward_batch
     aqs = W.config5_aquifers()
-    opts = dict(tol=1e-10, maxit=250, inner_relax=0.0, inner_rounds=6, inner_cycles=6, groups=2, check_every=4,
-                mg_tile=1)
+    # inner tolerance 3e-12 / (largest open projected residual of the basis), capped at 1e-2: 1.79x the
+    # throughput of fixed 1e-12 inner solves, every system still converged (measured 14,867 against 8,311 /s)
+    opts = dict(dict(tol=1e-10, maxit=250, inner_relax=1e-2, inner_tol=3e-12, inner_rounds=6, inner_cycles=6,
+                     groups=2, check_every=4, mg_tile=1), **(extra or {}))
     t_batch = t_seq = 0.0
     conv_b = conv_s = total = 0
     maxres = 0.0
@@ -326,11 +328,12 @@ def batch_throughput(dev, wave: int = 10):
            "shifted_systems": total, "converged": conv_b, "max_true_residual": maxres,
            "wave": wave, "seconds_batched": t_batch, "seconds_sequential": t_seq,
            "timing": "host wall clock around each call, device synchronised"}
-    out["adjoint"] = batch_adjoint(dev, aqs)
+    out["solver_options"] = opts
+    out["adjoint"] = batch_adjoint(dev, aqs, extra=adjoint_extra)
     return out
 
 
-def batch_adjoint(dev, aqs, budget_gb: float = 150.0):
+def batch_adjoint(dev, aqs, budget_gb: float = 150.0, extra=None):
     """Jacobian rows/s of the 40 aquifers: lt_adjoint_batch in vector-Jacobian-product form (every
     row of every aquifer's Jacobian contracted with a seeded g), in waves whose estimated Krylov
     workspace fits `budget_gb`; each wave timed on its second call (the first builds workspaces)."""
@@ -339,8 +342,8 @@ def batch_adjoint(dev, aqs, budget_gb: float = 150.0):
     from paper_1409_2556_gb300 import Engine
     from paper_1409_2556_gb300.batch import adjoint_batch
     M = 160
-    opts = dict(tol=1e-9, maxit=M, inner_relax=1e-4, inner_rounds=6, inner_cycles=6, groups=1, check_every=4,
-                mg_tile=1)
+    opts = dict(dict(tol=1e-9, maxit=M, inner_relax=1e-4, inner_rounds=6, inner_cycles=6, groups=1, check_every=4,
+                     mg_tile=1), **(extra or {}))
 
     def gbytes(p):
         nb = len(p.src_cells) + len(p.rec_cells)
@@ -384,7 +387,7 @@ def batch_adjoint(dev, aqs, budget_gb: float = 150.0):
         torch.cuda.empty_cache()
     return {"value": rows / t_tot, "unit": "Jacobian rows/s", "form": "vector-Jacobian product per aquifer",
             "rows": rows, "waves": len(waves), "seconds": t_tot, "shifted_systems": total, "converged": conv,
-            "max_true_residual": maxres, "solver_tol": opts["tol"],
+            "max_true_residual": maxres, "solver_tol": opts["tol"], "solver_options": opts,
             "timing": "host wall clock around each batched call, device synchronised"}
 
 
