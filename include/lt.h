@@ -375,6 +375,14 @@ int lt_unet_grad(lt_unet* net, int nimg, int H, int W, const float* in, const fl
 /* one Adam step (beta 0.9 / 0.999) on the batch */
 int lt_unet_train_step(lt_unet* net, int nimg, int H, int W, const float* in, const float* target, float lr,
                        double* loss);
+/* Poll limit of the bounded waits in the tensor-core convolutions (default 4,194,304 polls of the
+ * mbarrier that the MMAs complete on).  A wait that reaches the limit raises an error flag, keeps
+ * waiting (at most 16,777,216 more polls) until the MMAs in flight have finished, frees the block's
+ * tensor memory and returns; the call then returns -5 (LT_ERR_TIMEOUT) and its outputs are not valid.
+ * 0 makes every wait run out at once without any fault, which tests use to exercise that path.
+ * The limit also applies while the solver runs the network (lt_set_learned_preconditioner), where a
+ * timeout is reported as the solve's LT_ERR_TIMEOUT.  Returns 0, or -1 for a null network. */
+int lt_unet_set_wait_polls(lt_unet* net, unsigned polls);
 const char* lt_unet_last_error(lt_unet* net);
 void lt_unet_destroy(lt_unet* net);
 

@@ -95,6 +95,7 @@ EXPORTS = {
                                C.POINTER(C.c_double)]),
     "lt_unet_train_step": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_float,
                                      C.POINTER(C.c_double)]),
+    "lt_unet_set_wait_polls": (C.c_int, [C.c_void_p, C.c_uint]),
     "lt_unet_last_error": (C.c_char_p, [C.c_void_p]),
     "lt_unet_destroy": (None, [C.c_void_p]),
     "lt_precond_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),

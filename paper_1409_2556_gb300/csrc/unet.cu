@@ -65,7 +65,7 @@ constexpr int kOutChannels = 2;
 // for the MMAs in flight before the block frees its tensor memory and returns.
 // in: [nimg][H][W][cin], W: [9][cout][cin]; cin, cout multiples of 16, cin <= 96, cout <= 96.
 constexpr int kTcPix = 128;                   // MMA M = tensor-memory lanes = threads per CTA
-constexpr unsigned kTcPolls = 1u << 22;       // mbarrier polls before a wait counts as timed out
+constexpr unsigned kTcPolls = 1u << 22;       // default mbarrier polls before a wait counts as timed out
 constexpr unsigned kTcDrain = 1u << 24;       // further polls for the MMAs in flight after a timeout
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -84,8 +84,8 @@ __device__ __forceinline__ bool tc_try_wait(uint32_t bar, uint32_t parity) {
 }
 
 // bounded wait for the phase of the given parity; all threads take it, none branches on the outcome
-__device__ __forceinline__ void tc_wait(uint32_t bar, uint32_t parity, unsigned long long* flag) {
-  for (unsigned it = 0; it < kTcPolls; ++it)
+__device__ __forceinline__ void tc_wait(uint32_t bar, uint32_t parity, unsigned polls, unsigned long long* flag) {
+  for (unsigned it = 0; it < polls; ++it)
     if (tc_try_wait(bar, parity)) return;
   if (flag) atomicAdd(flag, 1ull);
   for (unsigned it = 0; it < kTcDrain; ++it)
@@ -152,7 +152,8 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32
 __global__ void __launch_bounds__(kTcPix, 1) k_conv3x3_tc(const bf16* __restrict__ in, const bf16* __restrict__ Wt,
                                                           const float* __restrict__ bias, bf16* out_bf, float* out_f,
                                                           int H, int Wd, int cin, int cout, int relu, int tcols,
-                                                          const int* img_on, unsigned long long* flag) {
+                                                          const int* img_on, unsigned polls,
+                                                          unsigned long long* flag) {
   if (img_on && !img_on[blockIdx.y]) return;   // image not needed (uniform per CTA, before any allocation)
   extern __shared__ __align__(1024) uint8_t tsm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(tsm);
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(kTcPix, 1) k_conv3x3_tc(const bf16* __restrict
       }
     tc_commit(su32(bar));
   }
-  tc_wait(su32(bar), 0u, flag);
+  tc_wait(su32(bar), 0u, polls, flag);
   tc_fence_after();
   // lane 32 warp + l of M-block mb = row g = (32 warp + l) / 8, column j = l % 8 of the block
   const int r = warp * 32 + (tid & 31);
@@ -266,8 +267,8 @@ static size_t tc_launch_smem(int cin, int cout) {
 constexpr size_t kTcSmemMax = 200 * 1024;   // above every layer's request (largest: 96 -> 32, 173 KB)
 
 static void conv3x3(const bf16* in, const bf16* Wt, const float* bias, bf16* out_bf, float* out_f, int nimg, int H,
-                    int Wd, int cin, int cout, int relu, const int* img_on, unsigned long long* flag,
-                    cudaStream_t st) {
+                    int Wd, int cin, int cout, int relu, const int* img_on, unsigned polls,
+                    unsigned long long* flag, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_conv3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
@@ -276,7 +277,7 @@ static void conv3x3(const bf16* in, const bf16* Wt, const float* bias, bf16* out
   const int mb = tc_mb(cout);
   dim3 g((unsigned)(((H + 15) / 16) * ((Wd + 8 * mb - 1) / (8 * mb))), nimg);
   k_conv3x3_tc<<<g, kTcPix, tc_launch_smem(cin, cout), st>>>(in, Wt, bias, out_bf, out_f, H, Wd, cin, cout, relu,
-                                                            tc_cols(cout), img_on, flag);
+                                                            tc_cols(cout), img_on, polls, flag);
 }
 
 // dW[tap][co][ci] += sum_p gout[p][co] * in[p + off(tap)][ci]; db[co] += sum_p gout[p][co]   (FP32)
@@ -486,6 +487,7 @@ struct lt_unet {
   unsigned long long* flag = nullptr;
   // images the network runs on (nullptr: all); set by the solver for the bases that still use the guess
   const int* img_on = nullptr;
+  unsigned polls = lt::kTcPolls;   // mbarrier polls of the convolutions before a wait counts as timed out
 };
 
 static size_t unet_npix(int nimg, int H, int W, int lvl) { return (size_t)nimg * (H >> lvl) * (W >> lvl); }
@@ -558,7 +560,7 @@ static void unet_forward_dev(lt_unet* u, int nimg, int H, int W) {
     bf16* out = kLOut[l] >= 0 ? u->A[kLOut[l]] : nullptr;
     float* outf = kLOut[l] >= 0 ? nullptr : u->outf;
     lt::conv3x3(u->A[kLIn[l]], u->wb + u->woff[l], u->w + u->boff[l], out, outf, nimg, h, w, c.cin, c.cout, c.relu,
-                u->img_on, u->flag, st);
+                u->img_on, u->polls, u->flag, st);
   };
   auto pool = [&](int src, int dst) {
     int lv = kSlotLvl[src];
@@ -601,7 +603,7 @@ static void unet_backward_dev(lt_unet* u, int nimg, int H, int W) {
                                         c.cout, chunk);
     if (l > 0)   // backward data: conv with flipped, transposed weights, FP32 output
       lt::conv3x3(u->gbf, u->wflip + u->woff[l], nullptr, nullptr, u->G[kLIn[l]], nimg, h, w, c.cout, c.cin, 0,
-                  nullptr, u->flag, st);
+                  nullptr, u->polls, u->flag, st);
   };
   auto upcat_bwd = [&](int a, int b, int dst) {
     int lv = kSlotLvl[dst];
@@ -774,6 +776,12 @@ int lt_unet_train_step(lt_unet* u, int nimg, int H, int W, const float* in, cons
                                                                        c.cin, c.cout);
   }
   return cudaStreamSynchronize(u->stream) == cudaSuccess ? 0 : unet_fail(u, -3, "CUDA error in the Adam step");
+}
+
+int lt_unet_set_wait_polls(lt_unet* u, unsigned polls) {
+  if (!u) return -1;
+  u->polls = polls;
+  return 0;
 }
 
 const char* lt_unet_last_error(lt_unet* u) { return u ? u->err.c_str() : "null network"; }

@@ -42,6 +42,10 @@ class UNet:
         t = np.ascontiguousarray(np.asarray(theta, dtype=np.float32))
         self._check(self.lib.lt_unet_set_params(self.h, t.ctypes.data_as(C.c_void_p), t.size), "set_params")
 
+    def set_wait_polls(self, polls: int):
+        """Poll limit of the convolutions' bounded waits (0: every wait runs out at once)."""
+        self._check(self.lib.lt_unet_set_wait_polls(self.h, int(polls)), "set_wait_polls")
+
     def forward(self, x):
         """x: CUDA float32 tensor [n, H, W, 5] -> CUDA float32 [n, H, W, 2]."""
         import torch

@@ -6,7 +6,8 @@ flight land (a second bounded wait) and returns, and the host reports
 LT_ERR_TIMEOUT.  Setting the limit to 0 makes every wait run out at once
 without any fault: the copies are ordinary in-bounds copies that complete.
 No shifted system may then be reported as converged, and the context must
-stay usable."""
+stay usable.  The tensor-core convolutions of the learned preconditioner wait
+on the mbarrier their MMAs complete on in the same bounded way."""
 import numpy as np
 import pytest
 
@@ -60,3 +61,26 @@ def test_precond_apply_reports_timeout():
     torch.cuda.synchronize()
     assert torch.isfinite(e).all()
     eng.close()
+
+
+def test_tensor_core_wait_that_runs_out_reports_timeout_and_network_recovers():
+    """Poll limit 0: every convolution's wait runs out at once (the MMAs are ordinary and complete),
+    the block waits for them within its second bound, frees its tensor memory and returns; the call
+    reports LT_ERR_TIMEOUT, and with the default limit the same network gives its earlier output."""
+    import torch
+
+    import __graft_entry__ as G
+    G.build()
+    from paper_1409_2556_gb300 import LtError, learned
+    net = learned.UNet(0, seed=3)
+    x = torch.randn(3, 32, 40, 5, device="cuda")
+    ref = net.forward(x)
+    net.set_wait_polls(0)
+    with pytest.raises(LtError) as e:
+        net.forward(x)
+    assert e.value.code == -5, e.value
+    net.set_wait_polls(1 << 22)
+    out = net.forward(x)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    net.close()
