@@ -112,7 +112,7 @@ typedef struct {
                                      1e-5 of an FP64 solve.  Rounding a solution to float32 alone leaves a true
                                      residual of about cond(K + z M) * 6e-8 (near 2e-7 for point sources, far
                                      more for smooth right-hand sides such as M phi_0), so in this mode set
-                                     true_residual = 0 and judge convergence by the projected residual */
+                                     true_residual = 0 and decide convergence by the projected residual */
 /* coefficient rule of Algorithm 1 (lt_opts.krylov) */
 #define LT_KRYLOV_GMRES 0
 #define LT_KRYLOV_FOM   1

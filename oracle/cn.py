@@ -12,7 +12,7 @@ that Crank-Nicolson does not damp, so the first interval starts with four
 backward-Euler quarter steps (Rannacher start); each interval between
 consecutive output times is then covered by uniform steps, and Richardson
 extrapolation over two step sizes (error O(dt^2)) gives the result.  An
-independent cross-check of O1; not the parity judge.
+independent cross-check of O1; not the parity reference.
 """
 from __future__ import annotations
 

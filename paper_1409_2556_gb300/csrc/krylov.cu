@@ -766,7 +766,7 @@ void launch_fields(const Batch& bt, const QuadItem* items, const double2* C, int
   k_fields<<<g, 256, 0, st>>>(bt, items, C, phi, nt, dense_q0);
 }
 
-// ------------------------------------------------------------ true residual (judge)
+// ------------------------------------------------------------ true residual (the convergence check)
 constexpr int kXS = 16;   // shifts per pass (U is read once per pass)
 
 // one-pass Gram-Schmidt: dot[0][i] = V_i^H (M u_j) with V and M u_j in df32; each thread sums its

@@ -350,7 +350,7 @@ def test_cluster_solve_semicoarsened_levels_and_neumann_faces(Engine, shape, bc)
 @pytest.mark.parametrize("cluster", [1, 0])
 def test_one_pass_gram_schmidt_with_df32_dots_matches_oracle(Engine, cluster):
     """gram_schmidt = 1: one classical pass with df32-accurate coefficients keeps the basis
-    orthogonal enough that the projected residual stays the judge (true = projected to rounding)."""
+    orthogonal enough that the projected residual stays a faithful convergence test (true = projected to rounding)."""
     p = W.random_problem(64, 64, 1, variance=1.5, seed=41, ns=3, nr=4, nt=6, Nz=32, tol=1e-11, groups=3)
     h, st = _solve(Engine, p, gram_schmidt=1, mg_cluster=cluster)
     assert _rel(h, direct.forward(p)) < TOL_H
